@@ -1,0 +1,357 @@
+"""FP64 CPU oracle of one 3D Gaussian Splatting training step (VkSplat,
+arxiv 2605.00219) -- Python side.
+
+TEST INFRASTRUCTURE ONLY: tests/, __graft_entry__.smoke() and bench.py's
+cpu_baseline / reference arm are the only users.  It imports nothing from the
+CUDA package; inputs come as plain numpy arrays (the seeded generators live in
+a module of their own).
+
+The heavy loops are plain C in gs_oracle.c (built here with gcc,
+-ffp-contract=off); this file strings them together in the order of the
+paper's training iteration (Sec. 2, Sec. 4):
+
+  project (FP64) -> FP32 binning: count, emit keys, stable sort, tile ranges
+  (Sec. 4.1, Sec. 4.4) -> compositing (FP64) -> L1 loss gradient (Sec. 4.5,
+  L1 term) -> compositing backward (Sec. 4.2) -> projection backward and Adam
+  in log-scale / logit-opacity space (Sec. 4.3).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gs_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+
+PSTRIDE = 24
+NTHETA = 59
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile gs_oracle.c into a shared library (gcc, FP contraction off)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-std=c99", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+               "-fexcess-precision=standard", "-fopenmp", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class OrcCam(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_float * 9), ("t", ctypes.c_float * 3),
+                ("fx", ctypes.c_float), ("fy", ctypes.c_float),
+                ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32)]
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB_PATH)
+        vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        cam = ctypes.POINTER(OrcCam)
+        L.orc_bin32_count.argtypes = [i64, vp, vp, vp, cam, vp, vp, vp]
+        L.orc_bin32_count.restype = None
+        L.orc_bin32_emit.argtypes = [i64, vp, vp, vp, cam, vp, vp, vp]
+        L.orc_bin32_emit.restype = i64
+        L.orc_stable_sort.argtypes = [i64, vp, vp]
+        L.orc_stable_sort.restype = None
+        L.orc_tile_ranges.argtypes = [i64, vp, cam, vp]
+        L.orc_tile_ranges.restype = None
+        L.orc_sh_basis.argtypes = [vp, vp, vp]
+        L.orc_sh_basis.restype = None
+        L.orc_project64.argtypes = [i64, vp, vp, vp, vp, vp, cam, vp]
+        L.orc_project64.restype = None
+        L.orc_render64.argtypes = [cam, i64, vp, vp, vp, vp, vp, vp, vp, dbl, vp, vp]
+        L.orc_render64.restype = i64
+        L.orc_render64_brute.argtypes = [cam, vp, i64, vp, vp, vp, vp]
+        L.orc_render64_brute.restype = i64
+        L.orc_raster_bwd64.argtypes = [cam, i64, vp, vp, vp, vp, vp, vp]
+        L.orc_raster_bwd64.restype = None
+        L.orc_project_bwd64.argtypes = [i64, vp, vp, vp, vp, vp, cam, vp, vp, vp]
+        L.orc_project_bwd64.restype = None
+        L.orc_adam64.argtypes = [i64, vp, vp, vp, vp, vp, dbl, dbl, dbl, i32]
+        L.orc_adam64.restype = None
+        _lib = L
+    return _lib
+
+
+def make_cam(cam, tile_w: int = 16, tile_h: int = 16) -> OrcCam:
+    """Camera in the oracle's struct: FP32 values, as the device stores them."""
+    c = OrcCam()
+    R = np.asarray(cam.R, np.float32).reshape(-1)
+    t = np.asarray(cam.t, np.float32).reshape(-1)
+    for i in range(9):
+        c.R[i] = float(R[i])
+    for i in range(3):
+        c.t[i] = float(t[i])
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.tile_w, c.tile_h = int(tile_w), int(tile_h)
+    return c
+
+
+def tiles_of(cam, tile_w=16, tile_h=16):
+    return (cam.width + tile_w - 1) // tile_w, (cam.height + tile_h - 1) // tile_h
+
+
+def tile_bits(n_tiles: int) -> int:
+    b = 0
+    while (1 << b) < n_tiles:
+        b += 1
+    return b
+
+
+def key_shift(n_tiles: int) -> int:
+    tb = tile_bits(n_tiles)
+    return 32 - tb if tb >= 9 else 23
+
+
+# --------------------------------------------------------------------------
+# FP32 binning (bit-specified; Sec. 4.1 and Sec. 4.4)
+# --------------------------------------------------------------------------
+
+@dataclass
+class Binning:
+    count: np.ndarray        # (n,) uint32 tiles per Gaussian
+    bin: np.ndarray          # (n, 8) float32 valid, mx, my, a, b, c, det, tz
+    mant: np.ndarray         # (n,) uint32 23-bit depth code
+    offset: np.ndarray       # (n + 1,) int64 exclusive scan of count
+    keys_emit: np.ndarray    # (K,) uint32 keys in emission order
+    gidx_emit: np.ndarray    # (K,) uint32 Gaussian of each emitted pair
+    keys: np.ndarray         # (K,) uint32 sorted keys (stable)
+    gidx: np.ndarray         # (K,) uint32 Gaussians in sorted order
+    perm: np.ndarray         # (K,) int64 emission slot of each sorted entry
+    ranges: np.ndarray       # (tiles, 2) int64 [start, end) per tile
+
+    @property
+    def K(self) -> int:
+        return int(self.keys.shape[0])
+
+
+def bin32(scene, cam, tile_w=16, tile_h=16) -> Binning:
+    L = lib()
+    c = make_cam(cam, tile_w, tile_h)
+    n = scene.n
+    means = np.ascontiguousarray(scene.means, np.float32)
+    quats = np.ascontiguousarray(scene.quats, np.float32)
+    scales = np.ascontiguousarray(scene.scales, np.float32)
+    count = np.zeros(n, np.uint32)
+    b = np.zeros((n, 8), np.float32)
+    mant = np.zeros(n, np.uint32)
+    L.orc_bin32_count(n, _ptr(means), _ptr(quats), _ptr(scales), ctypes.byref(c), _ptr(count), _ptr(b), _ptr(mant))
+    offset = np.zeros(n + 1, np.int64)
+    np.cumsum(count, out=offset[1:])
+    K = int(offset[-1])
+    keys = np.zeros(max(K, 1), np.uint32)
+    gidx = np.zeros(max(K, 1), np.uint32)
+    got = L.orc_bin32_emit(n, _ptr(means), _ptr(quats), _ptr(scales), ctypes.byref(c), _ptr(offset), _ptr(keys), _ptr(gidx))
+    assert got == K
+    keys, gidx = keys[:K], gidx[:K]
+    keys_emit, gidx_emit = keys.copy(), gidx.copy()
+    slot = np.arange(K, dtype=np.uint32)
+    skeys = keys.copy()
+    L.orc_stable_sort(K, _ptr(skeys), _ptr(slot))
+    tx, ty = tiles_of(cam, tile_w, tile_h)
+    ranges = np.zeros((tx * ty, 2), np.int64)
+    L.orc_tile_ranges(K, _ptr(skeys), ctypes.byref(c), _ptr(ranges))
+    return Binning(count, b, mant, offset, keys_emit, gidx_emit, skeys, gidx_emit[slot.astype(np.int64)],
+                   slot.astype(np.int64), ranges)
+
+
+# --------------------------------------------------------------------------
+# FP64 forward / backward / Adam
+# --------------------------------------------------------------------------
+
+@dataclass
+class Params64:
+    """Activated parameters in FP64: means, quats, scales, opacities, sh."""
+    means: np.ndarray
+    quats: np.ndarray
+    scales: np.ndarray
+    opacities: np.ndarray
+    sh: np.ndarray
+
+    @staticmethod
+    def from_scene(scene) -> "Params64":
+        f = lambda a: np.ascontiguousarray(a, np.float64)
+        return Params64(f(scene.means), f(scene.quats), f(scene.scales), f(scene.opacities),
+                        f(scene.sh).reshape(scene.n, 48))
+
+    @property
+    def n(self):
+        return self.means.shape[0]
+
+    def theta(self) -> np.ndarray:
+        """Optimised variables (n, 59): mean, quat, log-scale, logit-opacity, SH."""
+        o = self.opacities
+        return np.concatenate([self.means, self.quats, np.log(self.scales),
+                               np.log(o / (1 - o))[:, None], self.sh.reshape(self.n, 48)], axis=1)
+
+    @staticmethod
+    def from_theta(th: np.ndarray) -> "Params64":
+        th = np.asarray(th, np.float64)
+        return Params64(th[:, 0:3].copy(), th[:, 3:7].copy(), np.exp(th[:, 7:10]),
+                        1.0 / (1.0 + np.exp(-th[:, 10])), th[:, 11:59].copy())
+
+
+def project64(p: Params64, cam, tile_w=16, tile_h=16) -> np.ndarray:
+    L = lib()
+    c = make_cam(cam, tile_w, tile_h)
+    proj = np.zeros((p.n, PSTRIDE), np.float64)
+    L.orc_project64(p.n, _ptr(p.means), _ptr(p.quats), _ptr(p.scales), _ptr(p.opacities), _ptr(p.sh),
+                    ctypes.byref(c), _ptr(proj))
+    return proj
+
+
+@dataclass
+class Render:
+    image: np.ndarray        # (H, W, 3)
+    tfinal: np.ndarray       # (H, W)
+    nlast: np.ndarray        # (H, W) int32
+    blended: int
+    unstable_px: np.ndarray  # (H, W) bool
+    unstable_g: np.ndarray   # (n,) bool
+
+
+def render64(cam, proj, b: Binning, bg=(0.0, 0.0, 0.0), margin=1e-4, tile_w=16, tile_h=16) -> Render:
+    L = lib()
+    c = make_cam(cam, tile_w, tile_h)
+    H, W = cam.height, cam.width
+    n = proj.shape[0]
+    img = np.zeros((H, W, 3), np.float64)
+    tf = np.zeros((H, W), np.float64)
+    nl = np.zeros((H, W), np.int32)
+    upx = np.zeros((H, W), np.uint8)
+    ug = np.zeros(n, np.uint8)
+    bgv = np.asarray(bg, np.float64)
+    sg = np.ascontiguousarray(b.gidx, np.uint32)
+    rg = np.ascontiguousarray(b.ranges, np.int64)
+    blended = L.orc_render64(ctypes.byref(c), n, _ptr(proj), _ptr(sg), _ptr(rg), _ptr(bgv), _ptr(img),
+                             _ptr(tf), _ptr(nl), float(margin), _ptr(upx), _ptr(ug))
+    return Render(img, tf, nl, int(blended), upx.astype(bool), ug.astype(bool))
+
+
+def render64_brute(cam, proj, order, bg=(0.0, 0.0, 0.0)):
+    L = lib()
+    c = make_cam(cam)
+    H, W = cam.height, cam.width
+    img = np.zeros((H, W, 3), np.float64)
+    tf = np.zeros((H, W), np.float64)
+    order = np.ascontiguousarray(order, np.uint32)
+    bgv = np.asarray(bg, np.float64)
+    blended = L.orc_render64_brute(ctypes.byref(c), _ptr(proj), order.shape[0], _ptr(order), _ptr(bgv),
+                                   _ptr(img), _ptr(tf))
+    return img, tf, int(blended)
+
+
+def raster_bwd64(cam, proj, b: Binning, dLdC, bg=(0.0, 0.0, 0.0), tile_w=16, tile_h=16) -> np.ndarray:
+    L = lib()
+    c = make_cam(cam, tile_w, tile_h)
+    n = proj.shape[0]
+    g2 = np.zeros((n, 9), np.float64)
+    dl = np.ascontiguousarray(dLdC, np.float64)
+    bgv = np.asarray(bg, np.float64)
+    sg = np.ascontiguousarray(b.gidx, np.uint32)
+    rg = np.ascontiguousarray(b.ranges, np.int64)
+    L.orc_raster_bwd64(ctypes.byref(c), n, _ptr(proj), _ptr(sg), _ptr(rg), _ptr(bgv), _ptr(dl), _ptr(g2))
+    return g2
+
+
+def project_bwd64(p: Params64, cam, proj, grad2d, out=None) -> np.ndarray:
+    L = lib()
+    c = make_cam(cam)
+    g = np.zeros((p.n, NTHETA), np.float64) if out is None else out
+    g2 = np.ascontiguousarray(grad2d, np.float64)
+    L.orc_project_bwd64(p.n, _ptr(p.means), _ptr(p.quats), _ptr(p.scales), _ptr(p.opacities), _ptr(p.sh),
+                        ctypes.byref(c), _ptr(proj), _ptr(g2), _ptr(g))
+    return g
+
+
+def adam64(theta, m, v, grad, lr, step, b1=0.9, b2=0.999, eps=1e-15):
+    """In-place Adam on (n, 59) arrays; lr: 6 per-group rates."""
+    L = lib()
+    lr = np.asarray(lr, np.float64)
+    assert lr.shape == (6,)
+    for a in (theta, m, v, grad):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    L.orc_adam64(theta.shape[0], _ptr(theta), _ptr(m), _ptr(v), _ptr(grad), _ptr(lr), b1, b2, eps, int(step))
+
+
+def sh_basis(d):
+    L = lib()
+    d = np.ascontiguousarray(d, np.float64)
+    Y = np.zeros(16, np.float64)
+    dY = np.zeros(48, np.float64)
+    L.orc_sh_basis(_ptr(d), _ptr(Y), _ptr(dY))
+    return Y, dY.reshape(16, 3)
+
+
+def l1_loss_grad(images, targets):
+    """L1 loss over all pixels of all views, mean over 3 * sum(P):
+    dL/dC = sign(C - C*) / (3 sum P), sign(0) = 0 (Sec. 4.5, L1 term)."""
+    total = sum(int(np.prod(im.shape)) for im in images)
+    loss = sum(float(np.abs(im - tg).sum()) for im, tg in zip(images, targets)) / total
+    grads = [np.sign(im - tg) / total for im, tg in zip(images, targets)]
+    return loss, grads
+
+
+# --------------------------------------------------------------------------
+# Whole step
+# --------------------------------------------------------------------------
+
+@dataclass
+class StepResult:
+    binnings: list
+    projs: list
+    renders: list
+    loss: float
+    dLdC: list
+    grad2d: list
+    grad: np.ndarray         # (n, 59) theta gradient
+    theta: np.ndarray        # (n, 59) after Adam
+    m: np.ndarray
+    v: np.ndarray
+    params: Params64         # activated parameters after Adam
+
+
+def step(scene, cams, targets, lr, step_idx=1, m=None, v=None, bg=(0.0, 0.0, 0.0),
+         tile_w=16, tile_h=16, margin=1e-4, grad_only=False) -> StepResult:
+    """One training step over the views `cams` of one scene: forward, L1 over
+    all views, backward, one Adam update.  `targets` are (H, W, 3) arrays."""
+    p = Params64.from_scene(scene)
+    bins, projs, rends = [], [], []
+    for cam in cams:
+        b = bin32(scene, cam, tile_w, tile_h)
+        pr = project64(p, cam, tile_w, tile_h)
+        r = render64(cam, pr, b, bg, margin, tile_w, tile_h)
+        bins.append(b); projs.append(pr); rends.append(r)
+    loss, dl = l1_loss_grad([r.image for r in rends], targets)
+    grad = np.zeros((p.n, NTHETA), np.float64)
+    g2s = []
+    for cam, b, pr, d in zip(cams, bins, projs, dl):
+        g2 = raster_bwd64(cam, pr, b, d, bg, tile_w, tile_h)
+        g2s.append(g2)
+        project_bwd64(p, cam, pr, g2, out=grad)
+    theta = p.theta()
+    mm = np.zeros_like(theta) if m is None else np.array(m, np.float64, copy=True)
+    vv = np.zeros_like(theta) if v is None else np.array(v, np.float64, copy=True)
+    if not grad_only:
+        adam64(theta, mm, vv, grad, lr, step_idx)
+    return StepResult(bins, projs, rends, loss, dl, g2s, grad, theta, mm, vv, Params64.from_theta(theta))
