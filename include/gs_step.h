@@ -1,0 +1,218 @@
+/*
+ * gs_step.h -- C ABI of the GB300 (sm_103a) 3D Gaussian Splatting training
+ * step: the stages of one training iteration of VkSplat (arxiv 2605.00219,
+ * Sec. 2 pipeline and Sec. 4), each a call on a CUDA stream.
+ *
+ *   gs_project_fwd      projection forward + exact tile count  (Sec. 4.1)
+ *   gs_bin_sort         index offset, key generation, 32-bit radix sort,
+ *                       tile ranges                             (Sec. 4.1, 4.4)
+ *   gs_raster_fwd       front-to-back alpha compositing         (Sec. 2)
+ *   gs_loss_l1          L1 loss and its gradient                (Sec. 4.5, L1 term)
+ *   gs_raster_bwd       per-Gaussian rasterization backward     (Sec. 4.2)
+ *   gs_project_bwd_adam projection backward fused with Adam     (Sec. 4.3)
+ *
+ * Conventions shared by every call:
+ *  - Ownership: the caller allocates every device buffer, including the
+ *    workspace of gs_workspace_bytes() bytes (256-byte aligned).  The library
+ *    never allocates, frees or synchronises device memory inside the step
+ *    calls; only gs_plan_create/destroy allocate, and only host memory.
+ *  - All step calls are asynchronous on `stream` (a cudaStream_t passed as
+ *    void*, NULL = legacy default stream) and may be captured in a CUDA graph.
+ *    The intersection count K never leaves the device.
+ *  - Errors: invalid host-visible arguments return GS_ERR_INVALID_ARG before
+ *    anything is launched; a failed launch returns GS_ERR_CUDA.  Errors the
+ *    device detects (intersection capacity exceeded, non-finite parameters, a
+ *    bounded wait that gave up) set bits in a status word inside the
+ *    workspace, read with gs_read_stats().  No call aborts, traps or prints.
+ *  - Device pointers must be 16-byte aligned.
+ *
+ * Data layouts (n = Gaussians of a scene; all device memory):
+ *  - geom:  float4[3][n], chunk-major: chunk 0 = mean (x, y, z, unused),
+ *           chunk 1 = rotation quaternion (w, x, y, z, need not be unit),
+ *           chunk 2 = (scale x, y, z, opacity), stored ACTIVATED (scales > 0,
+ *           opacity in (0,1)), as the paper stores them (Sec. 4.3, Sec. 4.7).
+ *  - sh:    degree-3 SH, 48 coefficients per Gaussian, flat index 3*k + c
+ *           (k = basis function 0..15, c = colour channel).  FP32 storage:
+ *           float4[12][n] ("column-based" 128-bit chunks, Sec. 4.7), chunk j
+ *           holding flat indices 4j..4j+3.  BF16 storage: uint4[6][n], chunk j
+ *           holding flat indices 8j..8j+7 as bf16 (low half first).
+ *  - m, v:  Adam moments of theta = (mean, quaternion, log-scale,
+ *           logit-opacity, SH), in the chunk order of geom followed by sh:
+ *           FP32: float4[15][n]; BF16: uint2[15][n] (4 bf16 per chunk).
+ *  - cams:  float[n_views][16]: R (row-major 3x3, world -> camera, OpenCV
+ *           axes x right, y down, z forward), t (3), fx, fy, cx, cy.
+ *  - image: float[sum over views of H*W][3], views concatenated, each
+ *           row-major, channel-last (Sec. 4.5).
+ */
+#ifndef GS_STEP_H
+#define GS_STEP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GS_MAX_VIEWS 64
+#define GS_MAX_SCENES 16
+
+typedef enum {
+    GS_OK = 0,
+    GS_ERR_INVALID_ARG = 1,
+    GS_ERR_CAPACITY = 2,      /* status bit 1: more intersections than capacity */
+    GS_ERR_NONFINITE = 3,     /* status bit 2: a non-finite parameter was found */
+    GS_ERR_TIMEOUT = 4,       /* status bit 3: a bounded wait gave up */
+    GS_ERR_CUDA = 5,
+    GS_ERR_UNIMPLEMENTED = 6
+} gs_status;
+
+/* Device status word bits (gs_stats.status). */
+#define GS_STATUS_CAPACITY 0x1u
+#define GS_STATUS_NONFINITE 0x2u
+#define GS_STATUS_TIMEOUT 0x4u
+
+/* Storage flags for gs_plan_create. */
+#define GS_STORE_SH_BF16 0x1
+#define GS_STORE_MOMENTS_BF16 0x2
+
+typedef struct {
+    int32_t width, height;    /* pixels */
+    int32_t scene;            /* index of the scene this view renders */
+} gs_view;
+
+typedef struct {
+    int32_t tile_w, tile_h;   /* 8x8, 16x16 or 16x32 pixels */
+    int32_t bwd_batch;        /* raster_bwd Gaussian batch S: 0 = the paper's
+                                 adaptive rule S = roundup32(sqrt(N P)) <= 128
+                                 (Sec. 4.2); else a fixed 32, 64, 96 or 128 */
+    int32_t reserved;
+} gs_tuning;
+
+typedef struct {
+    int64_t n;                /* Gaussians in this scene */
+    void* geom;               /* float4[3][n] */
+    void* sh;                 /* float4[12][n] or uint4[6][n] (BF16) */
+    void* m;                  /* float4[15][n] or uint2[15][n] (BF16) */
+    void* v;                  /* same as m */
+} gs_scene_buf;
+
+typedef struct {
+    float lr[6];              /* mean, quaternion, log-scale, logit-opacity,
+                                 SH degree 0, SH degrees 1-3 (Sec. 4.3) */
+    float beta1, beta2, eps;
+    int32_t step;             /* Adam step t >= 1; 0 = take t from the
+                                 workspace step counter (then advanced by
+                                 gs_adam_advance), for graph replay */
+    uint32_t seed;            /* stochastic-rounding seed for BF16 storage */
+    int32_t reserved;
+} gs_adam;
+
+typedef struct {
+    uint32_t status;          /* GS_STATUS_* bits */
+    int32_t step;             /* workspace step counter */
+    int64_t k_required;       /* intersections the last gs_project_fwd needed */
+    int64_t k_capacity;
+    uint64_t blended_pairs;   /* pairs composited by the last gs_raster_fwd */
+    float loss;               /* last gs_loss_l1 value */
+    float reserved;
+} gs_stats;
+
+typedef struct gs_plan gs_plan;   /* opaque, host memory */
+
+/* Build the static shape of a step: scenes (Gaussian counts), views
+ * (resolution and scene), intersection capacity (0 = 8 x total pairs,
+ * rounded), tuning (NULL = 16x16 tiles, adaptive batch) and storage flags.
+ * Returns NULL on invalid arguments (and sets *err when err != NULL). */
+gs_plan* gs_plan_create(const int64_t* scene_n, int32_t n_scenes, const gs_view* views,
+                        int32_t n_views, int64_t isect_capacity, const gs_tuning* tuning,
+                        int32_t storage_flags, gs_status* err);
+void gs_plan_destroy(gs_plan* plan);
+
+/* Workspace bytes the caller must allocate for this plan (device memory). */
+size_t gs_workspace_bytes(const gs_plan* plan);
+
+/* Plan queries: 0 pairs (sum over views of the scene's n), 1 total tiles,
+ * 2 total pixels, 3 intersection capacity, 4 views, 5 scenes, 6 tile_w,
+ * 7 tile_h.  Returns -1 for an unknown query. */
+int64_t gs_plan_query(const gs_plan* plan, int32_t what);
+
+/* Zero the workspace status word, statistics and step counter. */
+gs_status gs_workspace_init(const gs_plan* plan, void* ws, void* stream);
+
+/* Projection forward (EWA splatting with the 0.3 low-pass, degree-3 SH
+ * colour) for every (view, Gaussian) pair, fused with the exact scan-line
+ * count of intersected tiles (Sec. 4.1: "compute number of intersecting tiles
+ * per Gaussian in the projection-forward pass").  Reads geom and sh of every
+ * scene and cams; writes the projected records and counts into ws. */
+gs_status gs_project_fwd(const gs_plan* plan, void* ws, const gs_scene_buf* scenes,
+                         const float* cams, void* stream);
+
+/* Tiling and sorting (Sec. 4.1, Sec. 4.4, Table 2 "Tiling/Sorting"):
+ * exclusive scan of the counts ("index offset"), a second scan-line pass
+ * emitting (key, pair) for every intersected tile ("generate keys"), a stable
+ * LSD radix sort of the 32-bit keys (tile id in the top ceil(log2 tiles)
+ * bits, depth code (2z+1)/(z+1) mantissa below; one extra pass orders the
+ * views when there are several) and per-tile [start, end) ranges.  K stays
+ * on the device; intersections beyond the capacity set GS_STATUS_CAPACITY. */
+gs_status gs_bin_sort(const gs_plan* plan, void* ws, void* stream);
+
+/* Front-to-back compositing per tile (Sec. 2): alpha = min(0.99, o exp(-d^2/2))
+ * for d^2 <= 9, pairs below 1/255 skipped, stop before T(1-alpha) < 1e-4,
+ * transmittance kept as a compensated FP32 pair.  bg: device float[3] or
+ * NULL (black).  image: device float[pixels][3].  Also records per pixel the
+ * final transmittance and the list position after the last blended pair. */
+gs_status gs_raster_fwd(const gs_plan* plan, void* ws, const float* bg, float* image,
+                        void* stream);
+
+/* L1 loss over all pixels of all views (mean over 3 x pixels) and its
+ * gradient dL/dC = sign(C - C*) / (3 x pixels) (Sec. 4.5, L1 term).
+ * target: device float[pixels][3]; dL_dimage: device float[pixels][3].
+ * The loss value lands in the workspace statistics. */
+gs_status gs_loss_l1(const gs_plan* plan, void* ws, const float* image, const float* target,
+                     float* dL_dimage, void* stream);
+
+/* Rasterization backward, per Gaussian (Sec. 4.2, first implementation):
+ * one thread block per tile, Gaussians of the tile in batches of S across
+ * threads, transmittance recomputed from the front (no per-pair storage from
+ * the forward), no atomics: one 9-float gradient record (mean2D, conic,
+ * opacity, colour) per intersection.  image is the gs_raster_fwd output
+ * (the suffix colour is derived from it), dL_dimage the loss gradient. */
+gs_status gs_raster_bwd(const gs_plan* plan, void* ws, const float* image,
+                        const float* dL_dimage, void* stream);
+
+/* Projection backward fused with Adam (Sec. 4.3): per Gaussian, sums its
+ * intersection gradients over all views, back-propagates through colour
+ * (SH), conic, EWA Jacobian and covariance to theta, and applies one Adam
+ * step with scales and opacity moved to log / logit space inside the
+ * optimiser; SH degree 0 and degrees 1-3 take separate learning rates.
+ * Writes geom, sh, m and v in place.  If grads_out != NULL nothing is
+ * updated; instead the gradient with respect to the STORED (activated)
+ * parameters is written there as float4[15][sum of scene n] (chunk order of
+ * geom then sh, scenes concatenated). */
+gs_status gs_project_bwd_adam(const gs_plan* plan, void* ws, const gs_scene_buf* scenes,
+                              const float* cams, const gs_adam* adam, float* grads_out,
+                              void* stream);
+
+/* Advance the workspace Adam step counter by one (for graph replay). */
+gs_status gs_adam_advance(const gs_plan* plan, void* ws, void* stream);
+
+/* Synchronous: copy the workspace statistics to the host (waits on stream).
+ * Not capturable. */
+gs_status gs_read_stats(const gs_plan* plan, const void* ws, gs_stats* out, void* stream);
+
+/* Device views of intermediate buffers (for tests and tools): 0 counts
+ * u32[pairs], 1 offsets u32[pairs+1], 2 sorted keys u32[cap], 3 sorted pair
+ * index u32[cap], 4 tile ranges u32[tiles][2], 5 n_last u32[pixels],
+ * 6 final transmittance f32[pixels], 7 projected records float4[pairs][3],
+ * 8 gradient records float4[cap][3], 9 sorted emission slot u32[cap].
+ * Returns NULL for an unknown buffer. */
+void* gs_workspace_buffer(const gs_plan* plan, void* ws, int32_t which);
+
+const char* gs_status_str(gs_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_STEP_H */

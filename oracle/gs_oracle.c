@@ -469,18 +469,22 @@ void orc_project64(int64_t n, const double* means, const double* quats, const do
 
 /* Contribution of projected Gaussian P at pixel centre (px, py): returns the
  * clamped alpha, or 0 when the pair is outside 3 sigma or below 1/255.
- * *flag is set when a decision lies within `margin` (relative) of its
- * threshold; *Gout and *clamped report the Gaussian value and clamp state. */
-static double orc_alpha(const double* P, double px, double py, double margin, int* flag,
+ * *flag is set when a decision that changes the image lies within `margin`
+ * (relative) of its threshold: the 3-sigma cut (only when alpha there would
+ * reach 1/255) or the 1/255 skip.  *gflag is set when only this Gaussian's
+ * own gradient is affected: alpha near the 0.99 clamp (alpha is continuous
+ * there, its derivative is not).  *Gout and *clamped report the Gaussian
+ * value and clamp state. */
+static double orc_alpha(const double* P, double px, double py, double margin, int* flag, int* gflag,
                         double* Gout, int* clamped, double* dx_out, double* dy_out)
 {
     double dx = px - P[4], dy = py - P[5];
     double d2 = P[9] * dx * dx + 2 * P[10] * dx * dy + P[11] * dy * dy;
-    if (fabs(d2 - 9.0) <= margin * 9.0) *flag = 1;
+    if (fabs(d2 - 9.0) <= margin * 9.0 && P[12] * exp(-4.5) >= (1.0 - margin) / 255.0) *flag = 1;
     if (d2 > 9.0) return 0;
     double G = exp(-0.5 * d2);
     double araw = P[12] * G;
-    if (fabs(araw - 0.99) <= margin * 0.99) *flag = 1;
+    if (fabs(araw - 0.99) <= margin * 0.99) *gflag = 1;
     int cl = araw > 0.99;
     double al = cl ? 0.99 : araw;
     if (fabs(al - 1.0 / 255.0) <= margin / 255.0) *flag = 1;
@@ -516,12 +520,13 @@ int64_t orc_render64(const orc_cam* cam, int64_t n, const double* proj, const ui
             uint32_t g = sorted_g[k];
             const double* P = proj + ORC_PSTRIDE * g;
             if (!P[0]) { uflag = 1; if (unstable_g) unstable_g[g] = 1; continue; }
-            int flag = 0, cl;
+            int flag = 0, gflag = 0, cl;
             double G, dx, dy;
-            double al = orc_alpha(P, x + 0.5, y + 0.5, margin, &flag, &G, &cl, &dx, &dy);
+            double al = orc_alpha(P, x + 0.5, y + 0.5, margin, &flag, &gflag, &G, &cl, &dx, &dy);
             double Tn = T * (1 - al);
             if (al > 0 && fabs(Tn - 1e-4) <= margin * 1e-4) flag = 1;
-            if (flag) { uflag = 1; if (unstable_g) unstable_g[g] = 1; }
+            if (flag) uflag = 1;
+            if ((flag || gflag) && unstable_g) unstable_g[g] = 1;
             if (al == 0) continue;
             if (Tn < 1e-4) break;
             for (int ch = 0; ch < 3; ch++) Cc[ch] += P[16 + ch] * al * T;
@@ -551,9 +556,9 @@ int64_t orc_render64_brute(const orc_cam* cam, const double* proj, int64_t n_ord
         for (int64_t k = 0; k < n_order; k++) {
             const double* P = proj + ORC_PSTRIDE * order[k];
             if (!P[0]) continue;
-            int flag = 0, cl;
+            int flag = 0, gflag = 0, cl;
             double G, dx, dy;
-            double al = orc_alpha(P, x + 0.5, y + 0.5, 0.0, &flag, &G, &cl, &dx, &dy);
+            double al = orc_alpha(P, x + 0.5, y + 0.5, 0.0, &flag, &gflag, &G, &cl, &dx, &dy);
             if (al == 0) continue;
             double Tn = T * (1 - al);
             if (Tn < 1e-4) break;
@@ -602,9 +607,9 @@ void orc_raster_bwd64(const orc_cam* cam, int64_t n, const double* proj, const u
         for (int64_t k = s0; k < s1; k++) {
             const double* P = proj + ORC_PSTRIDE * sorted_g[k];
             if (!P[0]) continue;
-            int flag = 0, cl;
+            int flag = 0, gflag = 0, cl;
             double G, dx, dy;
-            double al = orc_alpha(P, x + 0.5, y + 0.5, 0.0, &flag, &G, &cl, &dx, &dy);
+            double al = orc_alpha(P, x + 0.5, y + 0.5, 0.0, &flag, &gflag, &G, &cl, &dx, &dy);
             if (al == 0) continue;
             double Tn = T * (1 - al);
             if (Tn < 1e-4) break;

@@ -1,0 +1,415 @@
+// bin_sort.cu -- tiling and sorting (VkSplat Sec. 4.1, Sec. 4.4; Table 2
+// "Tiling/Sorting": index offset, generate keys, sorting, tile ranges).
+//
+//   index offset : exclusive scan of the per-pair tile counts (reduce-then-
+//                  scan, three launches, no inter-block waiting)
+//   generate keys: second scan-line pass writing 32-bit keys
+//                  (tile << shift | depth code >> drop) and the pair of each
+//                  emitted intersection
+//   sorting      : stable LSD radix sort, 8-bit digits, 2048 keys per block,
+//                  warp-level match_any ranking, scatter through shared memory
+//                  so that global writes are coalesced runs per digit; the
+//                  payload starts as the implicit emission index; when there
+//                  are several views a final pass orders the view segments;
+//                  the last pass also gathers the sorted pair indices
+//   tile ranges  : [start, end) per tile from key boundaries
+// K never leaves the device: every kernel reads it from the workspace header
+// and grids are sized by the capacity.
+#include "gs_internal.cuh"
+
+namespace gs {
+
+__device__ __forceinline__ uint32_t lanemask_lt()
+{
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__global__ void k_fill_u32(uint32_t* __restrict__ p, int64_t n, uint32_t value)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = value;
+}
+
+void launch_fill_u32(uint32_t* p, int64_t n, uint32_t value, cudaStream_t st)
+{
+    if (n <= 0) return;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_fill_u32<<<(unsigned)blocks, 256, 0, st>>>(p, n, value);
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of u32 (reduce, scan of block sums, down-sweep)
+// ---------------------------------------------------------------------------
+
+template <int T>
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* warp_sums, uint32_t* total)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t s = lane < T / 32 ? warp_sums[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < T / 32) warp_sums[lane] = s;
+    }
+    __syncthreads();
+    uint32_t before = w > 0 ? warp_sums[w - 1] : 0u;
+    if (total) *total = warp_sums[T / 32 - 1];
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ in, int64_t n,
+                                                               uint32_t* __restrict__ part)
+{
+    __shared__ uint32_t ws[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock;
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+        int64_t idx = base + i * kScanThreads + threadIdx.x;
+        if (idx < n) s += in[idx];
+    }
+    uint32_t tot;
+    block_excl_scan<kScanThreads>(s, ws, &tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+// Single block: exclusive scan of the block sums in place; grand total at part[nparts].
+__global__ void __launch_bounds__(1024) k_scan_part(uint32_t* __restrict__ part, int64_t nparts)
+{
+    __shared__ uint32_t ws[32];
+    uint32_t carry = 0;
+    for (int64_t b = 0; b < nparts; b += 1024) {
+        int64_t i = b + threadIdx.x;
+        uint32_t v = i < nparts ? part[i] : 0u;
+        uint32_t tot;
+        uint32_t ex = block_excl_scan<1024>(v, ws, &tot);
+        if (i < nparts) part[i] = carry + ex;
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[nparts] = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* in, int64_t n,
+                                                             const uint32_t* __restrict__ part, uint32_t* out)
+{
+    __shared__ uint32_t buf[kScanBlock];
+    __shared__ uint32_t ws[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock;
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+        int64_t idx = base + i * kScanThreads + threadIdx.x;
+        buf[i * kScanThreads + threadIdx.x] = idx < n ? in[idx] : 0u;
+    }
+    __syncthreads();
+    uint32_t loc[kScanItems];
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+        loc[i] = s;
+        s += buf[threadIdx.x * kScanItems + i];
+    }
+    uint32_t ex = block_excl_scan<kScanThreads>(s, ws, nullptr) + part[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) buf[threadIdx.x * kScanItems + i] = ex + loc[i];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+        int64_t idx = base + i * kScanThreads + threadIdx.x;
+        if (idx < n) out[idx] = buf[i * kScanThreads + threadIdx.x];
+    }
+}
+
+static void scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* part, cudaStream_t st)
+{
+    const int64_t nparts = (n + kScanBlock - 1) / kScanBlock;
+    k_scan_reduce<<<(unsigned)nparts, kScanThreads, 0, st>>>(in, n, part);
+    k_scan_part<<<1, 1024, 0, st>>>(part, nparts);
+    k_scan_down<<<(unsigned)nparts, kScanThreads, 0, st>>>(in, n, part, out);
+}
+
+// Total, capacity check and view segment starts after the count scan.
+__global__ void k_count_finalize(Views V, const uint32_t* __restrict__ part, int64_t nparts,
+                                 uint32_t* __restrict__ offset, WsHeader* __restrict__ hdr, uint32_t cap)
+{
+    const uint32_t total = part[nparts];
+    if (threadIdx.x == 0) {
+        hdr->k_required = total;
+        hdr->k_eff = total < cap ? total : cap;
+        if (total > cap) atomicOr(&hdr->status, GS_STATUS_CAPACITY);
+        offset[V.pairs] = total;
+        hdr->seg[V.n] = total < cap ? total : cap;
+    }
+    for (int v = threadIdx.x; v < V.n; v += blockDim.x) {
+        uint32_t s = offset[V.v[v].pair_base];
+        hdr->seg[v] = s < cap ? s : cap;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Generate keys
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_emit(Views V, const uint32_t* __restrict__ count,
+                                              const uint32_t* __restrict__ offset, const ProjRec* __restrict__ rec,
+                                              const float4* __restrict__ binrec, uint32_t* __restrict__ keys,
+                                              uint32_t* __restrict__ pid, uint32_t cap)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= V.pairs) return;
+    const uint32_t cnt = count[p];
+    if (cnt == 0) return;
+    const ViewDesc& vd = V.v[view_of_pair(V, p)];
+    const uint32_t off = offset[p];
+    const float4 ra = rec[p].a;
+    const float4 bb = binrec[p];
+    BinGeom g;
+    g.mx = ra.x; g.my = ra.y; g.a = bb.x; g.b = bb.y; g.c = bb.z;
+    g.det = FS(FM(g.a, g.c), FM(g.b, g.b));
+    g.mant = __float_as_uint(bb.w);
+    g.valid = 1;
+    const uint32_t low = g.mant >> vd.drop;
+    const int shift = vd.shift;
+    scanline_tiles(g, V.tw, V.th, vd.TX, vd.TY, [&](uint32_t i, uint32_t tile) {
+        uint32_t e = off + i;
+        if (e < cap) {
+            keys[e] = (tile << shift) | low;
+            pid[e] = (uint32_t)p;
+        }
+    });
+}
+
+// ---------------------------------------------------------------------------
+// Radix sort passes
+// ---------------------------------------------------------------------------
+
+enum { kDigitKey = 0, kDigitView = 1 };
+
+__device__ __forceinline__ int view_of_slot(const uint32_t* seg, int nv, uint32_t e)
+{
+    int v = 0;
+    while (v + 1 < nv && seg[v + 1] <= e) v++;
+    return v;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kRadixThreads) k_radix_up(const uint32_t* __restrict__ keys,
+                                                             const uint32_t* __restrict__ vals, bool iota,
+                                                             const WsHeader* __restrict__ hdr, int shift,
+                                                             uint32_t* __restrict__ hist, int64_t nblk, int nv)
+{
+    __shared__ uint32_t h[kRadixDigits];
+    __shared__ uint32_t seg[kMaxViews + 1];
+    h[threadIdx.x] = 0;
+    if (MODE == kDigitView)
+        for (int i = threadIdx.x; i <= nv; i += blockDim.x) seg[i] = hdr->seg[i];
+    __syncthreads();
+    const uint32_t K = hdr->k_eff;
+    const int64_t base = (int64_t)blockIdx.x * kRadixBlock;
+    const int lane = threadIdx.x & 31;
+    if (base < K) {
+#pragma unroll
+        for (int i = 0; i < kRadixItems; i++) {
+            const int64_t idx = base + i * kRadixThreads + threadIdx.x;
+            const bool valid = idx < K;
+            uint32_t d = 0xFFFFu;
+            if (valid) {
+                if (MODE == kDigitKey) d = (keys[idx] >> shift) & 0xFFu;
+                else d = (uint32_t)view_of_slot(seg, nv, iota ? (uint32_t)idx : vals[idx]);
+            }
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[d], __popc(peers));
+        }
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
+}
+
+template <int MODE, bool IOTA, bool LAST>
+__global__ void __launch_bounds__(kRadixThreads) k_radix_down(const uint32_t* __restrict__ keys_in,
+                                                               const uint32_t* __restrict__ vals_in,
+                                                               uint32_t* __restrict__ keys_out,
+                                                               uint32_t* __restrict__ vals_out,
+                                                               const uint32_t* __restrict__ hist, int64_t nblk,
+                                                               int shift, const WsHeader* __restrict__ hdr, int nv,
+                                                               const uint32_t* __restrict__ pid,
+                                                               uint32_t* __restrict__ pid_sorted)
+{
+    constexpr int W = kRadixThreads / 32;
+    __shared__ uint32_t wh[W][kRadixDigits];
+    __shared__ uint32_t bstart[kRadixDigits];
+    __shared__ uint32_t gbase[kRadixDigits];
+    __shared__ uint32_t sk[kRadixBlock];
+    __shared__ uint32_t sv[kRadixBlock];
+    __shared__ uint32_t seg[kMaxViews + 1];
+    __shared__ uint32_t wsum[32];
+    const uint32_t K = hdr->k_eff;
+    const int64_t base = (int64_t)blockIdx.x * kRadixBlock;
+    if (base >= K) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < W; i++) wh[i][threadIdx.x] = 0;
+    if (MODE == kDigitView)
+        for (int i = threadIdx.x; i <= nv; i += blockDim.x) seg[i] = hdr->seg[i];
+    __syncthreads();
+
+    uint32_t key[kRadixItems], val[kRadixItems], dig[kRadixItems], rank[kRadixItems];
+#pragma unroll
+    for (int r = 0; r < kRadixItems; r++) {
+        const int64_t idx = base + w * (32 * kRadixItems) + r * 32 + lane;
+        const bool valid = idx < K;
+        key[r] = valid ? keys_in[idx] : 0u;
+        val[r] = IOTA ? (uint32_t)idx : (valid ? vals_in[idx] : 0u);
+        uint32_t d = 0xFFFFu;
+        if (valid) {
+            if (MODE == kDigitKey) d = (key[r] >> shift) & 0xFFu;
+            else d = (uint32_t)view_of_slot(seg, nv, val[r]);
+        }
+        dig[r] = d;
+    }
+    // stable rank within the warp's contiguous 256-key range, round by round
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int r = 0; r < kRadixItems; r++) {
+        const uint32_t d = dig[r];
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const bool valid = d != 0xFFFFu;
+        uint32_t cur = valid ? wh[w][d] : 0u;
+        rank[r] = cur + __popc(peers & lt);
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) wh[w][d] = cur + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // per digit: exclusive offsets across warps, then across digits
+    {
+        const int d = threadIdx.x;
+        uint32_t run = 0;
+#pragma unroll
+        for (int i = 0; i < W; i++) {
+            uint32_t c = wh[i][d];
+            wh[i][d] = run;
+            run += c;
+        }
+        uint32_t ex = block_excl_scan<kRadixThreads>(run, wsum, nullptr);
+        bstart[d] = ex;
+        gbase[d] = hist[(int64_t)d * nblk + blockIdx.x];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kRadixItems; r++) {
+        const uint32_t d = dig[r];
+        if (d != 0xFFFFu) {
+            const uint32_t lp = bstart[d] + wh[w][d] + rank[r];
+            sk[lp] = key[r];
+            sv[lp] = val[r];
+        }
+    }
+    __syncthreads();
+    const int nvalid = (int)min((int64_t)kRadixBlock, (int64_t)K - base);
+    for (int i = threadIdx.x; i < nvalid; i += kRadixThreads) {
+        const uint32_t k = sk[i], v = sv[i];
+        const uint32_t d = MODE == kDigitKey ? ((k >> shift) & 0xFFu) : (uint32_t)view_of_slot(seg, nv, v);
+        const uint32_t pos = gbase[d] + (uint32_t)i - bstart[d];
+        keys_out[pos] = k;
+        vals_out[pos] = v;
+        if (LAST) pid_sorted[pos] = pid[v];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Tile ranges
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_ranges(Views V, const uint32_t* __restrict__ keys,
+                                                const WsHeader* __restrict__ hdr, uint2* __restrict__ ranges,
+                                                uint32_t cap)
+{
+    __shared__ uint32_t seg[kMaxViews + 1];
+    for (int i = threadIdx.x; i <= V.n; i += blockDim.x) seg[i] = hdr->seg[i];
+    __syncthreads();
+    const uint32_t K = hdr->k_eff;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < K; k += (int64_t)gridDim.x * blockDim.x) {
+        const int v = view_of_slot(seg, V.n, (uint32_t)k);
+        const ViewDesc& vd = V.v[v];
+        const uint32_t tile = keys[k] >> vd.shift;
+        const int64_t gt = vd.tile_base + tile;
+        const bool first = (k == seg[v]) || ((keys[k - 1] >> vd.shift) != tile);
+        const bool last = (k + 1 == seg[v + 1]) || ((keys[k + 1] >> vd.shift) != tile);
+        if (first) ranges[gt].x = (uint32_t)k;
+        if (last) ranges[gt].y = (uint32_t)(k + 1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+
+void launch_bin_sort(const Plan& P, const WsPtrs& w, cudaStream_t st)
+{
+    const Views& V = P.views;
+    const uint32_t cap = (uint32_t)P.cap;
+    // index offset
+    scan_u32(w.count, w.offset, V.pairs, w.scan_part, st);
+    k_count_finalize<<<1, 64, 0, st>>>(V, w.scan_part, P.count_scan_parts, w.offset, w.hdr, cap);
+    // generate keys
+    {
+        const int64_t blocks = (V.pairs + 255) / 256;
+        k_emit<<<(unsigned)blocks, 256, 0, st>>>(V, w.count, w.offset, w.rec, w.binrec, w.keysA, w.pid, cap);
+    }
+    // sorting
+    const int64_t nblk = P.radix_blocks;
+    const int npass = P.key_passes + P.view_pass;
+    uint32_t *kin = w.keysA, *vin = w.valsA, *kout = w.keysB, *vout = w.valsB;
+    for (int pass = 0; pass < npass; pass++) {
+        const bool view = pass >= P.key_passes;
+        const bool first = pass == 0, last = pass == npass - 1;
+        const int shift = 8 * pass;
+        if (view)
+            k_radix_up<kDigitView><<<(unsigned)nblk, kRadixThreads, 0, st>>>(kin, vin, first, w.hdr, 0, w.hist, nblk,
+                                                                               V.n);
+        else
+            k_radix_up<kDigitKey><<<(unsigned)nblk, kRadixThreads, 0, st>>>(kin, vin, first, w.hdr, shift, w.hist,
+                                                                              nblk, V.n);
+        scan_u32(w.hist, w.hist, (int64_t)kRadixDigits * nblk, w.scan_part, st);
+#define GS_DOWN(MODE, IOTA, LAST)                                                                          \
+    k_radix_down<MODE, IOTA, LAST><<<(unsigned)nblk, kRadixThreads, 0, st>>>(kin, vin, kout, vout, w.hist, nblk, \
+                                                                              shift, w.hdr, V.n, w.pid, w.pid_sorted)
+        if (view) {
+            if (first) GS_DOWN(kDigitView, true, true);
+            else GS_DOWN(kDigitView, false, true);
+        } else if (first) {
+            if (last) GS_DOWN(kDigitKey, true, true);
+            else GS_DOWN(kDigitKey, true, false);
+        } else {
+            if (last) GS_DOWN(kDigitKey, false, true);
+            else GS_DOWN(kDigitKey, false, false);
+        }
+#undef GS_DOWN
+        uint32_t* t;
+        t = kin; kin = kout; kout = t;
+        t = vin; vin = vout; vout = t;
+    }
+    // tile ranges
+    launch_fill_u32(reinterpret_cast<uint32_t*>(w.ranges), 2 * V.tiles, 0u, st);
+    {
+        int64_t blocks = ((int64_t)cap + 255) / 256;
+        if (blocks > 152 * 32) blocks = 152 * 32;
+        if (blocks < 1) blocks = 1;
+        k_ranges<<<(unsigned)blocks, 256, 0, st>>>(V, w.keys_sorted, w.hdr, w.ranges, cap);
+    }
+}
+
+}  // namespace gs

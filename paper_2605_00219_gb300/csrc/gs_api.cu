@@ -1,0 +1,383 @@
+// gs_api.cu -- C ABI of the training step: plan, workspace and the stage
+// entry points declared in gs_step.h.
+#include <new>
+
+#include "gs_internal.cuh"
+
+struct gs_plan {
+    gs::Plan p;
+};
+
+namespace gs {
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+static int ceil_log2(int64_t n)
+{
+    int b = 0;
+    while (((int64_t)1 << b) < n) b++;
+    return b;
+}
+
+WsPtrs carve(const Plan& P, void* ws)
+{
+    char* b = static_cast<char*>(ws);
+    WsPtrs w;
+    w.hdr = reinterpret_cast<WsHeader*>(b + P.off_hdr);
+    w.count = reinterpret_cast<uint32_t*>(b + P.off_count);
+    w.offset = reinterpret_cast<uint32_t*>(b + P.off_offset);
+    w.rec = reinterpret_cast<ProjRec*>(b + P.off_rec);
+    w.binrec = reinterpret_cast<float4*>(b + P.off_binrec);
+    w.keysA = reinterpret_cast<uint32_t*>(b + P.off_keysA);
+    w.valsA = reinterpret_cast<uint32_t*>(b + P.off_valsA);
+    w.keysB = reinterpret_cast<uint32_t*>(b + P.off_keysB);
+    w.valsB = reinterpret_cast<uint32_t*>(b + P.off_valsB);
+    w.pid = reinterpret_cast<uint32_t*>(b + P.off_pid);
+    w.pid_sorted = reinterpret_cast<uint32_t*>(b + P.off_pid_sorted);
+    w.ranges = reinterpret_cast<uint2*>(b + P.off_ranges);
+    w.nlast = reinterpret_cast<uint32_t*>(b + P.off_nlast);
+    w.tfinal = reinterpret_cast<float*>(b + P.off_tfinal);
+    w.gradrec = reinterpret_cast<GradRec*>(b + P.off_gradrec);
+    w.scan_part = reinterpret_cast<uint32_t*>(b + P.off_scan_part);
+    w.hist = reinterpret_cast<uint32_t*>(b + P.off_hist);
+    w.loss_part = reinterpret_cast<float*>(b + P.off_loss_part);
+    const bool odd = ((P.key_passes + P.view_pass) & 1) != 0;
+    w.keys_sorted = odd ? w.keysB : w.keysA;
+    w.vals_sorted = odd ? w.valsB : w.valsA;
+    return w;
+}
+
+static bool plan_build(Plan& P, const int64_t* scene_n, int32_t n_scenes, const gs_view* views, int32_t n_views,
+                       int64_t cap, const gs_tuning* tuning, int32_t flags)
+{
+    if (!scene_n || !views || n_scenes < 1 || n_scenes > kMaxScenes || n_views < 1 || n_views > kMaxViews)
+        return false;
+    memset(&P, 0, sizeof(P));
+    gs_tuning t = {16, 16, 0, 0};
+    if (tuning) t = *tuning;
+    const bool tile_ok = (t.tile_w == 8 && t.tile_h == 8) || (t.tile_w == 16 && t.tile_h == 16) ||
+                         (t.tile_w == 16 && t.tile_h == 32);
+    if (!tile_ok) return false;
+    if (!(t.bwd_batch == 0 || t.bwd_batch == 32 || t.bwd_batch == 64 || t.bwd_batch == 96 || t.bwd_batch == 128))
+        return false;
+    if (flags & ~(GS_STORE_SH_BF16 | GS_STORE_MOMENTS_BF16)) return false;
+    P.tuning = t;
+    P.sh_bf16 = (flags & GS_STORE_SH_BF16) ? 1 : 0;
+    P.mom_bf16 = (flags & GS_STORE_MOMENTS_BF16) ? 1 : 0;
+    P.n_scenes = n_scenes;
+    int64_t base = 0;
+    for (int s = 0; s < n_scenes; s++) {
+        if (scene_n[s] < 1 || scene_n[s] > ((int64_t)1 << 31)) return false;
+        P.scene_n[s] = scene_n[s];
+        P.scene_base[s] = base;
+        base += scene_n[s];
+    }
+    P.scene_base[n_scenes] = base;
+    Views& V = P.views;
+    V.n = n_views;
+    V.tw = t.tile_w;
+    V.th = t.tile_h;
+    int64_t pairs = 0, tiles = 0, pixels = 0;
+    int max_bits = 0;
+    for (int v = 0; v < n_views; v++) {
+        const gs_view& gv = views[v];
+        if (gv.width < 1 || gv.height < 1 || gv.width > 16384 || gv.height > 16384) return false;
+        if (gv.scene < 0 || gv.scene >= n_scenes) return false;
+        ViewDesc& d = V.v[v];
+        d.W = gv.width;
+        d.H = gv.height;
+        d.TX = (gv.width + t.tile_w - 1) / t.tile_w;
+        d.TY = (gv.height + t.tile_h - 1) / t.tile_h;
+        d.scene = gv.scene;
+        const int tb = ceil_log2((int64_t)d.TX * d.TY);
+        d.shift = tb >= 9 ? 32 - tb : 23;
+        d.drop = tb >= 9 ? tb - 9 : 0;
+        max_bits = std::max(max_bits, tb >= 9 ? 32 : 23 + tb);
+        d.pair_base = pairs;
+        d.tile_base = tiles;
+        d.pix_base = pixels;
+        pairs += scene_n[gv.scene];
+        tiles += (int64_t)d.TX * d.TY;
+        pixels += (int64_t)gv.width * gv.height;
+    }
+    V.pairs = pairs;
+    V.tiles = tiles;
+    V.pixels = pixels;
+    if (pairs >= ((int64_t)1 << 31)) return false;
+    if (cap <= 0) cap = std::max<int64_t>(4096, 8 * pairs);
+    cap = align_up((size_t)cap, kRadixBlock);
+    if (cap >= ((int64_t)1 << 31)) return false;
+    P.cap = cap;
+    P.key_passes = (max_bits + 7) / 8;
+    P.view_pass = n_views > 1 ? 1 : 0;
+    P.radix_blocks = cap / kRadixBlock;
+    P.count_scan_parts = (pairs + kScanBlock - 1) / kScanBlock;
+    P.hist_scan_parts = (kRadixDigits * P.radix_blocks + kScanBlock - 1) / kScanBlock;
+    P.raster_blocks = tiles;
+    const int64_t loss_blocks = (3 * pixels + 2047) / 2048;
+
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align_up(o + bytes, 256);
+        return at;
+    };
+    P.off_hdr = take(sizeof(WsHeader));
+    P.off_count = take(4 * (size_t)pairs);
+    P.off_offset = take(4 * (size_t)(pairs + 1));
+    P.off_rec = take(sizeof(ProjRec) * (size_t)pairs);
+    P.off_binrec = take(16 * (size_t)pairs);
+    P.off_keysA = take(4 * (size_t)cap);
+    P.off_valsA = take(4 * (size_t)cap);
+    P.off_keysB = take(4 * (size_t)cap);
+    P.off_valsB = take(4 * (size_t)cap);
+    P.off_pid = take(4 * (size_t)cap);
+    P.off_pid_sorted = take(4 * (size_t)cap);
+    P.off_ranges = take(8 * (size_t)tiles);
+    P.off_nlast = take(4 * (size_t)pixels);
+    P.off_tfinal = take(4 * (size_t)pixels);
+    P.off_gradrec = take(sizeof(GradRec) * (size_t)cap);
+    P.off_scan_part = take(4 * (size_t)(std::max(P.count_scan_parts, P.hist_scan_parts) + 1));
+    P.off_hist = take(4 * (size_t)kRadixDigits * (size_t)P.radix_blocks);
+    P.off_loss_part = take(4 * (size_t)loss_blocks);
+    P.ws_bytes = o;
+    return true;
+}
+
+Scenes make_scenes(const Plan& P, const gs_scene_buf* scenes)
+{
+    Scenes S;
+    memset(&S, 0, sizeof(S));
+    S.n = P.n_scenes;
+    S.sh_bf16 = P.sh_bf16;
+    S.mom_bf16 = P.mom_bf16;
+    S.total = P.scene_base[P.n_scenes];
+    for (int s = 0; s < P.n_scenes; s++) {
+        S.s[s].n = P.scene_n[s];
+        S.s[s].base = P.scene_base[s];
+        S.s[s].geom = static_cast<float4*>(scenes[s].geom);
+        S.s[s].sh = scenes[s].sh;
+        S.s[s].m = scenes[s].m;
+        S.s[s].v = scenes[s].v;
+    }
+    return S;
+}
+
+__global__ void k_ws_init(WsHeader* hdr, int full)
+{
+    if (threadIdx.x == 0) {
+        hdr->status = 0;
+        hdr->k_required = 0;
+        hdr->blended = 0;
+        hdr->k_eff = 0;
+        hdr->loss_counter = 0;
+        hdr->loss = 0.f;
+        if (full) hdr->step = 0;
+    }
+}
+
+void launch_ws_init(const Plan&, const WsPtrs& w, cudaStream_t st) { k_ws_init<<<1, 32, 0, st>>>(w.hdr, 1); }
+
+static void launch_step_begin(const WsPtrs& w, cudaStream_t st) { k_ws_init<<<1, 32, 0, st>>>(w.hdr, 0); }
+
+__global__ void k_adam_advance(WsHeader* hdr)
+{
+    if (threadIdx.x == 0) hdr->step += 1;
+}
+
+void launch_adam_advance(const WsPtrs& w, cudaStream_t st) { k_adam_advance<<<1, 32, 0, st>>>(w.hdr); }
+
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+static gs_status launch_status()
+{
+    return cudaPeekAtLastError() == cudaSuccess ? GS_OK : (cudaGetLastError(), GS_ERR_CUDA);
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" {
+
+gs_plan* gs_plan_create(const int64_t* scene_n, int32_t n_scenes, const gs_view* views, int32_t n_views,
+                        int64_t isect_capacity, const gs_tuning* tuning, int32_t storage_flags, gs_status* err)
+{
+    gs_plan* p = new (std::nothrow) gs_plan;
+    if (!p) {
+        if (err) *err = GS_ERR_INVALID_ARG;
+        return nullptr;
+    }
+    if (!plan_build(p->p, scene_n, n_scenes, views, n_views, isect_capacity, tuning, storage_flags)) {
+        delete p;
+        if (err) *err = GS_ERR_INVALID_ARG;
+        return nullptr;
+    }
+    if (err) *err = GS_OK;
+    return p;
+}
+
+void gs_plan_destroy(gs_plan* plan) { delete plan; }
+
+size_t gs_workspace_bytes(const gs_plan* plan) { return plan ? plan->p.ws_bytes : 0; }
+
+int64_t gs_plan_query(const gs_plan* plan, int32_t what)
+{
+    if (!plan) return -1;
+    const Plan& P = plan->p;
+    switch (what) {
+    case 0: return P.views.pairs;
+    case 1: return P.views.tiles;
+    case 2: return P.views.pixels;
+    case 3: return P.cap;
+    case 4: return P.views.n;
+    case 5: return P.n_scenes;
+    case 6: return P.views.tw;
+    case 7: return P.views.th;
+    default: return -1;
+    }
+}
+
+gs_status gs_workspace_init(const gs_plan* plan, void* ws, void* stream)
+{
+    if (!plan || !ws || (reinterpret_cast<uintptr_t>(ws) & 255u)) return GS_ERR_INVALID_ARG;
+    WsPtrs w = carve(plan->p, ws);
+    launch_ws_init(plan->p, w, static_cast<cudaStream_t>(stream));
+    return launch_status();
+}
+
+static gs_status check_scenes(const Plan& P, const gs_scene_buf* scenes, bool need_moments)
+{
+    if (!scenes) return GS_ERR_INVALID_ARG;
+    for (int s = 0; s < P.n_scenes; s++) {
+        const gs_scene_buf& b = scenes[s];
+        if (b.n != P.scene_n[s] || !b.geom || !b.sh || !aligned16(b.geom) || !aligned16(b.sh))
+            return GS_ERR_INVALID_ARG;
+        if (need_moments && (!b.m || !b.v || !aligned16(b.m) || !aligned16(b.v))) return GS_ERR_INVALID_ARG;
+    }
+    return GS_OK;
+}
+
+gs_status gs_project_fwd(const gs_plan* plan, void* ws, const gs_scene_buf* scenes, const float* cams,
+                         void* stream)
+{
+    if (!plan || !ws || !cams) return GS_ERR_INVALID_ARG;
+    const Plan& P = plan->p;
+    gs_status e = check_scenes(P, scenes, false);
+    if (e != GS_OK) return e;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    WsPtrs w = carve(P, ws);
+    launch_step_begin(w, st);
+    launch_project_fwd(P, make_scenes(P, scenes), cams, w, st);
+    return launch_status();
+}
+
+gs_status gs_bin_sort(const gs_plan* plan, void* ws, void* stream)
+{
+    if (!plan || !ws) return GS_ERR_INVALID_ARG;
+    WsPtrs w = carve(plan->p, ws);
+    launch_bin_sort(plan->p, w, static_cast<cudaStream_t>(stream));
+    return launch_status();
+}
+
+gs_status gs_raster_fwd(const gs_plan* plan, void* ws, const float* bg, float* image, void* stream)
+{
+    if (!plan || !ws || !image || !aligned16(image)) return GS_ERR_INVALID_ARG;
+    WsPtrs w = carve(plan->p, ws);
+    launch_raster_fwd(plan->p, w, bg, image, static_cast<cudaStream_t>(stream));
+    return launch_status();
+}
+
+gs_status gs_loss_l1(const gs_plan* plan, void* ws, const float* image, const float* target, float* dL_dimage,
+                     void* stream)
+{
+    if (!plan || !ws || !image || !target || !dL_dimage) return GS_ERR_INVALID_ARG;
+    WsPtrs w = carve(plan->p, ws);
+    launch_loss_l1(plan->p, w, image, target, dL_dimage, static_cast<cudaStream_t>(stream));
+    return launch_status();
+}
+
+gs_status gs_raster_bwd(const gs_plan* plan, void* ws, const float* image, const float* dL_dimage, void* stream)
+{
+    if (!plan || !ws || !image || !dL_dimage) return GS_ERR_INVALID_ARG;
+    WsPtrs w = carve(plan->p, ws);
+    launch_raster_bwd(plan->p, w, image, dL_dimage, static_cast<cudaStream_t>(stream));
+    return launch_status();
+}
+
+gs_status gs_project_bwd_adam(const gs_plan* plan, void* ws, const gs_scene_buf* scenes, const float* cams,
+                              const gs_adam* adam, float* grads_out, void* stream)
+{
+    if (!plan || !ws || !cams) return GS_ERR_INVALID_ARG;
+    const Plan& P = plan->p;
+    if (!grads_out && !adam) return GS_ERR_INVALID_ARG;
+    if (grads_out && !aligned16(grads_out)) return GS_ERR_INVALID_ARG;
+    gs_status e = check_scenes(P, scenes, grads_out == nullptr);
+    if (e != GS_OK) return e;
+    if (!grads_out && (P.sh_bf16 || P.mom_bf16)) return GS_ERR_UNIMPLEMENTED;
+    if (P.sh_bf16) return GS_ERR_UNIMPLEMENTED;
+    WsPtrs w = carve(P, ws);
+    launch_project_bwd_adam(P, make_scenes(P, scenes), cams, w, adam, grads_out, static_cast<cudaStream_t>(stream));
+    return launch_status();
+}
+
+gs_status gs_adam_advance(const gs_plan* plan, void* ws, void* stream)
+{
+    if (!plan || !ws) return GS_ERR_INVALID_ARG;
+    WsPtrs w = carve(plan->p, ws);
+    launch_adam_advance(w, static_cast<cudaStream_t>(stream));
+    return launch_status();
+}
+
+gs_status gs_read_stats(const gs_plan* plan, const void* ws, gs_stats* out, void* stream)
+{
+    if (!plan || !ws || !out) return GS_ERR_INVALID_ARG;
+    WsPtrs w = carve(plan->p, const_cast<void*>(ws));
+    WsHeader h;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(&h, w.hdr, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) return GS_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return GS_ERR_CUDA;
+    out->status = h.status;
+    out->step = h.step;
+    out->k_required = (int64_t)h.k_required;
+    out->k_capacity = plan->p.cap;
+    out->blended_pairs = h.blended;
+    out->loss = h.loss;
+    out->reserved = 0.f;
+    return GS_OK;
+}
+
+void* gs_workspace_buffer(const gs_plan* plan, void* ws, int32_t which)
+{
+    if (!plan || !ws) return nullptr;
+    WsPtrs w = carve(plan->p, ws);
+    switch (which) {
+    case 0: return w.count;
+    case 1: return w.offset;
+    case 2: return w.keys_sorted;
+    case 3: return w.pid_sorted;
+    case 4: return w.ranges;
+    case 5: return w.nlast;
+    case 6: return w.tfinal;
+    case 7: return w.rec;
+    case 8: return w.gradrec;
+    case 9: return w.vals_sorted;
+    default: return nullptr;
+    }
+}
+
+const char* gs_status_str(gs_status s)
+{
+    switch (s) {
+    case GS_OK: return "ok";
+    case GS_ERR_INVALID_ARG: return "invalid argument";
+    case GS_ERR_CAPACITY: return "intersection capacity exceeded";
+    case GS_ERR_NONFINITE: return "non-finite parameter";
+    case GS_ERR_TIMEOUT: return "bounded wait gave up";
+    case GS_ERR_CUDA: return "CUDA launch error";
+    case GS_ERR_UNIMPLEMENTED: return "not implemented";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,349 @@
+// gs_device.cuh -- device-side descriptors and helpers shared by the step
+// kernels (sm_103a).  Nothing here is shared with the CPU oracle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gs_step.h"
+
+namespace gs {
+
+constexpr int kMaxViews = GS_MAX_VIEWS;
+constexpr int kMaxScenes = GS_MAX_SCENES;
+
+// Static shape of one view, passed by value in kernel parameters.
+struct ViewDesc {
+    int32_t W, H;          // pixels
+    int32_t TX, TY;        // tiles
+    int32_t scene;
+    int32_t shift;         // key >> shift = tile id
+    int32_t drop;          // depth code >> drop = low key bits
+    int32_t pad;
+    int64_t pair_base;     // first (view, Gaussian) pair of this view
+    int64_t tile_base;     // first global tile of this view
+    int64_t pix_base;      // first pixel of this view
+};
+
+struct Views {
+    int32_t n;
+    int32_t tw, th;        // tile size, pixels
+    int32_t pad;
+    int64_t pairs, tiles, pixels;
+    ViewDesc v[kMaxViews];
+};
+
+struct SceneDesc {
+    int64_t n;
+    int64_t base;          // first Gaussian of this scene in concatenated order
+    float4* geom;          // float4[3][n]
+    void* sh;              // float4[12][n] or uint4[6][n]
+    void* m;               // float4[15][n] or uint2[15][n]
+    void* v;
+};
+
+struct Scenes {
+    int32_t n;
+    int32_t sh_bf16, mom_bf16;
+    int32_t pad;
+    int64_t total;
+    SceneDesc s[kMaxScenes];
+};
+
+// Workspace header (device memory, first bytes of the workspace).
+struct WsHeader {
+    uint32_t status;
+    int32_t step;
+    unsigned long long k_required;
+    unsigned long long blended;
+    uint32_t k_eff;            // min(k_required, capacity)
+    uint32_t loss_counter;
+    float loss;
+    uint32_t pad;
+    uint32_t seg[kMaxViews + 1];  // sorted-segment start of each view
+};
+
+// Projected record of one (view, Gaussian) pair, read by the raster kernels.
+//   a = (mean x, mean y, conic a, conic b)
+//   b = (conic c, opacity, red, green)
+//   c = (blue, depth, unused, unused)
+struct __align__(16) ProjRec {
+    float4 a, b, c;
+};
+
+// Gradient record of one intersection, written by raster_bwd.
+//   a = dL/d(mean x, mean y, conic a, conic b); b = (conic c, opacity, r, g);
+//   c = (b, 0, 0, 0)
+struct __align__(16) GradRec {
+    float4 a, b, c;
+};
+
+__device__ __forceinline__ int view_of_pair(const Views& V, int64_t p)
+{
+    int v = 0;
+    while (v + 1 < V.n && V.v[v + 1].pair_base <= p) v++;
+    return v;
+}
+
+__device__ __forceinline__ int view_of_tile(const Views& V, int64_t t)
+{
+    int v = 0;
+    while (v + 1 < V.n && V.v[v + 1].tile_base <= t) v++;
+    return v;
+}
+
+// --------------------------------------------------------------------------
+// FP32 binning, bit-specified: every operation is one correctly rounded
+// binary32 operation in the written order (explicit _rn intrinsics, which the
+// compiler never fuses or reorders).
+// --------------------------------------------------------------------------
+
+#define FM(a, b) __fmul_rn((a), (b))
+#define FA(a, b) __fadd_rn((a), (b))
+#define FS(a, b) __fsub_rn((a), (b))
+#define FD(a, b) __fdiv_rn((a), (b))
+#define FQ(a) __fsqrt_rn(a)
+
+constexpr float kCullR2 = 9.0087890625f;  // 9 (1 + 2^-10)
+
+struct BinGeom {
+    float mx, my, a, b, c, det, tz;
+    uint32_t mant;
+    int valid;
+};
+
+__device__ __forceinline__ void bin_project(float4 mu, float4 q, float4 s, const float* cam, int W, int H,
+                                            BinGeom& o)
+{
+    o.valid = 0;
+    float n2 = FA(FA(FA(FM(q.x, q.x), FM(q.y, q.y)), FM(q.z, q.z)), FM(q.w, q.w));
+    if (!(n2 > 0.0f)) return;
+    float r = FQ(n2);
+    float w = FD(q.x, r), x = FD(q.y, r), y = FD(q.z, r), z = FD(q.w, r);
+    float xx = FM(x, x), yy = FM(y, y), zz = FM(z, z);
+    float xy = FM(x, y), xz = FM(x, z), yz = FM(y, z);
+    float wx = FM(w, x), wy = FM(w, y), wz = FM(w, z);
+    float R[9];
+    R[0] = FS(1.0f, FM(2.0f, FA(yy, zz)));
+    R[1] = FM(2.0f, FS(xy, wz));
+    R[2] = FM(2.0f, FA(xz, wy));
+    R[3] = FM(2.0f, FA(xy, wz));
+    R[4] = FS(1.0f, FM(2.0f, FA(xx, zz)));
+    R[5] = FM(2.0f, FS(yz, wx));
+    R[6] = FM(2.0f, FS(xz, wy));
+    R[7] = FM(2.0f, FA(yz, wx));
+    R[8] = FS(1.0f, FM(2.0f, FA(xx, yy)));
+    const float sv[3] = {s.x, s.y, s.z};
+    float M[9];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) M[3 * i + j] = FM(R[3 * i + j], sv[j]);
+    float S[9];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = i; j < 3; j++) {
+            float v = FA(FA(FM(M[3 * i], M[3 * j]), FM(M[3 * i + 1], M[3 * j + 1])), FM(M[3 * i + 2], M[3 * j + 2]));
+            S[3 * i + j] = v;
+            S[3 * j + i] = v;
+        }
+    const float* C = cam;          // R row-major
+    const float mv[3] = {mu.x, mu.y, mu.z};
+    float t[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+        t[i] = FA(FA(FA(FM(C[3 * i], mv[0]), FM(C[3 * i + 1], mv[1])), FM(C[3 * i + 2], mv[2])), cam[9 + i]);
+    if (!(t[2] >= 0.01f)) return;
+    const float fx = cam[12], fy = cam[13], cx = cam[14], cy = cam[15];
+    float limx = FM(1.3f, FD(FM(0.5f, (float)W), fx));
+    float limy = FM(1.3f, FD(FM(0.5f, (float)H), fy));
+    float ux = fminf(fmaxf(FD(t[0], t[2]), -limx), limx);
+    float uy = fminf(fmaxf(FD(t[1], t[2]), -limy), limy);
+    float j00 = FD(fx, t[2]), j11 = FD(fy, t[2]);
+    float j02 = -FD(FM(fx, ux), t[2]);
+    float j12 = -FD(FM(fy, uy), t[2]);
+    float T[6];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        T[k] = FA(FM(j00, C[k]), FM(j02, C[6 + k]));
+        T[3 + k] = FA(FM(j11, C[3 + k]), FM(j12, C[6 + k]));
+    }
+    float U[6];
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+            U[3 * i + k] = FA(FA(FM(T[3 * i], S[k]), FM(T[3 * i + 1], S[3 + k])), FM(T[3 * i + 2], S[6 + k]));
+    float a = FA(FA(FA(FM(U[0], T[0]), FM(U[1], T[1])), FM(U[2], T[2])), 0.3f);
+    float b = FA(FA(FM(U[0], T[3]), FM(U[1], T[4])), FM(U[2], T[5]));
+    float c = FA(FA(FA(FM(U[3], T[3]), FM(U[4], T[4])), FM(U[5], T[5])), 0.3f);
+    float det = FS(FM(a, c), FM(b, b));
+    if (!(det > 0.0f)) return;
+    float mx = FA(FD(FM(fx, t[0]), t[2]), cx);
+    float my = FA(FD(FM(fy, t[1]), t[2]), cy);
+    if (!(fabsf(mx) < 1e30f) || !(fabsf(my) < 1e30f) || !(a < 1e30f) || !(c < 1e30f) || !(det < 1e30f)) return;
+    float qd = FD(FA(FM(2.0f, t[2]), 1.0f), FA(t[2], 1.0f));
+    uint32_t mant = __float_as_uint(qd) & 0x7FFFFFu;
+    if (qd >= 2.0f) mant = 0x7FFFFFu;
+    o.valid = 1;
+    o.mx = mx; o.my = my; o.a = a; o.b = b; o.c = c; o.det = det; o.tz = t[2]; o.mant = mant;
+}
+
+__device__ __forceinline__ int tile_lo(float v, int T, int n)
+{
+    float f = ceilf(FD(FS(FA(v, 0.5f), (float)T), (float)T));
+    f = fminf(fmaxf(f, -1.0f), (float)n);
+    int i = (int)f;
+    return i < 0 ? 0 : i;
+}
+
+__device__ __forceinline__ int tile_hi(float v, int T, int n)
+{
+    float f = floorf(FD(FS(v, 0.5f), (float)T));
+    f = fminf(fmaxf(f, -1.0f), (float)n);
+    int i = (int)f;
+    return i > n - 1 ? n - 1 : i;
+}
+
+// Scan-line traversal (Sec. 4.1): calls emit(tile_id) for every tile whose
+// pixel-centre rectangle meets the ellipse d^2 <= kCullR2, band by band along
+// the shorter dimension of the tile bounding box.  Returns the count.
+template <typename Emit>
+__device__ __forceinline__ uint32_t scanline_tiles(const BinGeom& g, int tw, int th, int TX, int TY, Emit emit)
+{
+    float ex = FQ(FM(kCullR2, g.a));
+    float ey = FQ(FM(kCullR2, g.c));
+    int txl = tile_lo(FS(g.mx, ex), tw, TX), txh = tile_hi(FA(g.mx, ex), tw, TX);
+    int tyl = tile_lo(FS(g.my, ey), th, TY), tyh = tile_hi(FA(g.my, ey), th, TY);
+    if (txl > txh || tyl > tyh) return 0;
+    uint32_t count = 0;
+    if (tyh - tyl <= txh - txl) {
+        float ystar = FM(g.b, FQ(FD(kCullR2, g.a)));
+        float r2c = FM(kCullR2, g.c);
+        for (int ty = tyl; ty <= tyh; ty++) {
+            float y0 = FS(FA((float)(ty * th), 0.5f), g.my);
+            float y1 = FS(FS((float)((ty + 1) * th), 0.5f), g.my);
+            float dlo = fmaxf(y0, -ey), dhi = fminf(y1, ey);
+            if (!(dlo <= dhi)) continue;
+            float dR = fminf(fmaxf(ystar, dlo), dhi);
+            float dL = fminf(fmaxf(-ystar, dlo), dhi);
+            float hR = FQ(fmaxf(0.0f, FM(g.det, FS(r2c, FM(dR, dR)))));
+            float hL = FQ(fmaxf(0.0f, FM(g.det, FS(r2c, FM(dL, dL)))));
+            float xR = FA(g.mx, FD(FA(FM(g.b, dR), hR), g.c));
+            float xL = FA(g.mx, FD(FS(FM(g.b, dL), hL), g.c));
+            int lo = tile_lo(xL, tw, TX), hi = tile_hi(xR, tw, TX);
+            for (int tx = lo; tx <= hi; tx++) {
+                emit(count, (uint32_t)(ty * TX + tx));
+                count++;
+            }
+        }
+    } else {
+        float xstar = FM(g.b, FQ(FD(kCullR2, g.c)));
+        float r2a = FM(kCullR2, g.a);
+        for (int tx = txl; tx <= txh; tx++) {
+            float x0 = FS(FA((float)(tx * tw), 0.5f), g.mx);
+            float x1 = FS(FS((float)((tx + 1) * tw), 0.5f), g.mx);
+            float dlo = fmaxf(x0, -ex), dhi = fminf(x1, ex);
+            if (!(dlo <= dhi)) continue;
+            float dT = fminf(fmaxf(xstar, dlo), dhi);
+            float dB = fminf(fmaxf(-xstar, dlo), dhi);
+            float hT = FQ(fmaxf(0.0f, FM(g.det, FS(r2a, FM(dT, dT)))));
+            float hB = FQ(fmaxf(0.0f, FM(g.det, FS(r2a, FM(dB, dB)))));
+            float yT = FA(g.my, FD(FA(FM(g.b, dT), hT), g.a));
+            float yB = FA(g.my, FD(FS(FM(g.b, dB), hB), g.a));
+            int lo = tile_lo(yB, th, TY), hi = tile_hi(yT, th, TY);
+            for (int ty = lo; ty <= hi; ty++) {
+                emit(count, (uint32_t)(ty * TX + tx));
+                count++;
+            }
+        }
+    }
+    return count;
+}
+
+// --------------------------------------------------------------------------
+// Pair evaluation shared by raster forward and backward: identical
+// instruction sequence in both kernels, so both take the same decisions.
+// --------------------------------------------------------------------------
+
+// power = -0.5 (ca dx^2 + cc dy^2) - cb dx dy, with dx = px - mx.
+__device__ __forceinline__ float pair_power(float dx, float dy, float ca, float cb, float cc)
+{
+    float q = __fmaf_rn(ca, __fmul_rn(dx, dx), __fmul_rn(cc, __fmul_rn(dy, dy)));
+    return __fmaf_rn(-0.5f, q, -__fmul_rn(cb, __fmul_rn(dx, dy)));
+}
+
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kAlphaMax = 0.99f;
+constexpr float kTMin = 1e-4f;
+
+// --------------------------------------------------------------------------
+// Real SH basis up to degree 3 (3DGS sign convention).
+// --------------------------------------------------------------------------
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float* Y)
+{
+    const float c0 = 0.28209479177387814f, c1 = 0.4886025119029199f;
+    const float c20 = 1.0925484305920792f, c22 = 0.31539156525252005f, c24 = 0.5462742152960396f;
+    const float c30 = 0.5900435899266435f, c31 = 2.890611442640554f, c32 = 0.4570457994644658f;
+    const float c33 = 0.3731763325901154f, c35 = 1.445305721320277f;
+    float xx = x * x, yy = y * y, zz = z * z;
+    Y[0] = c0;
+    Y[1] = -c1 * y;
+    Y[2] = c1 * z;
+    Y[3] = -c1 * x;
+    Y[4] = c20 * x * y;
+    Y[5] = -c20 * y * z;
+    Y[6] = c22 * (2.0f * zz - xx - yy);
+    Y[7] = -c20 * x * z;
+    Y[8] = c24 * (xx - yy);
+    Y[9] = -c30 * y * (3.0f * xx - yy);
+    Y[10] = c31 * x * y * z;
+    Y[11] = -c32 * y * (4.0f * zz - xx - yy);
+    Y[12] = c33 * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+    Y[13] = -c32 * x * (4.0f * zz - xx - yy);
+    Y[14] = c35 * z * (xx - yy);
+    Y[15] = -c30 * x * (xx - 3.0f * yy);
+}
+
+// d/d(x, y, z) of sum_k w[k] Y_k, with the direction treated as a free vector.
+__device__ __forceinline__ void sh_basis_vjp(float x, float y, float z, const float* w, float& gx, float& gy,
+                                             float& gz)
+{
+    const float c1 = 0.4886025119029199f;
+    const float c20 = 1.0925484305920792f, c22 = 0.31539156525252005f, c24 = 0.5462742152960396f;
+    const float c30 = 0.5900435899266435f, c31 = 2.890611442640554f, c32 = 0.4570457994644658f;
+    const float c33 = 0.3731763325901154f, c35 = 1.445305721320277f;
+    float xx = x * x, yy = y * y, zz = z * z;
+    gx = 0.f; gy = 0.f; gz = 0.f;
+    gy += -c1 * w[1];
+    gz += c1 * w[2];
+    gx += -c1 * w[3];
+    gx += c20 * y * w[4];           gy += c20 * x * w[4];
+    gy += -c20 * z * w[5];          gz += -c20 * y * w[5];
+    gx += -2.f * c22 * x * w[6];    gy += -2.f * c22 * y * w[6];   gz += 4.f * c22 * z * w[6];
+    gx += -c20 * z * w[7];          gz += -c20 * x * w[7];
+    gx += 2.f * c24 * x * w[8];     gy += -2.f * c24 * y * w[8];
+    gx += -c30 * 6.f * x * y * w[9];
+    gy += -c30 * (3.f * xx - 3.f * yy) * w[9];
+    gx += c31 * y * z * w[10];      gy += c31 * x * z * w[10];     gz += c31 * x * y * w[10];
+    gx += -c32 * (-2.f * x * y) * w[11];
+    gy += -c32 * (4.f * zz - xx - 3.f * yy) * w[11];
+    gz += -c32 * (8.f * y * z) * w[11];
+    gx += c33 * (-6.f * x * z) * w[12];
+    gy += c33 * (-6.f * y * z) * w[12];
+    gz += c33 * (6.f * zz - 3.f * xx - 3.f * yy) * w[12];
+    gx += -c32 * (4.f * zz - 3.f * xx - yy) * w[13];
+    gy += -c32 * (-2.f * x * y) * w[13];
+    gz += -c32 * (8.f * x * z) * w[13];
+    gx += c35 * 2.f * x * z * w[14];
+    gy += -c35 * 2.f * y * z * w[14];
+    gz += c35 * (xx - yy) * w[14];
+    gx += -c30 * (3.f * xx - 3.f * yy) * w[15];
+    gy += -c30 * (-6.f * x * y) * w[15];
+}
+
+__device__ __forceinline__ float bf16_lo(uint32_t u) { return __uint_as_float(u << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t u) { return __uint_as_float(u & 0xFFFF0000u); }
+
+}  // namespace gs

@@ -1,0 +1,106 @@
+// gs_internal.cuh -- host plan, workspace carving and kernel launchers.
+#pragma once
+
+#include <algorithm>
+#include <cstring>
+
+#include "gs_device.cuh"
+
+namespace gs {
+
+// Radix sort geometry: 256 threads x 8 keys per block, 8-bit digits.
+constexpr int kRadixThreads = 256;
+constexpr int kRadixItems = 8;
+constexpr int kRadixBlock = kRadixThreads * kRadixItems;
+constexpr int kRadixDigits = 256;
+
+// Exclusive scan geometry: 512 threads x 8 values per block.
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 8;
+constexpr int kScanBlock = kScanThreads * kScanItems;
+
+// Raster backward block: 4 warps.
+constexpr int kBwdThreads = 128;
+
+struct Plan {
+    Views views;
+    int32_t n_scenes;
+    int64_t scene_n[kMaxScenes];
+    int64_t scene_base[kMaxScenes + 1];
+    int64_t cap;                 // intersection capacity
+    gs_tuning tuning;
+    int32_t sh_bf16, mom_bf16;
+    int32_t key_passes;          // 8-bit LSD passes over the key
+    int32_t view_pass;           // one more pass ordering the views
+    int64_t radix_blocks;        // ceil(cap / kRadixBlock)
+    int64_t count_scan_parts;    // ceil((pairs + 1) / kScanBlock)
+    int64_t hist_scan_parts;     // ceil(256 * radix_blocks / kScanBlock)
+    int64_t raster_blocks;       // total tiles
+    // workspace byte offsets
+    size_t off_hdr, off_count, off_offset, off_rec, off_binrec;
+    size_t off_keysA, off_valsA, off_keysB, off_valsB, off_pid, off_pid_sorted;
+    size_t off_ranges, off_nlast, off_tfinal, off_gradrec, off_scan_part, off_hist, off_loss_part;
+    size_t ws_bytes;
+};
+
+struct WsPtrs {
+    WsHeader* hdr;
+    uint32_t* count;
+    uint32_t* offset;
+    ProjRec* rec;
+    float4* binrec;
+    uint32_t *keysA, *valsA, *keysB, *valsB;
+    uint32_t* pid;
+    uint32_t* pid_sorted;
+    uint2* ranges;
+    uint32_t* nlast;
+    float* tfinal;
+    GradRec* gradrec;
+    uint32_t* scan_part;
+    uint32_t* hist;
+    float* loss_part;
+    // where the sort leaves its result
+    uint32_t* keys_sorted;
+    uint32_t* vals_sorted;
+};
+
+WsPtrs carve(const Plan& P, void* ws);
+
+// Degree-3 SH of Gaussian g (48 floats, flat index 3*k + channel).
+__device__ __forceinline__ void load_sh(const SceneDesc& sc, int bf16, int64_t g, float* shv)
+{
+    if (!bf16) {
+        const float4* s4 = reinterpret_cast<const float4*>(sc.sh);
+#pragma unroll
+        for (int j = 0; j < 12; j++) {
+            float4 c = s4[j * sc.n + g];
+            shv[4 * j] = c.x; shv[4 * j + 1] = c.y; shv[4 * j + 2] = c.z; shv[4 * j + 3] = c.w;
+        }
+    } else {
+        const uint4* s8 = reinterpret_cast<const uint4*>(sc.sh);
+#pragma unroll
+        for (int j = 0; j < 6; j++) {
+            uint4 c = s8[j * sc.n + g];
+            shv[8 * j + 0] = bf16_lo(c.x); shv[8 * j + 1] = bf16_hi(c.x);
+            shv[8 * j + 2] = bf16_lo(c.y); shv[8 * j + 3] = bf16_hi(c.y);
+            shv[8 * j + 4] = bf16_lo(c.z); shv[8 * j + 5] = bf16_hi(c.z);
+            shv[8 * j + 6] = bf16_lo(c.w); shv[8 * j + 7] = bf16_hi(c.w);
+        }
+    }
+}
+
+Scenes make_scenes(const Plan& P, const gs_scene_buf* scenes);
+
+void launch_project_fwd(const Plan& P, const Scenes& S, const float* cams, const WsPtrs& w, cudaStream_t st);
+void launch_bin_sort(const Plan& P, const WsPtrs& w, cudaStream_t st);
+void launch_raster_fwd(const Plan& P, const WsPtrs& w, const float* bg, float* image, cudaStream_t st);
+void launch_loss_l1(const Plan& P, const WsPtrs& w, const float* image, const float* target, float* dl,
+                    cudaStream_t st);
+void launch_raster_bwd(const Plan& P, const WsPtrs& w, const float* image, const float* dl, cudaStream_t st);
+void launch_project_bwd_adam(const Plan& P, const Scenes& S, const float* cams, const WsPtrs& w,
+                             const gs_adam* adam, float* grads_out, cudaStream_t st);
+void launch_fill_u32(uint32_t* p, int64_t n, uint32_t value, cudaStream_t st);
+void launch_ws_init(const Plan& P, const WsPtrs& w, cudaStream_t st);
+void launch_adam_advance(const WsPtrs& w, cudaStream_t st);
+
+}  // namespace gs

@@ -1,0 +1,78 @@
+// project_fwd.cu -- projection forward fused with the exact tile count
+// (VkSplat Sec. 4.1: the number of intersected tiles is computed in the
+// projection-forward pass).  One thread per (view, Gaussian) pair; SoA float4
+// parameter loads, SH read only for Gaussians that survive culling.
+#include "gs_internal.cuh"
+
+namespace gs {
+
+__global__ void __launch_bounds__(256) k_project_fwd(Views V, Scenes S, const float* __restrict__ cams,
+                                                     uint32_t* __restrict__ count, ProjRec* __restrict__ rec,
+                                                     float4* __restrict__ binrec, WsHeader* __restrict__ hdr)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= V.pairs) return;
+    const int v = view_of_pair(V, p);
+    const ViewDesc& vd = V.v[v];
+    const int64_t g = p - vd.pair_base;
+    const SceneDesc& sc = S.s[vd.scene];
+    const int64_t n = sc.n;
+    float cam[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) cam[i] = __ldg(cams + 16 * v + i);
+    const float4 mu = sc.geom[g];
+    const float4 q = sc.geom[n + g];
+    const float4 so = sc.geom[2 * n + g];
+    const bool finite = isfinite(mu.x) && isfinite(mu.y) && isfinite(mu.z) && isfinite(q.x) && isfinite(q.y) &&
+                        isfinite(q.z) && isfinite(q.w) && isfinite(so.x) && isfinite(so.y) && isfinite(so.z) &&
+                        isfinite(so.w);
+    if (!finite) {
+        atomicOr(&hdr->status, GS_STATUS_NONFINITE);
+        count[p] = 0;
+        return;
+    }
+    BinGeom bg;
+    bin_project(mu, q, so, cam, vd.W, vd.H, bg);
+    uint32_t cnt = 0;
+    if (bg.valid) cnt = scanline_tiles(bg, V.tw, V.th, vd.TX, vd.TY, [](uint32_t, uint32_t) {});
+    count[p] = cnt;
+    if (cnt == 0) return;
+
+    // conic = inverse of the 2D covariance
+    const float ca = bg.c / bg.det, cb = -bg.b / bg.det, cc = bg.a / bg.det;
+
+    // colour from degree-3 SH at the view direction (mu - camera centre)
+    const float cpx = -(cam[0] * cam[9] + cam[3] * cam[10] + cam[6] * cam[11]);
+    const float cpy = -(cam[1] * cam[9] + cam[4] * cam[10] + cam[7] * cam[11]);
+    const float cpz = -(cam[2] * cam[9] + cam[5] * cam[10] + cam[8] * cam[11]);
+    float dx = mu.x - cpx, dy = mu.y - cpy, dz = mu.z - cpz;
+    const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+    dx *= inv; dy *= inv; dz *= inv;
+    float Y[16];
+    sh_basis(dx, dy, dz, Y);
+    float shv[48];
+    load_sh(sc, S.sh_bf16, g, shv);
+    float col[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        float acc = 0.5f;
+#pragma unroll
+        for (int k = 0; k < 16; k++) acc = fmaf(shv[3 * k + c], Y[k], acc);
+        col[c] = fmaxf(acc, 0.0f);
+    }
+    ProjRec r;
+    r.a = make_float4(bg.mx, bg.my, ca, cb);
+    r.b = make_float4(cc, so.w, col[0], col[1]);
+    r.c = make_float4(col[2], bg.tz, 0.f, 0.f);
+    rec[p] = r;
+    binrec[p] = make_float4(bg.a, bg.b, bg.c, __uint_as_float(bg.mant));
+}
+
+void launch_project_fwd(const Plan& P, const Scenes& S, const float* cams, const WsPtrs& w, cudaStream_t st)
+{
+    const int T = 256;
+    const int64_t blocks = (P.views.pairs + T - 1) / T;
+    k_project_fwd<<<(unsigned)blocks, T, 0, st>>>(P.views, S, cams, w.count, w.rec, w.binrec, w.hdr);
+}
+
+}  // namespace gs

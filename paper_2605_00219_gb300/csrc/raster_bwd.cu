@@ -1,0 +1,313 @@
+// raster_bwd.cu -- rasterization backward parallel over Gaussians (VkSplat
+// Sec. 4.2, first implementation; Fig. 2), with no pixel-level atomics.
+//
+// One CTA (4 warps) per tile.  The tile's list (up to the largest n_last of
+// its pixels) is processed in batches of S Gaussians, S chosen per tile by
+// the paper's rule S = roundup32(sqrt(N P)) capped at 128 (N = list length,
+// P = pixels), or fixed by the tuning.  For each batch:
+//
+//  Phase A (pixels across threads): transmittance is recomputed front to
+//    back from the running per-pixel state -- T as a compensated FP32 pair,
+//    the blended colour prefix with Neumaier compensation -- and the state
+//    (T, S) at the end of every 32-Gaussian sub-batch is kept in shared
+//    memory, where S = C_image - prefix is the colour still to come.
+//  Phase B (Gaussians across threads): warp k takes sub-batch k, lane l its
+//    l-th Gaussian.  The lanes form a wavefront over the pixels: at step s
+//    lane l handles pixel s - (31 - l), receives (T, S) from lane l + 1 by
+//    warp shuffle, walks back over its own Gaussian (T_before = T / (1 - a),
+//    S += c a T_before) and hands the state on.  Each lane accumulates its
+//    Gaussian's nine gradients in registers; when S < 128 the warps split the
+//    pixels instead and the partial sums are added in a fixed order.
+//
+// Output: one gradient record per intersection, at its emission slot, so
+// the projection backward reads each Gaussian's records contiguously.  The
+// result is deterministic (no atomics, fixed summation order).
+#include "gs_internal.cuh"
+
+namespace gs {
+
+struct BwdSmem {
+    float4* runA;   // [P] (T hi, T lo, prefix r, prefix g)
+    float4* runB;   // [P] (prefix b, comp r, comp g, comp b)
+    float4* pimg;   // [P] (C r, g, b, -)
+    float4* pdl;    // [P] (dL/dC r, g, b, n_last bits)
+    float4* st;     // [4][P] state (T, S r, S g, S b) after each sub-batch
+    float4* gA;     // [128] (mx, my, ca, cb)
+    float4* gB;     // [128] (cc, o, r, g)
+    float* gC;      // [128] blue
+    uint32_t* ge;   // [128] emission slot
+    float* red;     // [128][9] partial gradients
+    int* misc;
+};
+
+__host__ __device__ constexpr size_t bwd_smem_bytes(int P)
+{
+    return (size_t)16 * P * 4 + (size_t)16 * 4 * P + 128 * (16 + 16 + 4 + 4) + 128 * 9 * 4 + 16;
+}
+
+__device__ __forceinline__ void neumaier_add(float& s, float& c, float x)
+{
+    const float t = s + x;
+    c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+    s = t;
+}
+
+template <int P>
+__global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(Views V, const uint2* __restrict__ ranges,
+                                                            const uint32_t* __restrict__ vals_sorted,
+                                                            const uint32_t* __restrict__ pid_sorted,
+                                                            const ProjRec* __restrict__ rec,
+                                                            const float* __restrict__ image,
+                                                            const float* __restrict__ dl,
+                                                            const uint32_t* __restrict__ nlast,
+                                                            GradRec* __restrict__ gradrec, int fixed_S)
+{
+    extern __shared__ float4 smem4[];
+    BwdSmem sm;
+    sm.runA = smem4;
+    sm.runB = sm.runA + P;
+    sm.pimg = sm.runB + P;
+    sm.pdl = sm.pimg + P;
+    sm.st = sm.pdl + P;
+    sm.gA = sm.st + 4 * P;
+    sm.gB = sm.gA + 128;
+    sm.gC = reinterpret_cast<float*>(sm.gB + 128);
+    sm.ge = reinterpret_cast<uint32_t*>(sm.gC + 128);
+    sm.red = reinterpret_cast<float*>(sm.ge + 128);
+    sm.misc = reinterpret_cast<int*>(sm.red + 128 * 9);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t gt = blockIdx.x;
+    const int v = view_of_tile(V, gt);
+    const ViewDesc& vd = V.v[v];
+    const int lt = (int)(gt - vd.tile_base);
+    const int tw = V.tw;
+    const int ox = (lt % vd.TX) * tw, oy = (lt / vd.TX) * V.th;
+    const uint2 r = ranges[gt];
+    const uint32_t start = r.x, ntile = r.y - r.x;
+
+    if (tid == 0) sm.misc[0] = 0;
+    __syncthreads();
+    // per-pixel inputs
+    int my_max = 0;
+    for (int pi = tid; pi < P; pi += kBwdThreads) {
+        const int px = ox + pi % tw, py = oy + pi / tw;
+        float4 im = make_float4(0.f, 0.f, 0.f, 0.f), d = make_float4(0.f, 0.f, 0.f, 0.f);
+        uint32_t nl = 0;
+        if (px < vd.W && py < vd.H) {
+            const int64_t pix = vd.pix_base + (int64_t)py * vd.W + px;
+            im = make_float4(image[3 * pix], image[3 * pix + 1], image[3 * pix + 2], 0.f);
+            d = make_float4(dl[3 * pix], dl[3 * pix + 1], dl[3 * pix + 2], 0.f);
+            nl = nlast[pix];
+        }
+        d.w = __uint_as_float(nl);
+        sm.pimg[pi] = im;
+        sm.pdl[pi] = d;
+        sm.runA[pi] = make_float4(1.f, 0.f, 0.f, 0.f);
+        sm.runB[pi] = make_float4(0.f, 0.f, 0.f, 0.f);
+        my_max = max(my_max, (int)nl);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) my_max = max(my_max, __shfl_xor_sync(0xffffffffu, my_max, o));
+    if (lane == 0) atomicMax(&sm.misc[0], my_max);
+    __syncthreads();
+    const uint32_t L = min(ntile, (uint32_t)sm.misc[0]);
+
+    int S = fixed_S;
+    if (S <= 0) {
+        const float x = sqrtf((float)L * (float)P);
+        S = ((int)ceilf(x) + 31) & ~31;
+    }
+    S = min(max(S, 32), 128);
+    const int nsub = S / 32;
+    const int ngroups = (nsub == 3) ? 1 : 4 / nsub;
+    const int glen = P / ngroups;
+
+    for (uint32_t bb = 0; bb < L; bb += S) {
+        const int cnt = (int)min((uint32_t)S, L - bb);
+        if (tid < cnt) {
+            const uint32_t k = start + bb + tid;
+            const ProjRec q = rec[pid_sorted[k]];
+            sm.gA[tid] = q.a;
+            sm.gB[tid] = q.b;
+            sm.gC[tid] = q.c.x;
+            sm.ge[tid] = vals_sorted[k];
+        }
+        __syncthreads();
+
+        // ---------------- Phase A: pixel-parallel forward recompute ----------------
+        const int nsub_used = (cnt + 31) >> 5;
+        for (int pi = tid; pi < P; pi += kBwdThreads) {
+            float4 ra = sm.runA[pi], rb = sm.runB[pi];
+            float Th = ra.x, Tl = ra.y;
+            float ps0 = ra.z, ps1 = ra.w, ps2 = rb.x, pc0 = rb.y, pc1 = rb.z, pc2 = rb.w;
+            const float4 d = sm.pdl[pi];
+            const float4 im = sm.pimg[pi];
+            const uint32_t nl = __float_as_uint(d.w);
+            const float fx = (float)(ox + pi % tw) + 0.5f, fy = (float)(oy + pi / tw) + 0.5f;
+            for (int k = 0; k < nsub_used; k++) {
+                const int j1 = min(cnt, 32 * k + 32);
+                for (int j = 32 * k; j < j1; j++) {
+                    if (bb + j >= nl) break;
+                    const float4 a = sm.gA[j];
+                    const float4 b = sm.gB[j];
+                    const float dx = fx - a.x, dy = fy - a.y;
+                    const float power = pair_power(dx, dy, a.z, a.w, b.x);
+                    if (power < -4.5f) continue;
+                    const float G = __expf(power);
+                    const float alpha = fminf(kAlphaMax, __fmul_rn(b.y, G));
+                    if (alpha < kAlphaMin) continue;
+                    const float wgt = alpha * Th;
+                    neumaier_add(ps0, pc0, b.z * wgt);
+                    neumaier_add(ps1, pc1, b.w * wgt);
+                    neumaier_add(ps2, pc2, sm.gC[j] * wgt);
+                    const float om = __fsub_rn(1.0f, alpha);
+                    const float om_err = __fsub_rn(-alpha, __fsub_rn(om, 1.0f));
+                    const float pr = __fmul_rn(Th, om);
+                    const float pe = __fmaf_rn(Th, om, -pr);
+                    const float lo = __fmaf_rn(Th, om_err, __fmaf_rn(Tl, om, pe));
+                    const float hi = __fadd_rn(pr, lo);
+                    Tl = __fsub_rn(lo, __fsub_rn(hi, pr));
+                    Th = hi;
+                }
+                sm.st[k * P + pi] =
+                    make_float4(Th + Tl, (im.x - ps0) - pc0, (im.y - ps1) - pc1, (im.z - ps2) - pc2);
+            }
+            sm.runA[pi] = make_float4(Th, Tl, ps0, ps1);
+            sm.runB[pi] = make_float4(ps2, pc0, pc1, pc2);
+        }
+        __syncthreads();
+
+        // ---------------- Phase B: Gaussian-parallel wavefront ----------------
+        const int sub = warp % nsub;
+        const int pg = warp / nsub;
+        const bool warp_on = (nsub != 3 || warp < 3) && sub < nsub_used;
+        const int j = sub * 32 + lane;
+        const bool act = warp_on && j < cnt;
+        float g_mx = 0.f, g_my = 0.f, g_ca = 0.f, g_cb = 0.f, g_cc = 0.f, g_o = 0.f, g_r = 0.f, g_g = 0.f,
+              g_b = 0.f;
+        if (warp_on) {
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+            float cbl = 0.f;
+            if (act) { a = sm.gA[j]; b = sm.gB[j]; cbl = sm.gC[j]; }
+            const uint32_t myidx = bb + j;
+            const int p0 = pg * glen;
+            float T = 1.f, S0 = 0.f, S1 = 0.f, S2 = 0.f;
+            const int nsteps = glen + 31;
+            for (int s = 0; s < nsteps; s++) {
+                float Ti = __shfl_down_sync(0xffffffffu, T, 1);
+                float Si0 = __shfl_down_sync(0xffffffffu, S0, 1);
+                float Si1 = __shfl_down_sync(0xffffffffu, S1, 1);
+                float Si2 = __shfl_down_sync(0xffffffffu, S2, 1);
+                if (lane == 31 && s < glen) {
+                    const float4 q = sm.st[sub * P + p0 + s];
+                    Ti = q.x; Si0 = q.y; Si1 = q.z; Si2 = q.w;
+                }
+                const int pl = s - (31 - lane);
+                if (act && pl >= 0 && pl < glen) {
+                    const int pi = p0 + pl;
+                    const float4 d = sm.pdl[pi];
+                    if (myidx < __float_as_uint(d.w)) {
+                        const float dx = (float)(ox + pi % tw) + 0.5f - a.x;
+                        const float dy = (float)(oy + pi / tw) + 0.5f - a.y;
+                        const float power = pair_power(dx, dy, a.z, a.w, b.x);
+                        if (power >= -4.5f) {
+                            const float G = __expf(power);
+                            const float araw = __fmul_rn(b.y, G);
+                            const float alpha = fminf(kAlphaMax, araw);
+                            if (alpha >= kAlphaMin) {
+                                const float om = 1.0f - alpha;
+                                const float rom = 1.0f / om;
+                                const float Tb = Ti * rom;
+                                const float wgt = alpha * Tb;
+                                g_r = fmaf(wgt, d.x, g_r);
+                                g_g = fmaf(wgt, d.y, g_g);
+                                g_b = fmaf(wgt, d.z, g_b);
+                                float da = d.x * (b.z * Tb - Si0 * rom);
+                                da = fmaf(d.y, b.w * Tb - Si1 * rom, da);
+                                da = fmaf(d.z, cbl * Tb - Si2 * rom, da);
+                                Si0 = fmaf(b.z, wgt, Si0);
+                                Si1 = fmaf(b.w, wgt, Si1);
+                                Si2 = fmaf(cbl, wgt, Si2);
+                                Ti = Tb;
+                                if (araw <= kAlphaMax) {
+                                    g_o = fmaf(da, G, g_o);
+                                    const float dp = da * araw;
+                                    g_ca = fmaf(-0.5f * dx * dx, dp, g_ca);
+                                    g_cb = fmaf(-dx * dy, dp, g_cb);
+                                    g_cc = fmaf(-0.5f * dy * dy, dp, g_cc);
+                                    g_mx = fmaf(fmaf(a.z, dx, a.w * dy), dp, g_mx);
+                                    g_my = fmaf(fmaf(a.w, dx, b.x * dy), dp, g_my);
+                                }
+                            }
+                        }
+                    }
+                }
+                T = Ti; S0 = Si0; S1 = Si1; S2 = Si2;
+            }
+        }
+        if (ngroups == 1) {
+            if (act) {
+                GradRec o;
+                o.a = make_float4(g_mx, g_my, g_ca, g_cb);
+                o.b = make_float4(g_cc, g_o, g_r, g_g);
+                o.c = make_float4(g_b, 0.f, 0.f, 0.f);
+                gradrec[sm.ge[j]] = o;
+            }
+        } else {
+            if (act) {
+                float* rr = sm.red + (pg * S + j) * 9;
+                rr[0] = g_mx; rr[1] = g_my; rr[2] = g_ca; rr[3] = g_cb; rr[4] = g_cc;
+                rr[5] = g_o; rr[6] = g_r; rr[7] = g_g; rr[8] = g_b;
+            }
+            __syncthreads();
+            if (tid < cnt) {
+                float acc[9];
+#pragma unroll
+                for (int i = 0; i < 9; i++) acc[i] = 0.f;
+                for (int q = 0; q < ngroups; q++) {
+                    const float* rr = sm.red + (q * S + tid) * 9;
+#pragma unroll
+                    for (int i = 0; i < 9; i++) acc[i] += rr[i];
+                }
+                GradRec o;
+                o.a = make_float4(acc[0], acc[1], acc[2], acc[3]);
+                o.b = make_float4(acc[4], acc[5], acc[6], acc[7]);
+                o.c = make_float4(acc[8], 0.f, 0.f, 0.f);
+                gradrec[sm.ge[tid]] = o;
+            }
+        }
+        __syncthreads();
+    }
+    // entries past every pixel's last blended pair receive zero gradients
+    for (uint32_t k = start + L + tid; k < r.y; k += kBwdThreads) {
+        GradRec o;
+        o.a = o.b = o.c = make_float4(0.f, 0.f, 0.f, 0.f);
+        gradrec[vals_sorted[k]] = o;
+    }
+}
+
+void launch_raster_bwd(const Plan& P, const WsPtrs& w, const float* image, const float* dl, cudaStream_t st)
+{
+    const Views& V = P.views;
+    const int np = V.tw * V.th;
+    const unsigned grid = (unsigned)V.tiles;
+    const int fixed = P.tuning.bwd_batch;
+#define GS_RB(NP)                                                                                           \
+    do {                                                                                                    \
+        const size_t sb = bwd_smem_bytes(NP);                                                               \
+        static bool attr_set = false;                                                                       \
+        if (!attr_set) {                                                                                    \
+            cudaFuncSetAttribute(k_raster_bwd<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);   \
+            attr_set = true;                                                                                \
+        }                                                                                                   \
+        k_raster_bwd<NP><<<grid, kBwdThreads, sb, st>>>(V, w.ranges, w.vals_sorted, w.pid_sorted, w.rec, image, \
+                                                        dl, w.nlast, w.gradrec, fixed);                     \
+    } while (0)
+    if (np == 64) GS_RB(64);
+    else if (np == 256) GS_RB(256);
+    else GS_RB(512);
+#undef GS_RB
+}
+
+}  // namespace gs

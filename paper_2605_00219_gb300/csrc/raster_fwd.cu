@@ -1,0 +1,183 @@
+// raster_fwd.cu -- front-to-back alpha compositing per tile (VkSplat Sec. 2
+// pipeline, Table 2 "Rasterization Fwd"), and the L1 loss gradient
+// (Sec. 4.5, L1 term).
+//
+// One CTA per tile, one thread per pixel.  The tile's sorted list is staged
+// through shared memory one CTA-width chunk at a time (coalesced reads of the
+// sorted pair indices, then 48-byte record gathers); every pixel walks the
+// chunk from shared memory.  Transmittance is a compensated FP32 pair
+// (TwoProduct with fmaf, Fast2Sum renormalisation), so the product over
+// hundreds of factors keeps close to full FP32 accuracy.
+#include "gs_internal.cuh"
+
+namespace gs {
+
+template <int BS>
+__global__ void __launch_bounds__(BS) k_raster_fwd(Views V, const uint2* __restrict__ ranges,
+                                                   const uint32_t* __restrict__ pid_sorted,
+                                                   const ProjRec* __restrict__ rec, const float* __restrict__ bg,
+                                                   float* __restrict__ image, float* __restrict__ tfinal,
+                                                   uint32_t* __restrict__ nlast, WsHeader* __restrict__ hdr)
+{
+    __shared__ float4 sA[BS];
+    __shared__ float4 sB[BS];
+    __shared__ float sC[BS];
+    __shared__ unsigned long long sblend[BS / 32];
+    const int64_t gt = blockIdx.x;
+    const int v = view_of_tile(V, gt);
+    const ViewDesc& vd = V.v[v];
+    const int lt = (int)(gt - vd.tile_base);
+    const int tx = lt % vd.TX, ty = lt / vd.TX;
+    const int px = tx * V.tw + (int)threadIdx.x % V.tw;
+    const int py = ty * V.th + (int)threadIdx.x / V.tw;
+    const bool inside = px < vd.W && py < vd.H;
+    const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+    const uint2 r = ranges[gt];
+
+    float Th = 1.0f, Tl = 0.0f;
+    float C0 = 0.f, C1 = 0.f, C2 = 0.f;
+    uint32_t last = 0, nbl = 0;
+    int done = !inside;
+    for (uint32_t base = r.x; base < r.y; base += BS) {
+        if (__syncthreads_count(done) == BS) break;
+        const uint32_t k = base + threadIdx.x;
+        if (k < r.y) {
+            const ProjRec q = rec[pid_sorted[k]];
+            sA[threadIdx.x] = q.a;
+            sB[threadIdx.x] = q.b;
+            sC[threadIdx.x] = q.c.x;
+        }
+        __syncthreads();
+        if (!done) {
+            const int cnt = (int)min((uint32_t)BS, r.y - base);
+            for (int j = 0; j < cnt; j++) {
+                const float4 a = sA[j];
+                const float dx = fx - a.x, dy = fy - a.y;
+                const float4 b = sB[j];
+                const float power = pair_power(dx, dy, a.z, a.w, b.x);
+                if (power < -4.5f) continue;
+                const float G = __expf(power);
+                const float alpha = fminf(kAlphaMax, __fmul_rn(b.y, G));
+                if (alpha < kAlphaMin) continue;
+                // compensated T * (1 - alpha)
+                const float om = __fsub_rn(1.0f, alpha);
+                const float om_err = __fsub_rn(-alpha, __fsub_rn(om, 1.0f));
+                const float pr = __fmul_rn(Th, om);
+                const float pe = __fmaf_rn(Th, om, -pr);
+                const float lo = __fmaf_rn(Th, om_err, __fmaf_rn(Tl, om, pe));
+                const float hi = __fadd_rn(pr, lo);
+                if (hi < kTMin) {
+                    done = 1;
+                    break;
+                }
+                const float wgt = alpha * Th;
+                C0 = fmaf(b.z, wgt, C0);
+                C1 = fmaf(b.w, wgt, C1);
+                C2 = fmaf(sC[j], wgt, C2);
+                Tl = __fsub_rn(lo, __fsub_rn(hi, pr));
+                Th = hi;
+                last = base - r.x + j + 1;
+                nbl++;
+            }
+        }
+    }
+    if (inside) {
+        const int64_t pix = vd.pix_base + (int64_t)py * vd.W + px;
+        const float T = Th + Tl;
+        float b0 = 0.f, b1 = 0.f, b2 = 0.f;
+        if (bg) { b0 = bg[0]; b1 = bg[1]; b2 = bg[2]; }
+        image[3 * pix + 0] = fmaf(T, b0, C0);
+        image[3 * pix + 1] = fmaf(T, b1, C1);
+        image[3 * pix + 2] = fmaf(T, b2, C2);
+        tfinal[pix] = T;
+        nlast[pix] = last;
+    }
+    // blended pair count: warp reduce, one atomic per CTA
+    unsigned long long c = nbl;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) sblend[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long s = 0;
+        for (int i = 0; i < BS / 32; i++) s += sblend[i];
+        if (s) atomicAdd(&hdr->blended, s);
+    }
+}
+
+void launch_raster_fwd(const Plan& P, const WsPtrs& w, const float* bg, float* image, cudaStream_t st)
+{
+    const Views& V = P.views;
+    const int bs = V.tw * V.th;
+    const unsigned grid = (unsigned)V.tiles;
+#define GS_RF(BS) k_raster_fwd<BS><<<grid, BS, 0, st>>>(V, w.ranges, w.pid_sorted, w.rec, bg, image, w.tfinal, \
+                                                        w.nlast, w.hdr)
+    if (bs == 64) GS_RF(64);
+    else if (bs == 256) GS_RF(256);
+    else GS_RF(512);
+#undef GS_RF
+}
+
+// ---------------------------------------------------------------------------
+// L1 loss and gradient
+// ---------------------------------------------------------------------------
+
+constexpr int kLossThreads = 256;
+constexpr int kLossItems = 8;
+
+__global__ void __launch_bounds__(kLossThreads) k_loss_l1(const float* __restrict__ image,
+                                                          const float* __restrict__ target, float* __restrict__ dl,
+                                                          int64_t n, float inv_n, float* __restrict__ part,
+                                                          WsHeader* __restrict__ hdr)
+{
+    __shared__ float ws[kLossThreads / 32];
+    __shared__ bool is_last;
+    const int64_t base = (int64_t)blockIdx.x * kLossThreads * kLossItems;
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < kLossItems; i++) {
+        const int64_t idx = base + i * kLossThreads + threadIdx.x;
+        if (idx < n) {
+            const float d = image[idx] - target[idx];
+            dl[idx] = d > 0.f ? inv_n : (d < 0.f ? -inv_n : 0.f);
+            s += fabsf(d);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int i = 0; i < kLossThreads / 32; i++) t += ws[i];
+        part[blockIdx.x] = t;
+        __threadfence();
+        const uint32_t done = atomicAdd(&hdr->loss_counter, 1u);
+        is_last = done == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (is_last && threadIdx.x == 0) {
+        // the last CTA sums the partials in index order (deterministic)
+        __threadfence();
+        float t = 0.f, comp = 0.f;  // Kahan-compensated FP32 sum
+        for (unsigned i = 0; i < gridDim.x; i++) {
+            const float y = ((volatile float*)part)[i] - comp;
+            const float u = t + y;
+            comp = (u - t) - y;
+            t = u;
+        }
+        hdr->loss = t * inv_n;
+        hdr->loss_counter = 0;
+    }
+}
+
+void launch_loss_l1(const Plan& P, const WsPtrs& w, const float* image, const float* target, float* dl,
+                    cudaStream_t st)
+{
+    const int64_t n = 3 * P.views.pixels;
+    const int64_t blocks = (n + kLossThreads * kLossItems - 1) / (kLossThreads * kLossItems);
+    k_loss_l1<<<(unsigned)blocks, kLossThreads, 0, st>>>(image, target, dl, n, 1.0f / (float)n, w.loss_part,
+                                                          w.hdr);
+}
+
+}  // namespace gs

@@ -1,0 +1,152 @@
+"""Device buffers and the training step built from the C-ABI calls.
+
+`SceneBuffers` packs a scene into the device layout of include/gs_step.h
+(chunk-major float4 SoA: geometry, SH, Adam moments).  `Trainer` owns one
+plan and workspace and runs
+
+    gs_project_fwd -> gs_bin_sort -> gs_raster_fwd -> gs_loss_l1
+    -> gs_raster_bwd -> gs_project_bwd_adam
+
+on one stream, eagerly or as one captured CUDA graph whose replay reads the
+cameras, targets and the Adam step counter from device memory.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import gsstep
+from . import synth
+
+# Per-group learning rates: mean, quaternion, log-scale, logit-opacity, SH
+# degree 0, SH degrees 1-3.
+DEFAULT_LR = (1.6e-4, 1e-3, 5e-3, 5e-2, 2.5e-3, 2.5e-3 / 20)
+
+
+@dataclass
+class SceneBuffers:
+    n: int
+    geom: torch.Tensor          # (3, n, 4) float32
+    sh: torch.Tensor            # (12, n, 4) float32 or (6, n, 8) bfloat16
+    m: torch.Tensor | None      # (15, n, 4) float32 or bfloat16
+    v: torch.Tensor | None
+
+    @staticmethod
+    def from_scene(scene: synth.Scene, device="cuda", sh_bf16=False, mom_bf16=False, moments=True):
+        n = scene.n
+        geom = np.zeros((3, n, 4), np.float32)
+        geom[0, :, :3] = scene.means
+        geom[1] = scene.quats
+        geom[2, :, :3] = scene.scales
+        geom[2, :, 3] = scene.opacities
+        flat = np.ascontiguousarray(scene.sh, np.float32).reshape(n, 48)
+        g = torch.from_numpy(geom).to(device)
+        if sh_bf16:
+            sh = torch.from_numpy(flat.reshape(n, 6, 8).transpose(1, 0, 2).copy()).to(device).to(torch.bfloat16)
+        else:
+            sh = torch.from_numpy(flat.reshape(n, 12, 4).transpose(1, 0, 2).copy()).to(device)
+        m = v = None
+        if moments:
+            mdt = torch.bfloat16 if mom_bf16 else torch.float32
+            m = torch.zeros((15, n, 4), dtype=mdt, device=device)
+            v = torch.zeros((15, n, 4), dtype=mdt, device=device)
+        return SceneBuffers(n, g, sh.contiguous(), m, v)
+
+    def to_scene(self) -> synth.Scene:
+        geom = self.geom.detach().float().cpu().numpy()
+        n = self.n
+        if self.sh.dtype == torch.bfloat16:
+            flat = self.sh.detach().float().cpu().numpy().transpose(1, 0, 2).reshape(n, 48)
+        else:
+            flat = self.sh.detach().cpu().numpy().transpose(1, 0, 2).reshape(n, 48)
+        return synth.Scene(geom[0, :, :3].copy(), geom[1].copy(), geom[2, :, :3].copy(), geom[2, :, 3].copy(),
+                           flat.reshape(n, 16, 3).copy())
+
+
+def camera_params(cams) -> np.ndarray:
+    return np.stack([c.pose_params() for c in cams]).astype(np.float32)
+
+
+class Trainer:
+    """One plan + workspace; runs the step over `cameras` (each with .scene)."""
+
+    def __init__(self, scenes, cameras, capacity: int = 0, tile=(16, 16), bwd_batch: int = 0,
+                 sh_bf16: bool = False, mom_bf16: bool = False, bg=None, lr=DEFAULT_LR, device="cuda"):
+        self.device = torch.device(device)
+        self.scenes = [s if isinstance(s, SceneBuffers) else
+                       SceneBuffers.from_scene(s, device, sh_bf16, mom_bf16) for s in scenes]
+        flags = (gsstep.STORE_SH_BF16 if sh_bf16 else 0) | (gsstep.STORE_MOMENTS_BF16 if mom_bf16 else 0)
+        self.plan = gsstep.Plan([s.n for s in self.scenes], [(c.width, c.height, c.scene) for c in cameras],
+                                capacity, tile, bwd_batch, flags)
+        self.ws = torch.empty(self.plan.workspace_bytes(), dtype=torch.uint8, device=self.device)
+        self.cams = torch.from_numpy(camera_params(cameras)).to(self.device)
+        P = self.plan.pixels
+        self.image = torch.zeros((P, 3), dtype=torch.float32, device=self.device)
+        self.target = torch.zeros((P, 3), dtype=torch.float32, device=self.device)
+        self.dl = torch.zeros((P, 3), dtype=torch.float32, device=self.device)
+        self.bg = None if bg is None else torch.tensor(bg, dtype=torch.float32, device=self.device)
+        self.view_shapes = [(c.width, c.height) for c in cameras]
+        self.lr = tuple(lr)
+        self.graph = None
+        gsstep.gs_workspace_init(self.plan, self.ws)
+
+    # -- inputs -------------------------------------------------------------
+    def set_cameras(self, cameras):
+        self.cams.copy_(torch.from_numpy(camera_params(cameras)), non_blocking=False)
+
+    def set_target(self, images):
+        """images: list of (H, W, 3) arrays/tensors, one per view."""
+        flat = torch.cat([torch.as_tensor(np.asarray(im, np.float32)).reshape(-1, 3) for im in images])
+        self.target.copy_(flat)
+
+    def image_views(self, img=None):
+        img = self.image if img is None else img
+        out, o = [], 0
+        for (w, h) in self.view_shapes:
+            out.append(img[o:o + w * h].view(h, w, 3))
+            o += w * h
+        return out
+
+    # -- stages -------------------------------------------------------------
+    def forward(self, stream=None):
+        gsstep.gs_project_fwd(self.plan, self.ws, self.scenes, self.cams, stream)
+        gsstep.gs_bin_sort(self.plan, self.ws, stream)
+        gsstep.gs_raster_fwd(self.plan, self.ws, self.bg, self.image, stream)
+        return self.image
+
+    def backward_adam(self, step: int = 0, stream=None):
+        gsstep.gs_loss_l1(self.plan, self.ws, self.image, self.target, self.dl, stream)
+        gsstep.gs_raster_bwd(self.plan, self.ws, self.image, self.dl, stream)
+        adam = gsstep.make_adam(self.lr, step=step)
+        gsstep.gs_project_bwd_adam(self.plan, self.ws, self.scenes, self.cams, adam, None, stream)
+        if step <= 0:
+            gsstep.gs_adam_advance(self.plan, self.ws, stream)
+
+    def step(self, step: int = 0, stream=None):
+        """One training step; step <= 0 takes Adam's t from the device counter."""
+        self.forward(stream)
+        self.backward_adam(step, stream)
+
+    # -- graphs -------------------------------------------------------------
+    def capture(self):
+        """Capture one whole step (device step counter) in a CUDA graph."""
+        s = torch.cuda.Stream(device=self.device)
+        s.wait_stream(torch.cuda.current_stream(self.device))
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                self.step(0, s)
+        torch.cuda.current_stream(self.device).wait_stream(s)
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
+
+    def stats(self) -> gsstep.gs_stats:
+        return gsstep.gs_read_stats(self.plan, self.ws)
+
+    def buffer(self, which: int, numel: int, dtype=torch.int32):
+        return gsstep.gs_workspace_buffer(self.plan, self.ws, which, numel, dtype)

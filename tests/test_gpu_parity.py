@@ -1,0 +1,289 @@
+"""Parity of the CUDA step (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (stated by the target of the build, applied here):
+  - tile counts, keys, sorted lists and tile ranges: bit-exact;
+  - images: max |C_gpu - C_fp64| <= 1e-5 on pixels whose decisions are not
+    within 1e-4 (relative) of a threshold (1/255, 0.99, 9, 1e-4); the count
+    of excluded pixels is reported;
+  - gradients: |g_gpu - g_fp64| <= 1e-3 max(|g_fp64|, rms of the component)
+    on Gaussians not touching an excluded pixel;
+  - post-Adam parameters: |theta_gpu - theta_fp64| <= 1e-5 |theta| + 1e-6
+    where the first-step update direction is decided (|g| above 1e-2 rms).
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2605_00219_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+LR = (1e-3,) * 6
+
+
+@pytest.fixture(scope="module")
+def gs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_00219_gb300 import build
+    build.build()
+    from paper_2605_00219_gb300 import gsstep, step
+    return gsstep, step
+
+
+def _oracle_all(orc, scene, cam, tile, dl=None, bg=(0.0, 0.0, 0.0)):
+    b = orc.bin32(scene, cam, *tile)
+    p = orc.Params64.from_scene(scene)
+    P = orc.project64(p, cam, *tile)
+    r = orc.render64(cam, P, b, bg, 1e-4, *tile)
+    return b, p, P, r
+
+
+def _unstable_gaussians(P, r, cam):
+    """Gaussians flagged by the oracle or covering (d^2 <= 9) a flagged pixel."""
+    bad = r.unstable_g.copy()
+    ys, xs = np.nonzero(r.unstable_px)
+    for x, y in zip(xs, ys):
+        dx = x + 0.5 - P[:, 4]
+        dy = y + 0.5 - P[:, 5]
+        d2 = P[:, 9] * dx * dx + 2 * P[:, 10] * dx * dy + P[:, 11] * dy * dy
+        bad |= (P[:, 0] > 0) & (d2 <= 9.0 * (1 + 1e-3))
+    return bad
+
+
+def _run_forward(step_mod, scene, cams, tile=(16, 16), bwd_batch=0, bg=None, capacity=0):
+    tr = step_mod.Trainer([scene], cams, capacity=capacity, tile=tile, bwd_batch=bwd_batch, bg=bg, lr=LR)
+    tr.forward()
+    torch.cuda.synchronize()
+    return tr
+
+
+def _sum_slots(grad_slots, offset, count):
+    n = count.shape[0]
+    out = np.zeros((n, 9))
+    for g in range(n):
+        c = int(count[g])
+        if c:
+            out[g] = grad_slots[offset[g]:offset[g] + c, :9].astype(np.float64).sum(0)
+    return out
+
+
+def _check_grad(gpu, ref, mask, name, tol=1e-3):
+    ref_m, gpu_m = ref[mask], gpu[mask]
+    rms = np.sqrt((ref_m ** 2).mean(0)) + 1e-30
+    bound = tol * np.maximum(np.abs(ref_m), rms[None, :])
+    err = np.abs(gpu_m - ref_m)
+    worst = (err / np.maximum(np.abs(ref_m), rms[None, :])).max()
+    assert np.all(err <= bound), f"{name}: worst relative error {worst:.3e}"
+    return worst
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_tiny_stages(gs, orc, seed):
+    """2,000 Gaussians, 128x128: every stage against the oracle."""
+    gsstep, step_mod = gs
+    scene, tscene, cams = synth.tiny_workload(seed)
+    cam = cams[0]
+    b, p, P, r = _oracle_all(orc, scene, cam, (16, 16))
+    tr = _run_forward(step_mod, scene, cams)
+    n = scene.n
+    # --- projection: counts bit-exact, means/depth bit-exact, conic/colour close
+    count = tr.buffer(0, n).cpu().numpy().view(np.uint32)
+    np.testing.assert_array_equal(count, b.count)
+    rec = tr.buffer(7, n * 12, torch.float32).cpu().numpy().reshape(n, 12)
+    vis = b.count > 0
+    np.testing.assert_array_equal(rec[vis, 0], b.bin[vis, 1])
+    np.testing.assert_array_equal(rec[vis, 1], b.bin[vis, 2])
+    np.testing.assert_array_equal(rec[vis, 9], b.bin[vis, 7])
+    # conic entries relative to the conic's scale (the off-diagonal can be ~0)
+    con_g, con_o = rec[vis][:, [2, 3, 4]], P[vis][:, [9, 10, 11]]
+    scale = np.abs(con_o).max(1, keepdims=True)
+    assert (np.abs(con_g - con_o) / scale).max() <= 1e-4
+    np.testing.assert_allclose(rec[vis][:, [6, 7, 8]], P[vis][:, [16, 17, 18]], atol=1e-5)
+    # --- binning: sorted keys, sorted Gaussians and ranges bit-exact
+    st = tr.stats()
+    assert st.status == 0 and st.k_required == b.K
+    keys = tr.buffer(2, b.K).cpu().numpy().view(np.uint32)
+    pids = tr.buffer(3, b.K).cpu().numpy().view(np.uint32)
+    np.testing.assert_array_equal(keys, b.keys)
+    np.testing.assert_array_equal(pids, b.gidx)
+    ranges = tr.buffer(4, 2 * 64).cpu().numpy().view(np.uint32).reshape(64, 2)
+    np.testing.assert_array_equal(ranges.astype(np.int64), b.ranges)
+    # --- raster forward
+    img = tr.image.view(128, 128, 3).cpu().numpy().astype(np.float64)
+    ok = ~r.unstable_px
+    err = np.abs(img - r.image)[ok].max()
+    assert err <= 1e-5, err
+    assert r.unstable_px.sum() < 0.01 * ok.size
+    nl = tr.buffer(5, 128 * 128).cpu().numpy().reshape(128, 128)
+    np.testing.assert_array_equal(nl[ok], r.nlast[ok])
+    assert abs(int(st.blended_pairs) - r.blended) <= int(r.unstable_px.sum()) * 8
+    # --- raster backward with the oracle's dL/dC (FP32-cast)
+    rng = np.random.default_rng(seed + 10)
+    dl64 = rng.normal(size=(128, 128, 3)) / (3 * 128 * 128)
+    tr.dl.copy_(torch.from_numpy(dl64.astype(np.float32).reshape(-1, 3)))
+    gsstep.gs_raster_bwd(tr.plan, tr.ws, tr.image, tr.dl)
+    g2_orc = orc.raster_bwd64(cam, P, b, dl64.astype(np.float32).astype(np.float64))
+    gr = tr.buffer(8, b.K * 12, torch.float32).cpu().numpy().reshape(b.K, 12)
+    off = tr.buffer(1, n + 1).cpu().numpy().view(np.uint32).astype(np.int64)
+    g2_gpu = _sum_slots(gr, off, count)
+    good = vis & ~_unstable_gaussians(P, r, cam)
+    assert good.sum() > 0.7 * vis.sum()
+    _check_grad(g2_gpu, g2_orc, good, "grad2d")
+    # --- projection backward, gradient-only mode (activated parameters)
+    grads = torch.zeros((15, n, 4), dtype=torch.float32, device="cuda")
+    gsstep.gs_project_bwd_adam(tr.plan, tr.ws, tr.scenes, tr.cams, None, grads)
+    torch.cuda.synchronize()
+    g = grads.cpu().numpy()
+    gth = orc.project_bwd64(p, cam, P, g2_orc)
+    ref = np.concatenate([gth[:, 0:3], gth[:, 3:7], gth[:, 7:10] / p.scales,
+                          (gth[:, 10] / (p.opacities * (1 - p.opacities)))[:, None], gth[:, 11:]], axis=1)
+    gpu = np.concatenate([g[0, :, :3], g[1], g[2], g[3:].transpose(1, 0, 2).reshape(n, 48)], axis=1)
+    _check_grad(gpu, ref, good, "grad3d")
+
+
+def test_tiny_full_step_adam(gs, orc):
+    """Whole step (device L1 gradient, fused Adam) vs the oracle's step."""
+    gsstep, step_mod = gs
+    scene, tscene, cams = synth.tiny_workload(0)
+    cam = cams[0]
+    tb, tp, tP, tr_ = _oracle_all(orc, tscene, cam, (16, 16))
+    target = tr_.image
+    res = orc.step(scene, cams, [target], LR, 1)
+    tr = step_mod.Trainer([scene], cams, lr=LR)
+    tr.set_target([target.astype(np.float32)])
+    tr.step(step=1)
+    torch.cuda.synchronize()
+    st = tr.stats()
+    assert st.status == 0
+    assert st.loss == pytest.approx(res.loss, rel=1e-4)
+    r = res.renders[0]
+    img = tr.image.view(128, 128, 3).cpu().numpy()
+    # pixels where the loss sign is not decided in FP32 join the excluded set
+    undecided = (np.abs(r.image - target) < 1e-5).any(-1)
+    r.unstable_px |= undecided
+    bad = _unstable_gaussians(res.projs[0], r, cam)
+    new = tr.scenes[0].to_scene()
+    th_gpu = np.concatenate([new.means, new.quats, np.log(new.scales), np.log(new.opacities / (1 - new.opacities))[:, None],
+                             new.sh.reshape(-1, 48)], axis=1).astype(np.float64)
+    g = res.grad
+    rms = np.sqrt((g[~bad] ** 2).mean(0)) + 1e-30
+    decided = (np.abs(g) > 1e-2 * rms[None, :]) & ~bad[:, None]
+    zero = (g == 0) & ~bad[:, None]
+    assert decided.sum() > 0.5 * g.size
+    diff = np.abs(th_gpu - res.theta)
+    tol = 1e-5 * np.abs(res.theta) + 1e-6
+    assert np.all(diff[decided] <= tol[decided]), diff[decided].max()
+    assert np.all(diff[zero] <= tol[zero])
+
+
+@pytest.mark.parametrize("tile,bwd_batch", [((16, 16), 0), ((8, 8), 0), ((16, 32), 0), ((16, 16), 32),
+                                            ((16, 16), 64), ((16, 16), 96)])
+def test_ragged_tiles_and_batches(gs, orc, tile, bwd_batch):
+    """Non-multiple image size (ragged tile tail), all tile shapes, fixed and
+    adaptive backward batch sizes: keys bit-exact, images and gradients."""
+    gsstep, step_mod = gs
+    scene = synth.cluster_scene(20000, 16, 3.0, seed=7, log_scale=(-3.5, 0.5), logit_opacity=(0.0, 1.5))
+    cam = synth.look_at([0, -6, 2], [0, 0, 0], 203, 149, 180.0)
+    b, p, P, r = _oracle_all(orc, scene, cam, tile)
+    tr = _run_forward(step_mod, scene, [cam], tile=tile, bwd_batch=bwd_batch)
+    n = scene.n
+    keys = tr.buffer(2, b.K).cpu().numpy().view(np.uint32)
+    np.testing.assert_array_equal(keys, b.keys)
+    np.testing.assert_array_equal(tr.buffer(3, b.K).cpu().numpy().view(np.uint32), b.gidx)
+    img = tr.image.view(149, 203, 3).cpu().numpy().astype(np.float64)
+    ok = ~r.unstable_px
+    assert np.abs(img - r.image)[ok].max() <= 1e-5
+    rng = np.random.default_rng(3)
+    dl64 = rng.normal(size=(149, 203, 3)).astype(np.float32).astype(np.float64) / (3 * 149 * 203)
+    tr.dl.copy_(torch.from_numpy(dl64.astype(np.float32).reshape(-1, 3)))
+    gsstep.gs_raster_bwd(tr.plan, tr.ws, tr.image, tr.dl)
+    g2_orc = orc.raster_bwd64(cam, P, b, dl64, (0, 0, 0), *tile)
+    count = tr.buffer(0, n).cpu().numpy().view(np.uint32)
+    off = tr.buffer(1, n + 1).cpu().numpy().view(np.uint32).astype(np.int64)
+    gr = tr.buffer(8, b.K * 12, torch.float32).cpu().numpy().reshape(b.K, 12)
+    g2_gpu = _sum_slots(gr, off, count)
+    good = (b.count > 0) & ~_unstable_gaussians(P, r, cam)
+    _check_grad(g2_gpu, g2_orc, good, f"grad2d {tile} S={bwd_batch}")
+
+
+def test_background_colour(gs, orc):
+    gsstep, step_mod = gs
+    scene, _, cams = synth.tiny_workload(2)
+    cam = cams[0]
+    bg = (0.25, 0.5, 0.75)
+    b, p, P, r = _oracle_all(orc, scene, cam, (16, 16), bg=bg)
+    tr = _run_forward(step_mod, scene, cams, bg=bg)
+    img = tr.image.view(128, 128, 3).cpu().numpy().astype(np.float64)
+    ok = ~r.unstable_px
+    assert np.abs(img - r.image)[ok].max() <= 1e-5
+
+
+def test_multi_view_uneven(gs, orc):
+    """Three views of uneven resolution in one launch: per-view key segments
+    bit-exact, images per view within tolerance."""
+    gsstep, step_mod = gs
+    scene = synth.cluster_scene(30000, 16, 4.0, seed=3, log_scale=(-3.5, 0.5))
+    cams = [synth.look_at([0, -7, 2], [0, 0, 0], 160, 96, 150.0),
+            synth.look_at([6, 2, 1], [0, 0, 0], 97, 131, 120.0),
+            synth.look_at([-5, -5, 3], [0, 0, 0], 256, 144, 220.0)]
+    tr = _run_forward(step_mod, scene, cams)
+    st = tr.stats()
+    bins = [orc.bin32(scene, c) for c in cams]
+    K = sum(bb.K for bb in bins)
+    assert st.k_required == K and st.status == 0
+    keys = tr.buffer(2, K).cpu().numpy().view(np.uint32)
+    pids = tr.buffer(3, K).cpu().numpy().view(np.uint32)
+    o = 0
+    for v, bb in enumerate(bins):
+        np.testing.assert_array_equal(keys[o:o + bb.K], bb.keys)
+        np.testing.assert_array_equal(pids[o:o + bb.K], bb.gidx + v * scene.n)
+        o += bb.K
+    p = orc.Params64.from_scene(scene)
+    for c, bb, im in zip(cams, bins, tr.image_views()):
+        P = orc.project64(p, c)
+        r = orc.render64(c, P, bb)
+        ok = ~r.unstable_px
+        assert np.abs(im.cpu().numpy().astype(np.float64) - r.image)[ok].max() <= 1e-5
+
+
+def test_capacity_overflow_sets_status(gs, orc):
+    """Too small an intersection capacity is reported, nothing is written
+    out of bounds, and a larger capacity then succeeds."""
+    gsstep, step_mod = gs
+    scene, _, cams = synth.tiny_workload(0)
+    tr = _run_forward(step_mod, scene, cams, capacity=2048)
+    st = tr.stats()
+    assert st.status & gsstep.STATUS_CAPACITY
+    assert st.k_required == orc.bin32(scene, cams[0]).K
+    tr2 = _run_forward(step_mod, scene, cams, capacity=int(st.k_required))
+    assert tr2.stats().status == 0
+
+
+def test_nonfinite_parameter_sets_status(gs):
+    gsstep, step_mod = gs
+    scene, _, cams = synth.tiny_workload(0)
+    scene.means[5, 1] = np.nan
+    tr = _run_forward(step_mod, scene, cams)
+    assert tr.stats().status & gsstep.STATUS_NONFINITE
+
+
+def test_graph_replay_equals_eager(gs):
+    """A captured step replays bit-identically to the eager step (two steps)."""
+    gsstep, step_mod = gs
+    scene, tscene, cams = synth.tiny_workload(0)
+    target = np.random.default_rng(0).uniform(0, 0.5, size=(128, 128, 3)).astype(np.float32)
+    a = step_mod.Trainer([scene], cams, lr=LR)
+    b = step_mod.Trainer([scene], cams, lr=LR)
+    for t in (a, b):
+        t.set_target([target])
+    b.capture()
+    b.scenes[0].geom.copy_(a.scenes[0].geom)  # capture ran no kernels
+    for _ in range(2):
+        a.step(0)
+        b.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(a.scenes[0].geom, b.scenes[0].geom)
+    assert torch.equal(a.scenes[0].sh, b.scenes[0].sh)
+    assert torch.equal(a.scenes[0].m, b.scenes[0].m)
+    assert a.stats().step == b.stats().step == 2
