@@ -211,6 +211,32 @@ void* gs_workspace_buffer(const gs_plan* plan, void* ws, int32_t which);
 
 const char* gs_status_str(gs_status s);
 
+/* L1 loss and gradient without any device allocation (no plan, no
+ * workspace).  The paper has no counterpart to this call: it exists for
+ * callers that may not allocate device memory -- a host framework that owns
+ * the GPU's memory through its own pool and forbids cudaMalloc in libraries,
+ * or a frame loop that must never wait on the allocator.
+ *
+ * Computes the same values as gs_loss_l1 over n_values floats (3 x pixels):
+ * dL_dimage[i] = sign(image[i] - target[i]) / n_values, and
+ * *loss = sum |image - target| / n_values written to the DEVICE float `loss`.
+ * All four pointers are device memory owned by the caller.
+ *
+ * Its scratch (block partial sums and a completion counter, about 128 KiB)
+ * is a static array inside the library, held by every GPU that loads the
+ * library until the process exits.  The first call on a device looks up that
+ * array's device address (with the device current) and caches it; make that
+ * first call before any stream capture.  The array is shared by every call on
+ * the device and keeps the last call's contents (the counter is cleared at
+ * the start of each call), so calls whose executions overlap on the GPU race
+ * and must be ordered by the caller.
+ * Returns GS_ERR_INVALID_ARG for a NULL pointer or for n_values <= 0 or
+ * n_values > GS_L1_NOALLOC_MAX_VALUES, GS_ERR_CUDA if the set-up or the
+ * launch fails. */
+#define GS_L1_NOALLOC_MAX_VALUES 67108864LL   /* 3 x 22,369,621 pixels */
+gs_status gs_loss_l1_noalloc(const float* image, const float* target, float* dL_dimage, float* loss,
+                             int64_t n_values, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

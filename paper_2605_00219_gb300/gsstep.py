@@ -30,7 +30,9 @@ STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_CAPACITY", 3: "G
 # exported symbols (the C ABI)
 SYMBOLS = ["gs_plan_create", "gs_plan_destroy", "gs_workspace_bytes", "gs_plan_query", "gs_workspace_init",
            "gs_project_fwd", "gs_bin_sort", "gs_raster_fwd", "gs_loss_l1", "gs_raster_bwd",
-           "gs_project_bwd_adam", "gs_adam_advance", "gs_read_stats", "gs_workspace_buffer", "gs_status_str"]
+           "gs_project_bwd_adam", "gs_adam_advance", "gs_read_stats", "gs_workspace_buffer", "gs_status_str",
+           "gs_loss_l1_noalloc"]
+L1_NOALLOC_MAX_VALUES = 67108864
 
 
 class gs_view(ctypes.Structure):
@@ -94,6 +96,8 @@ def lib():
         L.gs_read_stats.argtypes = [vp, vp, ctypes.POINTER(gs_stats), vp]
         L.gs_workspace_buffer.argtypes = [vp, vp, i32]
         L.gs_workspace_buffer.restype = vp
+        L.gs_loss_l1_noalloc.argtypes = [vp, vp, vp, vp, i64, vp]
+        L.gs_loss_l1_noalloc.restype = ctypes.c_int
         L.gs_status_str.argtypes = [ctypes.c_int]
         L.gs_status_str.restype = ctypes.c_char_p
         for name in ["gs_workspace_init", "gs_project_fwd", "gs_bin_sort", "gs_raster_fwd", "gs_loss_l1",
@@ -236,3 +240,11 @@ def gs_workspace_buffer(plan: Plan, ws, which: int, numel: int, dtype=torch.int3
     esz = torch.tensor([], dtype=dtype).element_size()
     assert off % esz == 0
     return ws.view(torch.uint8)[off:off + numel * esz].view(dtype)
+
+
+def gs_loss_l1_noalloc(image, target, dl, loss, stream=None):
+    """L1 loss and gradient with no plan, no workspace and no device
+    allocation (for callers that may not allocate); `loss` is a 1-element
+    device float tensor.  See include/gs_step.h for the shared-scratch rules."""
+    _check(lib().gs_loss_l1_noalloc(_ptr(image), _ptr(target), _ptr(dl), _ptr(loss), int(image.numel()),
+                                    _stream(stream)), "gs_loss_l1_noalloc")
