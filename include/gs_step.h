@@ -142,9 +142,9 @@ gs_status gs_workspace_init(const gs_plan* plan, void* ws, void* stream);
 
 /* Projection forward (EWA splatting with the 0.3 low-pass, degree-3 SH
  * colour) for every (view, Gaussian) pair, fused with the exact scan-line
- * count of intersected tiles (Sec. 4.1: "compute number of intersecting tiles
- * per Gaussian in the projection-forward pass").  Reads geom and sh of every
- * scene and cams; writes the projected records and counts into ws. */
+ * count of intersected tiles (Sec. 4.1 counts tiles during projection and
+ * emits them in a later pass).  Reads geom and sh of every scene and cams;
+ * writes the projected records and counts into ws. */
 gs_status gs_project_fwd(const gs_plan* plan, void* ws, const gs_scene_buf* scenes,
                          const float* cams, void* stream);
 
