@@ -43,6 +43,9 @@ def _args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_GAUSS)
+    ap.add_argument("--bwd-impl", type=int, default=0, choices=[0, 1],
+                    help="raster backward: 0 pixel-parallel warp reductions, 1 per-Gaussian batches")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--cpu-sample-tiles", type=int, default=16,
                     help="oracle renders 1 in this many tiles (bounded CPU sample)")
     return ap.parse_args()
@@ -191,7 +194,7 @@ def main():
     tgt_tr.forward()
     target = tgt_tr.image.clone()
     del tgt_tr
-    tr = stepmod.Trainer([scene], [cam], lr=LR)
+    tr = stepmod.Trainer([scene], [cam], lr=LR, bwd_impl=args.bwd_impl)
     tr.target.copy_(target)
     torch.cuda.synchronize()
 
@@ -308,7 +311,7 @@ def main():
     roof["kernel"] = dom
 
     cpu = None
-    if rank == 0 and ws == 1:
+    if rank == 0 and ws == 1 and not args.no_cpu:
         from oracle import oracle as orc
         orc.build()
         tgt_np = target.view(RES[1], RES[0], 3).cpu().numpy().astype(np.float64)

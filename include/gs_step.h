@@ -83,10 +83,15 @@ typedef struct {
 
 typedef struct {
     int32_t tile_w, tile_h;   /* 8x8, 16x16 or 16x32 pixels */
-    int32_t bwd_batch;        /* raster_bwd Gaussian batch S: 0 = the paper's
-                                 adaptive rule S = roundup32(sqrt(N P)) <= 128
-                                 (Sec. 4.2); else a fixed 32, 64, 96 or 128 */
-    int32_t reserved;
+    int32_t bwd_batch;        /* per-Gaussian raster_bwd batch S: 0 = the
+                                 paper's adaptive rule S = roundup32(sqrt(N P))
+                                 <= 128 (Sec. 4.2); else a fixed 32, 64, 96 or
+                                 128 */
+    int32_t bwd_impl;         /* raster_bwd implementation: 0 = pixels across
+                                 threads with per-Gaussian warp-shuffle
+                                 reductions, 1 = Gaussians across threads in
+                                 batches of S (the paper's first
+                                 implementation, Sec. 4.2) */
 } gs_tuning;
 
 typedef struct {
@@ -172,12 +177,16 @@ gs_status gs_raster_fwd(const gs_plan* plan, void* ws, const float* bg, float* i
 gs_status gs_loss_l1(const gs_plan* plan, void* ws, const float* image, const float* target,
                      float* dL_dimage, void* stream);
 
-/* Rasterization backward, per Gaussian (Sec. 4.2, first implementation):
- * one thread block per tile, Gaussians of the tile in batches of S across
- * threads, transmittance recomputed from the front (no per-pair storage from
- * the forward), no atomics: one 9-float gradient record (mean2D, conic,
- * opacity, colour) per intersection.  image is the gs_raster_fwd output
- * (the suffix colour is derived from it), dL_dimage the loss gradient. */
+/* Rasterization backward (Sec. 4.2), one thread block per tile, no atomics:
+ * one 9-float gradient record (mean2D, conic, opacity, colour) per
+ * intersection, summed in a fixed order (deterministic).  Transmittance is
+ * recomputed per tile (nothing per pair is kept from the forward).
+ * tuning.bwd_impl = 1: the paper's first implementation -- Gaussians of the
+ * tile in batches of S across threads, T recomputed front to back;
+ * tuning.bwd_impl = 0: pixels across threads walking back from their last
+ * blended pair (compensated division by 1 - alpha), per-Gaussian gradients
+ * reduced across each warp's pixels with shuffles.
+ * image is the gs_raster_fwd output, dL_dimage the loss gradient. */
 gs_status gs_raster_bwd(const gs_plan* plan, void* ws, const float* image,
                         const float* dL_dimage, void* stream);
 

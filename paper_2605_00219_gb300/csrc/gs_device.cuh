@@ -60,6 +60,7 @@ struct WsHeader {
     uint32_t loss_counter;
     float loss;
     uint32_t pad;
+    float bg[4];                  // background colour of the last raster_fwd
     uint32_t seg[kMaxViews + 1];  // sorted-segment start of each view
 };
 

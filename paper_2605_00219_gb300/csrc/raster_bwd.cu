@@ -287,8 +287,15 @@ __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(Views V, const uint2
     }
 }
 
+void launch_raster_bwd_px(const Plan& P, const WsPtrs& w, const float* bg, const float* dl, cudaStream_t st);
+
 void launch_raster_bwd(const Plan& P, const WsPtrs& w, const float* image, const float* dl, cudaStream_t st)
 {
+    if (P.tuning.bwd_impl == 0) {
+        const float* bg = reinterpret_cast<const float*>(reinterpret_cast<const char*>(w.hdr) + offsetof(WsHeader, bg));
+        launch_raster_bwd_px(P, w, bg, dl, st);
+        return;
+    }
     const Views& V = P.views;
     const int np = V.tw * V.th;
     const unsigned grid = (unsigned)V.tiles;
@@ -308,6 +315,190 @@ void launch_raster_bwd(const Plan& P, const WsPtrs& w, const float* image, const
     else if (np == 256) GS_RB(256);
     else GS_RB(512);
 #undef GS_RB
+}
+
+}  // namespace gs
+
+// ===========================================================================
+// Second implementation: pixels across threads, per-Gaussian gradients
+// reduced across each warp's pixels by shuffles (no atomics).
+//
+// One CTA per tile, one thread per pixel, each warp an 8x4 pixel block (so a
+// small Gaussian touches few warps).  Every pixel walks its own list prefix
+// back to front from its last blended entry: T before an entry is recovered
+// by a compensated division of T after it by (1 - alpha), and the colour
+// still to come S grows from T_final * bg without cancellation.  For each
+// list entry the warp sums the nine gradients of its pixels with a butterfly
+// of shuffles, but only when at least one of its pixels blended the entry;
+// lane (entry mod 32) keeps the warp's sum, and after every 32 entries the
+// warps' sums are added in warp order and written to the entry's emission
+// slot.
+// ===========================================================================
+
+namespace gs {
+
+template <int BS, int TW>
+__global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint2* __restrict__ ranges,
+                                                      const uint32_t* __restrict__ vals_sorted,
+                                                      const uint32_t* __restrict__ pid_sorted,
+                                                      const ProjRec* __restrict__ rec,
+                                                      const float* __restrict__ tfinal,
+                                                      const float* __restrict__ bg, const float* __restrict__ dl,
+                                                      const uint32_t* __restrict__ nlast,
+                                                      GradRec* __restrict__ gradrec)
+{
+    constexpr int NW = BS / 32;
+    constexpr int WPR = TW / 8;   // 8x4 warp blocks per tile row
+    __shared__ float4 sA[BS];
+    __shared__ float4 sB[BS];
+    __shared__ float sC[BS];
+    __shared__ uint32_t sE[BS];
+    __shared__ float part[NW][32][9];
+    __shared__ int smax[NW];
+
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int64_t gt = blockIdx.x;
+    const int v = view_of_tile(V, gt);
+    const ViewDesc& vd = V.v[v];
+    const int lt = (int)(gt - vd.tile_base);
+    const int px = (lt % vd.TX) * TW + (w % WPR) * 8 + (lane & 7);
+    const int py = (lt / vd.TX) * V.th + (w / WPR) * 4 + (lane >> 3);
+    const bool inside = px < vd.W && py < vd.H;
+    const uint2 r = ranges[gt];
+    const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+
+    uint32_t nl = 0;
+    float Th = 1.f, Tl = 0.f, d0 = 0.f, d1 = 0.f, d2 = 0.f;
+    if (inside) {
+        const int64_t pix = vd.pix_base + (int64_t)py * vd.W + px;
+        nl = nlast[pix];
+        Th = tfinal[pix];
+        d0 = dl[3 * pix]; d1 = dl[3 * pix + 1]; d2 = dl[3 * pix + 2];
+    }
+    float S0 = 0.f, S1 = 0.f, S2 = 0.f;
+    if (bg) { S0 = Th * bg[0]; S1 = Th * bg[1]; S2 = Th * bg[2]; }
+    int m = (int)nl;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) smax[w] = m;
+    __syncthreads();
+    int L = 0;
+#pragma unroll
+    for (int i = 0; i < NW; i++) L = max(L, smax[i]);
+    L = min(L, (int)(r.y - r.x));
+
+    for (int bb = ((L + BS - 1) / BS - 1) * BS; bb >= 0; bb -= BS) {
+        const int cnt = min(BS, L - bb);
+        __syncthreads();
+        if (tid < cnt) {
+            const uint32_t k = r.x + bb + tid;
+            const ProjRec q = rec[pid_sorted[k]];
+            sA[tid] = q.a;
+            sB[tid] = q.b;
+            sC[tid] = q.c.x;
+            sE[tid] = vals_sorted[k];
+        }
+        __syncthreads();
+        for (int c = (cnt - 1) >> 5; c >= 0; c--) {
+            float acc[9];
+#pragma unroll
+            for (int i = 0; i < 9; i++) acc[i] = 0.f;
+            const int jtop = min(31, cnt - 1 - 32 * c);
+            for (int jj = jtop; jj >= 0; jj--) {
+                const int j = 32 * c + jj;
+                float g[9];
+#pragma unroll
+                for (int i = 0; i < 9; i++) g[i] = 0.f;
+                bool hit = false;
+                if (bb + j < (int)nl) {
+                    const float4 a = sA[j];
+                    const float4 b = sB[j];
+                    const float dx = fx - a.x, dy = fy - a.y;
+                    const float power = pair_power(dx, dy, a.z, a.w, b.x);
+                    if (power >= -4.5f) {
+                        const float G = __expf(power);
+                        const float araw = __fmul_rn(b.y, G);
+                        const float alpha = fminf(kAlphaMax, araw);
+                        if (alpha >= kAlphaMin) {
+                            hit = true;
+                            const float cb = sC[j];
+                            // compensated T_before = (Th + Tl) / (1 - alpha)
+                            const float om = __fsub_rn(1.0f, alpha);
+                            const float om_err = __fsub_rn(-alpha, __fsub_rn(om, 1.0f));
+                            const float rom = __frcp_rn(om);
+                            const float q = Th * rom;
+                            const float rem = __fmaf_rn(-q, om, Th);
+                            const float lo = (rem + Tl - q * om_err) * rom;
+                            const float hi = q + lo;
+                            Tl = lo - (hi - q);
+                            Th = hi;
+                            const float wgt = alpha * Th;
+                            g[6] = wgt * d0;
+                            g[7] = wgt * d1;
+                            g[8] = wgt * d2;
+                            float da = d0 * fmaf(b.z, Th, -S0 * rom);
+                            da = fmaf(d1, fmaf(b.w, Th, -S1 * rom), da);
+                            da = fmaf(d2, fmaf(cb, Th, -S2 * rom), da);
+                            S0 = fmaf(b.z, wgt, S0);
+                            S1 = fmaf(b.w, wgt, S1);
+                            S2 = fmaf(cb, wgt, S2);
+                            if (araw <= kAlphaMax) {
+                                g[5] = da * G;
+                                const float dp = da * araw;
+                                g[2] = -0.5f * dx * dx * dp;
+                                g[3] = -dx * dy * dp;
+                                g[4] = -0.5f * dy * dy * dp;
+                                g[0] = fmaf(a.z, dx, a.w * dy) * dp;
+                                g[1] = fmaf(a.w, dx, b.x * dy) * dp;
+                            }
+                        }
+                    }
+                }
+                if (__any_sync(0xffffffffu, hit)) {
+#pragma unroll
+                    for (int i = 0; i < 9; i++) {
+                        float x = g[i];
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                        if (lane == jj) acc[i] = x;
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 9; i++) part[w][lane][i] = acc[i];
+            __syncthreads();
+            for (int t = tid; t < 32 * 9; t += BS) {
+                const int gi = t / 9, comp = t % 9;
+                const int j = 32 * c + gi;
+                if (j < cnt) {
+                    float s = 0.f;
+#pragma unroll
+                    for (int i = 0; i < NW; i++) s += part[i][gi][comp];
+                    float* dst = reinterpret_cast<float*>(gradrec + sE[j]);
+                    dst[comp < 8 ? comp : 8] = s;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // entries past every pixel's last blended pair receive zero gradients
+    for (uint32_t k = r.x + (uint32_t)L + tid; k < r.y; k += BS) {
+        GradRec o;
+        o.a = o.b = o.c = make_float4(0.f, 0.f, 0.f, 0.f);
+        gradrec[vals_sorted[k]] = o;
+    }
+}
+
+void launch_raster_bwd_px(const Plan& P, const WsPtrs& w, const float* bg, const float* dl, cudaStream_t st)
+{
+    const Views& V = P.views;
+    const unsigned grid = (unsigned)V.tiles;
+#define GS_RBP(BS, TW) k_raster_bwd_px<BS, TW><<<grid, BS, 0, st>>>(V, w.ranges, w.vals_sorted, w.pid_sorted, \
+                                                                   w.rec, w.tfinal, bg, dl, w.nlast, w.gradrec)
+    if (V.tw == 8) GS_RBP(64, 8);
+    else if (V.th == 16) GS_RBP(256, 16);
+    else GS_RBP(512, 16);
+#undef GS_RBP
 }
 
 }  // namespace gs

@@ -81,6 +81,7 @@ __global__ void __launch_bounds__(BS) k_raster_fwd(Views V, const uint2* __restr
             }
         }
     }
+    if (gt == 0 && threadIdx.x < 3) hdr->bg[threadIdx.x] = bg ? bg[threadIdx.x] : 0.f;
     if (inside) {
         const int64_t pix = vd.pix_base + (int64_t)py * vd.W + px;
         const float T = Th + Tl;

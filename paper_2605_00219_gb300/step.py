@@ -73,13 +73,14 @@ class Trainer:
     """One plan + workspace; runs the step over `cameras` (each with .scene)."""
 
     def __init__(self, scenes, cameras, capacity: int = 0, tile=(16, 16), bwd_batch: int = 0,
-                 sh_bf16: bool = False, mom_bf16: bool = False, bg=None, lr=DEFAULT_LR, device="cuda"):
+                 sh_bf16: bool = False, mom_bf16: bool = False, bg=None, lr=DEFAULT_LR, device="cuda",
+                 bwd_impl: int = 0):
         self.device = torch.device(device)
         self.scenes = [s if isinstance(s, SceneBuffers) else
                        SceneBuffers.from_scene(s, device, sh_bf16, mom_bf16) for s in scenes]
         flags = (gsstep.STORE_SH_BF16 if sh_bf16 else 0) | (gsstep.STORE_MOMENTS_BF16 if mom_bf16 else 0)
         self.plan = gsstep.Plan([s.n for s in self.scenes], [(c.width, c.height, c.scene) for c in cameras],
-                                capacity, tile, bwd_batch, flags)
+                                capacity, tile, bwd_batch, flags, bwd_impl)
         self.ws = torch.empty(self.plan.workspace_bytes(), dtype=torch.uint8, device=self.device)
         self.cams = torch.from_numpy(camera_params(cameras)).to(self.device)
         P = self.plan.pixels

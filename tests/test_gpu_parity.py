@@ -51,8 +51,9 @@ def _unstable_gaussians(P, r, cam):
     return bad
 
 
-def _run_forward(step_mod, scene, cams, tile=(16, 16), bwd_batch=0, bg=None, capacity=0):
-    tr = step_mod.Trainer([scene], cams, capacity=capacity, tile=tile, bwd_batch=bwd_batch, bg=bg, lr=LR)
+def _run_forward(step_mod, scene, cams, tile=(16, 16), bwd_batch=0, bg=None, capacity=0, bwd_impl=0):
+    tr = step_mod.Trainer([scene], cams, capacity=capacity, tile=tile, bwd_batch=bwd_batch, bg=bg, lr=LR,
+                          bwd_impl=bwd_impl)
     tr.forward()
     torch.cuda.synchronize()
     return tr
@@ -78,14 +79,15 @@ def _check_grad(gpu, ref, mask, name, tol=1e-3):
     return worst
 
 
-@pytest.mark.parametrize("seed", [0, 1])
-def test_tiny_stages(gs, orc, seed):
-    """2,000 Gaussians, 128x128: every stage against the oracle."""
+@pytest.mark.parametrize("seed,bwd_impl", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_tiny_stages(gs, orc, seed, bwd_impl):
+    """2,000 Gaussians, 128x128: every stage against the oracle (both
+    raster-backward implementations)."""
     gsstep, step_mod = gs
     scene, tscene, cams = synth.tiny_workload(seed)
     cam = cams[0]
     b, p, P, r = _oracle_all(orc, scene, cam, (16, 16))
-    tr = _run_forward(step_mod, scene, cams)
+    tr = _run_forward(step_mod, scene, cams, bwd_impl=bwd_impl)
     n = scene.n
     # --- projection: counts bit-exact, means/depth bit-exact, conic/colour close
     count = tr.buffer(0, n).cpu().numpy().view(np.uint32)
@@ -177,16 +179,17 @@ def test_tiny_full_step_adam(gs, orc):
     assert np.all(diff[zero] <= tol[zero])
 
 
-@pytest.mark.parametrize("tile,bwd_batch", [((16, 16), 0), ((8, 8), 0), ((16, 32), 0), ((16, 16), 32),
-                                            ((16, 16), 64), ((16, 16), 96)])
-def test_ragged_tiles_and_batches(gs, orc, tile, bwd_batch):
+@pytest.mark.parametrize("tile,bwd_batch,bwd_impl", [((16, 16), 0, 1), ((8, 8), 0, 1), ((16, 32), 0, 1),
+                                                     ((16, 16), 32, 1), ((16, 16), 64, 1), ((16, 16), 96, 1),
+                                                     ((16, 16), 0, 0), ((8, 8), 0, 0), ((16, 32), 0, 0)])
+def test_ragged_tiles_and_batches(gs, orc, tile, bwd_batch, bwd_impl):
     """Non-multiple image size (ragged tile tail), all tile shapes, fixed and
     adaptive backward batch sizes: keys bit-exact, images and gradients."""
     gsstep, step_mod = gs
     scene = synth.cluster_scene(20000, 16, 3.0, seed=7, log_scale=(-3.5, 0.5), logit_opacity=(0.0, 1.5))
     cam = synth.look_at([0, -6, 2], [0, 0, 0], 203, 149, 180.0)
     b, p, P, r = _oracle_all(orc, scene, cam, tile)
-    tr = _run_forward(step_mod, scene, [cam], tile=tile, bwd_batch=bwd_batch)
+    tr = _run_forward(step_mod, scene, [cam], tile=tile, bwd_batch=bwd_batch, bwd_impl=bwd_impl)
     n = scene.n
     keys = tr.buffer(2, b.K).cpu().numpy().view(np.uint32)
     np.testing.assert_array_equal(keys, b.keys)
@@ -204,19 +207,33 @@ def test_ragged_tiles_and_batches(gs, orc, tile, bwd_batch):
     gr = tr.buffer(8, b.K * 12, torch.float32).cpu().numpy().reshape(b.K, 12)
     g2_gpu = _sum_slots(gr, off, count)
     good = (b.count > 0) & ~_unstable_gaussians(P, r, cam)
-    _check_grad(g2_gpu, g2_orc, good, f"grad2d {tile} S={bwd_batch}")
+    _check_grad(g2_gpu, g2_orc, good, f"grad2d {tile} S={bwd_batch} impl={bwd_impl}")
 
 
-def test_background_colour(gs, orc):
+@pytest.mark.parametrize("bwd_impl", [0, 1])
+def test_background_colour(gs, orc, bwd_impl):
+    """Non-black background: image, and gradients (the background enters
+    every dL/d alpha through the colour still to come)."""
     gsstep, step_mod = gs
     scene, _, cams = synth.tiny_workload(2)
     cam = cams[0]
     bg = (0.25, 0.5, 0.75)
     b, p, P, r = _oracle_all(orc, scene, cam, (16, 16), bg=bg)
-    tr = _run_forward(step_mod, scene, cams, bg=bg)
+    tr = _run_forward(step_mod, scene, cams, bg=bg, bwd_impl=bwd_impl)
     img = tr.image.view(128, 128, 3).cpu().numpy().astype(np.float64)
     ok = ~r.unstable_px
     assert np.abs(img - r.image)[ok].max() <= 1e-5
+    rng = np.random.default_rng(4)
+    dl64 = rng.normal(size=(128, 128, 3)).astype(np.float32).astype(np.float64) / (3 * 128 * 128)
+    tr.dl.copy_(torch.from_numpy(dl64.astype(np.float32).reshape(-1, 3)))
+    gsstep.gs_raster_bwd(tr.plan, tr.ws, tr.image, tr.dl)
+    g2_orc = orc.raster_bwd64(cam, P, b, dl64, bg)
+    n = scene.n
+    count = tr.buffer(0, n).cpu().numpy().view(np.uint32)
+    off = tr.buffer(1, n + 1).cpu().numpy().view(np.uint32).astype(np.int64)
+    gr = tr.buffer(8, b.K * 12, torch.float32).cpu().numpy().reshape(b.K, 12)
+    good = (b.count > 0) & ~_unstable_gaussians(P, r, cam)
+    _check_grad(_sum_slots(gr, off, count), g2_orc, good, f"grad2d bg impl={bwd_impl}")
 
 
 def test_multi_view_uneven(gs, orc):
