@@ -275,6 +275,30 @@ __device__ __forceinline__ float pair_power(float dx, float dy, float ca, float 
     return __fmaf_rn(-0.5f, q, -__fmul_rn(cb, __fmul_rn(dx, dy)));
 }
 
+// Conservative mask of the 8x4-pixel warp blocks of a tile (WPR blocks per
+// row, RPB rows of blocks) that the 3-sigma box of a Gaussian (mean, conic)
+// can touch.  (ox, oy) is the tile's first pixel.  Pairs in a masked-out block
+// have d^2 > 9 with a margin, so skipping them changes no result.
+__device__ __forceinline__ uint32_t warp_block_mask(float mx, float my, float ca, float cb, float cc, int ox, int oy,
+                                                    int WPR, int RPB)
+{
+    const float det = ca * cc - cb * cb;
+    if (!(det > 0.0f)) return 0xffffffffu;
+    const float ex = fmaf(3.0f * 1.001f, sqrtf(cc / det), 0.01f);
+    const float ey = fmaf(3.0f * 1.001f, sqrtf(ca / det), 0.01f);
+    // pixel-centre coordinates relative to the tile's first centre
+    const float xl = fminf(fmaxf(mx - ex - ((float)ox + 0.5f), -1e4f), 1e4f);
+    const float xh = fminf(fmaxf(mx + ex - ((float)ox + 0.5f), -1e4f), 1e4f);
+    const float yl = fminf(fmaxf(my - ey - ((float)oy + 0.5f), -1e4f), 1e4f);
+    const float yh = fminf(fmaxf(my + ey - ((float)oy + 0.5f), -1e4f), 1e4f);
+    const int bx0 = max(0, (int)ceilf((xl - 7.0f) * 0.125f)), bx1 = min(WPR - 1, (int)floorf(xh * 0.125f));
+    const int by0 = max(0, (int)ceilf((yl - 3.0f) * 0.25f)), by1 = min(RPB - 1, (int)floorf(yh * 0.25f));
+    uint32_t m = 0;
+    for (int by = by0; by <= by1; by++)
+        for (int bx = bx0; bx <= bx1; bx++) m |= 1u << (by * WPR + bx);
+    return m;
+}
+
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTMin = 1e-4f;

@@ -29,11 +29,24 @@ __device__ __forceinline__ void adam1(float& th, float& m, float& v, float g, fl
     th -= lr * (m * ibc1) / (sqrtf(v * ibc2) + eps);
 }
 
-// Per-view backward of one Gaussian: adds to dmu, dq, ds (activated scale),
-// dop (activated opacity) and dsh.
+// SH coefficient chunk j (flat indices 4j..4j+3) of Gaussian g.
+__device__ __forceinline__ float4 sh_chunk(const SceneDesc& sc, int bf16, int64_t g, int j)
+{
+    if (!bf16) return reinterpret_cast<const float4*>(sc.sh)[(int64_t)j * sc.n + g];
+    const uint4 c = reinterpret_cast<const uint4*>(sc.sh)[(int64_t)(j >> 1) * sc.n + g];
+    const uint32_t u0 = (j & 1) ? c.z : c.x, u1 = (j & 1) ? c.w : c.y;
+    return make_float4(bf16_lo(u0), bf16_hi(u0), bf16_lo(u1), bf16_hi(u1));
+}
+
+// Per-view backward of one Gaussian through projection and colour:
+// accumulates dmu, dq, ds (activated scale) and dop (activated opacity), and
+// returns the SH basis at the view direction (Y) and dL/d(raw colour) (draw)
+// so that the SH gradient sum_v Y_v[k] draw_v[c] can be formed later.  The
+// SH coefficients are streamed twice (clamp test, then the direction
+// gradient) instead of being held in registers.
 __device__ __forceinline__ void proj_bwd_view(const float* cam, int W, int H, float4 mu, float4 q, float4 so,
-                                              const float* shv, const float* g2, float* dmu, float* dq, float* ds,
-                                              float& dop, float* dsh)
+                                              const SceneDesc& sc, int bf16, int64_t g, const float* g2,
+                                              float* dmu, float* dq, float* ds, float& dop, float* Y, float* draw)
 {
     const float fx = cam[12], fy = cam[13];
     const float* C = cam;
@@ -49,23 +62,26 @@ __device__ __forceinline__ void proj_bwd_view(const float* cam, int W, int H, fl
     const float ddx = mu.x - cpx, ddy = mu.y - cpy, ddz = mu.z - cpz;
     const float idist = rsqrtf(ddx * ddx + ddy * ddy + ddz * ddz);
     const float dirx = ddx * idist, diry = ddy * idist, dirz = ddz * idist;
-    float Y[16];
     sh_basis(dirx, diry, dirz, Y);
-    float draw[3];
+    float raw[3] = {0.5f, 0.5f, 0.5f};
 #pragma unroll
-    for (int c = 0; c < 3; c++) {
-        float acc = 0.5f;
+    for (int j = 0; j < 12; j++) {
+        const float4 c4 = sh_chunk(sc, bf16, g, j);
+        const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
-        for (int k = 0; k < 16; k++) acc = fmaf(shv[3 * k + c], Y[k], acc);
-        draw[c] = acc < 0.0f ? 0.0f : g2[6 + c];
+        for (int i = 0; i < 4; i++) raw[(4 * j + i) % 3] = fmaf(cv[i], Y[(4 * j + i) / 3], raw[(4 * j + i) % 3]);
     }
+#pragma unroll
+    for (int c = 0; c < 3; c++) draw[c] = raw[c] < 0.0f ? 0.0f : g2[6 + c];
     float wk[16];
 #pragma unroll
-    for (int k = 0; k < 16; k++) {
-        dsh[3 * k + 0] = fmaf(Y[k], draw[0], dsh[3 * k + 0]);
-        dsh[3 * k + 1] = fmaf(Y[k], draw[1], dsh[3 * k + 1]);
-        dsh[3 * k + 2] = fmaf(Y[k], draw[2], dsh[3 * k + 2]);
-        wk[k] = shv[3 * k] * draw[0] + shv[3 * k + 1] * draw[1] + shv[3 * k + 2] * draw[2];
+    for (int k = 0; k < 16; k++) wk[k] = 0.f;
+#pragma unroll
+    for (int j = 0; j < 12; j++) {
+        const float4 c4 = sh_chunk(sc, bf16, g, j);
+        const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+        for (int i = 0; i < 4; i++) wk[(4 * j + i) / 3] = fmaf(cv[i], draw[(4 * j + i) % 3], wk[(4 * j + i) / 3]);
     }
     float gdx, gdy, gdz;
     sh_basis_vjp(dirx, diry, dirz, wk, gdx, gdy, gdz);
@@ -107,7 +123,6 @@ __device__ __forceinline__ void proj_bwd_view(const float* cam, int W, int H, fl
         T[k] = j00 * C[k] + j02 * C[6 + k];
         T[3 + k] = j11 * C[3 + k] + j12 * C[6 + k];
     }
-    // 2D covariance and its inverse (conic)
     float TS[6];
 #pragma unroll
     for (int i = 0; i < 2; i++)
@@ -181,6 +196,9 @@ __device__ __forceinline__ void proj_bwd_view(const float* cam, int W, int H, fl
     dq[3] += (dqn[3] - z * dqq) * qn_r;
 }
 
+// MAXV: views of one scene whose (Y, draw) are kept for the SH update; a
+// scene with more views than MAXV uses the MAXV = kMaxViews instance.
+template <int MAXV>
 __global__ void __launch_bounds__(128) k_project_bwd_adam(Views V, Scenes S, const float* __restrict__ cams,
                                                           const uint32_t* __restrict__ count,
                                                           const uint32_t* __restrict__ offset,
@@ -198,14 +216,10 @@ __global__ void __launch_bounds__(128) k_project_bwd_adam(Views V, Scenes S, con
     float4 mu = sc.geom[g];
     float4 q = sc.geom[n + g];
     float4 so = sc.geom[2 * n + g];
-    float shv[48];
-    load_sh(sc, S.sh_bf16, g, shv);
 
     float dmu[3] = {0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f}, ds[3] = {0.f, 0.f, 0.f}, dop = 0.f;
-    float dsh[48];
-#pragma unroll
-    for (int i = 0; i < 48; i++) dsh[i] = 0.f;
-
+    float Yv[MAXV][16], drawv[MAXV][3];
+    int nvis = 0;
     for (int v = 0; v < V.n; v++) {
         const ViewDesc& vd = V.v[v];
         if (vd.scene != s) continue;
@@ -224,8 +238,24 @@ __global__ void __launch_bounds__(128) k_project_bwd_adam(Views V, Scenes S, con
         float cam[16];
 #pragma unroll
         for (int i = 0; i < 16; i++) cam[i] = __ldg(cams + 16 * v + i);
-        proj_bwd_view(cam, vd.W, vd.H, mu, q, so, shv, g2, dmu, dq, ds, dop, dsh);
+        float Y[16], draw[3];
+        proj_bwd_view(cam, vd.W, vd.H, mu, q, so, sc, S.sh_bf16, g, g2, dmu, dq, ds, dop, Y, draw);
+        if (nvis < MAXV) {
+#pragma unroll
+            for (int k = 0; k < 16; k++) Yv[nvis][k] = Y[k];
+            drawv[nvis][0] = draw[0]; drawv[nvis][1] = draw[1]; drawv[nvis][2] = draw[2];
+            nvis++;
+        }
     }
+
+    // SH gradient of flat coefficient f = 3k + c: sum over views of Y_v[k] draw_v[c]
+    auto dsh = [&](int f) {
+        float acc = 0.f;
+#pragma unroll
+        for (int i = 0; i < MAXV; i++)
+            if (i < nvis) acc = fmaf(Yv[i][f / 3], drawv[i][f % 3], acc);
+        return acc;
+    };
 
     if (A.grad_only) {
         float4* go = grads_out;
@@ -235,7 +265,7 @@ __global__ void __launch_bounds__(128) k_project_bwd_adam(Views V, Scenes S, con
         go[2 * N + gi] = make_float4(ds[0], ds[1], ds[2], dop);
 #pragma unroll
         for (int j = 0; j < 12; j++)
-            go[(3 + j) * N + gi] = make_float4(dsh[4 * j], dsh[4 * j + 1], dsh[4 * j + 2], dsh[4 * j + 3]);
+            go[(3 + j) * N + gi] = make_float4(dsh(4 * j), dsh(4 * j + 1), dsh(4 * j + 2), dsh(4 * j + 3));
         return;
     }
 
@@ -278,13 +308,14 @@ __global__ void __launch_bounds__(128) k_project_bwd_adam(Views V, Scenes S, con
     for (int j = 0; j < 12; j++) {
         const int64_t ci = (int64_t)(3 + j) * n + g;
         float4 m = m4[ci], vv = v4[ci];
-        float th[4] = {shv[4 * j], shv[4 * j + 1], shv[4 * j + 2], shv[4 * j + 3]};
+        const float4 c4 = s4[(int64_t)j * n + g];
+        float th[4] = {c4.x, c4.y, c4.z, c4.w};
         float* mp = &m.x;
         float* vp = &vv.x;
 #pragma unroll
         for (int i = 0; i < 4; i++) {
             const float lr = (4 * j + i) < 3 ? A.lr[4] : A.lr[5];
-            adam1(th[i], mp[i], vp[i], dsh[4 * j + i], lr, A.b1, A.b2, A.eps, ibc1, ibc2);
+            adam1(th[i], mp[i], vp[i], dsh(4 * j + i), lr, A.b1, A.b2, A.eps, ibc1, ibc2);
         }
         m4[ci] = m; v4[ci] = vv;
         s4[(int64_t)j * n + g] = make_float4(th[0], th[1], th[2], th[3]);
@@ -301,11 +332,20 @@ void launch_project_bwd_adam(const Plan& P, const Scenes& S, const float* cams, 
     A.eps = adam ? adam->eps : 1e-15f;
     A.step = adam ? adam->step : 1;
     A.grad_only = grads_out != nullptr;
+    // views per scene decides how many (Y, draw) sets a thread keeps
+    int per_scene[kMaxScenes] = {0};
+    int maxv = 0;
+    for (int v = 0; v < P.views.n; v++) maxv = std::max(maxv, ++per_scene[P.views.v[v].scene]);
     const int T = 128;
     const int64_t blocks = (S.total + T - 1) / T;
-    k_project_bwd_adam<<<(unsigned)blocks, T, 0, st>>>(P.views, S, cams, w.count, w.offset, w.gradrec, A,
-                                                       reinterpret_cast<float4*>(grads_out), w.hdr,
-                                                       (uint32_t)P.cap);
+#define GS_PBA(MV) k_project_bwd_adam<MV><<<(unsigned)blocks, T, 0, st>>>(P.views, S, cams, w.count, w.offset, \
+                                                                     w.gradrec, A, reinterpret_cast<float4*>(grads_out), \
+                                                                     w.hdr, (uint32_t)P.cap)
+    if (maxv <= 1) GS_PBA(1);
+    else if (maxv <= 2) GS_PBA(2);
+    else if (maxv <= 4) GS_PBA(4);
+    else GS_PBA(kMaxViews);
+#undef GS_PBA
 }
 
 }  // namespace gs

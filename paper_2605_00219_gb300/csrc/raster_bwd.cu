@@ -353,7 +353,9 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint2* __re
     __shared__ float4 sB[BS];
     __shared__ float sC[BS];
     __shared__ uint32_t sE[BS];
+    __shared__ uint32_t sM[BS];
     __shared__ float part[NW][32][9];
+    constexpr int RPB = BS / TW / 4;
     __shared__ int smax[NW];
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -361,8 +363,10 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint2* __re
     const int v = view_of_tile(V, gt);
     const ViewDesc& vd = V.v[v];
     const int lt = (int)(gt - vd.tile_base);
-    const int px = (lt % vd.TX) * TW + (w % WPR) * 8 + (lane & 7);
-    const int py = (lt / vd.TX) * V.th + (w / WPR) * 4 + (lane >> 3);
+    const int ox = (lt % vd.TX) * TW, oy = (lt / vd.TX) * (BS / TW);
+    const int px = ox + (w % WPR) * 8 + (lane & 7);
+    const int py = oy + (w / WPR) * 4 + (lane >> 3);
+    const uint32_t wbit = 1u << w;
     const bool inside = px < vd.W && py < vd.H;
     const uint2 r = ranges[gt];
     const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
@@ -397,14 +401,18 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint2* __re
             sB[tid] = q.b;
             sC[tid] = q.c.x;
             sE[tid] = vals_sorted[k];
+            sM[tid] = warp_block_mask(q.a.x, q.a.y, q.a.z, q.a.w, q.b.x, ox, oy, WPR, RPB);
         }
         __syncthreads();
         for (int c = (cnt - 1) >> 5; c >= 0; c--) {
             float acc[9];
 #pragma unroll
             for (int i = 0; i < 9; i++) acc[i] = 0.f;
-            const int jtop = min(31, cnt - 1 - 32 * c);
-            for (int jj = jtop; jj >= 0; jj--) {
+            // entries of this chunk whose 3-sigma box touches this warp's block
+            uint32_t bits = __ballot_sync(0xffffffffu, 32 * c + lane < cnt && (sM[32 * c + lane] & wbit));
+            while (bits) {
+                const int jj = 31 - __clz(bits);
+                bits &= ~(1u << jj);
                 const int j = 32 * c + jj;
                 float g[9];
 #pragma unroll

@@ -2,17 +2,19 @@
 // pipeline, Table 2 "Rasterization Fwd"), and the L1 loss gradient
 // (Sec. 4.5, L1 term).
 //
-// One CTA per tile, one thread per pixel.  The tile's sorted list is staged
-// through shared memory one CTA-width chunk at a time (coalesced reads of the
-// sorted pair indices, then 48-byte record gathers); every pixel walks the
-// chunk from shared memory.  Transmittance is a compensated FP32 pair
+// One CTA per tile, one thread per pixel, each warp an 8x4 pixel block.  The
+// tile's sorted list is staged through shared memory one CTA-width chunk at a
+// time (coalesced reads of the sorted pair indices, then 48-byte record
+// gathers); with each entry the loader stores a mask of the warp blocks its
+// 3-sigma box touches, and each warp walks only its entries (ballot over 32
+// entries, then the set bits in order).  Transmittance is a compensated FP32 pair
 // (TwoProduct with fmaf, Fast2Sum renormalisation), so the product over
 // hundreds of factors keeps close to full FP32 accuracy.
 #include "gs_internal.cuh"
 
 namespace gs {
 
-template <int BS>
+template <int BS, int TW>
 __global__ void __launch_bounds__(BS) k_raster_fwd(Views V, const uint2* __restrict__ ranges,
                                                    const uint32_t* __restrict__ pid_sorted,
                                                    const ProjRec* __restrict__ rec, const float* __restrict__ bg,
@@ -22,14 +24,18 @@ __global__ void __launch_bounds__(BS) k_raster_fwd(Views V, const uint2* __restr
     __shared__ float4 sA[BS];
     __shared__ float4 sB[BS];
     __shared__ float sC[BS];
+    __shared__ uint32_t sM[BS];
     __shared__ unsigned long long sblend[BS / 32];
+    constexpr int WPR = TW / 8, RPB = BS / TW / 4;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t wbit = 1u << w;
     const int64_t gt = blockIdx.x;
     const int v = view_of_tile(V, gt);
     const ViewDesc& vd = V.v[v];
     const int lt = (int)(gt - vd.tile_base);
-    const int tx = lt % vd.TX, ty = lt / vd.TX;
-    const int px = tx * V.tw + (int)threadIdx.x % V.tw;
-    const int py = ty * V.th + (int)threadIdx.x / V.tw;
+    const int ox = (lt % vd.TX) * TW, oy = (lt / vd.TX) * (BS / TW);
+    const int px = ox + (w % WPR) * 8 + (lane & 7);
+    const int py = oy + (w / WPR) * 4 + (lane >> 3);
     const bool inside = px < vd.W && py < vd.H;
     const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
     const uint2 r = ranges[gt];
@@ -46,11 +52,16 @@ __global__ void __launch_bounds__(BS) k_raster_fwd(Views V, const uint2* __restr
             sA[threadIdx.x] = q.a;
             sB[threadIdx.x] = q.b;
             sC[threadIdx.x] = q.c.x;
+            sM[threadIdx.x] = warp_block_mask(q.a.x, q.a.y, q.a.z, q.a.w, q.b.x, ox, oy, WPR, RPB);
         }
         __syncthreads();
-        if (!done) {
-            const int cnt = (int)min((uint32_t)BS, r.y - base);
-            for (int j = 0; j < cnt; j++) {
+        const int cnt = (int)min((uint32_t)BS, r.y - base);
+        for (int c0 = 0; c0 < cnt; c0 += 32) {
+            uint32_t bits = __ballot_sync(0xffffffffu, c0 + lane < cnt && (sM[c0 + lane] & wbit));
+            if (done) continue;
+            while (bits) {
+                const int j = c0 + __ffs(bits) - 1;
+                bits &= bits - 1;
                 const float4 a = sA[j];
                 const float dx = fx - a.x, dy = fy - a.y;
                 const float4 b = sB[j];
@@ -111,11 +122,11 @@ void launch_raster_fwd(const Plan& P, const WsPtrs& w, const float* bg, float* i
     const Views& V = P.views;
     const int bs = V.tw * V.th;
     const unsigned grid = (unsigned)V.tiles;
-#define GS_RF(BS) k_raster_fwd<BS><<<grid, BS, 0, st>>>(V, w.ranges, w.pid_sorted, w.rec, bg, image, w.tfinal, \
-                                                        w.nlast, w.hdr)
-    if (bs == 64) GS_RF(64);
-    else if (bs == 256) GS_RF(256);
-    else GS_RF(512);
+#define GS_RF(BS, TW) k_raster_fwd<BS, TW><<<grid, BS, 0, st>>>(V, w.ranges, w.pid_sorted, w.rec, bg, image, \
+                                                                w.tfinal, w.nlast, w.hdr)
+    if (bs == 64) GS_RF(64, 8);
+    else if (bs == 256) GS_RF(256, 16);
+    else GS_RF(512, 16);
 #undef GS_RF
 }
 
