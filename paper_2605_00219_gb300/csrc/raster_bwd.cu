@@ -327,15 +327,55 @@ void launch_raster_bwd(const Plan& P, const WsPtrs& w, const float* image, const
 // small Gaussian touches few warps).  Every pixel walks its own list prefix
 // back to front from its last blended entry: T before an entry is recovered
 // by a compensated division of T after it by (1 - alpha), and the colour
-// still to come S grows from T_final * bg without cancellation.  For each
-// list entry the warp sums the nine gradients of its pixels with a butterfly
-// of shuffles, but only when at least one of its pixels blended the entry;
-// lane (entry mod 32) keeps the warp's sum, and after every 32 entries the
-// warps' sums are added in warp order and written to the entry's emission
-// slot.
+// still to come S grows from T_final * bg without cancellation.  The list is
+// staged BB entries at a time with a mask of the warp blocks each entry's
+// 3-sigma box touches; a warp visits only its entries, and for an entry that
+// at least one of its pixels blended it sums the nine gradients over its 32
+// pixels with a halving butterfly (12 shuffles; afterwards nine lanes each
+// hold one fully reduced value) into its own shared-memory slot.  After each
+// batch the warps' slots are added in warp order and written to each entry's
+// emission slot, so the result does not depend on scheduling.
 // ===========================================================================
 
 namespace gs {
+
+// Halving-butterfly reduction of nine per-lane values over a warp: returns
+// the lane's share of the result; `vi` (from bfly_index) says which of the
+// nine sums it is (-1: none).
+__device__ __forceinline__ float bfly9(const float* v, int lane)
+{
+    const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4, h1 = lane & 2;
+    float k[5];
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        const float lo = v[i], hi = i < 4 ? v[5 + i] : 0.f;
+        k[i] = (h4 ? hi : lo) + __shfl_xor_sync(0xffffffffu, h4 ? lo : hi, 16);
+    }
+    float m[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const float lo = k[i], hi = i < 2 ? k[3 + i] : 0.f;
+        m[i] = (h3 ? hi : lo) + __shfl_xor_sync(0xffffffffu, h3 ? lo : hi, 8);
+    }
+    float nn[2];
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        const float lo = m[i], hi = i < 1 ? m[2 + i] : 0.f;
+        nn[i] = (h2 ? hi : lo) + __shfl_xor_sync(0xffffffffu, h2 ? lo : hi, 4);
+    }
+    float p = (h1 ? nn[1] : nn[0]) + __shfl_xor_sync(0xffffffffu, h1 ? nn[0] : nn[1], 2);
+    return p + __shfl_xor_sync(0xffffffffu, p, 1);
+}
+
+__device__ __forceinline__ int bfly_index(int lane)
+{
+    if (lane & 1) return -1;
+    const int mi = ((lane & 4) ? 2 : 0) + ((lane & 2) ? 1 : 0);
+    if (mi == 3) return -1;
+    const int ki = (lane & 8) ? (mi < 2 ? 3 + mi : -1) : mi;
+    if (ki < 0) return -1;
+    return (lane & 16) ? (ki < 4 ? 5 + ki : -1) : ki;
+}
 
 template <int BS, int TW>
 __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint2* __restrict__ ranges,
@@ -348,14 +388,16 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint2* __re
                                                       GradRec* __restrict__ gradrec)
 {
     constexpr int NW = BS / 32;
-    constexpr int WPR = TW / 8;   // 8x4 warp blocks per tile row
-    __shared__ float4 sA[BS];
-    __shared__ float4 sB[BS];
-    __shared__ float sC[BS];
-    __shared__ uint32_t sE[BS];
-    __shared__ uint32_t sM[BS];
-    __shared__ float part[NW][32][9];
-    constexpr int RPB = BS / TW / 4;
+    constexpr int WPR = TW / 8;            // 8x4 warp blocks per tile row
+    constexpr int RPB = BS / TW / 4;       // rows of warp blocks
+    constexpr int BB = NW <= 8 ? 128 : 64; // list entries per staged batch
+    __shared__ float4 sA[BB];
+    __shared__ float4 sB[BB];
+    __shared__ float sC[BB];
+    __shared__ uint32_t sE[BB];
+    __shared__ uint32_t sM[BB];
+    __shared__ float part[NW][BB][9];
+    __shared__ uint32_t pmask[NW][BB / 32];
     __shared__ int smax[NW];
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -370,6 +412,7 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint2* __re
     const bool inside = px < vd.W && py < vd.H;
     const uint2 r = ranges[gt];
     const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+    const int vi = bfly_index(lane);
 
     uint32_t nl = 0;
     float Th = 1.f, Tl = 0.f, d0 = 0.f, d1 = 0.f, d2 = 0.f;
@@ -381,35 +424,33 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint2* __re
     }
     float S0 = 0.f, S1 = 0.f, S2 = 0.f;
     if (bg) { S0 = Th * bg[0]; S1 = Th * bg[1]; S2 = Th * bg[2]; }
-    int m = (int)nl;
+    int mx_nl = (int)nl;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) smax[w] = m;
+    for (int o = 16; o > 0; o >>= 1) mx_nl = max(mx_nl, __shfl_xor_sync(0xffffffffu, mx_nl, o));
+    if (lane == 0) smax[w] = mx_nl;
     __syncthreads();
     int L = 0;
 #pragma unroll
     for (int i = 0; i < NW; i++) L = max(L, smax[i]);
     L = min(L, (int)(r.y - r.x));
 
-    for (int bb = ((L + BS - 1) / BS - 1) * BS; bb >= 0; bb -= BS) {
-        const int cnt = min(BS, L - bb);
+    for (int bb = ((L + BB - 1) / BB - 1) * BB; bb >= 0; bb -= BB) {
+        const int cnt = min(BB, L - bb);
         __syncthreads();
-        if (tid < cnt) {
-            const uint32_t k = r.x + bb + tid;
+        for (int i = tid; i < cnt; i += BS) {  // BB may exceed the CTA width
+            const uint32_t k = r.x + bb + i;
             const ProjRec q = rec[pid_sorted[k]];
-            sA[tid] = q.a;
-            sB[tid] = q.b;
-            sC[tid] = q.c.x;
-            sE[tid] = vals_sorted[k];
-            sM[tid] = warp_block_mask(q.a.x, q.a.y, q.a.z, q.a.w, q.b.x, ox, oy, WPR, RPB);
+            sA[i] = q.a;
+            sB[i] = q.b;
+            sC[i] = q.c.x;
+            sE[i] = vals_sorted[k];
+            sM[i] = warp_block_mask(q.a.x, q.a.y, q.a.z, q.a.w, q.b.x, ox, oy, WPR, RPB);
         }
         __syncthreads();
         for (int c = (cnt - 1) >> 5; c >= 0; c--) {
-            float acc[9];
-#pragma unroll
-            for (int i = 0; i < 9; i++) acc[i] = 0.f;
             // entries of this chunk whose 3-sigma box touches this warp's block
             uint32_t bits = __ballot_sync(0xffffffffu, 32 * c + lane < cnt && (sM[32 * c + lane] & wbit));
+            uint32_t done_bits = 0;
             while (bits) {
                 const int jj = 31 - __clz(bits);
                 bits &= ~(1u << jj);
@@ -463,30 +504,22 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint2* __re
                     }
                 }
                 if (__any_sync(0xffffffffu, hit)) {
-#pragma unroll
-                    for (int i = 0; i < 9; i++) {
-                        float x = g[i];
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-                        if (lane == jj) acc[i] = x;
-                    }
+                    const float x = bfly9(g, lane);
+                    if (vi >= 0) part[w][j][vi] = x;
+                    done_bits |= 1u << jj;
                 }
             }
+            if (lane == 0) pmask[w][c] = done_bits;
+        }
+        __syncthreads();
+        // add the warps' partial sums in warp order; write each entry's record
+        for (int t = tid; t < cnt * 9; t += BS) {
+            const int j = t / 9, comp = t - 9 * j;
+            float s = 0.f;
 #pragma unroll
-            for (int i = 0; i < 9; i++) part[w][lane][i] = acc[i];
-            __syncthreads();
-            for (int t = tid; t < 32 * 9; t += BS) {
-                const int gi = t / 9, comp = t % 9;
-                const int j = 32 * c + gi;
-                if (j < cnt) {
-                    float s = 0.f;
-#pragma unroll
-                    for (int i = 0; i < NW; i++) s += part[i][gi][comp];
-                    float* dst = reinterpret_cast<float*>(gradrec + sE[j]);
-                    dst[comp < 8 ? comp : 8] = s;
-                }
-            }
-            __syncthreads();
+            for (int i = 0; i < NW; i++)
+                if ((pmask[i][j >> 5] >> (j & 31)) & 1u) s += part[i][j][comp];
+            reinterpret_cast<float*>(gradrec + sE[j])[comp] = s;
         }
     }
     // entries past every pixel's last blended pair receive zero gradients
