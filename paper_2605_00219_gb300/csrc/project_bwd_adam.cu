@@ -19,6 +19,7 @@ struct AdamArgs {
     float b1, b2, eps;
     int step;        // > 0: use it; otherwise the workspace counter + 1
     int grad_only;
+    uint32_t seed;   // stochastic rounding of bf16 storage
 };
 
 __device__ __forceinline__ void adam1(float& th, float& m, float& v, float g, float lr, float b1, float b2,
@@ -196,129 +197,210 @@ __device__ __forceinline__ void proj_bwd_view(const float* cam, int W, int H, fl
     dq[3] += (dqn[3] - z * dqq) * qn_r;
 }
 
-// MAXV: views of one scene whose (Y, draw) are kept for the SH update; a
-// scene with more views than MAXV uses the MAXV = kMaxViews instance.
-template <int MAXV>
-__global__ void __launch_bounds__(128) k_project_bwd_adam(Views V, Scenes S, const float* __restrict__ cams,
-                                                          const uint32_t* __restrict__ count,
-                                                          const uint32_t* __restrict__ offset,
-                                                          const GradRec* __restrict__ gradrec, AdamArgs A,
-                                                          float4* __restrict__ grads_out,
-                                                          const WsHeader* __restrict__ hdr, uint32_t cap)
+// Stochastic rounding to bf16 (storage form of SH and Adam moments): add a
+// 16-bit random number below the kept bits, then truncate.  The random bits
+// come from the MurmurHash3 32-bit finaliser applied to a counter built from
+// (seed, step, element), so the rounding is reproducible.
+__device__ __forceinline__ uint32_t fmix32(uint32_t x)
 {
-    const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    x ^= x >> 16;
+    x *= 0x85ebca6bu;
+    x ^= x >> 13;
+    x *= 0xc2b2ae35u;
+    x ^= x >> 16;
+    return x;
+}
+
+__device__ __forceinline__ uint32_t bf16_sr(float f, uint32_t rnd)
+{
+    uint32_t u = __float_as_uint(f);
+    if ((u & 0x7f800000u) != 0x7f800000u) u += rnd & 0xFFFFu;
+    return u >> 16;
+}
+
+__device__ __forceinline__ uint32_t sr_rand(uint32_t seed, int step, uint32_t stream, int64_t elem)
+{
+    return fmix32(seed ^ fmix32((uint32_t)step * 0x9E3779B9u ^ fmix32(stream * 0x85ebca6bu ^ (uint32_t)elem ^
+                                                                      (uint32_t)(elem >> 32) * 0xc2b2ae35u)));
+}
+
+// Moment chunk ci (4 values) of Gaussian g: FP32 float4 or 4 x bf16.
+template <bool MOM16>
+__device__ __forceinline__ float4 load_mom(const void* base, int64_t idx)
+{
+    if (!MOM16) return reinterpret_cast<const float4*>(base)[idx];
+    const uint2 u = reinterpret_cast<const uint2*>(base)[idx];
+    return make_float4(bf16_lo(u.x), bf16_hi(u.x), bf16_lo(u.y), bf16_hi(u.y));
+}
+
+template <bool MOM16>
+__device__ __forceinline__ void store_mom(void* base, int64_t idx, float4 m, uint32_t seed, int step,
+                                          uint32_t stream)
+{
+    if (!MOM16) {
+        reinterpret_cast<float4*>(base)[idx] = m;
+        return;
+    }
+    const int64_t e = 4 * idx;
+    const uint32_t a = bf16_sr(m.x, sr_rand(seed, step, stream, e));
+    const uint32_t b = bf16_sr(m.y, sr_rand(seed, step, stream, e + 1));
+    const uint32_t c = bf16_sr(m.z, sr_rand(seed, step, stream, e + 2));
+    const uint32_t d = bf16_sr(m.w, sr_rand(seed, step, stream, e + 3));
+    reinterpret_cast<uint2*>(base)[idx] = make_uint2(a | (b << 16), c | (d << 16));
+}
+
+constexpr int kPbaThreads = 128;
+
+// Phase 1 (one thread per Gaussian): sum the intersection records per view,
+// back-propagate through projection and colour, apply Adam to mean,
+// quaternion and (log-scale, logit-opacity); the 48 SH gradients accumulate
+// in the thread's own column of shared memory.  Phase 2: Adam on the SH
+// chunks, streaming coefficients and moments with few live registers.
+template <bool SH16, bool MOM16>
+__global__ void __launch_bounds__(kPbaThreads, 4) k_project_bwd_adam(Views V, Scenes S, const float* __restrict__ cams,
+                                                                  const uint32_t* __restrict__ count,
+                                                                  const uint32_t* __restrict__ offset,
+                                                                  const GradRec* __restrict__ gradrec, AdamArgs A,
+                                                                  float4* __restrict__ grads_out,
+                                                                  const WsHeader* __restrict__ hdr, uint32_t cap)
+{
+    __shared__ float sG[48][kPbaThreads];
+    const int tid = threadIdx.x;
+    const int64_t gi = (int64_t)blockIdx.x * kPbaThreads + tid;
+    const int t = A.step > 0 ? A.step : hdr->step + 1;
+#pragma unroll
+    for (int f = 0; f < 48; f++) sG[f][tid] = 0.f;
+
+    if (gi < S.total) {
+        int s = 0;
+        while (s + 1 < S.n && S.s[s + 1].base <= gi) s++;
+        const SceneDesc& sc = S.s[s];
+        const int64_t g = gi - sc.base;
+        const int64_t n = sc.n;
+        float4 mu = sc.geom[g];
+        float4 q = sc.geom[n + g];
+        float4 so = sc.geom[2 * n + g];
+        float dmu[3] = {0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f}, ds[3] = {0.f, 0.f, 0.f}, dop = 0.f;
+        for (int v = 0; v < V.n; v++) {
+            const ViewDesc& vd = V.v[v];
+            if (vd.scene != s) continue;
+            const int64_t p = vd.pair_base + g;
+            const uint32_t cnt = count[p];
+            if (cnt == 0) continue;
+            const uint32_t off = offset[p];
+            const uint32_t end = min(off + cnt, cap);
+            float g2[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            for (uint32_t e = off; e < end; e++) {
+                const GradRec r = gradrec[e];
+                g2[0] += r.a.x; g2[1] += r.a.y; g2[2] += r.a.z; g2[3] += r.a.w;
+                g2[4] += r.b.x; g2[5] += r.b.y; g2[6] += r.b.z; g2[7] += r.b.w;
+                g2[8] += r.c.x;
+            }
+            float cam[16];
+#pragma unroll
+            for (int i = 0; i < 16; i++) cam[i] = __ldg(cams + 16 * v + i);
+            float Y[16], draw[3];
+            proj_bwd_view(cam, vd.W, vd.H, mu, q, so, sc, SH16 ? 1 : 0, g, g2, dmu, dq, ds, dop, Y, draw);
+#pragma unroll
+            for (int f = 0; f < 48; f++) sG[f][tid] = fmaf(Y[f / 3], draw[f % 3], sG[f][tid]);
+        }
+        if (A.grad_only) {
+            const int64_t N = S.total;
+            grads_out[0 * N + gi] = make_float4(dmu[0], dmu[1], dmu[2], 0.f);
+            grads_out[1 * N + gi] = make_float4(dq[0], dq[1], dq[2], dq[3]);
+            grads_out[2 * N + gi] = make_float4(ds[0], ds[1], ds[2], dop);
+        } else {
+            const float ibc1 = 1.0f / (1.0f - powf(A.b1, (float)t));
+            const float ibc2 = 1.0f / (1.0f - powf(A.b2, (float)t));
+            {
+                float4 m = load_mom<MOM16>(sc.m, g), vv = load_mom<MOM16>(sc.v, g);
+                adam1(mu.x, m.x, vv.x, dmu[0], A.lr[0], A.b1, A.b2, A.eps, ibc1, ibc2);
+                adam1(mu.y, m.y, vv.y, dmu[1], A.lr[0], A.b1, A.b2, A.eps, ibc1, ibc2);
+                adam1(mu.z, m.z, vv.z, dmu[2], A.lr[0], A.b1, A.b2, A.eps, ibc1, ibc2);
+                store_mom<MOM16>(sc.m, g, m, A.seed, t, 2u * s);
+                store_mom<MOM16>(sc.v, g, vv, A.seed, t, 2u * s + 1u);
+                sc.geom[g] = mu;
+            }
+            {
+                float4 m = load_mom<MOM16>(sc.m, n + g), vv = load_mom<MOM16>(sc.v, n + g);
+                adam1(q.x, m.x, vv.x, dq[0], A.lr[1], A.b1, A.b2, A.eps, ibc1, ibc2);
+                adam1(q.y, m.y, vv.y, dq[1], A.lr[1], A.b1, A.b2, A.eps, ibc1, ibc2);
+                adam1(q.z, m.z, vv.z, dq[2], A.lr[1], A.b1, A.b2, A.eps, ibc1, ibc2);
+                adam1(q.w, m.w, vv.w, dq[3], A.lr[1], A.b1, A.b2, A.eps, ibc1, ibc2);
+                store_mom<MOM16>(sc.m, n + g, m, A.seed, t, 2u * s);
+                store_mom<MOM16>(sc.v, n + g, vv, A.seed, t, 2u * s + 1u);
+                sc.geom[n + g] = q;
+            }
+            {
+                float4 m = load_mom<MOM16>(sc.m, 2 * n + g), vv = load_mom<MOM16>(sc.v, 2 * n + g);
+                float th0 = logf(so.x), th1 = logf(so.y), th2 = logf(so.z);
+                float tho = logf(so.w) - log1pf(-so.w);
+                adam1(th0, m.x, vv.x, ds[0] * so.x, A.lr[2], A.b1, A.b2, A.eps, ibc1, ibc2);
+                adam1(th1, m.y, vv.y, ds[1] * so.y, A.lr[2], A.b1, A.b2, A.eps, ibc1, ibc2);
+                adam1(th2, m.z, vv.z, ds[2] * so.z, A.lr[2], A.b1, A.b2, A.eps, ibc1, ibc2);
+                adam1(tho, m.w, vv.w, dop * so.w * (1.0f - so.w), A.lr[3], A.b1, A.b2, A.eps, ibc1, ibc2);
+                store_mom<MOM16>(sc.m, 2 * n + g, m, A.seed, t, 2u * s);
+                store_mom<MOM16>(sc.v, 2 * n + g, vv, A.seed, t, 2u * s + 1u);
+                sc.geom[2 * n + g] = make_float4(expf(th0), expf(th1), expf(th2), 1.0f / (1.0f + expf(-tho)));
+            }
+        }
+    }
+    // ---------------- Phase 2: SH chunks ----------------
     if (gi >= S.total) return;
     int s = 0;
     while (s + 1 < S.n && S.s[s + 1].base <= gi) s++;
     const SceneDesc& sc = S.s[s];
     const int64_t g = gi - sc.base;
     const int64_t n = sc.n;
-    float4 mu = sc.geom[g];
-    float4 q = sc.geom[n + g];
-    float4 so = sc.geom[2 * n + g];
-
-    float dmu[3] = {0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f}, ds[3] = {0.f, 0.f, 0.f}, dop = 0.f;
-    float Yv[MAXV][16], drawv[MAXV][3];
-    int nvis = 0;
-    for (int v = 0; v < V.n; v++) {
-        const ViewDesc& vd = V.v[v];
-        if (vd.scene != s) continue;
-        const int64_t p = vd.pair_base + g;
-        const uint32_t cnt = count[p];
-        if (cnt == 0) continue;
-        const uint32_t off = offset[p];
-        const uint32_t end = min(off + cnt, cap);
-        float g2[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        for (uint32_t e = off; e < end; e++) {
-            const GradRec r = gradrec[e];
-            g2[0] += r.a.x; g2[1] += r.a.y; g2[2] += r.a.z; g2[3] += r.a.w;
-            g2[4] += r.b.x; g2[5] += r.b.y; g2[6] += r.b.z; g2[7] += r.b.w;
-            g2[8] += r.c.x;
-        }
-        float cam[16];
-#pragma unroll
-        for (int i = 0; i < 16; i++) cam[i] = __ldg(cams + 16 * v + i);
-        float Y[16], draw[3];
-        proj_bwd_view(cam, vd.W, vd.H, mu, q, so, sc, S.sh_bf16, g, g2, dmu, dq, ds, dop, Y, draw);
-        if (nvis < MAXV) {
-#pragma unroll
-            for (int k = 0; k < 16; k++) Yv[nvis][k] = Y[k];
-            drawv[nvis][0] = draw[0]; drawv[nvis][1] = draw[1]; drawv[nvis][2] = draw[2];
-            nvis++;
-        }
-    }
-
-    // SH gradient of flat coefficient f = 3k + c: sum over views of Y_v[k] draw_v[c]
-    auto dsh = [&](int f) {
-        float acc = 0.f;
-#pragma unroll
-        for (int i = 0; i < MAXV; i++)
-            if (i < nvis) acc = fmaf(Yv[i][f / 3], drawv[i][f % 3], acc);
-        return acc;
-    };
-
     if (A.grad_only) {
-        float4* go = grads_out;
         const int64_t N = S.total;
-        go[0 * N + gi] = make_float4(dmu[0], dmu[1], dmu[2], 0.f);
-        go[1 * N + gi] = make_float4(dq[0], dq[1], dq[2], dq[3]);
-        go[2 * N + gi] = make_float4(ds[0], ds[1], ds[2], dop);
 #pragma unroll
         for (int j = 0; j < 12; j++)
-            go[(3 + j) * N + gi] = make_float4(dsh(4 * j), dsh(4 * j + 1), dsh(4 * j + 2), dsh(4 * j + 3));
+            grads_out[(3 + j) * N + gi] = make_float4(sG[4 * j][tid], sG[4 * j + 1][tid], sG[4 * j + 2][tid],
+                                                      sG[4 * j + 3][tid]);
         return;
     }
-
-    // ---- Adam (FP32 moments), theta = (mean, quat, log s, logit o, SH)
-    const int t = A.step > 0 ? A.step : hdr->step + 1;
     const float ibc1 = 1.0f / (1.0f - powf(A.b1, (float)t));
     const float ibc2 = 1.0f / (1.0f - powf(A.b2, (float)t));
-    float4* m4 = reinterpret_cast<float4*>(sc.m);
-    float4* v4 = reinterpret_cast<float4*>(sc.v);
-    {
-        float4 m = m4[g], vv = v4[g];
-        adam1(mu.x, m.x, vv.x, dmu[0], A.lr[0], A.b1, A.b2, A.eps, ibc1, ibc2);
-        adam1(mu.y, m.y, vv.y, dmu[1], A.lr[0], A.b1, A.b2, A.eps, ibc1, ibc2);
-        adam1(mu.z, m.z, vv.z, dmu[2], A.lr[0], A.b1, A.b2, A.eps, ibc1, ibc2);
-        m4[g] = m; v4[g] = vv;
-        sc.geom[g] = mu;
-    }
-    {
-        float4 m = m4[n + g], vv = v4[n + g];
-        adam1(q.x, m.x, vv.x, dq[0], A.lr[1], A.b1, A.b2, A.eps, ibc1, ibc2);
-        adam1(q.y, m.y, vv.y, dq[1], A.lr[1], A.b1, A.b2, A.eps, ibc1, ibc2);
-        adam1(q.z, m.z, vv.z, dq[2], A.lr[1], A.b1, A.b2, A.eps, ibc1, ibc2);
-        adam1(q.w, m.w, vv.w, dq[3], A.lr[1], A.b1, A.b2, A.eps, ibc1, ibc2);
-        m4[n + g] = m; v4[n + g] = vv;
-        sc.geom[n + g] = q;
-    }
-    {
-        float4 m = m4[2 * n + g], vv = v4[2 * n + g];
-        float th0 = logf(so.x), th1 = logf(so.y), th2 = logf(so.z);
-        float tho = logf(so.w) - log1pf(-so.w);
-        adam1(th0, m.x, vv.x, ds[0] * so.x, A.lr[2], A.b1, A.b2, A.eps, ibc1, ibc2);
-        adam1(th1, m.y, vv.y, ds[1] * so.y, A.lr[2], A.b1, A.b2, A.eps, ibc1, ibc2);
-        adam1(th2, m.z, vv.z, ds[2] * so.z, A.lr[2], A.b1, A.b2, A.eps, ibc1, ibc2);
-        adam1(tho, m.w, vv.w, dop * so.w * (1.0f - so.w), A.lr[3], A.b1, A.b2, A.eps, ibc1, ibc2);
-        m4[2 * n + g] = m; v4[2 * n + g] = vv;
-        sc.geom[2 * n + g] = make_float4(expf(th0), expf(th1), expf(th2), 1.0f / (1.0f + expf(-tho)));
-    }
-    float4* s4 = reinterpret_cast<float4*>(sc.sh);
-#pragma unroll
-    for (int j = 0; j < 12; j++) {
-        const int64_t ci = (int64_t)(3 + j) * n + g;
-        float4 m = m4[ci], vv = v4[ci];
-        const float4 c4 = s4[(int64_t)j * n + g];
-        float th[4] = {c4.x, c4.y, c4.z, c4.w};
-        float* mp = &m.x;
-        float* vp = &vv.x;
-#pragma unroll
-        for (int i = 0; i < 4; i++) {
-            const float lr = (4 * j + i) < 3 ? A.lr[4] : A.lr[5];
-            adam1(th[i], mp[i], vp[i], dsh(4 * j + i), lr, A.b1, A.b2, A.eps, ibc1, ibc2);
+#pragma unroll 2
+    for (int jp = 0; jp < 6; jp++) {          // pairs of chunks = 8 coefficients
+        float th[8];
+        if (!SH16) {
+            const float4 a = reinterpret_cast<const float4*>(sc.sh)[(int64_t)(2 * jp) * n + g];
+            const float4 b = reinterpret_cast<const float4*>(sc.sh)[(int64_t)(2 * jp + 1) * n + g];
+            th[0] = a.x; th[1] = a.y; th[2] = a.z; th[3] = a.w; th[4] = b.x; th[5] = b.y; th[6] = b.z; th[7] = b.w;
+        } else {
+            const uint4 c = reinterpret_cast<const uint4*>(sc.sh)[(int64_t)jp * n + g];
+            th[0] = bf16_lo(c.x); th[1] = bf16_hi(c.x); th[2] = bf16_lo(c.y); th[3] = bf16_hi(c.y);
+            th[4] = bf16_lo(c.z); th[5] = bf16_hi(c.z); th[6] = bf16_lo(c.w); th[7] = bf16_hi(c.w);
         }
-        m4[ci] = m; v4[ci] = vv;
-        s4[(int64_t)j * n + g] = make_float4(th[0], th[1], th[2], th[3]);
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int j = 2 * jp + h;
+            const int64_t ci = (int64_t)(3 + j) * n + g;
+            float4 m = load_mom<MOM16>(sc.m, ci), vv = load_mom<MOM16>(sc.v, ci);
+            float* mp = &m.x;
+            float* vp = &vv.x;
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                const int f = 4 * j + i;
+                adam1(th[4 * h + i], mp[i], vp[i], sG[f][tid], f < 3 ? A.lr[4] : A.lr[5], A.b1, A.b2, A.eps, ibc1,
+                      ibc2);
+            }
+            store_mom<MOM16>(sc.m, ci, m, A.seed, t, 2u * s);
+            store_mom<MOM16>(sc.v, ci, vv, A.seed, t, 2u * s + 1u);
+        }
+        if (!SH16) {
+            reinterpret_cast<float4*>(sc.sh)[(int64_t)(2 * jp) * n + g] = make_float4(th[0], th[1], th[2], th[3]);
+            reinterpret_cast<float4*>(sc.sh)[(int64_t)(2 * jp + 1) * n + g] = make_float4(th[4], th[5], th[6], th[7]);
+        } else {
+            uint32_t u[8];
+            const int64_t e = 8 * ((int64_t)jp * n + g);
+#pragma unroll
+            for (int i = 0; i < 8; i++) u[i] = bf16_sr(th[i], sr_rand(A.seed, t, 0x5348u + 2u * s, e + i));
+            reinterpret_cast<uint4*>(sc.sh)[(int64_t)jp * n + g] =
+                make_uint4(u[0] | (u[1] << 16), u[2] | (u[3] << 16), u[4] | (u[5] << 16), u[6] | (u[7] << 16));
+        }
     }
 }
 
@@ -332,19 +414,14 @@ void launch_project_bwd_adam(const Plan& P, const Scenes& S, const float* cams, 
     A.eps = adam ? adam->eps : 1e-15f;
     A.step = adam ? adam->step : 1;
     A.grad_only = grads_out != nullptr;
-    // views per scene decides how many (Y, draw) sets a thread keeps
-    int per_scene[kMaxScenes] = {0};
-    int maxv = 0;
-    for (int v = 0; v < P.views.n; v++) maxv = std::max(maxv, ++per_scene[P.views.v[v].scene]);
-    const int T = 128;
-    const int64_t blocks = (S.total + T - 1) / T;
-#define GS_PBA(MV) k_project_bwd_adam<MV><<<(unsigned)blocks, T, 0, st>>>(P.views, S, cams, w.count, w.offset, \
-                                                                     w.gradrec, A, reinterpret_cast<float4*>(grads_out), \
-                                                                     w.hdr, (uint32_t)P.cap)
-    if (maxv <= 1) GS_PBA(1);
-    else if (maxv <= 2) GS_PBA(2);
-    else if (maxv <= 4) GS_PBA(4);
-    else GS_PBA(kMaxViews);
+    A.seed = adam ? adam->seed : 0u;
+    const int64_t blocks = (S.total + kPbaThreads - 1) / kPbaThreads;
+#define GS_PBA(SH, MO) k_project_bwd_adam<SH, MO><<<(unsigned)blocks, kPbaThreads, 0, st>>>(P.views, S, cams, w.count, \
+                              w.offset, w.gradrec, A, reinterpret_cast<float4*>(grads_out), w.hdr, (uint32_t)P.cap)
+    if (!P.sh_bf16 && !P.mom_bf16) GS_PBA(false, false);
+    else if (P.sh_bf16 && P.mom_bf16) GS_PBA(true, true);
+    else if (P.sh_bf16) GS_PBA(true, false);
+    else GS_PBA(false, true);
 #undef GS_PBA
 }
 
