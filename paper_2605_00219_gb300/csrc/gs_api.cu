@@ -315,8 +315,6 @@ gs_status gs_project_bwd_adam(const gs_plan* plan, void* ws, const gs_scene_buf*
     if (grads_out && !aligned16(grads_out)) return GS_ERR_INVALID_ARG;
     gs_status e = check_scenes(P, scenes, grads_out == nullptr);
     if (e != GS_OK) return e;
-    if (!grads_out && (P.sh_bf16 || P.mom_bf16)) return GS_ERR_UNIMPLEMENTED;
-    if (P.sh_bf16) return GS_ERR_UNIMPLEMENTED;
     WsPtrs w = carve(P, ws);
     launch_project_bwd_adam(P, make_scenes(P, scenes), cams, w, adam, grads_out, static_cast<cudaStream_t>(stream));
     return launch_status();

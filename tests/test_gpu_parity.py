@@ -304,3 +304,64 @@ def test_graph_replay_equals_eager(gs):
     assert torch.equal(a.scenes[0].sh, b.scenes[0].sh)
     assert torch.equal(a.scenes[0].m, b.scenes[0].m)
     assert a.stats().step == b.stats().step == 2
+
+
+def _bf16_round(x):
+    return torch.from_numpy(np.ascontiguousarray(x, np.float32)).to(torch.bfloat16).float().numpy()
+
+
+def _bf16_ulp(x):
+    """Spacing of bf16 numbers at |x| (8 significant bits)."""
+    ax = np.maximum(np.abs(x), np.finfo(np.float32).tiny)
+    return 2.0 ** (np.floor(np.log2(ax)) - 7)
+
+
+def test_bf16_storage_step(gs, orc):
+    """SH and both Adam moments stored in BF16 (FP32 arithmetic): image and
+    post-Adam geometry as in FP32; post-Adam SH and moments within one BF16
+    ulp (stochastic rounding) of the FP64 oracle fed the same stored SH."""
+    gsstep, step_mod = gs
+    scene, tscene, cams = synth.tiny_workload(0)
+    cam = cams[0]
+    scene.sh = _bf16_round(scene.sh)            # what BF16 storage holds
+    tgt = orc.render64(cam, orc.project64(orc.Params64.from_scene(tscene), cam), orc.bin32(tscene, cam)).image
+    res = orc.step(scene, cams, [tgt], LR, 1)
+    tr = step_mod.Trainer([scene], cams, lr=LR, sh_bf16=True, mom_bf16=True)
+    assert tr.scenes[0].sh.dtype == torch.bfloat16 and tr.scenes[0].m.dtype == torch.bfloat16
+    tr.set_target([tgt.astype(np.float32)])
+    tr.forward()
+    torch.cuda.synchronize()
+    r = res.renders[0]
+    img = tr.image.view(128, 128, 3).cpu().numpy().astype(np.float64)
+    assert np.abs(img - r.image)[~r.unstable_px].max() <= 1e-5
+    tr.backward_adam(step=1)
+    torch.cuda.synchronize()
+    assert tr.stats().status == 0
+    undecided = (np.abs(r.image - tgt) < 1e-5).any(-1)
+    r.unstable_px |= undecided
+    bad = _unstable_gaussians(res.projs[0], r, cam)
+    g = res.grad
+    rms = np.sqrt((g[~bad] ** 2).mean(0)) + 1e-30
+    decided = (np.abs(g) > 1e-2 * rms[None, :]) & ~bad[:, None]
+    new = tr.scenes[0].to_scene()
+    n = scene.n
+    # SH parameters: one bf16 ulp of the FP64 result (plus FP32 slack)
+    sh_gpu = new.sh.reshape(n, 48).astype(np.float64)
+    sh_orc = res.theta[:, 11:]
+    tol = _bf16_ulp(sh_orc) + 1e-6
+    d = decided[:, 11:]
+    assert np.all(np.abs(sh_gpu - sh_orc)[d] <= tol[d])
+    # geometry stays FP32
+    geo_gpu = np.concatenate([new.means, new.quats, np.log(new.scales)], axis=1).astype(np.float64)
+    dg = decided[:, :10]
+    assert np.all(np.abs(geo_gpu - res.theta[:, :10])[dg] <= (1e-5 * np.abs(res.theta[:, :10]) + 1e-6)[dg])
+    # moments (15 chunks x 4, bf16) against the oracle's m, v in theta order
+    def unpack(t):
+        a = t.float().cpu().numpy()
+        return np.concatenate([a[0, :, :3], a[1], a[2], a[3:].transpose(1, 0, 2).reshape(n, 48)], axis=1)
+    for name, gpu_t, orc_a in (("m", tr.scenes[0].m, res.m), ("v", tr.scenes[0].v, res.v)):
+        mg = unpack(gpu_t).astype(np.float64)
+        ok = decided & (orc_a != 0)
+        # one bf16 ulp of rounding plus the FP32 gradient's own 1e-3 (x2 for v)
+        bound = _bf16_ulp(orc_a) + 2e-3 * np.abs(orc_a)
+        assert np.all(np.abs(mg - orc_a)[ok] <= bound[ok]), name
