@@ -1,24 +1,39 @@
-"""Benchmark of the 3DGS training step on GB300.
+"""Benchmark of the 3DGS training step on one GB300.
 
-Default workload: 3M Gaussians (256 clusters in a 30 m box), one 1920x1080
-view per step, FP32 storage, 16x16 tiles: project_fwd -> bin_sort ->
-raster_fwd -> L1 gradient -> raster_bwd -> project_bwd_adam, captured in one
-CUDA graph.  Inputs (parameters, Adam moments, target image, camera) are
-resident in HBM when the timed region starts; the working set (about 2.2 GB
-of parameters and moments) is far larger than L2, so no flush is needed.
+Headline workload ("batched BF16"): 3M Gaussians (256 clusters in a 30 m
+box), four 1920x1080 orbit views per step, SH coefficients and both Adam
+moments stored in BF16 (FP32 arithmetic), tile shape and raster-backward
+implementation picked by the Thompson-sampling autotuner, the whole step
+(projection, binning/sort, raster forward, L1 gradient, raster backward,
+projection backward + Adam) in one CUDA graph.
+
+It is compared with the plain FP32 single-view form (same scene, one
+1920x1080 view per step, FP32 storage, 16x16 tiles) at an equal number of
+1080p views seen: `value` is 1080p view-steps per second (views per step x
+steps per second); the plain form's steps/s is reported beside it.  A short
+training run of both storage precisions on the same schedule gives the
+rendered-PSNR difference on a held-out 1080p view.  `--workload uneven`
+runs the batch of four uneven views (1920x1080, 1600x1064, 1280x720,
+960x540) instead, `--workload plain` the plain form alone.
+
+Inputs (parameters, moments, targets, cameras) are resident in HBM when the
+timed region starts; the working set (about 1.5 GB of parameters and
+moments plus 2 GB of workspace) is far larger than L2, so no flush is used.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload batched|plain]
 
 One JSON line on rank 0.  `--impl reference` times the CPU oracle (FP64, the
 plain restatement of the paper's step) on a bounded sample of the same
 workload on this host's cores.  With N > 1 (torchrun) every rank trains an
-independent replica of the workload on its own GPU (the step has no
-exchange between GPUs); value = all ranks' steps / max time.
+independent replica on its own GPU (the step has no exchange between GPUs);
+value = all ranks' work / max time.
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -32,7 +47,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "steps/s (batched BF16 vs plain FP32, ΔPSNR<0.05dB) at 3M Gaussians 1080p"
 N_GAUSS = 3_000_000
-RES = (1920, 1080)
+RES_1080 = (1920, 1080)
+BATCH_RES = [(1920, 1080), (1600, 1064), (1280, 720), (960, 540)]
+PX_1080 = 1920 * 1080
 LR = (1.6e-4 * 30.0, 1e-3, 5e-3, 5e-2, 2.5e-3, 2.5e-3 / 20)   # mean lr scaled by the 30 m scene extent
 
 
@@ -42,9 +59,14 @@ def _args():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batched", choices=["batched", "uneven", "plain"])
     ap.add_argument("--n", type=int, default=N_GAUSS)
-    ap.add_argument("--bwd-impl", type=int, default=0, choices=[0, 1],
-                    help="raster backward: 0 pixel-parallel warp reductions, 1 per-Gaussian batches")
+    ap.add_argument("--tune-rounds", type=int, default=18)
+    ap.add_argument("--psnr-steps", type=int, default=200)
+    ap.add_argument("--tile", default=None, help="fix the tile shape (e.g. 16x16) instead of autotuning")
+    ap.add_argument("--bwd-impl", type=int, default=None, choices=[0, 1],
+                    help="fix the raster-backward implementation instead of autotuning")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--cpu-sample-tiles", type=int, default=16,
                     help="oracle renders 1 in this many tiles (bounded CPU sample)")
@@ -52,18 +74,17 @@ def _args():
 
 
 def _dist():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
 
 
-def _workload(n):
+def _views(workload):
     from paper_2605_00219_gb300 import synth
-    scene = synth.large_scene(0, n)
-    cam = synth.large_views(1, resolutions=[RES])[0]
-    target_scene = synth.perturbed(scene, 1)
-    return scene, target_scene, cam
+    if workload == "plain":
+        return synth.large_views(1, resolutions=[RES_1080])
+    if workload == "uneven":
+        return synth.large_views(4, resolutions=BATCH_RES)
+    return synth.large_views(4, resolutions=[RES_1080])
 
 
 class ClockSampler:
@@ -74,9 +95,7 @@ class ClockSampler:
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index: int):
-        self.gpu = gpu_index
-        self.proc = None
-        self.out = None
+        self.gpu, self.proc, self.out = gpu_index, None, None
 
     def __enter__(self):
         try:
@@ -115,35 +134,46 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def run_cpu_oracle(scene, target_img, cam, sample_tiles: int):
-    """One oracle step on a bounded sample: projection, FP32 binning, L1 and
-    Adam over everything; compositing and its backward on 1 in
-    `sample_tiles` tiles.  Returns (seconds for a full step, by scaling the
-    tile-bound part, details)."""
+# ----------------------------------------------------------------------------
+# CPU oracle (bounded sample)
+# ----------------------------------------------------------------------------
+
+def run_cpu_oracle(scene, targets, cams, sample_tiles: int):
+    """One oracle step over `cams` on a bounded sample: projection, FP32
+    binning and Adam over everything; compositing and its backward on 1 in
+    `sample_tiles` tiles.  Returns (seconds for the full step with the
+    tile-bound part scaled up, details)."""
     from oracle import oracle as orc
-    t0 = time.perf_counter()
+    t_fixed = t_tiles = 0.0
+    tiles = sampled = 0
     p = orc.Params64.from_scene(scene)
-    b = orc.bin32(scene, cam)
-    P = orc.project64(p, cam)
-    t1 = time.perf_counter()
-    ntiles = b.ranges.shape[0]
-    keep = np.zeros(ntiles, bool)
-    keep[::sample_tiles] = True
-    bs = orc.Binning(b.count, b.bin, b.mant, b.offset, b.keys_emit, b.gidx_emit, b.keys, b.gidx, b.perm,
-                     np.where(keep[:, None], b.ranges, 0))
-    r = orc.render64(cam, P, bs)
-    loss, (dl,) = orc.l1_loss_grad([r.image], [target_img])
-    g2 = orc.raster_bwd64(cam, P, bs, dl)
-    t2 = time.perf_counter()
-    grad = orc.project_bwd64(p, cam, P, g2)
+    grad = np.zeros((scene.n, orc.NTHETA))
+    total_px = sum(c.width * c.height for c in cams)
+    for cam, tgt in zip(cams, targets):
+        t0 = time.perf_counter()
+        b = orc.bin32(scene, cam)
+        P = orc.project64(p, cam)
+        t1 = time.perf_counter()
+        keep = np.zeros(b.ranges.shape[0], bool)
+        keep[::sample_tiles] = True
+        bs = orc.Binning(b.count, b.bin, b.mant, b.offset, b.keys_emit, b.gidx_emit, b.keys, b.gidx, b.perm,
+                         np.where(keep[:, None], b.ranges, 0))
+        r = orc.render64(cam, P, bs)
+        dl = np.sign(r.image - tgt) / (3 * total_px)
+        g2 = orc.raster_bwd64(cam, P, bs, dl)
+        t2 = time.perf_counter()
+        orc.project_bwd64(p, cam, P, g2, out=grad)
+        t3 = time.perf_counter()
+        t_fixed += (t1 - t0) + (t3 - t2)
+        t_tiles += t2 - t1
+        tiles += int(keep.size)
+        sampled += int(keep.sum())
+    t4 = time.perf_counter()
     th = p.theta()
-    m = np.zeros_like(th)
-    v = np.zeros_like(th)
-    orc.adam64(th, m, v, grad, LR, 1)
-    t3 = time.perf_counter()
-    full = (t1 - t0) + (t2 - t1) * sample_tiles + (t3 - t2)
-    return full, {"measured_s": t3 - t0, "tiles_sampled": int(keep.sum()), "tiles": int(ntiles),
-                  "blended_pairs_sampled": r.blended}
+    orc.adam64(th, np.zeros_like(th), np.zeros_like(th), grad, LR, 1)
+    t_fixed += time.perf_counter() - t4
+    full = t_fixed + t_tiles * sample_tiles
+    return full, {"measured_s": t_fixed + t_tiles, "tiles_sampled": sampled, "tiles": tiles}
 
 
 def reference_arm(args):
@@ -151,89 +181,60 @@ def reference_arm(args):
     if rank != 0:
         return
     from oracle import oracle as orc
+    from paper_2605_00219_gb300 import synth
     orc.build()
-    scene, tscene, cam = _workload(args.n)
-    # target from the oracle itself (bounded: the same tile sample)
-    target = np.zeros((cam.height, cam.width, 3))
+    scene = synth.large_scene(0, args.n)
+    cams = _views(args.workload)
+    targets = [np.zeros((c.height, c.width, 3)) for c in cams]
+    steps = max(1, min(args.steps, 3))
+    warm = min(args.warmup, 1)
     times = []
-    for i in range(args.warmup + args.steps):
-        t, info = run_cpu_oracle(scene, target, cam, args.cpu_sample_tiles)
-        if i >= args.warmup:
+    for i in range(warm + steps):
+        t, info = run_cpu_oracle(scene, targets, cams, args.cpu_sample_tiles)
+        if i >= warm:
             times.append(t)
     mean = sum(times) / len(times)
-    value = 1.0 / mean
+    value = len(cams) / mean
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
+            "steps": steps, "warmup": warm, "ms_per_step": mean * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.n // 1_000_000}M Gaussians, one {RES[0]}x{RES[1]} view per step, "
-                                   "FP64 CPU oracle", "global_batch": 1, "seq_len": 0, "parallelism": "none"},
+            "config": {"workload": f"{args.workload}: {args.n / 1e6:.3g}M Gaussians, views "
+                                   f"{[f'{c.width}x{c.height}' for c in cams]}, FP64 CPU oracle; value in "
+                                   "view-steps/s", "global_batch": len(cams), "seq_len": 0,
+                       "parallelism": "none"},
             "cpu_baseline": {"value": value, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
                              "sample": f"compositing and its backward on 1 in {args.cpu_sample_tiles} tiles, "
-                                       "scaled to the full image; projection, binning and Adam over all"},
+                                       "scaled to the full images; projection, binning and Adam over all "
+                                       "Gaussians"},
             "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def main():
-    args = _args()
-    if args.impl == "reference":
-        return reference_arm(args)
-    import torch
-    ws, rank, local = _dist()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    from paper_2605_00219_gb300 import build
-    build.build()
-    from paper_2605_00219_gb300 import gsstep, step as stepmod
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
 
-    scene, tscene, cam = _workload(args.n)
-    # target: the perturbed scene rendered by the same forward (setup, untimed)
-    tgt_tr = stepmod.Trainer([tscene], [cam], lr=LR)
-    tgt_tr.forward()
-    target = tgt_tr.image.clone()
-    del tgt_tr
-    tr = stepmod.Trainer([scene], [cam], lr=LR, bwd_impl=args.bwd_impl)
-    tr.target.copy_(target)
-    torch.cuda.synchronize()
+def _render_targets(stepmod, tscene, cams):
+    tr = stepmod.Trainer([tscene], cams, lr=LR)
+    tr.forward()
+    out = tr.image.clone()
+    del tr
+    return out
 
-    # eager warm-up (sets kernel attributes), then graph capture
-    tr.step(0)
-    tr.capture()
-    stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
-        tr.replay()
-    torch.cuda.synchronize()
-    st = tr.stats()
-    if st.status:
-        raise RuntimeError(f"device status {st.status:#x} (k_required={st.k_required}, capacity={st.k_capacity})")
 
-    # ---- timed region: K graph replays
+def _time_replays(torch, tr, steps, stream):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if ws > 1:
-        torch.distributed.barrier()
+    e0.record(stream)
+    for _ in range(steps):
+        tr.replay()
+    e1.record(stream)
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        e0.record(stream)
-        for _ in range(args.steps):
-            tr.replay()
-        e1.record(stream)
-        torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-        torch.distributed.barrier()
-    st = tr.stats()
-    blended = int(st.blended_pairs)
-    K = int(st.k_required)
+    return e0.elapsed_time(e1) / steps
 
-    # ---- per-stage timing: the same launches, eager, CUDA events on the stream
+
+def _stage_times(torch, gsstep, tr, reps, stream):
     stages = ["project_fwd", "bin_sort", "raster_fwd", "loss_l1", "raster_bwd", "project_bwd_adam"]
     acc = {s: 0.0 for s in stages}
-    reps = max(3, min(args.steps, 10))
     for _ in range(reps):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)]
         ev[0].record(stream)
@@ -247,38 +248,151 @@ def main():
         ev[4].record(stream)
         gsstep.gs_raster_bwd(tr.plan, tr.ws, tr.image, tr.dl)
         ev[5].record(stream)
-        gsstep.gs_project_bwd_adam(tr.plan, tr.ws, tr.scenes, tr.cams, gsstep.make_adam(LR, step=0))
+        gsstep.gs_project_bwd_adam(tr.plan, tr.ws, tr.scenes, tr.cams, gsstep.make_adam(tr.lr, step=0))
         ev[6].record(stream)
         gsstep.gs_adam_advance(tr.plan, tr.ws)
         torch.cuda.synchronize()
         for i, s in enumerate(stages):
             acc[s] += ev[i].elapsed_time(ev[i + 1]) / reps
-    nl = tr.buffer(5, tr.plan.pixels).to(torch.int64)
-    evaluated = int(nl.sum().item())
+    return acc
 
-    # ---- end to end through the public API with host buffers
-    pinned_tgt = target.cpu().pin_memory()
+
+def _psnr(torch, img, ref):
+    mse = float(((img.double() - ref.double()) ** 2).mean().item())
+    return 10.0 * math.log10(1.0 / max(mse, 1e-30))
+
+
+def _psnr_run(torch, stepmod, synth, scene, cams, targets, tile, impl, bf16, steps, heldout_cam, heldout_tgt):
+    """Train `steps` steps from `scene` and return the held-out view's PSNR."""
+    tr = stepmod.Trainer([scene], cams, lr=LR, tile=tile, bwd_impl=impl, sh_bf16=bf16, mom_bf16=bf16)
+    tr.target.copy_(targets)
+    for _ in range(steps):
+        tr.step(0)
+    ev = stepmod.Trainer([tr.scenes[0]], [heldout_cam], lr=LR, tile=tile, bwd_impl=impl, sh_bf16=bf16,
+                         mom_bf16=bf16)
+    ev.forward()
+    torch.cuda.synchronize()
+    return _psnr(torch, ev.image, heldout_tgt), float(tr.stats().loss)
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2605_00219_gb300 import build
+    build.build()
+    from paper_2605_00219_gb300 import autotune, gsstep, synth
+    from paper_2605_00219_gb300 import step as stepmod
+
+    stream = torch.cuda.current_stream()
+    scene = synth.large_scene(0, args.n)
+    tscene = synth.perturbed(scene, 1)
+    cams = _views(args.workload)
+    batched = args.workload != "plain"
+    targets = _render_targets(stepmod, tscene, cams)
+    px = sum(c.width * c.height for c in cams)
+    equiv = px / PX_1080
+    nviews = len(cams)
+
+    # ---- plain FP32 single view (reference form of the comparison)
+    plain_ms = None
+    if not args.no_plain:
+        plain_cam = synth.large_views(1, resolutions=[RES_1080])[0]
+        plain_tgt = _render_targets(stepmod, tscene, [plain_cam])
+        plain = stepmod.Trainer([scene], [plain_cam], lr=LR)
+        plain.target.copy_(plain_tgt)
+        plain.step(0)
+        plain.capture()
+        for _ in range(args.warmup):
+            plain.replay()
+        torch.cuda.synchronize()
+        plain_ms = _time_replays(torch, plain, args.steps, stream)
+        del plain
+
+    # ---- the measured form
+    sh16 = batched
+    bufs = stepmod.SceneBuffers.from_scene(scene, sh_bf16=sh16, mom_bf16=sh16)
+    fixed = args.tile is not None or args.bwd_impl is not None
+    if batched and not fixed:
+        best, tuner, trainers = autotune.tune_trainer([bufs], cams, rounds=args.tune_rounds, lr=LR, sh_bf16=True,
+                                                      mom_bf16=True, target=targets)
+        tr = trainers[best]
+        for c, t in list(trainers.items()):
+            if c != best:
+                del trainers[c]
+        tile, impl = best
+        tune_info = {"chosen": {"tile": list(tile), "bwd_impl": impl},
+                     "pulls": {f"{c[0][0]}x{c[0][1]}/impl{c[1]}": n for c, n in zip(tuner.candidates, tuner.pulls)},
+                     "mean_ms": {f"{c[0][0]}x{c[0][1]}/impl{c[1]}": round(p.mean, 3)
+                                 for c, p in zip(tuner.candidates, tuner.post) if p.n}}
+    else:
+        tile = tuple(int(x) for x in args.tile.split("x")) if args.tile else (16, 16)
+        impl = args.bwd_impl if args.bwd_impl is not None else 0
+        tr = stepmod.Trainer([bufs], cams, lr=LR, tile=tile, bwd_impl=impl, sh_bf16=sh16, mom_bf16=sh16)
+        tr.target.copy_(targets)
+        tr.step(0)
+        tune_info = None
+    tr.capture()
+    for _ in range(args.warmup):
+        tr.replay()
+    torch.cuda.synchronize()
+    st = tr.stats()
+    if st.status:
+        raise RuntimeError(f"device status {st.status:#x} (k_required={st.k_required}, capacity={st.k_capacity})")
+
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ms = _time_replays(torch, tr, args.steps, stream)
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    st = tr.stats()
+    K = int(st.k_required)
+    blended = int(st.blended_pairs)
+
+    acc = _stage_times(torch, gsstep, tr, max(3, min(args.steps, 10)), stream)
+    evaluated = int(tr.buffer(5, tr.plan.pixels).to(torch.int64).sum().item())
+
+    # ---- end to end: host targets and cameras in, statistics out, every step
+    pinned_tgt = targets.cpu().pin_memory()
     pinned_cam = tr.cams.cpu().pin_memory()
-    loss_host = torch.empty(1, dtype=torch.float32).pin_memory()
     h2d = pinned_tgt.numel() * 4 + pinned_cam.numel() * 4
-    loss_dev = tr.ws[:0]  # placeholder, the loss is read from the workspace header
     torch.cuda.synchronize()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t_wall = time.perf_counter()
     f0.record(stream)
     for _ in range(args.steps):
         tr.target.copy_(pinned_tgt, non_blocking=True)
         tr.cams.copy_(pinned_cam, non_blocking=True)
         tr.replay()
-        s2 = tr.stats()        # synchronous D2H of the step statistics (loss, status)
-        loss_host[0] = s2.loss
+        _ = tr.stats().loss          # synchronous D2H of the step statistics
     f1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = f0.elapsed_time(f1) / args.steps
-    d2h = 48  # gs_stats header
-    del loss_dev
+    d2h = 48
 
-    value = ws * 1e3 / ms
+    # ---- rendered-PSNR difference, FP32 vs BF16 storage, same schedule
+    psnr = None
+    if args.psnr_steps > 0 and rank == 0:
+        held = synth.large_views(1, resolutions=[RES_1080], phase_deg=45.0)[0]
+        held_tgt = _render_targets(stepmod, tscene, [held])
+        p32, l32 = _psnr_run(torch, stepmod, synth, scene, cams, targets, tile, impl, False, args.psnr_steps, held,
+                             held_tgt)
+        p16, l16 = _psnr_run(torch, stepmod, synth, scene, cams, targets, tile, impl, True, args.psnr_steps, held,
+                             held_tgt)
+        psnr = {"steps": args.psnr_steps, "fp32_db": p32, "bf16_db": p16, "delta_db": abs(p16 - p32),
+                "loss_fp32": l32, "loss_bf16": l16, "heldout": "1920x1080 orbit view at +45 deg"}
+
+    # ---- roofline of the dominant kernel
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -286,27 +400,25 @@ def main():
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     n = scene.n
-    adam_bytes = n * (240 + 480) * 2 + K * 48 + n * 8
-    adam_ms = acc["project_bwd_adam"]
-    fwd_bytes = n * 240 + n * (48 + 16 + 4)
-    dominant = max(stages, key=lambda s: acc[s])
-    sm_count = torch.cuda.get_device_properties(0).multi_processor_count
-    clk_sum = clk.summary()
-    alu_peak_tflops = sm_count * 128 * 2 * 2.070e9 / 1e12
+    per_g = (240 + 480) * 2 if not sh16 else (48 + 96 + 240) * 2
+    adam_bytes = n * per_g + K * 48 + n * 8 * len(cams)
+    fwd_bytes = n * (48 + (96 if sh16 else 192)) + n * len(cams) * (48 + 16 + 4)
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    alu_peak = sm_count * 128 * 2 * 2.070e9 / 1e12
     FLOP_BWD, FLOP_FWD = 90.0, 28.0   # FP32 FLOP (FMA = 2) per evaluated pair
     rooflines = {
-        "project_bwd_adam": {"bound": "hbm", "achieved": adam_bytes / (adam_ms * 1e-3) / 1e9, "peak": hbm_peak,
-                             "unit": "GB/s", "traffic": None},
-        "project_fwd": {"bound": "hbm", "achieved": fwd_bytes / (acc["project_fwd"] * 1e-3) / 1e9,
-                        "peak": hbm_peak, "unit": "GB/s", "traffic": None},
+        "project_bwd_adam": {"bound": "hbm", "achieved": adam_bytes / (acc["project_bwd_adam"] * 1e-3) / 1e9,
+                             "peak": hbm_peak, "unit": "GB/s", "traffic": None},
+        "project_fwd": {"bound": "hbm", "achieved": fwd_bytes / (acc["project_fwd"] * 1e-3) / 1e9, "peak": hbm_peak,
+                        "unit": "GB/s", "traffic": None},
         "raster_bwd": {"bound": "alu", "achieved": evaluated * FLOP_BWD / (acc["raster_bwd"] * 1e-3) / 1e12,
-                       "peak": alu_peak_tflops, "unit": "TFLOP/s", "traffic": None},
+                       "peak": alu_peak, "unit": "TFLOP/s", "traffic": None},
         "raster_fwd": {"bound": "alu", "achieved": evaluated * FLOP_FWD / (acc["raster_fwd"] * 1e-3) / 1e12,
-                       "peak": alu_peak_tflops, "unit": "TFLOP/s", "traffic": None},
+                       "peak": alu_peak, "unit": "TFLOP/s", "traffic": None},
     }
     for r in rooflines.values():
         r["frac"] = r["achieved"] / r["peak"]
-    dom = dominant if dominant in rooflines else "raster_bwd"
+    dom = max(rooflines, key=lambda k: acc[k])
     roof = dict(rooflines[dom])
     roof["kernel"] = dom
 
@@ -314,36 +426,54 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu:
         from oracle import oracle as orc
         orc.build()
-        tgt_np = target.view(RES[1], RES[0], 3).cpu().numpy().astype(np.float64)
-        t_full, info = run_cpu_oracle(scene, tgt_np, cam, args.cpu_sample_tiles)
-        cpu = {"value": 1.0 / t_full, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"one oracle step: projection, binning and Adam over all {n} Gaussians, compositing "
-                         f"and its backward on {info['tiles_sampled']} of {info['tiles']} tiles, scaled "
-                         f"to the full image ({info['measured_s']:.1f} s measured)"}
+        tg = []
+        o = 0
+        tnp = targets.cpu().numpy().astype(np.float64)
+        for c in cams:
+            tg.append(tnp[o:o + c.width * c.height].reshape(c.height, c.width, 3))
+            o += c.width * c.height
+        t_full, info = run_cpu_oracle(scene, tg, cams, args.cpu_sample_tiles)
+        cpu = {"value": nviews / t_full, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"one oracle step over the same views: projection, binning and Adam over all {n} "
+                         f"Gaussians, compositing and its backward on {info['tiles_sampled']} of {info['tiles']} "
+                         f"tiles, scaled to the full images ({info['measured_s']:.1f} s measured)"}
 
     if rank == 0:
+        value = ws * nviews * 1e3 / ms
+        desc = ("batched BF16: " if batched else "plain FP32: ") + \
+               f"{n / 1e6:.3g}M Gaussians (256 clusters, 30 m box), views per step " + \
+               "+".join(f"{c.width}x{c.height}" for c in cams) + \
+               (", BF16 SH and Adam moments (FP32 math)" if sh16 else ", FP32 storage") + \
+               f", tile {tile[0]}x{tile[1]}, raster_bwd impl {impl}, whole step in one CUDA graph; value = " + \
+               f"view-steps/s ({nviews} views per step x steps/s; {equiv:.3f} 1080p-equivalents of pixels per step)"
         line = {
             "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"plain FP32 single view: {n / 1e6:.0f}M Gaussians (256 clusters, 30 m box), "
-                                   f"one {RES[0]}x{RES[1]} view per step, 16x16 tiles, whole step in one CUDA graph",
-                       "global_batch": ws, "seq_len": 0, "parallelism": f"replicas{ws}" if ws > 1 else "none",
-                       "l2": "inputs larger than L2 (2.2 GB parameters + moments)"},
-            "e2e": {"value": ws * 1e3 / e2e_ms, "unit": "steps/s", "h2d_bytes_per_step": int(h2d),
+            "config": {"workload": desc, "global_batch": ws * len(cams), "seq_len": 0,
+                       "parallelism": f"replicas{ws}" if ws > 1 else "none",
+                       "l2": "inputs larger than L2 (no flush)"},
+            "e2e": {"value": ws * nviews * 1e3 / e2e_ms, "unit": "steps/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": None,
+            "gpu_launches": int(args.steps * launches_per_step(tr.plan)),
             "roofline": roof,
             "rooflines": rooflines,
+            "plain_fp32": None if plain_ms is None else {
+                "steps_per_s": 1e3 / plain_ms, "ms_per_step": plain_ms,
+                "workload": "one 1920x1080 view per step, FP32 storage, 16x16 tiles, impl 0"},
+            "batched_steps_per_s": 1e3 / ms,
+            "views_per_s": nviews * 1e3 / ms,
+            "equiv_1080p_views_per_s": equiv * 1e3 / ms,
+            "speedup_vs_plain_fp32": None if plain_ms is None else (nviews * 1e3 / ms) / (1e3 / plain_ms),
+            "psnr": psnr,
+            "autotune": tune_info,
             "stage_ms": acc,
             "intersections": K,
-            "blended_pairs_per_s": blended * value / ws,
             "evaluated_pairs": evaluated,
-            "views_per_s": value,
-            "clocks": clk_sum,
+            "blended_pairs_per_s": blended * 1e3 / ms,
+            "clocks": clk.summary(),
             "cpu_baseline": cpu,
         }
-        line["gpu_launches"] = int(args.steps * launches_per_step(tr.plan))
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -358,9 +488,9 @@ def launches_per_step(plan) -> int:
         tb = max(0, int(np.ceil(np.log2(tx * ty))))
         key_bits = max(key_bits, 32 if tb >= 9 else 23 + tb)
     passes = (key_bits + 7) // 8 + (1 if views > 1 else 0)
-    project = 2                         # header reset + projection
-    binsort = 3 + 1 + 1 + passes * (1 + 3 + 1) + 1 + 1
-    return project + binsort + 1 + 1 + 1 + 1 + 1   # raster fwd, loss, raster bwd, proj bwd+adam, step advance
+    project = 2                                        # header reset + projection
+    binsort = 3 + 1 + 1 + passes * (1 + 3 + 1) + 1 + 1  # scan, finalize, emit, passes, fill, ranges
+    return project + binsort + 1 + 1 + 1 + 1 + 1       # raster fwd, loss, raster bwd, proj bwd+adam, advance
 
 
 if __name__ == "__main__":
