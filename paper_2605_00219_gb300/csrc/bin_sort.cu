@@ -212,31 +212,36 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_up(const uint32_t* __re
                                                              const WsHeader* __restrict__ hdr, int shift,
                                                              uint32_t* __restrict__ hist, int64_t nblk, int nv)
 {
-    __shared__ uint32_t h[kRadixDigits];
+    // digit counts of this block's 2048 keys: one private histogram per warp
+    // (plain shared-memory atomics), summed per digit at the end
+    constexpr int W = kRadixThreads / 32;
+    __shared__ uint32_t h[W][kRadixDigits];
     __shared__ uint32_t seg[kMaxViews + 1];
-    h[threadIdx.x] = 0;
+    const int w = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < W; i++) h[i][threadIdx.x] = 0;
     if (MODE == kDigitView)
         for (int i = threadIdx.x; i <= nv; i += blockDim.x) seg[i] = hdr->seg[i];
     __syncthreads();
     const uint32_t K = hdr->k_eff;
     const int64_t base = (int64_t)blockIdx.x * kRadixBlock;
-    const int lane = threadIdx.x & 31;
     if (base < K) {
 #pragma unroll
         for (int i = 0; i < kRadixItems; i++) {
             const int64_t idx = base + i * kRadixThreads + threadIdx.x;
-            const bool valid = idx < K;
-            uint32_t d = 0xFFFFu;
-            if (valid) {
+            if (idx < K) {
+                uint32_t d;
                 if (MODE == kDigitKey) d = (keys[idx] >> shift) & 0xFFu;
                 else d = (uint32_t)view_of_slot(seg, nv, iota ? (uint32_t)idx : vals[idx]);
+                atomicAdd(&h[w][d], 1u);
             }
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
-            if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[d], __popc(peers));
         }
     }
     __syncthreads();
-    hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
+    uint32_t c = 0;
+#pragma unroll
+    for (int i = 0; i < W; i++) c += h[i][threadIdx.x];
+    hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = c;
 }
 
 template <int MODE, bool IOTA, bool LAST>

@@ -218,11 +218,15 @@ __device__ __forceinline__ uint32_t bf16_sr(float f, uint32_t rnd)
     return u >> 16;
 }
 
-__device__ __forceinline__ uint32_t sr_rand(uint32_t seed, int step, uint32_t stream, int64_t elem)
+// Per-thread stream key: one hash of (seed, step, Gaussian); each stored
+// group of values then takes fmix32(key ^ group counter), whose 32 bits serve
+// two bf16 roundings.
+__device__ __forceinline__ uint32_t sr_key(uint32_t seed, int step, int64_t gi)
 {
-    return fmix32(seed ^ fmix32((uint32_t)step * 0x9E3779B9u ^ fmix32(stream * 0x85ebca6bu ^ (uint32_t)elem ^
-                                                                      (uint32_t)(elem >> 32) * 0xc2b2ae35u)));
+    return fmix32(seed ^ fmix32((uint32_t)step * 0x9E3779B9u ^ (uint32_t)gi ^ (uint32_t)(gi >> 32) * 0xc2b2ae35u));
 }
+
+__device__ __forceinline__ uint32_t sr_bits(uint32_t key, uint32_t ctr) { return fmix32(key ^ (ctr * 0x9E3779B9u)); }
 
 // Moment chunk ci (4 values) of Gaussian g: FP32 float4 or 4 x bf16.
 template <bool MOM16>
@@ -234,18 +238,15 @@ __device__ __forceinline__ float4 load_mom(const void* base, int64_t idx)
 }
 
 template <bool MOM16>
-__device__ __forceinline__ void store_mom(void* base, int64_t idx, float4 m, uint32_t seed, int step,
-                                          uint32_t stream)
+__device__ __forceinline__ void store_mom(void* base, int64_t idx, float4 m, uint32_t key, uint32_t ctr)
 {
     if (!MOM16) {
         reinterpret_cast<float4*>(base)[idx] = m;
         return;
     }
-    const int64_t e = 4 * idx;
-    const uint32_t a = bf16_sr(m.x, sr_rand(seed, step, stream, e));
-    const uint32_t b = bf16_sr(m.y, sr_rand(seed, step, stream, e + 1));
-    const uint32_t c = bf16_sr(m.z, sr_rand(seed, step, stream, e + 2));
-    const uint32_t d = bf16_sr(m.w, sr_rand(seed, step, stream, e + 3));
+    const uint32_t r0 = sr_bits(key, 2u * ctr), r1 = sr_bits(key, 2u * ctr + 1u);
+    const uint32_t a = bf16_sr(m.x, r0), b = bf16_sr(m.y, r0 >> 16);
+    const uint32_t c = bf16_sr(m.z, r1), d = bf16_sr(m.w, r1 >> 16);
     reinterpret_cast<uint2*>(base)[idx] = make_uint2(a | (b << 16), c | (d << 16));
 }
 
@@ -268,6 +269,7 @@ __global__ void __launch_bounds__(kPbaThreads, 4) k_project_bwd_adam(Views V, Sc
     const int tid = threadIdx.x;
     const int64_t gi = (int64_t)blockIdx.x * kPbaThreads + tid;
     const int t = A.step > 0 ? A.step : hdr->step + 1;
+    const uint32_t key = MOM16 || SH16 ? sr_key(A.seed, t, gi) : 0u;
 #pragma unroll
     for (int f = 0; f < 48; f++) sG[f][tid] = 0.f;
 
@@ -317,8 +319,8 @@ __global__ void __launch_bounds__(kPbaThreads, 4) k_project_bwd_adam(Views V, Sc
                 adam1(mu.x, m.x, vv.x, dmu[0], A.lr[0], A.b1, A.b2, A.eps, ibc1, ibc2);
                 adam1(mu.y, m.y, vv.y, dmu[1], A.lr[0], A.b1, A.b2, A.eps, ibc1, ibc2);
                 adam1(mu.z, m.z, vv.z, dmu[2], A.lr[0], A.b1, A.b2, A.eps, ibc1, ibc2);
-                store_mom<MOM16>(sc.m, g, m, A.seed, t, 2u * s);
-                store_mom<MOM16>(sc.v, g, vv, A.seed, t, 2u * s + 1u);
+                store_mom<MOM16>(sc.m, g, m, key, 0u);
+                store_mom<MOM16>(sc.v, g, vv, key, 1u);
                 sc.geom[g] = mu;
             }
             {
@@ -327,8 +329,8 @@ __global__ void __launch_bounds__(kPbaThreads, 4) k_project_bwd_adam(Views V, Sc
                 adam1(q.y, m.y, vv.y, dq[1], A.lr[1], A.b1, A.b2, A.eps, ibc1, ibc2);
                 adam1(q.z, m.z, vv.z, dq[2], A.lr[1], A.b1, A.b2, A.eps, ibc1, ibc2);
                 adam1(q.w, m.w, vv.w, dq[3], A.lr[1], A.b1, A.b2, A.eps, ibc1, ibc2);
-                store_mom<MOM16>(sc.m, n + g, m, A.seed, t, 2u * s);
-                store_mom<MOM16>(sc.v, n + g, vv, A.seed, t, 2u * s + 1u);
+                store_mom<MOM16>(sc.m, n + g, m, key, 2u);
+                store_mom<MOM16>(sc.v, n + g, vv, key, 3u);
                 sc.geom[n + g] = q;
             }
             {
@@ -339,8 +341,8 @@ __global__ void __launch_bounds__(kPbaThreads, 4) k_project_bwd_adam(Views V, Sc
                 adam1(th1, m.y, vv.y, ds[1] * so.y, A.lr[2], A.b1, A.b2, A.eps, ibc1, ibc2);
                 adam1(th2, m.z, vv.z, ds[2] * so.z, A.lr[2], A.b1, A.b2, A.eps, ibc1, ibc2);
                 adam1(tho, m.w, vv.w, dop * so.w * (1.0f - so.w), A.lr[3], A.b1, A.b2, A.eps, ibc1, ibc2);
-                store_mom<MOM16>(sc.m, 2 * n + g, m, A.seed, t, 2u * s);
-                store_mom<MOM16>(sc.v, 2 * n + g, vv, A.seed, t, 2u * s + 1u);
+                store_mom<MOM16>(sc.m, 2 * n + g, m, key, 4u);
+                store_mom<MOM16>(sc.v, 2 * n + g, vv, key, 5u);
                 sc.geom[2 * n + g] = make_float4(expf(th0), expf(th1), expf(th2), 1.0f / (1.0f + expf(-tho)));
             }
         }
@@ -387,17 +389,20 @@ __global__ void __launch_bounds__(kPbaThreads, 4) k_project_bwd_adam(Views V, Sc
                 adam1(th[4 * h + i], mp[i], vp[i], sG[f][tid], f < 3 ? A.lr[4] : A.lr[5], A.b1, A.b2, A.eps, ibc1,
                       ibc2);
             }
-            store_mom<MOM16>(sc.m, ci, m, A.seed, t, 2u * s);
-            store_mom<MOM16>(sc.v, ci, vv, A.seed, t, 2u * s + 1u);
+            store_mom<MOM16>(sc.m, ci, m, key, 6u + 2u * j);
+            store_mom<MOM16>(sc.v, ci, vv, key, 7u + 2u * j);
         }
         if (!SH16) {
             reinterpret_cast<float4*>(sc.sh)[(int64_t)(2 * jp) * n + g] = make_float4(th[0], th[1], th[2], th[3]);
             reinterpret_cast<float4*>(sc.sh)[(int64_t)(2 * jp + 1) * n + g] = make_float4(th[4], th[5], th[6], th[7]);
         } else {
             uint32_t u[8];
-            const int64_t e = 8 * ((int64_t)jp * n + g);
 #pragma unroll
-            for (int i = 0; i < 8; i++) u[i] = bf16_sr(th[i], sr_rand(A.seed, t, 0x5348u + 2u * s, e + i));
+            for (int i = 0; i < 8; i += 2) {
+                const uint32_t r = sr_bits(key, 64u + 8u * jp + i);
+                u[i] = bf16_sr(th[i], r);
+                u[i + 1] = bf16_sr(th[i + 1], r >> 16);
+            }
             reinterpret_cast<uint4*>(sc.sh)[(int64_t)jp * n + g] =
                 make_uint4(u[0] | (u[1] << 16), u[2] | (u[3] << 16), u[4] | (u[5] << 16), u[6] | (u[7] << 16));
         }

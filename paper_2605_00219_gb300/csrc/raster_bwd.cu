@@ -391,11 +391,12 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint2* __re
     constexpr int WPR = TW / 8;            // 8x4 warp blocks per tile row
     constexpr int RPB = BS / TW / 4;       // rows of warp blocks
     constexpr int BB = NW <= 8 ? 128 : 64; // list entries per staged batch
-    __shared__ float4 sA[BB];
-    __shared__ float4 sB[BB];
-    __shared__ float sC[BB];
-    __shared__ uint32_t sE[BB];
-    __shared__ uint32_t sM[BB];
+    constexpr int IPT = (BB + BS - 1) / BS;   // staged entries per thread
+    __shared__ float4 sA[2][BB];
+    __shared__ float4 sB[2][BB];
+    __shared__ float sC[2][BB];
+    __shared__ uint32_t sE[2][BB];
+    __shared__ uint32_t sM[2][BB];
     __shared__ float part[NW][BB][9];
     __shared__ uint32_t pmask[NW][BB / 32];
     __shared__ int smax[NW];
@@ -434,22 +435,49 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint2* __re
     for (int i = 0; i < NW; i++) L = max(L, smax[i]);
     L = min(L, (int)(r.y - r.x));
 
-    for (int bb = ((L + BB - 1) / BB - 1) * BB; bb >= 0; bb -= BB) {
-        const int cnt = min(BB, L - bb);
-        __syncthreads();
-        for (int i = tid; i < cnt; i += BS) {  // BB may exceed the CTA width
+    // Batches from the back; the batch below the current one is gathered into
+    // registers while the current one is processed, then stored to the other
+    // buffer: two barriers per batch.
+    auto stage = [&](int bbx, int buf, int i, const ProjRec& q, uint32_t e) {
+        (void)bbx;
+        sA[buf][i] = q.a;
+        sB[buf][i] = q.b;
+        sC[buf][i] = q.c.x;
+        sE[buf][i] = e;
+        sM[buf][i] = warp_block_mask(q.a.x, q.a.y, q.a.z, q.a.w, q.b.x, ox, oy, WPR, RPB);
+    };
+    int bb = ((L + BB - 1) / BB - 1) * BB;
+    if (bb >= 0) {
+        const int cnt0 = min(BB, L - bb);
+        for (int i = tid; i < cnt0; i += BS) {
             const uint32_t k = r.x + bb + i;
-            const ProjRec q = rec[pid_sorted[k]];
-            sA[i] = q.a;
-            sB[i] = q.b;
-            sC[i] = q.c.x;
-            sE[i] = vals_sorted[k];
-            sM[i] = warp_block_mask(q.a.x, q.a.y, q.a.z, q.a.w, q.b.x, ox, oy, WPR, RPB);
+            stage(bb, 0, i, rec[pid_sorted[k]], vals_sorted[k]);
         }
-        __syncthreads();
+    }
+    __syncthreads();
+    for (int cur = 0; bb >= 0; bb -= BB, cur ^= 1) {
+        const int cnt = min(BB, L - bb);
+        const float4* __restrict__ cA = sA[cur];
+        const float4* __restrict__ cB = sB[cur];
+        const float* __restrict__ cC = sC[cur];
+        const uint32_t* __restrict__ cM = sM[cur];
+        // gathers for the next (lower) batch, all entries full since bb > 0
+        ProjRec qn[IPT];
+        uint32_t en[IPT];
+        if (bb > 0) {
+#pragma unroll
+            for (int u = 0; u < IPT; u++) {
+                const int i = tid + u * BS;
+                if (i < BB) {
+                    const uint32_t k = r.x + bb - BB + i;
+                    en[u] = vals_sorted[k];
+                    qn[u] = rec[pid_sorted[k]];
+                }
+            }
+        }
         for (int c = (cnt - 1) >> 5; c >= 0; c--) {
             // entries of this chunk whose 3-sigma box touches this warp's block
-            uint32_t bits = __ballot_sync(0xffffffffu, 32 * c + lane < cnt && (sM[32 * c + lane] & wbit));
+            uint32_t bits = __ballot_sync(0xffffffffu, 32 * c + lane < cnt && (cM[32 * c + lane] & wbit));
             uint32_t done_bits = 0;
             while (bits) {
                 const int jj = 31 - __clz(bits);
@@ -460,8 +488,8 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint2* __re
                 for (int i = 0; i < 9; i++) g[i] = 0.f;
                 bool hit = false;
                 if (bb + j < (int)nl) {
-                    const float4 a = sA[j];
-                    const float4 b = sB[j];
+                    const float4 a = cA[j];
+                    const float4 b = cB[j];
                     const float dx = fx - a.x, dy = fy - a.y;
                     const float power = pair_power(dx, dy, a.z, a.w, b.x);
                     if (power >= -4.5f) {
@@ -470,7 +498,7 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint2* __re
                         const float alpha = fminf(kAlphaMax, araw);
                         if (alpha >= kAlphaMin) {
                             hit = true;
-                            const float cb = sC[j];
+                            const float cb = cC[j];
                             // compensated T_before = (Th + Tl) / (1 - alpha)
                             const float om = __fsub_rn(1.0f, alpha);
                             const float om_err = __fsub_rn(-alpha, __fsub_rn(om, 1.0f));
@@ -519,8 +547,16 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint2* __re
 #pragma unroll
             for (int i = 0; i < NW; i++)
                 if ((pmask[i][j >> 5] >> (j & 31)) & 1u) s += part[i][j][comp];
-            reinterpret_cast<float*>(gradrec + sE[j])[comp] = s;
+            reinterpret_cast<float*>(gradrec + sE[cur][j])[comp] = s;
         }
+        if (bb > 0) {
+#pragma unroll
+            for (int u = 0; u < IPT; u++) {
+                const int i = tid + u * BS;
+                if (i < BB) stage(bb - BB, cur ^ 1, i, qn[u], en[u]);
+            }
+        }
+        __syncthreads();
     }
     // entries past every pixel's last blended pair receive zero gradients
     for (uint32_t k = r.x + (uint32_t)L + tid; k < r.y; k += BS) {

@@ -21,10 +21,10 @@ __global__ void __launch_bounds__(BS) k_raster_fwd(Views V, const uint2* __restr
                                                    float* __restrict__ image, float* __restrict__ tfinal,
                                                    uint32_t* __restrict__ nlast, WsHeader* __restrict__ hdr)
 {
-    __shared__ float4 sA[BS];
-    __shared__ float4 sB[BS];
-    __shared__ float sC[BS];
-    __shared__ uint32_t sM[BS];
+    __shared__ float4 sA[2][BS];
+    __shared__ float4 sB[2][BS];
+    __shared__ float sC[2][BS];
+    __shared__ uint32_t sM[2][BS];
     __shared__ unsigned long long sblend[BS / 32];
     constexpr int WPR = TW / 8, RPB = BS / TW / 4;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -44,27 +44,37 @@ __global__ void __launch_bounds__(BS) k_raster_fwd(Views V, const uint2* __restr
     float C0 = 0.f, C1 = 0.f, C2 = 0.f;
     uint32_t last = 0, nbl = 0;
     int done = !inside;
-    for (uint32_t base = r.x; base < r.y; base += BS) {
+    // chunk 0 staged directly; afterwards chunk i+1's records are gathered
+    // while chunk i is composited (pair indices one chunk further ahead)
+    if (r.x + threadIdx.x < r.y) {
+        const ProjRec q = rec[pid_sorted[r.x + threadIdx.x]];
+        sA[0][threadIdx.x] = q.a;
+        sB[0][threadIdx.x] = q.b;
+        sC[0][threadIdx.x] = q.c.x;
+        sM[0][threadIdx.x] = warp_block_mask(q.a.x, q.a.y, q.a.z, q.a.w, q.b.x, ox, oy, WPR, RPB);
+    }
+    uint32_t pid_next = r.x + BS + threadIdx.x < r.y ? pid_sorted[r.x + BS + threadIdx.x] : 0u;
+    int cur = 0;
+    for (uint32_t base = r.x; base < r.y; base += BS, cur ^= 1) {
         if (__syncthreads_count(done) == BS) break;
-        const uint32_t k = base + threadIdx.x;
-        if (k < r.y) {
-            const ProjRec q = rec[pid_sorted[k]];
-            sA[threadIdx.x] = q.a;
-            sB[threadIdx.x] = q.b;
-            sC[threadIdx.x] = q.c.x;
-            sM[threadIdx.x] = warp_block_mask(q.a.x, q.a.y, q.a.z, q.a.w, q.b.x, ox, oy, WPR, RPB);
-        }
-        __syncthreads();
+        const bool have_next = base + BS + threadIdx.x < r.y;
+        ProjRec qn;
+        if (have_next) qn = rec[pid_next];
+        if (base + 2 * BS + threadIdx.x < r.y) pid_next = pid_sorted[base + 2 * BS + threadIdx.x];
+        const float4* __restrict__ cA = sA[cur];
+        const float4* __restrict__ cB = sB[cur];
+        const float* __restrict__ cC = sC[cur];
+        const uint32_t* __restrict__ cM = sM[cur];
         const int cnt = (int)min((uint32_t)BS, r.y - base);
         for (int c0 = 0; c0 < cnt; c0 += 32) {
-            uint32_t bits = __ballot_sync(0xffffffffu, c0 + lane < cnt && (sM[c0 + lane] & wbit));
+            uint32_t bits = __ballot_sync(0xffffffffu, c0 + lane < cnt && (cM[c0 + lane] & wbit));
             if (done) continue;
             while (bits) {
                 const int j = c0 + __ffs(bits) - 1;
                 bits &= bits - 1;
-                const float4 a = sA[j];
+                const float4 a = cA[j];
                 const float dx = fx - a.x, dy = fy - a.y;
-                const float4 b = sB[j];
+                const float4 b = cB[j];
                 const float power = pair_power(dx, dy, a.z, a.w, b.x);
                 if (power < -4.5f) continue;
                 const float G = __expf(power);
@@ -84,12 +94,19 @@ __global__ void __launch_bounds__(BS) k_raster_fwd(Views V, const uint2* __restr
                 const float wgt = alpha * Th;
                 C0 = fmaf(b.z, wgt, C0);
                 C1 = fmaf(b.w, wgt, C1);
-                C2 = fmaf(sC[j], wgt, C2);
+                C2 = fmaf(cC[j], wgt, C2);
                 Tl = __fsub_rn(lo, __fsub_rn(hi, pr));
                 Th = hi;
                 last = base - r.x + j + 1;
                 nbl++;
             }
+        }
+        if (have_next) {
+            const int nb = cur ^ 1;
+            sA[nb][threadIdx.x] = qn.a;
+            sB[nb][threadIdx.x] = qn.b;
+            sC[nb][threadIdx.x] = qn.c.x;
+            sM[nb][threadIdx.x] = warp_block_mask(qn.a.x, qn.a.y, qn.a.z, qn.a.w, qn.b.x, ox, oy, WPR, RPB);
         }
     }
     if (gt == 0 && threadIdx.x < 3) hdr->bg[threadIdx.x] = bg ? bg[threadIdx.x] : 0.f;
@@ -168,18 +185,27 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_l1(const float* __restric
         is_last = done == gridDim.x - 1;
     }
     __syncthreads();
-    if (is_last && threadIdx.x == 0) {
-        // the last CTA sums the partials in index order (deterministic)
+    if (is_last) {
+        // the last CTA sums the partials: thread t takes indices t, t + 256,
+        // ... (Kahan-compensated), then a fixed-order tree -- deterministic
         __threadfence();
-        float t = 0.f, comp = 0.f;  // Kahan-compensated FP32 sum
-        for (unsigned i = 0; i < gridDim.x; i++) {
+        float t = 0.f, comp = 0.f;
+        for (unsigned i = threadIdx.x; i < gridDim.x; i += kLossThreads) {
             const float y = ((volatile float*)part)[i] - comp;
             const float u = t + y;
             comp = (u - t) - y;
             t = u;
         }
-        hdr->loss = t * inv_n;
-        hdr->loss_counter = 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = t;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float tt = 0.f;
+            for (int i = 0; i < kLossThreads / 32; i++) tt += ws[i];
+            hdr->loss = tt * inv_n;
+            hdr->loss_counter = 0;
+        }
     }
 }
 
