@@ -226,14 +226,21 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_up(const uint32_t* __re
     const uint32_t K = hdr->k_eff;
     const int64_t base = (int64_t)blockIdx.x * kRadixBlock;
     if (base < K) {
+        uint32_t d[kRadixItems];
+#pragma unroll
+        for (int i = 0; i < kRadixItems; i++) {   // all loads first, then the counts
+            const int64_t idx = base + i * kRadixThreads + threadIdx.x;
+            d[i] = 0xFFFFFFFFu;
+            if (idx < K) {
+                if (MODE == kDigitKey) d[i] = keys[idx];
+                else d[i] = iota ? (uint32_t)idx : vals[idx];
+            }
+        }
 #pragma unroll
         for (int i = 0; i < kRadixItems; i++) {
-            const int64_t idx = base + i * kRadixThreads + threadIdx.x;
-            if (idx < K) {
-                uint32_t d;
-                if (MODE == kDigitKey) d = (keys[idx] >> shift) & 0xFFu;
-                else d = (uint32_t)view_of_slot(seg, nv, iota ? (uint32_t)idx : vals[idx]);
-                atomicAdd(&h[w][d], 1u);
+            if (base + i * kRadixThreads + threadIdx.x < K) {
+                const uint32_t dg = MODE == kDigitKey ? (d[i] >> shift) & 0xFFu : (uint32_t)view_of_slot(seg, nv, d[i]);
+                atomicAdd(&h[w][dg], 1u);
             }
         }
     }
