@@ -52,6 +52,34 @@ BATCH_RES = [(1920, 1080), (1600, 1064), (1280, 720), (960, 540)]
 PX_1080 = 1920 * 1080
 LR = (1.6e-4 * 30.0, 1e-3, 5e-3, 5e-2, 2.5e-3, 2.5e-3 / 20)   # mean lr scaled by the 30 m scene extent
 
+# DRAM bytes (read + write) of one launch, from one ncu capture of the
+# headline workload (batched BF16, 4 x 1920x1080, 16x16 tiles, pixel-parallel
+# raster backward; profiles/step_batched_bf16_3M_4x1080p_launch_list.md).
+# Valid only while the kernel sources hash to the recorded prefixes.
+MEASURED_TRAFFIC = {
+    "raster_bwd": (2155676160 + 1030893312, {"raster_bwd.cu": "f6f38f5977885d34"}),
+    "project_bwd_adam": (2128118016 + 1099712256, {"project_bwd_adam.cu": "3400fcbaf8be17f7"}),
+    "raster_fwd": (1059240960 + 166127616, {"raster_fwd.cu": "3f2b98cc012db5e7"}),
+    "project_fwd": (1869304064 + 666724096, {"project_fwd.cu": "182c89940c0d24b9"}),
+}
+TRAFFIC_COMMON = {"gs_device.cuh": "f40b1e771be92640", "gs_internal.cuh": "33ad950b1776db18"}
+
+
+def _measured_traffic(kernel: str, headline: bool):
+    """ncu DRAM bytes of `kernel` if its sources are unchanged, else None."""
+    import hashlib
+    if not headline or kernel not in MEASURED_TRAFFIC:
+        return None
+    nbytes, files = MEASURED_TRAFFIC[kernel]
+    for name, prefix in {**files, **TRAFFIC_COMMON}.items():
+        path = os.path.join(ROOT, "paper_2605_00219_gb300", "csrc", name)
+        try:
+            if hashlib.sha1(open(path, "rb").read()).hexdigest()[:16] != prefix:
+                return None
+        except OSError:
+            return None
+    return nbytes
+
 
 def _args():
     ap = argparse.ArgumentParser()
@@ -416,8 +444,10 @@ def main():
         "raster_fwd": {"bound": "alu", "achieved": evaluated * FLOP_FWD / (acc["raster_fwd"] * 1e-3) / 1e12,
                        "peak": alu_peak, "unit": "TFLOP/s", "traffic": None},
     }
-    for r in rooflines.values():
+    headline = args.workload == "batched" and args.n == N_GAUSS and tuple(tile) == (16, 16) and impl == 0
+    for k, r in rooflines.items():
         r["frac"] = r["achieved"] / r["peak"]
+        r["traffic"] = _measured_traffic(k, headline)
     dom = max(rooflines, key=lambda k: acc[k])
     roof = dict(rooflines[dom])
     roof["kernel"] = dom

@@ -268,24 +268,24 @@ __device__ __forceinline__ uint32_t scanline_tiles(const BinGeom& g, int tw, int
 // instruction sequence in both kernels, so both take the same decisions.
 // --------------------------------------------------------------------------
 
-// power = -0.5 (ca dx^2 + cc dy^2) - cb dx dy, with dx = px - mx.
-__device__ __forceinline__ float pair_power(float dx, float dy, float ca, float cb, float cc)
-{
-    float q = __fmaf_rn(ca, __fmul_rn(dx, dx), __fmul_rn(cc, __fmul_rn(dy, dy)));
-    return __fmaf_rn(-0.5f, q, -__fmul_rn(cb, __fmul_rn(dx, dy)));
-}
 
 // Conservative mask of the 8x4-pixel warp blocks of a tile (WPR blocks per
-// row, RPB rows of blocks) that the 3-sigma box of a Gaussian (mean, conic)
-// can touch.  (ox, oy) is the tile's first pixel.  Pairs in a masked-out block
-// have d^2 > 9 with a margin, so skipping them changes no result.
-__device__ __forceinline__ uint32_t warp_block_mask(float mx, float my, float ca, float cb, float cc, int ox, int oy,
-                                                    int WPR, int RPB)
+// row, RPB rows of blocks) that a Gaussian (mean, conic, opacity) can
+// contribute to.  A pair needs d^2 <= 9 and o exp(-d^2/2) >= 1/255, i.e.
+// d^2 <= r^2 = min(9, 2 ln(255 o)); the box of that ellipse, widened by 0.1%
+// and 0.01 px, is intersected with each block.  (ox, oy) is the tile's first
+// pixel.  Pairs in a masked-out block would be skipped by the raster's own
+// tests, so skipping them changes no result.
+__device__ __forceinline__ uint32_t warp_block_mask(float mx, float my, float ca, float cb, float cc, float op,
+                                                    int ox, int oy, int WPR, int RPB)
 {
+    if (!(op * 255.0f > 1.0f)) return 0u;  // alpha never reaches 1/255
     const float det = ca * cc - cb * cb;
     if (!(det > 0.0f)) return 0xffffffffu;
-    const float ex = fmaf(3.0f * 1.001f, sqrtf(cc / det), 0.01f);
-    const float ey = fmaf(3.0f * 1.001f, sqrtf(ca / det), 0.01f);
+    const float r2 = fminf(9.0f, 2.0f * __logf(op * 255.0f)) * 1.002f + 1e-3f;
+    const float rr = sqrtf(r2);
+    const float ex = fmaf(rr, sqrtf(cc / det), 0.01f);
+    const float ey = fmaf(rr, sqrtf(ca / det), 0.01f);
     // pixel-centre coordinates relative to the tile's first centre
     const float xl = fminf(fmaxf(mx - ex - ((float)ox + 0.5f), -1e4f), 1e4f);
     const float xh = fminf(fmaxf(mx + ex - ((float)ox + 0.5f), -1e4f), 1e4f);
@@ -297,6 +297,32 @@ __device__ __forceinline__ uint32_t warp_block_mask(float mx, float my, float ca
     for (int by = by0; by <= by1; by++)
         for (int bx = bx0; bx <= bx1; bx++) m |= 1u << (by * WPR + bx);
     return m;
+}
+
+// Exponent in base 2: power2 = log2(e) * power = dx (A dx + B dy) + C dy^2
+// with (A, B, C) = -log2(e) (ca / 2, cb, cc / 2), prescaled once per staged
+// list entry; G = 2^power2 by the hardware exp2.  Raster forward and backward
+// use these same helpers, so they take the same decisions.
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kPow2Min = -4.5f * 1.4426950408889634f;   // d^2 = 9
+
+__device__ __forceinline__ float4 pair_coefs(float mx, float my, float ca, float cb, float cc)
+{
+    return make_float4(mx, my, __fmul_rn(-0.5f * kLog2e, ca), __fmul_rn(-kLog2e, cb));
+}
+
+__device__ __forceinline__ float pair_c2(float cc) { return __fmul_rn(-0.5f * kLog2e, cc); }
+
+__device__ __forceinline__ float pair_power2(float dx, float dy, float A, float B, float C)
+{
+    return __fmaf_rn(dx, __fmaf_rn(A, dx, __fmul_rn(B, dy)), __fmul_rn(__fmul_rn(C, dy), dy));
+}
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
 constexpr float kAlphaMin = 1.0f / 255.0f;

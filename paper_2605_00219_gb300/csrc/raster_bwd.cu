@@ -152,9 +152,10 @@ __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(Views V, const uint2
                     const float4 a = sm.gA[j];
                     const float4 b = sm.gB[j];
                     const float dx = fx - a.x, dy = fy - a.y;
-                    const float power = pair_power(dx, dy, a.z, a.w, b.x);
-                    if (power < -4.5f) continue;
-                    const float G = __expf(power);
+                    const float4 pc = pair_coefs(a.x, a.y, a.z, a.w, b.x);
+                    const float p2 = pair_power2(dx, dy, pc.z, pc.w, pair_c2(b.x));
+                    if (p2 < kPow2Min) continue;
+                    const float G = ex2_approx(p2);
                     const float alpha = fminf(kAlphaMax, __fmul_rn(b.y, G));
                     if (alpha < kAlphaMin) continue;
                     const float wgt = alpha * Th;
@@ -210,9 +211,10 @@ __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(Views V, const uint2
                     if (myidx < __float_as_uint(d.w)) {
                         const float dx = (float)(ox + pi % tw) + 0.5f - a.x;
                         const float dy = (float)(oy + pi / tw) + 0.5f - a.y;
-                        const float power = pair_power(dx, dy, a.z, a.w, b.x);
-                        if (power >= -4.5f) {
-                            const float G = __expf(power);
+                        const float4 pc = pair_coefs(a.x, a.y, a.z, a.w, b.x);
+                        const float p2 = pair_power2(dx, dy, pc.z, pc.w, pair_c2(b.x));
+                        if (p2 >= kPow2Min) {
+                            const float G = ex2_approx(p2);
                             const float araw = __fmul_rn(b.y, G);
                             const float alpha = fminf(kAlphaMax, araw);
                             if (alpha >= kAlphaMin) {
@@ -390,11 +392,11 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint2* __re
     constexpr int NW = BS / 32;
     constexpr int WPR = TW / 8;            // 8x4 warp blocks per tile row
     constexpr int RPB = BS / TW / 4;       // rows of warp blocks
-    constexpr int BB = NW <= 8 ? 128 : 64; // list entries per staged batch
+    constexpr int BB = NW <= 8 ? 96 : 64;  // list entries per staged batch
     constexpr int IPT = (BB + BS - 1) / BS;   // staged entries per thread
     __shared__ float4 sA[2][BB];
     __shared__ float4 sB[2][BB];
-    __shared__ float sC[2][BB];
+    __shared__ float4 sD[2][BB];          // (conic a, b, c, blue)
     __shared__ uint32_t sE[2][BB];
     __shared__ uint32_t sM[2][BB];
     __shared__ float part[NW][BB][9];
@@ -440,11 +442,11 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint2* __re
     // buffer: two barriers per batch.
     auto stage = [&](int bbx, int buf, int i, const ProjRec& q, uint32_t e) {
         (void)bbx;
-        sA[buf][i] = q.a;
-        sB[buf][i] = q.b;
-        sC[buf][i] = q.c.x;
+        sA[buf][i] = pair_coefs(q.a.x, q.a.y, q.a.z, q.a.w, q.b.x);
+        sB[buf][i] = make_float4(pair_c2(q.b.x), q.b.y, q.b.z, q.b.w);
+        sD[buf][i] = make_float4(q.a.z, q.a.w, q.b.x, q.c.x);
         sE[buf][i] = e;
-        sM[buf][i] = warp_block_mask(q.a.x, q.a.y, q.a.z, q.a.w, q.b.x, ox, oy, WPR, RPB);
+        sM[buf][i] = warp_block_mask(q.a.x, q.a.y, q.a.z, q.a.w, q.b.x, q.b.y, ox, oy, WPR, RPB);
     };
     int bb = ((L + BB - 1) / BB - 1) * BB;
     if (bb >= 0) {
@@ -459,7 +461,7 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint2* __re
         const int cnt = min(BB, L - bb);
         const float4* __restrict__ cA = sA[cur];
         const float4* __restrict__ cB = sB[cur];
-        const float* __restrict__ cC = sC[cur];
+        const float4* __restrict__ cD = sD[cur];
         const uint32_t* __restrict__ cM = sM[cur];
         // gathers for the next (lower) batch, all entries full since bb > 0
         ProjRec qn[IPT];
@@ -491,14 +493,15 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint2* __re
                     const float4 a = cA[j];
                     const float4 b = cB[j];
                     const float dx = fx - a.x, dy = fy - a.y;
-                    const float power = pair_power(dx, dy, a.z, a.w, b.x);
-                    if (power >= -4.5f) {
-                        const float G = __expf(power);
+                    const float p2 = pair_power2(dx, dy, a.z, a.w, b.x);
+                    if (p2 >= kPow2Min) {
+                        const float G = ex2_approx(p2);
                         const float araw = __fmul_rn(b.y, G);
                         const float alpha = fminf(kAlphaMax, araw);
                         if (alpha >= kAlphaMin) {
                             hit = true;
-                            const float cb = cC[j];
+                            const float4 cd = cD[j];
+                            const float cb = cd.w;
                             // compensated T_before = (Th + Tl) / (1 - alpha)
                             const float om = __fsub_rn(1.0f, alpha);
                             const float om_err = __fsub_rn(-alpha, __fsub_rn(om, 1.0f));
@@ -525,8 +528,8 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint2* __re
                                 g[2] = -0.5f * dx * dx * dp;
                                 g[3] = -dx * dy * dp;
                                 g[4] = -0.5f * dy * dy * dp;
-                                g[0] = fmaf(a.z, dx, a.w * dy) * dp;
-                                g[1] = fmaf(a.w, dx, b.x * dy) * dp;
+                                g[0] = fmaf(cd.x, dx, cd.y * dy) * dp;
+                                g[1] = fmaf(cd.y, dx, cd.z * dy) * dp;
                             }
                         }
                     }

@@ -48,10 +48,10 @@ __global__ void __launch_bounds__(BS) k_raster_fwd(Views V, const uint2* __restr
     // while chunk i is composited (pair indices one chunk further ahead)
     if (r.x + threadIdx.x < r.y) {
         const ProjRec q = rec[pid_sorted[r.x + threadIdx.x]];
-        sA[0][threadIdx.x] = q.a;
-        sB[0][threadIdx.x] = q.b;
+        sA[0][threadIdx.x] = pair_coefs(q.a.x, q.a.y, q.a.z, q.a.w, q.b.x);
+        sB[0][threadIdx.x] = make_float4(pair_c2(q.b.x), q.b.y, q.b.z, q.b.w);
         sC[0][threadIdx.x] = q.c.x;
-        sM[0][threadIdx.x] = warp_block_mask(q.a.x, q.a.y, q.a.z, q.a.w, q.b.x, ox, oy, WPR, RPB);
+        sM[0][threadIdx.x] = warp_block_mask(q.a.x, q.a.y, q.a.z, q.a.w, q.b.x, q.b.y, ox, oy, WPR, RPB);
     }
     uint32_t pid_next = r.x + BS + threadIdx.x < r.y ? pid_sorted[r.x + BS + threadIdx.x] : 0u;
     int cur = 0;
@@ -75,9 +75,9 @@ __global__ void __launch_bounds__(BS) k_raster_fwd(Views V, const uint2* __restr
                 const float4 a = cA[j];
                 const float dx = fx - a.x, dy = fy - a.y;
                 const float4 b = cB[j];
-                const float power = pair_power(dx, dy, a.z, a.w, b.x);
-                if (power < -4.5f) continue;
-                const float G = __expf(power);
+                const float p2 = pair_power2(dx, dy, a.z, a.w, b.x);
+                if (p2 < kPow2Min) continue;
+                const float G = ex2_approx(p2);
                 const float alpha = fminf(kAlphaMax, __fmul_rn(b.y, G));
                 if (alpha < kAlphaMin) continue;
                 // compensated T * (1 - alpha)
@@ -103,10 +103,10 @@ __global__ void __launch_bounds__(BS) k_raster_fwd(Views V, const uint2* __restr
         }
         if (have_next) {
             const int nb = cur ^ 1;
-            sA[nb][threadIdx.x] = qn.a;
-            sB[nb][threadIdx.x] = qn.b;
+            sA[nb][threadIdx.x] = pair_coefs(qn.a.x, qn.a.y, qn.a.z, qn.a.w, qn.b.x);
+            sB[nb][threadIdx.x] = make_float4(pair_c2(qn.b.x), qn.b.y, qn.b.z, qn.b.w);
             sC[nb][threadIdx.x] = qn.c.x;
-            sM[nb][threadIdx.x] = warp_block_mask(qn.a.x, qn.a.y, qn.a.z, qn.a.w, qn.b.x, ox, oy, WPR, RPB);
+            sM[nb][threadIdx.x] = warp_block_mask(qn.a.x, qn.a.y, qn.a.z, qn.a.w, qn.b.x, qn.b.y, ox, oy, WPR, RPB);
         }
     }
     if (gt == 0 && threadIdx.x < 3) hdr->bg[threadIdx.x] = bg ? bg[threadIdx.x] : 0.f;
