@@ -365,3 +365,40 @@ def test_bf16_storage_step(gs, orc):
         # one bf16 ulp of rounding plus the FP32 gradient's own 1e-3 (x2 for v)
         bound = _bf16_ulp(orc_a) + 2e-3 * np.abs(orc_a)
         assert np.all(np.abs(mg - orc_a)[ok] <= bound[ok]), name
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+def test_multi_view_full_step_adam(gs, orc, bf16):
+    """Four views of one scene in one step (loss over all views, one Adam
+    update; the fused kernel then spreads each Gaussian over four lanes):
+    post-Adam parameters against the oracle's multi-view step."""
+    gsstep, step_mod = gs
+    scene = synth.cluster_scene(8000, 8, 2.5, seed=4, log_scale=(-3.4, 0.4), logit_opacity=(0.0, 1.0))
+    if bf16:
+        scene.sh = _bf16_round(scene.sh)
+    cams = synth.orbit_cameras(4, 5.0, 96, 72, hfov_deg=55.0)
+    tscene = synth.perturbed(scene, 9)
+    targets = []
+    for c in cams:
+        targets.append(orc.render64(c, orc.project64(orc.Params64.from_scene(tscene), c), orc.bin32(tscene, c)).image)
+    res = orc.step(scene, cams, targets, LR, 1)
+    tr = step_mod.Trainer([scene], cams, lr=LR, sh_bf16=bf16, mom_bf16=bf16)
+    tr.set_target([t.astype(np.float32) for t in targets])
+    tr.step(step=1)
+    torch.cuda.synchronize()
+    assert tr.stats().status == 0
+    bad = np.zeros(scene.n, bool)
+    for c, r, P, tg in zip(cams, res.renders, res.projs, targets):
+        r.unstable_px |= (np.abs(r.image - tg) < 1e-5).any(-1)
+        bad |= _unstable_gaussians(P, r, c)
+    g = res.grad
+    rms = np.sqrt((g[~bad] ** 2).mean(0)) + 1e-30
+    decided = (np.abs(g) > 1e-2 * rms[None, :]) & ~bad[:, None]
+    assert decided.sum() > 0.3 * g.size
+    new = tr.scenes[0].to_scene()
+    th = np.concatenate([new.means, new.quats, np.log(new.scales), np.log(new.opacities / (1 - new.opacities))[:, None],
+                         new.sh.reshape(-1, 48)], axis=1).astype(np.float64)
+    tol = 1e-5 * np.abs(res.theta) + 1e-6
+    if bf16:
+        tol[:, 11:] += _bf16_ulp(res.theta[:, 11:])
+    assert np.all(np.abs(th - res.theta)[decided] <= tol[decided])
