@@ -106,6 +106,23 @@ def _dist():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def max_over_ranks(value: float, device="cpu") -> float:
+    """Largest `value` over all ranks of the initialised process group (the
+    bench's time is the slowest replica's); the value itself with one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, views_per_step: int, ms_per_step: float) -> float:
+    """Views trained per second by all replicas (each rank one replica)."""
+    return world * views_per_step * 1e3 / ms_per_step
+
+
 def _views(workload):
     from paper_2605_00219_gb300 import synth
     if workload == "plain":
@@ -380,9 +397,7 @@ def main():
     with ClockSampler(local) as clk:
         ms = _time_replays(torch, tr, args.steps, stream)
     if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, "cuda")
         torch.distributed.barrier()
     st = tr.stats()
     K = int(st.k_required)
@@ -469,7 +484,7 @@ def main():
                          f"tiles, scaled to the full images ({info['measured_s']:.1f} s measured)"}
 
     if rank == 0:
-        value = ws * nviews * 1e3 / ms
+        value = whole_job_rate(ws, nviews, ms)
         desc = ("batched BF16: " if batched else "plain FP32: ") + \
                f"{n / 1e6:.3g}M Gaussians (256 clusters, 30 m box), views per step " + \
                "+".join(f"{c.width}x{c.height}" for c in cams) + \

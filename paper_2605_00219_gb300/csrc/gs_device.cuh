@@ -67,7 +67,10 @@ struct WsHeader {
 // Projected record of one (view, Gaussian) pair, read by the raster kernels.
 //   a = (mean x, mean y, conic a, conic b)
 //   b = (conic c, opacity, red, green)
-//   c = (blue, depth, unused, unused)
+//   c = (blue, depth, mean x residual, mean y residual)
+// The mean is the bit-specified binning value; the residuals make
+// mean + residual the pixel-space mean to about 1e-12 relative, so pixel
+// offsets near x ~ 2000 px keep full FP32 accuracy.
 struct __align__(16) ProjRec {
     float4 a, b, c;
 };
@@ -323,6 +326,61 @@ __device__ __forceinline__ float ex2_approx(float x)
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+
+// Pixel-centre offset from a Gaussian's mean: (p - mean) - residual.  Both
+// raster kernels use this one expression, so they agree bit for bit.
+__device__ __forceinline__ float pix_offset(float pc, float m_hi, float m_lo)
+{
+    return __fsub_rn(__fsub_rn(pc, m_hi), m_lo);
+}
+
+// Error-free transforms (Knuth TwoSum, FMA-based TwoProduct) for the
+// compensated pixel-space mean.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// mean2D = f * t_u / t_z + c with t = R mu + tcam, to about 1e-12 relative:
+// returns hi + lo (hi is a rounded value, lo the residual).
+__device__ __forceinline__ void accurate_mean2d(const float* cam, float4 mu, float& mx, float& mx_lo, float& my,
+                                                float& my_lo)
+{
+    float th[3], tl[3];
+    const float mv[3] = {mu.x, mu.y, mu.z};
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        float p[3], e[3];
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            p[j] = __fmul_rn(cam[3 * i + j], mv[j]);
+            e[j] = __fmaf_rn(cam[3 * i + j], mv[j], -p[j]);
+        }
+        float s1, e1, s2, e2, s3, e3;
+        two_sum(p[0], p[1], s1, e1);
+        two_sum(s1, p[2], s2, e2);
+        two_sum(s2, cam[9 + i], s3, e3);
+        th[i] = s3;
+        tl[i] = ((e[0] + e[1]) + (e[2] + e1)) + (e2 + e3);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const float f = cam[12 + k], c = cam[14 + k];
+        const float q = __fdiv_rn(th[k], th[2]);
+        const float rem = __fmaf_rn(-q, th[2], th[k]);                   // exact
+        const float ql = (rem + tl[k] - q * tl[2]) / th[2];
+        const float p = __fmul_rn(f, q);
+        const float pe = __fmaf_rn(f, q, -p);
+        float s, se;
+        two_sum(p, c, s, se);
+        const float lo = pe + f * ql + se;
+        float hi, hl;
+        two_sum(s, lo, hi, hl);
+        if (k == 0) { mx = hi; mx_lo = hl; } else { my = hi; my_lo = hl; }
+    }
 }
 
 constexpr float kAlphaMin = 1.0f / 255.0f;

@@ -60,10 +60,14 @@ __global__ void __launch_bounds__(256) k_project_fwd(Views V, Scenes S, const fl
         for (int k = 0; k < 16; k++) acc = fmaf(shv[3 * k + c], Y[k], acc);
         col[c] = fmaxf(acc, 0.0f);
     }
+    // residuals of the binning mean against the compensated mean
+    float amx, amx_lo, amy, amy_lo;
+    accurate_mean2d(cam, mu, amx, amx_lo, amy, amy_lo);
+    const float rx = (amx - bg.mx) + amx_lo, ry = (amy - bg.my) + amy_lo;
     ProjRec r;
     r.a = make_float4(bg.mx, bg.my, ca, cb);
     r.b = make_float4(cc, so.w, col[0], col[1]);
-    r.c = make_float4(col[2], bg.tz, 0.f, 0.f);
+    r.c = make_float4(col[2], bg.tz, rx, ry);
     rec[p] = r;
     binrec[p] = make_float4(bg.a, bg.b, bg.c, __uint_as_float(bg.mant));
 }

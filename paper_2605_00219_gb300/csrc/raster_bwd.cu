@@ -35,6 +35,7 @@ struct BwdSmem {
     float4* gA;     // [128] (mx, my, ca, cb)
     float4* gB;     // [128] (cc, o, r, g)
     float* gC;      // [128] blue
+    float2* gL;     // [128] mean residuals
     uint32_t* ge;   // [128] emission slot
     float* red;     // [128][9] partial gradients
     int* misc;
@@ -42,7 +43,7 @@ struct BwdSmem {
 
 __host__ __device__ constexpr size_t bwd_smem_bytes(int P)
 {
-    return (size_t)16 * P * 4 + (size_t)16 * 4 * P + 128 * (16 + 16 + 4 + 4) + 128 * 9 * 4 + 16;
+    return (size_t)16 * P * 4 + (size_t)16 * 4 * P + 128 * (16 + 16 + 8 + 4 + 4) + 128 * 9 * 4 + 16;
 }
 
 __device__ __forceinline__ void neumaier_add(float& s, float& c, float x)
@@ -71,7 +72,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(Views V, const uint2
     sm.st = sm.pdl + P;
     sm.gA = sm.st + 4 * P;
     sm.gB = sm.gA + 128;
-    sm.gC = reinterpret_cast<float*>(sm.gB + 128);
+    sm.gL = reinterpret_cast<float2*>(sm.gB + 128);
+    sm.gC = reinterpret_cast<float*>(sm.gL + 128);
     sm.ge = reinterpret_cast<uint32_t*>(sm.gC + 128);
     sm.red = reinterpret_cast<float*>(sm.ge + 128);
     sm.misc = reinterpret_cast<int*>(sm.red + 128 * 9);
@@ -131,6 +133,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(Views V, const uint2
             sm.gA[tid] = q.a;
             sm.gB[tid] = q.b;
             sm.gC[tid] = q.c.x;
+            sm.gL[tid] = make_float2(q.c.z, q.c.w);
             sm.ge[tid] = vals_sorted[k];
         }
         __syncthreads();
@@ -151,7 +154,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(Views V, const uint2
                     if (bb + j >= nl) break;
                     const float4 a = sm.gA[j];
                     const float4 b = sm.gB[j];
-                    const float dx = fx - a.x, dy = fy - a.y;
+                    const float2 ml = sm.gL[j];
+                    const float dx = pix_offset(fx, a.x, ml.x), dy = pix_offset(fy, a.y, ml.y);
                     const float4 pc = pair_coefs(a.x, a.y, a.z, a.w, b.x);
                     const float p2 = pair_power2(dx, dy, pc.z, pc.w, pair_c2(b.x));
                     if (p2 < kPow2Min) continue;
@@ -190,7 +194,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(Views V, const uint2
         if (warp_on) {
             float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
             float cbl = 0.f;
-            if (act) { a = sm.gA[j]; b = sm.gB[j]; cbl = sm.gC[j]; }
+            float2 ml = make_float2(0.f, 0.f);
+            if (act) { a = sm.gA[j]; b = sm.gB[j]; cbl = sm.gC[j]; ml = sm.gL[j]; }
             const uint32_t myidx = bb + j;
             const int p0 = pg * glen;
             float T = 1.f, S0 = 0.f, S1 = 0.f, S2 = 0.f;
@@ -209,8 +214,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(Views V, const uint2
                     const int pi = p0 + pl;
                     const float4 d = sm.pdl[pi];
                     if (myidx < __float_as_uint(d.w)) {
-                        const float dx = (float)(ox + pi % tw) + 0.5f - a.x;
-                        const float dy = (float)(oy + pi / tw) + 0.5f - a.y;
+                        const float dx = pix_offset((float)(ox + pi % tw) + 0.5f, a.x, ml.x);
+                        const float dy = pix_offset((float)(oy + pi / tw) + 0.5f, a.y, ml.y);
                         const float4 pc = pair_coefs(a.x, a.y, a.z, a.w, b.x);
                         const float p2 = pair_power2(dx, dy, pc.z, pc.w, pair_c2(b.x));
                         if (p2 >= kPow2Min) {
@@ -397,6 +402,7 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint2* __re
     __shared__ float4 sA[2][BB];
     __shared__ float4 sB[2][BB];
     __shared__ float4 sD[2][BB];          // (conic a, b, c, blue)
+    __shared__ float2 sL[2][BB];          // mean residuals
     __shared__ uint32_t sE[2][BB];
     __shared__ uint32_t sM[2][BB];
     __shared__ float part[NW][BB][9];
@@ -445,6 +451,7 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint2* __re
         sA[buf][i] = pair_coefs(q.a.x, q.a.y, q.a.z, q.a.w, q.b.x);
         sB[buf][i] = make_float4(pair_c2(q.b.x), q.b.y, q.b.z, q.b.w);
         sD[buf][i] = make_float4(q.a.z, q.a.w, q.b.x, q.c.x);
+        sL[buf][i] = make_float2(q.c.z, q.c.w);
         sE[buf][i] = e;
         sM[buf][i] = warp_block_mask(q.a.x, q.a.y, q.a.z, q.a.w, q.b.x, q.b.y, ox, oy, WPR, RPB);
     };
@@ -462,6 +469,7 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint2* __re
         const float4* __restrict__ cA = sA[cur];
         const float4* __restrict__ cB = sB[cur];
         const float4* __restrict__ cD = sD[cur];
+        const float2* __restrict__ cL = sL[cur];
         const uint32_t* __restrict__ cM = sM[cur];
         // gathers for the next (lower) batch, all entries full since bb > 0
         ProjRec qn[IPT];
@@ -492,7 +500,8 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint2* __re
                 if (bb + j < (int)nl) {
                     const float4 a = cA[j];
                     const float4 b = cB[j];
-                    const float dx = fx - a.x, dy = fy - a.y;
+                    const float2 ml = cL[j];
+                    const float dx = pix_offset(fx, a.x, ml.x), dy = pix_offset(fy, a.y, ml.y);
                     const float p2 = pair_power2(dx, dy, a.z, a.w, b.x);
                     if (p2 >= kPow2Min) {
                         const float G = ex2_approx(p2);

@@ -21,10 +21,11 @@ __global__ void __launch_bounds__(BS) k_raster_fwd(Views V, const uint2* __restr
                                                    float* __restrict__ image, float* __restrict__ tfinal,
                                                    uint32_t* __restrict__ nlast, WsHeader* __restrict__ hdr)
 {
-    __shared__ float4 sA[2][BS];
-    __shared__ float4 sB[2][BS];
-    __shared__ float sC[2][BS];
-    __shared__ uint32_t sM[2][BS];
+    constexpr int CH = BS > 256 ? 256 : BS;   // list entries per staged chunk
+    __shared__ float4 sA[2][CH];
+    __shared__ float4 sB[2][CH];
+    __shared__ float4 sC[2][CH];   // (blue, mean residual x, y, -)
+    __shared__ uint32_t sM[2][CH];
     __shared__ unsigned long long sblend[BS / 32];
     constexpr int WPR = TW / 8, RPB = BS / TW / 4;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -46,26 +47,26 @@ __global__ void __launch_bounds__(BS) k_raster_fwd(Views V, const uint2* __restr
     int done = !inside;
     // chunk 0 staged directly; afterwards chunk i+1's records are gathered
     // while chunk i is composited (pair indices one chunk further ahead)
-    if (r.x + threadIdx.x < r.y) {
+    if (threadIdx.x < CH && r.x + threadIdx.x < r.y) {
         const ProjRec q = rec[pid_sorted[r.x + threadIdx.x]];
         sA[0][threadIdx.x] = pair_coefs(q.a.x, q.a.y, q.a.z, q.a.w, q.b.x);
         sB[0][threadIdx.x] = make_float4(pair_c2(q.b.x), q.b.y, q.b.z, q.b.w);
-        sC[0][threadIdx.x] = q.c.x;
+        sC[0][threadIdx.x] = make_float4(q.c.x, q.c.z, q.c.w, 0.f);
         sM[0][threadIdx.x] = warp_block_mask(q.a.x, q.a.y, q.a.z, q.a.w, q.b.x, q.b.y, ox, oy, WPR, RPB);
     }
-    uint32_t pid_next = r.x + BS + threadIdx.x < r.y ? pid_sorted[r.x + BS + threadIdx.x] : 0u;
+    uint32_t pid_next = threadIdx.x < CH && r.x + CH + threadIdx.x < r.y ? pid_sorted[r.x + CH + threadIdx.x] : 0u;
     int cur = 0;
-    for (uint32_t base = r.x; base < r.y; base += BS, cur ^= 1) {
+    for (uint32_t base = r.x; base < r.y; base += CH, cur ^= 1) {
         if (__syncthreads_count(done) == BS) break;
-        const bool have_next = base + BS + threadIdx.x < r.y;
+        const bool have_next = threadIdx.x < CH && base + CH + threadIdx.x < r.y;
         ProjRec qn;
         if (have_next) qn = rec[pid_next];
-        if (base + 2 * BS + threadIdx.x < r.y) pid_next = pid_sorted[base + 2 * BS + threadIdx.x];
+        if (threadIdx.x < CH && base + 2 * CH + threadIdx.x < r.y) pid_next = pid_sorted[base + 2 * CH + threadIdx.x];
         const float4* __restrict__ cA = sA[cur];
         const float4* __restrict__ cB = sB[cur];
-        const float* __restrict__ cC = sC[cur];
+        const float4* __restrict__ cC = sC[cur];
         const uint32_t* __restrict__ cM = sM[cur];
-        const int cnt = (int)min((uint32_t)BS, r.y - base);
+        const int cnt = (int)min((uint32_t)CH, r.y - base);
         for (int c0 = 0; c0 < cnt; c0 += 32) {
             uint32_t bits = __ballot_sync(0xffffffffu, c0 + lane < cnt && (cM[c0 + lane] & wbit));
             if (done) continue;
@@ -73,7 +74,8 @@ __global__ void __launch_bounds__(BS) k_raster_fwd(Views V, const uint2* __restr
                 const int j = c0 + __ffs(bits) - 1;
                 bits &= bits - 1;
                 const float4 a = cA[j];
-                const float dx = fx - a.x, dy = fy - a.y;
+                const float4 cl = cC[j];
+                const float dx = pix_offset(fx, a.x, cl.y), dy = pix_offset(fy, a.y, cl.z);
                 const float4 b = cB[j];
                 const float p2 = pair_power2(dx, dy, a.z, a.w, b.x);
                 if (p2 < kPow2Min) continue;
@@ -94,7 +96,7 @@ __global__ void __launch_bounds__(BS) k_raster_fwd(Views V, const uint2* __restr
                 const float wgt = alpha * Th;
                 C0 = fmaf(b.z, wgt, C0);
                 C1 = fmaf(b.w, wgt, C1);
-                C2 = fmaf(cC[j], wgt, C2);
+                C2 = fmaf(cl.x, wgt, C2);
                 Tl = __fsub_rn(lo, __fsub_rn(hi, pr));
                 Th = hi;
                 last = base - r.x + j + 1;
@@ -105,7 +107,7 @@ __global__ void __launch_bounds__(BS) k_raster_fwd(Views V, const uint2* __restr
             const int nb = cur ^ 1;
             sA[nb][threadIdx.x] = pair_coefs(qn.a.x, qn.a.y, qn.a.z, qn.a.w, qn.b.x);
             sB[nb][threadIdx.x] = make_float4(pair_c2(qn.b.x), qn.b.y, qn.b.z, qn.b.w);
-            sC[nb][threadIdx.x] = qn.c.x;
+            sC[nb][threadIdx.x] = make_float4(qn.c.x, qn.c.z, qn.c.w, 0.f);
             sM[nb][threadIdx.x] = warp_block_mask(qn.a.x, qn.a.y, qn.a.z, qn.a.w, qn.b.x, qn.b.y, ox, oy, WPR, RPB);
         }
     }
