@@ -355,3 +355,74 @@ def step(scene, cams, targets, lr, step_idx=1, m=None, v=None, bg=(0.0, 0.0, 0.0
     if not grad_only:
         adam64(theta, mm, vv, grad, lr, step_idx)
     return StepResult(bins, projs, rends, loss, dl, g2s, grad, theta, mm, vv, Params64.from_theta(theta))
+
+
+# --------------------------------------------------------------------------
+# L1 + SSIM loss (Sec. 4.5: weighted sum of L1 and SSIM on channel-last
+# renders, reference image stored as 8-bit RGBA)
+# --------------------------------------------------------------------------
+
+SSIM_C1 = 0.01 ** 2
+SSIM_C2 = 0.03 ** 2
+
+
+def ssim_window(size: int = 11, sigma: float = 1.5) -> np.ndarray:
+    """1-D Gaussian window, normalised to sum 1 (the 2-D window is its outer
+    product)."""
+    x = np.arange(size, dtype=np.float64) - size // 2
+    g = np.exp(-x * x / (2.0 * sigma * sigma))
+    return g / g.sum()
+
+
+def _wfilter(img, g):
+    """Window-weighted sum with zero padding outside the image, same size."""
+    from scipy.ndimage import correlate1d
+    t = correlate1d(img, g, axis=0, mode="constant", cval=0.0)
+    return correlate1d(t, g, axis=1, mode="constant", cval=0.0)
+
+
+def rgba8_to_float(target_rgba8):
+    """8-bit RGBA reference -> float RGB in [0, 1]."""
+    return np.asarray(target_rgba8, np.float64)[..., :3] / 255.0
+
+
+def l1_ssim_loss_grad(images, targets, lam: float = 0.2):
+    """L = (1 - lam) L1 + lam (1 - SSIM) over all pixels and channels of all
+    views (means over 3 x pixels); SSIM per channel with an 11x11 Gaussian
+    window (sigma 1.5), zero padding, C1 = 0.01^2, C2 = 0.03^2.  Returns
+    (loss, [dL/dC per view]).
+
+    The SSIM map at q depends on the rendered image x through the window
+    moments mu_x, E[x^2], E[xy] at q; with A = dSSIM/dmu_x, B = dSSIM/dE[x^2]
+    and Cc = dSSIM/dE[xy] at every q, dSSIM_sum/dx_p = (w * A)(p) +
+    2 x_p (w * B)(p) + y_p (w * Cc)(p) (the window is symmetric)."""
+    g = ssim_window()
+    total = sum(int(np.prod(im.shape)) for im in images)
+    l1 = 0.0
+    ssim_sum = 0.0
+    grads = []
+    for x3, y3 in zip(images, targets):
+        x3 = np.asarray(x3, np.float64)
+        y3 = np.asarray(y3, np.float64)
+        d = np.zeros_like(x3)
+        for c in range(3):
+            x, y = x3[..., c], y3[..., c]
+            mx, my = _wfilter(x, g), _wfilter(y, g)
+            vx = _wfilter(x * x, g) - mx * mx
+            vy = _wfilter(y * y, g) - my * my
+            cxy = _wfilter(x * y, g) - mx * my
+            a1 = 2 * mx * my + SSIM_C1
+            a2 = 2 * cxy + SSIM_C2
+            b1 = mx * mx + my * my + SSIM_C1
+            b2 = vx + vy + SSIM_C2
+            s = a1 * a2 / (b1 * b2)
+            ssim_sum += float(s.sum())
+            A = 2 * my * (a2 - a1) / (b1 * b2) - 2 * mx * s / b1 + 2 * mx * s / b2
+            B = -s / b2
+            Cc = 2 * a1 / (b1 * b2)
+            dS = _wfilter(A, g) + 2 * x * _wfilter(B, g) + y * _wfilter(Cc, g)
+            d[..., c] = (1 - lam) * np.sign(x - y) / total - lam * dS / total
+        l1 += float(np.abs(x3 - y3).sum())
+        grads.append(d)
+    loss = (1 - lam) * l1 / total + lam * (1 - ssim_sum / total)
+    return loss, grads

@@ -1,0 +1,72 @@
+"""Pins of the oracle's L1 + SSIM loss and gradient (no GPU)."""
+import numpy as np
+import pytest
+
+
+def test_ssim_constant_images_closed_form(orc):
+    """Constant images a, b: away from the border (window inside the image)
+    SSIM = (2ab + C1) / (a^2 + b^2 + C1) per channel."""
+    H, W = 40, 48
+    x = np.full((H, W, 3), 0.6)
+    y = np.full((H, W, 3), 0.25)
+    g = orc.ssim_window()
+    from scipy.ndimage import correlate1d
+
+    def f(img):
+        return correlate1d(correlate1d(img, g, axis=0, mode="constant"), g, axis=1, mode="constant")
+    mx, my = f(x[..., 0]), f(y[..., 0])
+    s = (2 * mx * my + orc.SSIM_C1) * (2 * (f(x[..., 0] * y[..., 0]) - mx * my) + orc.SSIM_C2) / (
+        (mx * mx + my * my + orc.SSIM_C1) * (f(x[..., 0] ** 2) - mx * mx + f(y[..., 0] ** 2) - my * my + orc.SSIM_C2))
+    expect = (2 * 0.6 * 0.25 + orc.SSIM_C1) / (0.6 ** 2 + 0.25 ** 2 + orc.SSIM_C1)
+    assert s[10:-10, 10:-10] == pytest.approx(expect, rel=1e-12)
+    # the loss with lam = 1 averages exactly these maps
+    loss, _ = orc.l1_ssim_loss_grad([x], [y], lam=1.0)
+    assert loss == pytest.approx(1 - s.mean(), rel=1e-12)
+
+
+def test_ssim_identical_images():
+    """x = y: SSIM = 1 everywhere and the SSIM term has zero gradient."""
+    from oracle import oracle as orc
+    rng = np.random.default_rng(0)
+    x = rng.uniform(size=(20, 24, 3))
+    loss, (g,) = orc.l1_ssim_loss_grad([x], [x.copy()], lam=1.0)
+    assert loss == pytest.approx(0.0, abs=1e-12)
+    assert np.abs(g).max() < 1e-12
+
+
+def test_ssim_symmetric():
+    from oracle import oracle as orc
+    rng = np.random.default_rng(1)
+    x, y = rng.uniform(size=(2, 16, 18, 3))
+    l1, _ = orc.l1_ssim_loss_grad([x], [y], lam=1.0)
+    l2, _ = orc.l1_ssim_loss_grad([y], [x], lam=1.0)
+    assert l1 == pytest.approx(l2, rel=1e-13)
+
+
+@pytest.mark.parametrize("lam", [0.2, 1.0])
+def test_l1_ssim_gradient_fd(orc, lam):
+    """Analytic gradient against central differences (two views, border
+    pixels included, zero padding)."""
+    rng = np.random.default_rng(2)
+    xs = [rng.uniform(0.1, 0.9, size=(13, 11, 3)), rng.uniform(0.1, 0.9, size=(9, 15, 3))]
+    ys = [rng.uniform(0.1, 0.9, size=x.shape) for x in xs]
+    loss, grads = orc.l1_ssim_loss_grad(xs, ys, lam=lam)
+    h = 1e-6
+    for v in range(2):
+        for idx in [(0, 0, 0), (6, 5, 1), (12, 10, 2), (3, 0, 2), (8, 14, 0)][: (5 if v else 3)]:
+            if v == 0 and (idx[0] >= 13 or idx[1] >= 11):
+                continue
+            if v == 1 and (idx[0] >= 9 or idx[1] >= 15):
+                continue
+            xp = [x.copy() for x in xs]
+            xm = [x.copy() for x in xs]
+            xp[v][idx] += h
+            xm[v][idx] -= h
+            fd = (orc.l1_ssim_loss_grad(xp, ys, lam)[0] - orc.l1_ssim_loss_grad(xm, ys, lam)[0]) / (2 * h)
+            assert grads[v][idx] == pytest.approx(fd, rel=1e-5, abs=1e-12)
+
+
+def test_rgba8_target():
+    from oracle import oracle as orc
+    t = np.array([[[255, 0, 51, 7]]], np.uint8)
+    np.testing.assert_allclose(orc.rgba8_to_float(t), [[[1.0, 0.0, 0.2]]])
