@@ -8,6 +8,7 @@
  *                       tile ranges                             (Sec. 4.1, 4.4)
  *   gs_raster_fwd       front-to-back alpha compositing         (Sec. 2)
  *   gs_loss_l1          L1 loss and its gradient                (Sec. 4.5, L1 term)
+ *   gs_loss_l1_ssim     L1 + SSIM loss, RGBA8 reference         (Sec. 4.5)
  *   gs_raster_bwd       per-Gaussian rasterization backward     (Sec. 4.2)
  *   gs_project_bwd_adam projection backward fused with Adam     (Sec. 4.3)
  *
@@ -119,7 +120,7 @@ typedef struct {
     int64_t k_required;       /* intersections the last gs_project_fwd needed */
     int64_t k_capacity;
     uint64_t blended_pairs;   /* pairs composited by the last gs_raster_fwd */
-    float loss;               /* last gs_loss_l1 value */
+    float loss;               /* last gs_loss_l1 / gs_loss_l1_ssim value */
     float reserved;
 } gs_stats;
 
@@ -176,6 +177,20 @@ gs_status gs_raster_fwd(const gs_plan* plan, void* ws, const float* bg, float* i
  * The loss value lands in the workspace statistics. */
 gs_status gs_loss_l1(const gs_plan* plan, void* ws, const float* image, const float* target,
                      float* dL_dimage, void* stream);
+
+/* Weighted L1 + SSIM loss (Sec. 4.5) against an 8-bit RGBA reference and its
+ * gradient, fused in one kernel:
+ *   L = (1 - lambda) mean|C - C*| + lambda (1 - mean SSIM),
+ * SSIM per colour channel with an 11x11 Gaussian window (sigma 1.5), zero
+ * padding at the image border, C1 = 0.01^2, C2 = 0.03^2; means over
+ * 3 x pixels of all views.  target_rgba8: device uint8[pixels][4] (R, G, B, A;
+ * A ignored; colour = byte / 255), 4-byte aligned; image and dL_dimage:
+ * device float[pixels][3].  lambda in [0, 1] (the paper uses 0.2), else
+ * GS_ERR_INVALID_ARG.  The loss value lands in the workspace statistics.
+ * Deterministic: per-tile partial sums added in a fixed order. */
+gs_status gs_loss_l1_ssim(const gs_plan* plan, void* ws, const float* image,
+                          const void* target_rgba8, float lambda, float* dL_dimage,
+                          void* stream);
 
 /* Rasterization backward (Sec. 4.2), one thread block per tile, no atomics:
  * one 9-float gradient record (mean2D, conic, opacity, colour) per

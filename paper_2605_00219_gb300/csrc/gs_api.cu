@@ -115,7 +115,7 @@ static bool plan_build(Plan& P, const int64_t* scene_n, int32_t n_scenes, const 
     P.count_scan_parts = (pairs + kScanBlock - 1) / kScanBlock;
     P.hist_scan_parts = (kRadixDigits * P.radix_blocks + kScanBlock - 1) / kScanBlock;
     P.raster_blocks = tiles;
-    const int64_t loss_blocks = (3 * pixels + 2047) / 2048;
+    const int64_t loss_blocks = std::max<int64_t>((3 * pixels + 2047) / 2048, 2 * ssim_tiles(V));
 
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -295,6 +295,17 @@ gs_status gs_loss_l1(const gs_plan* plan, void* ws, const float* image, const fl
     if (!plan || !ws || !image || !target || !dL_dimage) return GS_ERR_INVALID_ARG;
     WsPtrs w = carve(plan->p, ws);
     launch_loss_l1(plan->p, w, image, target, dL_dimage, static_cast<cudaStream_t>(stream));
+    return launch_status();
+}
+
+gs_status gs_loss_l1_ssim(const gs_plan* plan, void* ws, const float* image, const void* target_rgba8, float lambda,
+                          float* dL_dimage, void* stream)
+{
+    if (!plan || !ws || !image || !target_rgba8 || !dL_dimage) return GS_ERR_INVALID_ARG;
+    if (!(lambda >= 0.f && lambda <= 1.f)) return GS_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(target_rgba8) % 4 != 0) return GS_ERR_INVALID_ARG;
+    WsPtrs w = carve(plan->p, ws);
+    launch_loss_l1_ssim(plan->p, w, image, target_rgba8, lambda, dL_dimage, static_cast<cudaStream_t>(stream));
     return launch_status();
 }
 

@@ -4,8 +4,9 @@
 (chunk-major float4 SoA: geometry, SH, Adam moments).  `Trainer` owns one
 plan and workspace and runs
 
-    gs_project_fwd -> gs_bin_sort -> gs_raster_fwd -> gs_loss_l1
-    -> gs_raster_bwd -> gs_project_bwd_adam
+    gs_project_fwd -> gs_bin_sort -> gs_raster_fwd -> gs_loss_l1 (or
+    gs_loss_l1_ssim against an 8-bit RGBA target) -> gs_raster_bwd
+    -> gs_project_bwd_adam
 
 on one stream, eagerly or as one captured CUDA graph whose replay reads the
 cameras, targets and the Adam step counter from device memory.
@@ -74,7 +75,11 @@ class Trainer:
 
     def __init__(self, scenes, cameras, capacity: int = 0, tile=(16, 16), bwd_batch: int = 0,
                  sh_bf16: bool = False, mom_bf16: bool = False, bg=None, lr=DEFAULT_LR, device="cuda",
-                 bwd_impl: int = 0):
+                 bwd_impl: int = 0, loss: str = "l1", ssim_lambda: float = 0.2):
+        if loss not in ("l1", "l1_ssim"):
+            raise ValueError(f"loss must be 'l1' or 'l1_ssim', not {loss!r}")
+        self.loss = loss
+        self.ssim_lambda = float(ssim_lambda)
         self.device = torch.device(device)
         self.scenes = [s if isinstance(s, SceneBuffers) else
                        SceneBuffers.from_scene(s, device, sh_bf16, mom_bf16) for s in scenes]
@@ -85,7 +90,10 @@ class Trainer:
         self.cams = torch.from_numpy(camera_params(cameras)).to(self.device)
         P = self.plan.pixels
         self.image = torch.zeros((P, 3), dtype=torch.float32, device=self.device)
-        self.target = torch.zeros((P, 3), dtype=torch.float32, device=self.device)
+        if loss == "l1":
+            self.target = torch.zeros((P, 3), dtype=torch.float32, device=self.device)
+        else:
+            self.target = torch.zeros((P, 4), dtype=torch.uint8, device=self.device)
         self.dl = torch.zeros((P, 3), dtype=torch.float32, device=self.device)
         self.bg = None if bg is None else torch.tensor(bg, dtype=torch.float32, device=self.device)
         self.view_shapes = [(c.width, c.height) for c in cameras]
@@ -98,9 +106,22 @@ class Trainer:
         self.cams.copy_(torch.from_numpy(camera_params(cameras)), non_blocking=False)
 
     def set_target(self, images):
-        """images: list of (H, W, 3) arrays/tensors, one per view."""
-        flat = torch.cat([torch.as_tensor(np.asarray(im, np.float32)).reshape(-1, 3) for im in images])
-        self.target.copy_(flat)
+        """images: list of (H, W, 3) arrays/tensors, one per view.  With the
+        L1 + SSIM loss the target is 8-bit RGBA: uint8 (H, W, 4) images are
+        taken as they are, float images in [0, 1] are rounded to bytes."""
+        if self.loss == "l1":
+            flat = torch.cat([torch.as_tensor(np.asarray(im, np.float32)).reshape(-1, 3) for im in images])
+            self.target.copy_(flat)
+            return
+        parts = []
+        for im in images:
+            a = np.asarray(im)
+            if a.dtype != np.uint8:
+                a = np.clip(np.rint(np.asarray(a, np.float64) * 255.0), 0, 255).astype(np.uint8)
+            if a.shape[-1] == 3:
+                a = np.concatenate([a, np.full(a.shape[:-1] + (1,), 255, np.uint8)], axis=-1)
+            parts.append(torch.from_numpy(np.ascontiguousarray(a).reshape(-1, 4)))
+        self.target.copy_(torch.cat(parts))
 
     def image_views(self, img=None):
         img = self.image if img is None else img
@@ -118,7 +139,10 @@ class Trainer:
         return self.image
 
     def backward_adam(self, step: int = 0, stream=None):
-        gsstep.gs_loss_l1(self.plan, self.ws, self.image, self.target, self.dl, stream)
+        if self.loss == "l1":
+            gsstep.gs_loss_l1(self.plan, self.ws, self.image, self.target, self.dl, stream)
+        else:
+            gsstep.gs_loss_l1_ssim(self.plan, self.ws, self.image, self.target, self.ssim_lambda, self.dl, stream)
         gsstep.gs_raster_bwd(self.plan, self.ws, self.image, self.dl, stream)
         adam = gsstep.make_adam(self.lr, step=step)
         gsstep.gs_project_bwd_adam(self.plan, self.ws, self.scenes, self.cams, adam, None, stream)

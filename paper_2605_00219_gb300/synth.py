@@ -196,3 +196,31 @@ def large_views(n_views: int = 4, radius: float = 36.0, phase_deg: float = 0.0,
         w, h = res[i % len(res)]
         cams += orbit_cameras(1, radius, w, h, phase_deg=phase_deg + 360.0 * i / n_views)
     return cams
+
+
+def loss_images(shapes, seed: int, smooth: bool = False):
+    """Rendered-image stand-ins and 8-bit RGBA references for the loss
+    kernels: one (H, W, 3) float32 image in [0, 1] and one (H, W, 4) uint8
+    target per (W, H).  smooth=True gives low-frequency images with flat
+    regions (small window variances), otherwise uniform noise."""
+    rng = np.random.default_rng(seed)
+    imgs, tgts = [], []
+    for (w, h) in shapes:
+        if smooth:
+            yy, xx = np.meshgrid(np.arange(h), np.arange(w), indexing="ij")
+            base = np.empty((h, w, 3))
+            for c in range(3):
+                fx, fy, ph = rng.uniform(0.01, 0.08), rng.uniform(0.01, 0.08), rng.uniform(0, 2 * np.pi)
+                base[..., c] = 0.5 + 0.4 * np.sin(fx * xx + ph) * np.cos(fy * yy)
+            img = np.clip(base + rng.normal(0, 0.01, base.shape), 0, 1)
+            img[: h // 3, : w // 3] = 0.25            # a flat block
+            tgt = np.clip(base + rng.normal(0, 0.03, base.shape), 0, 1)
+        else:
+            img = rng.uniform(0, 1, (h, w, 3))
+            tgt = rng.uniform(0, 1, (h, w, 3))
+        t8 = np.empty((h, w, 4), np.uint8)
+        t8[..., :3] = np.rint(tgt * 255).astype(np.uint8)
+        t8[..., 3] = rng.integers(0, 256, (h, w), dtype=np.uint8)
+        imgs.append(img.astype(np.float32))
+        tgts.append(t8)
+    return imgs, tgts
