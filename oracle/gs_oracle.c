@@ -14,8 +14,10 @@
  *      (tile, depth) keys of Sec. 4.4, a stable sort and the tile ranges.
  *      Every floating-point operation is one IEEE binary32 operation rounded
  *      to nearest, in the order written; the file is compiled with
- *      -ffp-contract=off so no multiply-add is fused.  No transcendental
- *      function appears (scales are stored activated, Sec. 4.3).
+ *      -ffp-contract=off so no multiply-add is fused.  No library
+ *      transcendental function appears (scales are stored activated,
+ *      Sec. 4.3); the one logarithm, of the opacity-aware cull radius, is a
+ *      fixed series written out below.
  *   2. FP64 reference of what the step computes (Sec. 2 "Related works",
  *      Sec. 4.2, Sec. 4.3): EWA projection with the 0.3 low-pass and degree-3
  *      SH colour, front-to-back compositing over the tile lists, the analytic
@@ -42,9 +44,44 @@ typedef struct {
 /* Part 1: FP32 bit-specified binning                                        */
 /* ------------------------------------------------------------------------- */
 
-/* r^2 of the culling ellipse: 9 (3 sigma) times (1 + 2^-10), a margin that
- * keeps FP32 culling conservative against the raster's d^2 <= 9 test. */
-static const float ORC_R2 = 9.0087890625f;
+/* Natural logarithm in FP32 as a fixed sequence of rounded operations
+ * (argument reduction x = 2^e m, m in [sqrt(1/2), sqrt(2)), then
+ * ln m = 2 atanh(s) with s = (m - 1) / (m + 1) by the odd Taylor series of
+ * atanh to s^9; |s| <= 0.1716 leaves a truncation error below 1e-9).  For
+ * finite normal x > 0 only; the absolute error is about 2e-7 over [1, 256]. */
+float orc_log32(float x)
+{
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    int e = (int)(u >> 23) - 127;
+    u = (u & 0x7FFFFFu) | 0x3F800000u;
+    float m;
+    memcpy(&m, &u, 4);
+    if (m > 1.41421356f) {
+        m = 0.5f * m;
+        e += 1;
+    }
+    float s = (m - 1.0f) / (m + 1.0f);
+    float s2 = s * s;
+    float p = s2 * 0.111111111f + 0.142857143f;
+    p = s2 * p + 0.2f;
+    p = s2 * p + 0.333333333f;
+    p = s2 * p + 1.0f;
+    return (float)e * 0.693147181f + (2.0f * s) * p;
+}
+
+/* r^2 of the culling ellipse for opacity o (Sec. 4.1): a pixel takes part
+ * only if d^2 <= 9 and o exp(-d^2 / 2) >= 1/255, i.e. d^2 <= min(9,
+ * 2 ln(255 o)); widened by 2^-10 relative and 2^-10 absolute so that the FP32
+ * culling stays conservative against the raster's own tests.  Returns a
+ * negative value when 255 o <= 1 (alpha never reaches 1/255). */
+float orc_cull_r2(float o)
+{
+    float x = 255.0f * o;
+    if (!(x > 1.0f)) return -1.0f;
+    float r = fminf(9.0f, 2.0f * orc_log32(x));
+    return r * 1.0009765625f + 0.0009765625f;
+}
 
 typedef struct {
     int valid;
@@ -52,6 +89,7 @@ typedef struct {
     float a, b, c;         /* 2D covariance incl. low-pass */
     float det;
     float tz;
+    float r2;              /* cull radius^2 (orc_cull_r2) */
     uint32_t mant;         /* 23-bit depth code */
 } orc_bin;
 
@@ -66,10 +104,12 @@ static int orc_tiles_x(const orc_cam* c) { return (c->width + c->tile_w - 1) / c
 static int orc_tiles_y(const orc_cam* c) { return (c->height + c->tile_h - 1) / c->tile_h; }
 
 /* Steps B1-B14 of the binning specification. */
-static void orc_bin_project(const float* mu, const float* q, const float* s,
+static void orc_bin_project(const float* mu, const float* q, const float* s, float op,
                             const orc_cam* cam, orc_bin* o)
 {
     o->valid = 0;
+    float r2 = orc_cull_r2(op);
+    if (!(r2 > 0.0f)) return;
     float n2 = ((q[0] * q[0] + q[1] * q[1]) + q[2] * q[2]) + q[3] * q[3];
     if (!(n2 > 0.0f)) return;
     float r = sqrtf(n2);
@@ -128,7 +168,7 @@ static void orc_bin_project(const float* mu, const float* q, const float* s,
     if (qd >= 2.0f) mant = 0x7FFFFFu;
     o->valid = 1;
     o->mx = mx; o->my = my; o->a = a; o->b = b; o->c = c; o->det = det;
-    o->tz = t[2]; o->mant = mant;
+    o->tz = t[2]; o->mant = mant; o->r2 = r2;
 }
 
 /* First tile whose pixel-centre hull reaches coordinate v from above, and the
@@ -150,7 +190,7 @@ static int orc_tile_hi(float v, int T, int n)
 }
 
 /* Scan-line tile culling (Sec. 4.1, Fig. 1).  Counts the tiles whose
- * pixel-centre rectangle meets the ellipse d^2 <= ORC_R2; when `tiles` is not
+ * pixel-centre rectangle meets the ellipse d^2 <= r2; when `tiles` is not
  * NULL the tile ids are written in traversal order.  Iterates over the
  * shorter tile dimension of the bounding box. */
 static uint32_t orc_bin_scan(const orc_bin* g, const orc_cam* cam, uint32_t* tiles)
@@ -158,15 +198,16 @@ static uint32_t orc_bin_scan(const orc_bin* g, const orc_cam* cam, uint32_t* til
     if (!g->valid) return 0;
     int TW = orc_tiles_x(cam), TH = orc_tiles_y(cam);
     int tw = cam->tile_w, th = cam->tile_h;
-    float ex = sqrtf(ORC_R2 * g->a);
-    float ey = sqrtf(ORC_R2 * g->c);
+    const float r2 = g->r2;
+    float ex = sqrtf(r2 * g->a);
+    float ey = sqrtf(r2 * g->c);
     int txl = orc_tile_lo(g->mx - ex, tw, TW), txh = orc_tile_hi(g->mx + ex, tw, TW);
     int tyl = orc_tile_lo(g->my - ey, th, TH), tyh = orc_tile_hi(g->my + ey, th, TH);
     if (txl > txh || tyl > tyh) return 0;
     uint32_t count = 0;
     if (tyh - tyl <= txh - txl) {
         /* rows: for each band of tile rows, the ellipse's x-range */
-        float ystar = g->b * sqrtf(ORC_R2 / g->a);
+        float ystar = g->b * sqrtf(r2 / g->a);
         for (int ty = tyl; ty <= tyh; ty++) {
             float y0 = ((float)(ty * th) + 0.5f) - g->my;
             float y1 = ((float)((ty + 1) * th) - 0.5f) - g->my;
@@ -174,8 +215,8 @@ static uint32_t orc_bin_scan(const orc_bin* g, const orc_cam* cam, uint32_t* til
             if (!(dlo <= dhi)) continue;
             float dR = fminf(fmaxf(ystar, dlo), dhi);
             float dL = fminf(fmaxf(-ystar, dlo), dhi);
-            float hR = sqrtf(fmaxf(0.0f, g->det * (ORC_R2 * g->c - dR * dR)));
-            float hL = sqrtf(fmaxf(0.0f, g->det * (ORC_R2 * g->c - dL * dL)));
+            float hR = sqrtf(fmaxf(0.0f, g->det * (r2 * g->c - dR * dR)));
+            float hL = sqrtf(fmaxf(0.0f, g->det * (r2 * g->c - dL * dL)));
             float xR = g->mx + (g->b * dR + hR) / g->c;
             float xL = g->mx + (g->b * dL - hL) / g->c;
             int lo = orc_tile_lo(xL, tw, TW), hi = orc_tile_hi(xR, tw, TW);
@@ -186,7 +227,7 @@ static uint32_t orc_bin_scan(const orc_bin* g, const orc_cam* cam, uint32_t* til
         }
     } else {
         /* columns: for each band of tile columns, the ellipse's y-range */
-        float xstar = g->b * sqrtf(ORC_R2 / g->c);
+        float xstar = g->b * sqrtf(r2 / g->c);
         for (int tx = txl; tx <= txh; tx++) {
             float x0 = ((float)(tx * tw) + 0.5f) - g->mx;
             float x1 = ((float)((tx + 1) * tw) - 0.5f) - g->mx;
@@ -194,8 +235,8 @@ static uint32_t orc_bin_scan(const orc_bin* g, const orc_cam* cam, uint32_t* til
             if (!(dlo <= dhi)) continue;
             float dT = fminf(fmaxf(xstar, dlo), dhi);
             float dB = fminf(fmaxf(-xstar, dlo), dhi);
-            float hT = sqrtf(fmaxf(0.0f, g->det * (ORC_R2 * g->a - dT * dT)));
-            float hB = sqrtf(fmaxf(0.0f, g->det * (ORC_R2 * g->a - dB * dB)));
+            float hT = sqrtf(fmaxf(0.0f, g->det * (r2 * g->a - dT * dT)));
+            float hB = sqrtf(fmaxf(0.0f, g->det * (r2 * g->a - dB * dB)));
             float yT = g->my + (g->b * dT + hT) / g->a;
             float yB = g->my + (g->b * dB - hB) / g->a;
             int lo = orc_tile_lo(yB, th, TH), hi = orc_tile_hi(yT, th, TH);
@@ -219,12 +260,13 @@ static uint32_t orc_key(uint32_t tile, uint32_t mant, int tb)
 /* Per-Gaussian FP32 binning record and tile count.
  * out_bin: n x 8 floats (valid, mx, my, a, b, c, det, tz); out_mant: n. */
 void orc_bin32_count(int64_t n, const float* means, const float* quats, const float* scales,
-                     const orc_cam* cam, uint32_t* count, float* out_bin, uint32_t* out_mant)
+                     const float* opac, const orc_cam* cam, uint32_t* count, float* out_bin,
+                     uint32_t* out_mant)
 {
 #pragma omp parallel for schedule(static)
     for (int64_t g = 0; g < n; g++) {
         orc_bin b;
-        orc_bin_project(means + 3 * g, quats + 4 * g, scales + 3 * g, cam, &b);
+        orc_bin_project(means + 3 * g, quats + 4 * g, scales + 3 * g, opac[g], cam, &b);
         count[g] = orc_bin_scan(&b, cam, NULL);
         if (out_bin) {
             float* o = out_bin + 8 * g;
@@ -238,14 +280,15 @@ void orc_bin32_count(int64_t n, const float* means, const float* quats, const fl
 /* Emit (key, Gaussian) pairs in (Gaussian, traversal) order at the exclusive
  * offsets of the counts.  Returns the number of pairs. */
 int64_t orc_bin32_emit(int64_t n, const float* means, const float* quats, const float* scales,
-                       const orc_cam* cam, const int64_t* offset, uint32_t* keys, uint32_t* gidx)
+                       const float* opac, const orc_cam* cam, const int64_t* offset, uint32_t* keys,
+                       uint32_t* gidx)
 {
     int tb = orc_ceil_log2((int64_t)orc_tiles_x(cam) * orc_tiles_y(cam));
     int64_t total = 0;
 #pragma omp parallel for schedule(static) reduction(+ : total)
     for (int64_t g = 0; g < n; g++) {
         orc_bin b;
-        orc_bin_project(means + 3 * g, quats + 4 * g, scales + 3 * g, cam, &b);
+        orc_bin_project(means + 3 * g, quats + 4 * g, scales + 3 * g, opac[g], cam, &b);
         uint32_t* tl = keys + offset[g];
         uint32_t cnt = orc_bin_scan(&b, cam, tl);
         for (uint32_t i = 0; i < cnt; i++) {

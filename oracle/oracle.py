@@ -66,9 +66,13 @@ def lib():
         L = ctypes.CDLL(_LIB_PATH)
         vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
         cam = ctypes.POINTER(OrcCam)
-        L.orc_bin32_count.argtypes = [i64, vp, vp, vp, cam, vp, vp, vp]
+        L.orc_log32.argtypes = [ctypes.c_float]
+        L.orc_log32.restype = ctypes.c_float
+        L.orc_cull_r2.argtypes = [ctypes.c_float]
+        L.orc_cull_r2.restype = ctypes.c_float
+        L.orc_bin32_count.argtypes = [i64, vp, vp, vp, vp, cam, vp, vp, vp]
         L.orc_bin32_count.restype = None
-        L.orc_bin32_emit.argtypes = [i64, vp, vp, vp, cam, vp, vp, vp]
+        L.orc_bin32_emit.argtypes = [i64, vp, vp, vp, vp, cam, vp, vp, vp]
         L.orc_bin32_emit.restype = i64
         L.orc_stable_sort.argtypes = [i64, vp, vp]
         L.orc_stable_sort.restype = None
@@ -145,6 +149,16 @@ class Binning:
         return int(self.keys.shape[0])
 
 
+def log32(x: float) -> float:
+    """The binning's FP32 natural logarithm (fixed atanh series)."""
+    return float(lib().orc_log32(float(np.float32(x))))
+
+
+def cull_r2(o: float) -> float:
+    """The binning's cull radius^2 for opacity o (negative: never blended)."""
+    return float(lib().orc_cull_r2(float(np.float32(o))))
+
+
 def bin32(scene, cam, tile_w=16, tile_h=16) -> Binning:
     L = lib()
     c = make_cam(cam, tile_w, tile_h)
@@ -152,16 +166,19 @@ def bin32(scene, cam, tile_w=16, tile_h=16) -> Binning:
     means = np.ascontiguousarray(scene.means, np.float32)
     quats = np.ascontiguousarray(scene.quats, np.float32)
     scales = np.ascontiguousarray(scene.scales, np.float32)
+    opac = np.ascontiguousarray(scene.opacities, np.float32)
     count = np.zeros(n, np.uint32)
     b = np.zeros((n, 8), np.float32)
     mant = np.zeros(n, np.uint32)
-    L.orc_bin32_count(n, _ptr(means), _ptr(quats), _ptr(scales), ctypes.byref(c), _ptr(count), _ptr(b), _ptr(mant))
+    L.orc_bin32_count(n, _ptr(means), _ptr(quats), _ptr(scales), _ptr(opac), ctypes.byref(c), _ptr(count), _ptr(b),
+                      _ptr(mant))
     offset = np.zeros(n + 1, np.int64)
     np.cumsum(count, out=offset[1:])
     K = int(offset[-1])
     keys = np.zeros(max(K, 1), np.uint32)
     gidx = np.zeros(max(K, 1), np.uint32)
-    got = L.orc_bin32_emit(n, _ptr(means), _ptr(quats), _ptr(scales), ctypes.byref(c), _ptr(offset), _ptr(keys), _ptr(gidx))
+    got = L.orc_bin32_emit(n, _ptr(means), _ptr(quats), _ptr(scales), _ptr(opac), ctypes.byref(c), _ptr(offset),
+                           _ptr(keys), _ptr(gidx))
     assert got == K
     keys, gidx = keys[:K], gidx[:K]
     keys_emit, gidx_emit = keys.copy(), gidx.copy()

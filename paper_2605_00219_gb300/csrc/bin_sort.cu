@@ -180,6 +180,7 @@ __global__ void __launch_bounds__(256) k_emit(Views V, const uint32_t* __restric
     BinGeom g;
     g.mx = ra.x; g.my = ra.y; g.a = bb.x; g.b = bb.y; g.c = bb.z;
     g.det = FS(FM(g.a, g.c), FM(g.b, g.b));
+    g.r2 = cull_r2(rec[p].b.y);   // same bits as in the projection pass
     g.mant = __float_as_uint(bb.w);
     g.valid = 1;
     const uint32_t low = g.mant >> vd.drop;

@@ -108,10 +108,44 @@ __device__ __forceinline__ int view_of_tile(const Views& V, int64_t t)
 #define FD(a, b) __fdiv_rn((a), (b))
 #define FQ(a) __fsqrt_rn(a)
 
-constexpr float kCullR2 = 9.0087890625f;  // 9 (1 + 2^-10)
+// Natural logarithm of a finite normal x > 0 as a fixed sequence of rounded
+// binary32 operations, so that the cull radius below is the same bit pattern
+// wherever it is evaluated: x = 2^e m with m in [sqrt(1/2), sqrt(2)), and
+// ln m = 2 atanh(s), s = (m - 1) / (m + 1), by the odd Taylor series of atanh
+// to s^9 (|s| <= 0.1716: truncation below 1e-9; about 2e-7 absolute error
+// over [1, 256]).
+__device__ __forceinline__ float bin_log(float x)
+{
+    uint32_t u = __float_as_uint(x);
+    int e = (int)(u >> 23) - 127;
+    float m = __uint_as_float((u & 0x7FFFFFu) | 0x3F800000u);
+    if (m > 1.41421356f) {
+        m = FM(0.5f, m);
+        e += 1;
+    }
+    const float sv = FD(FS(m, 1.0f), FA(m, 1.0f));
+    const float s2 = FM(sv, sv);
+    float p = FA(FM(s2, 0.111111111f), 0.142857143f);
+    p = FA(FM(s2, p), 0.2f);
+    p = FA(FM(s2, p), 0.333333333f);
+    p = FA(FM(s2, p), 1.0f);
+    return FA(FM((float)e, 0.693147181f), FM(FM(2.0f, sv), p));
+}
+
+// Cull radius^2 for opacity o (Sec. 4.1): a pixel takes part only if
+// d^2 <= 9 and o exp(-d^2 / 2) >= 1/255, i.e. d^2 <= min(9, 2 ln(255 o));
+// widened by 2^-10 relative and 2^-10 absolute so that the FP32 culling stays
+// conservative against the raster's own tests.  Negative when 255 o <= 1.
+__device__ __forceinline__ float cull_r2(float o)
+{
+    const float x = FM(255.0f, o);
+    if (!(x > 1.0f)) return -1.0f;
+    const float r = fminf(9.0f, FM(2.0f, bin_log(x)));
+    return FA(FM(r, 1.0009765625f), 0.0009765625f);
+}
 
 struct BinGeom {
-    float mx, my, a, b, c, det, tz;
+    float mx, my, a, b, c, det, tz, r2;
     uint32_t mant;
     int valid;
 };
@@ -120,6 +154,8 @@ __device__ __forceinline__ void bin_project(float4 mu, float4 q, float4 s, const
                                             BinGeom& o)
 {
     o.valid = 0;
+    const float r2 = cull_r2(s.w);
+    if (!(r2 > 0.0f)) return;
     float n2 = FA(FA(FA(FM(q.x, q.x), FM(q.y, q.y)), FM(q.z, q.z)), FM(q.w, q.w));
     if (!(n2 > 0.0f)) return;
     float r = FQ(n2);
@@ -191,7 +227,7 @@ __device__ __forceinline__ void bin_project(float4 mu, float4 q, float4 s, const
     uint32_t mant = __float_as_uint(qd) & 0x7FFFFFu;
     if (qd >= 2.0f) mant = 0x7FFFFFu;
     o.valid = 1;
-    o.mx = mx; o.my = my; o.a = a; o.b = b; o.c = c; o.det = det; o.tz = t[2]; o.mant = mant;
+    o.mx = mx; o.my = my; o.a = a; o.b = b; o.c = c; o.det = det; o.tz = t[2]; o.mant = mant; o.r2 = r2;
 }
 
 __device__ __forceinline__ int tile_lo(float v, int T, int n)
@@ -211,20 +247,21 @@ __device__ __forceinline__ int tile_hi(float v, int T, int n)
 }
 
 // Scan-line traversal (Sec. 4.1): calls emit(tile_id) for every tile whose
-// pixel-centre rectangle meets the ellipse d^2 <= kCullR2, band by band along
+// pixel-centre rectangle meets the ellipse d^2 <= g.r2, band by band along
 // the shorter dimension of the tile bounding box.  Returns the count.
 template <typename Emit>
 __device__ __forceinline__ uint32_t scanline_tiles(const BinGeom& g, int tw, int th, int TX, int TY, Emit emit)
 {
-    float ex = FQ(FM(kCullR2, g.a));
-    float ey = FQ(FM(kCullR2, g.c));
+    const float r2 = g.r2;
+    float ex = FQ(FM(r2, g.a));
+    float ey = FQ(FM(r2, g.c));
     int txl = tile_lo(FS(g.mx, ex), tw, TX), txh = tile_hi(FA(g.mx, ex), tw, TX);
     int tyl = tile_lo(FS(g.my, ey), th, TY), tyh = tile_hi(FA(g.my, ey), th, TY);
     if (txl > txh || tyl > tyh) return 0;
     uint32_t count = 0;
     if (tyh - tyl <= txh - txl) {
-        float ystar = FM(g.b, FQ(FD(kCullR2, g.a)));
-        float r2c = FM(kCullR2, g.c);
+        float ystar = FM(g.b, FQ(FD(r2, g.a)));
+        float r2c = FM(r2, g.c);
         for (int ty = tyl; ty <= tyh; ty++) {
             float y0 = FS(FA((float)(ty * th), 0.5f), g.my);
             float y1 = FS(FS((float)((ty + 1) * th), 0.5f), g.my);
@@ -243,8 +280,8 @@ __device__ __forceinline__ uint32_t scanline_tiles(const BinGeom& g, int tw, int
             }
         }
     } else {
-        float xstar = FM(g.b, FQ(FD(kCullR2, g.c)));
-        float r2a = FM(kCullR2, g.a);
+        float xstar = FM(g.b, FQ(FD(r2, g.c)));
+        float r2a = FM(r2, g.a);
         for (int tx = txl; tx <= txh; tx++) {
             float x0 = FS(FA((float)(tx * tw), 0.5f), g.mx);
             float x1 = FS(FS((float)((tx + 1) * tw), 0.5f), g.mx);

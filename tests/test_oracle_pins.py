@@ -254,19 +254,53 @@ def test_tiled_equals_bruteforce(orc, seed):
 # ---------------------------------------------------------------------------
 
 def _big_scene(seed, n=60):
+    """Opacities 10^U(-2.6, 0): some below 1/255 (never blended), many with
+    2 ln(255 o) < 9 (cull radius below 3 sigma), the rest at 3 sigma."""
     rng = np.random.default_rng(seed)
     means = rng.uniform(-1.4, 1.4, size=(n, 3)).astype(np.float32)
     means[:, 2] = rng.uniform(-1, 1, size=n)
     scales = np.exp(rng.normal(-2.2, 0.8, size=(n, 3))).astype(np.float32)
     q = rng.normal(size=(n, 4)).astype(np.float32)
-    return _one_scene(means, q, scales, np.full(n, 0.5, np.float32))
+    opac = (10.0 ** rng.uniform(-2.6, 0.0, size=n)).astype(np.float32)
+    return _one_scene(means, q, scales, opac)
+
+
+def _cull_r2_64(o):
+    """The cull radius^2 of the binning, in FP64 from its definition:
+    min(9, 2 ln(255 o)) widened by 2^-10 relative and absolute."""
+    x = 255.0 * float(np.float32(o))
+    if x <= 1.0:
+        return -1.0
+    return min(9.0, 2.0 * math.log(x)) * (1.0 + 2.0 ** -10) + 2.0 ** -10
+
+
+def test_log32_and_cull_radius(orc):
+    """The binning's FP32 logarithm against the library logarithm (absolute
+    error <= 3e-7 on [1, 256], exact at 1), and its cull radius^2 against the
+    definition: 3 sigma for opaque Gaussians, shrinking with the opacity,
+    negative (never listed) once 255 o <= 1."""
+    xs = np.concatenate([np.linspace(1.0, 256.0, 4001), 1.0 + np.geomspace(1e-7, 1.0, 200),
+                         np.float32(2.0) ** np.arange(0, 9)]).astype(np.float32)
+    err = max(abs(orc.log32(x) - math.log(float(x))) for x in xs)
+    assert err <= 3e-7, err
+    assert orc.log32(1.0) == 0.0
+    assert orc.cull_r2(1.0) == 9.009765625
+    assert orc.cull_r2(0.5) == 9.009765625          # 2 ln(127.5) > 9
+    assert orc.cull_r2(1.0 / 255.0 * 0.999) < 0.0
+    assert orc.cull_r2(0.0) < 0.0
+    for o in np.geomspace(1.0 / 255.0 * 1.0001, 1.0, 500):
+        r64 = _cull_r2_64(o)
+        assert abs(orc.cull_r2(o) - r64) <= 1e-6 + 1e-6 * r64, o
+    # opacity 0.1: 2 ln(25.5) = 6.478..., well inside 3 sigma
+    assert abs(orc.cull_r2(0.1) - (2 * math.log(25.5) * (1 + 2 ** -10) + 2 ** -10)) < 2e-6
 
 
 @pytest.mark.parametrize("seed,tile", [(0, (16, 16)), (1, (8, 8)), (2, (16, 32)), (3, (16, 16))])
 def test_scanline_equals_exact_rectangle_test(orc, seed, tile):
     """Scan-line culling lists exactly the tiles whose pixel-centre rectangle
-    meets the ellipse (checked against an independent exact test, sandwiched
-    between r^2 (1 -+ 1e-5) to absorb FP32 rounding)."""
+    meets the ellipse d^2 <= r^2(o) (checked against an independent exact
+    test, sandwiched between r^2 (1 -+ 1e-5) -+ 1e-6 to absorb FP32
+    rounding); Gaussians with 255 o <= 1 list nothing."""
     tw, th = tile
     sc = _big_scene(seed)
     cam = synth.tiny_camera()
@@ -274,14 +308,18 @@ def test_scanline_equals_exact_rectangle_test(orc, seed, tile):
     b = orc.bin32(sc, cam, tw, th)
     TX, TY = orc.tiles_of(cam, tw, th)
     shift = orc.key_shift(TX * TY)
-    r2 = 9.0087890625
-    rows_mode = cols_mode = 0
+    rows_mode = cols_mode = small = dropped = 0
     for g in range(sc.n):
         v, mx, my, a, bb, c, det, tz = [float(x) for x in b.bin[g]]
         listed = set((b.keys_emit[b.offset[g]:b.offset[g + 1]] >> shift).tolist())
+        r2 = _cull_r2_64(sc.opacities[g])
+        if r2 < 0:
+            dropped += 1
+            assert not v and not listed
         if not v:
             assert not listed
             continue
+        small += r2 < 9.0
         Q = np.linalg.inv(np.array([[a, bb], [bb, c]]))
         inner, outer = set(), set()
         for ty in range(TY):
@@ -290,9 +328,9 @@ def test_scanline_equals_exact_rectangle_test(orc, seed, tile):
                 y0, y1 = ty * th + 0.5, min((ty + 1) * th, cam.height) - 0.5
                 x1 = (tx + 1) * tw - 0.5
                 y1 = (ty + 1) * th - 0.5
-                if _rect_meets_ellipse(mx, my, Q, r2 * (1 - 1e-5), x0, x1, y0, y1):
+                if _rect_meets_ellipse(mx, my, Q, r2 * (1 - 1e-5) - 1e-6, x0, x1, y0, y1):
                     inner.add(ty * TX + tx)
-                if _rect_meets_ellipse(mx, my, Q, r2 * (1 + 1e-5), x0, x1, y0, y1):
+                if _rect_meets_ellipse(mx, my, Q, r2 * (1 + 1e-5) + 1e-6, x0, x1, y0, y1):
                     outer.add(ty * TX + tx)
         assert inner <= listed <= outer, g
         assert len(listed) == b.count[g]
@@ -303,10 +341,12 @@ def test_scanline_equals_exact_rectangle_test(orc, seed, tile):
             else:
                 cols_mode += 1
     assert rows_mode > 0 and cols_mode > 0
+    assert small > 5 and dropped > 0
 
 
 def test_no_false_negatives_against_raster_rule(orc):
-    """Every pixel where the FP64 rule d^2 <= 9 holds lies in a listed tile."""
+    """Every pixel where the FP64 rule (d^2 <= 9 and o exp(-d^2/2) >= 1/255)
+    holds lies in a listed tile."""
     sc, _, cams = synth.tiny_workload(0)
     cam = cams[0]
     b = orc.bin32(sc, cam)
@@ -319,7 +359,8 @@ def test_no_false_negatives_against_raster_rule(orc):
             continue
         dx, dy = xs - P[g, 4], ys - P[g, 5]
         d2 = P[g, 9] * dx * dx + 2 * P[g, 10] * dx * dy + P[g, 11] * dy * dy
-        need = set(np.unique(tiles_px[d2 <= 9.0]).tolist())
+        alpha = P[g, 12] * np.exp(-0.5 * d2)
+        need = set(np.unique(tiles_px[(d2 <= 9.0) & (alpha >= 1.0 / 255.0)]).tolist())
         listed = set((b.keys_emit[b.offset[g]:b.offset[g + 1]] >> shift).tolist())
         assert need <= listed, g
 
