@@ -31,10 +31,10 @@
  *  - geom:  float4[3][n], chunk-major: chunk 0 = mean (x, y, z, unused),
  *           chunk 1 = rotation quaternion (w, x, y, z, need not be unit),
  *           chunk 2 = (scale x, y, z, opacity), stored ACTIVATED (scales > 0,
- *           opacity in (0,1)), as the paper stores them (Sec. 4.3, Sec. 4.7).
+ *           opacity in (0,1)), as the paper stores them (Sec. 4.3, Sec. 4.6).
  *  - sh:    degree-3 SH, 48 coefficients per Gaussian, flat index 3*k + c
  *           (k = basis function 0..15, c = colour channel).  FP32 storage:
- *           float4[12][n] ("column-based" 128-bit chunks, Sec. 4.7), chunk j
+ *           float4[12][n] ("column-based" 128-bit chunks, Sec. 4.6), chunk j
  *           holding flat indices 4j..4j+3.  BF16 storage: uint4[6][n], chunk j
  *           holding flat indices 8j..8j+7 as bf16 (low half first).
  *  - m, v:  Adam moments of theta = (mean, quaternion, log-scale,
@@ -101,6 +101,13 @@ typedef struct {
     void* sh;                 /* float4[12][n] or uint4[6][n] (BF16) */
     void* m;                  /* float4[15][n] or uint2[15][n] (BF16) */
     void* v;                  /* same as m */
+    void* stats;              /* NULL, or float2[n] densification statistics
+                                 that gs_project_bwd_adam adds to: x += the
+                                 norm of dL/d(mean2D) of every view in which
+                                 the Gaussian is listed, in half-image units
+                                 (x scaled by W/2, y by H/2) and as if that
+                                 view's loss were its own mean (x P_all/P_v);
+                                 y += the number of such views */
 } gs_scene_buf;
 
 typedef struct {
@@ -221,6 +228,10 @@ gs_status gs_project_bwd_adam(const gs_plan* plan, void* ws, const gs_scene_buf*
 /* Advance the workspace Adam step counter by one (for graph replay). */
 gs_status gs_adam_advance(const gs_plan* plan, void* ws, void* stream);
 
+/* Set the workspace Adam step counter (to carry it into a new workspace,
+ * e.g. after densification changed the plan).  step >= 0. */
+gs_status gs_workspace_set_step(const gs_plan* plan, void* ws, int32_t step, void* stream);
+
 /* Synchronous: copy the workspace statistics to the host (waits on stream).
  * Not capturable. */
 gs_status gs_read_stats(const gs_plan* plan, const void* ws, gs_stats* out, void* stream);
@@ -260,6 +271,66 @@ const char* gs_status_str(gs_status s);
 #define GS_L1_NOALLOC_MAX_VALUES 67108864LL   /* 3 x 22,369,621 pixels */
 gs_status gs_loss_l1_noalloc(const float* image, const float* target, float* dL_dimage, float* loss,
                              int64_t n_values, void* stream);
+
+/* ---------------------------------------------------------------------
+ * Default densification (Sec. 4.6: the 3DGS default strategy,
+ * which the paper follows): every refinement interval, Gaussians whose mean
+ * statistic (stats.x / max(stats.y, 1)) exceeds grow_grad2d are cloned when
+ * small (max scale <= grow_scale3d * scene_scale) or split when large; then
+ * Gaussians with opacity < prune_opa -- and, with prune_big, those whose max
+ * scale exceeds prune_scale3d * scene_scale -- are removed.  The decisions
+ * are binary32 comparisons of stored values (opacity and scales are stored
+ * activated), so they are exact and reproducible.
+ *
+ * Output order (one Gaussian per row of every chunk-major array):
+ *   [survivors that are not split, in input order]
+ *   [clones of the cloned survivors, in input order]
+ *   [first product of each surviving split, in input order]
+ *   [second product of each surviving split, in input order]
+ * A clone copies its Gaussian; a split product keeps quaternion, opacity and
+ * SH, takes scale / split_factor and mean + R(q) (scale * eps), eps the
+ * caller's standard normal draws.  New Gaussians start with zero Adam
+ * moments; survivors keep theirs; all output statistics are zero.
+ * --------------------------------------------------------------------- */
+typedef struct {
+    float grow_grad2d;        /* 2e-4 */
+    float grow_scale3d;       /* 0.01 (x scene_scale) */
+    float prune_opa;          /* 0.005 */
+    float prune_scale3d;      /* 0.1 (x scene_scale), when prune_big != 0 */
+    float scene_scale;        /* scene extent, world units */
+    float split_factor;       /* 1.6 */
+    int32_t grow;             /* 0: prune only */
+    int32_t prune_big;        /* 1 once opacities have been reset */
+} gs_densify_cfg;
+
+/* Device scratch for n input Gaussians (caller-allocated, 256-byte aligned). */
+size_t gs_densify_scratch_bytes(int64_t n);
+
+/* Decides every Gaussian's fate and the output positions.  scene: one
+ * scene's buffers with stats != NULL; storage_flags: GS_STORE_* of its
+ * layout.  Asynchronous; read the counts with gs_densify_counts.
+ * GS_ERR_INVALID_ARG for NULL pointers, n < 1, n >= 2^31 or a config with a
+ * non-finite or non-positive scale, factor or threshold. */
+gs_status gs_densify_count(const gs_scene_buf* scene, int32_t storage_flags, const gs_densify_cfg* cfg,
+                           void* scratch, void* stream);
+
+/* Synchronises `stream` and returns, in counts[4] (host), the number of
+ * survivors kept as they are, clones, surviving splits (each giving two
+ * products) and the output total. */
+gs_status gs_densify_counts(const void* scratch, int64_t counts[4], void* stream);
+
+/* Writes the densified scene into `out` (out->n = the total from
+ * gs_densify_counts; buffers of that size in the same layout; out->stats
+ * zeroed when not NULL).  eps: device float[in->n][6], standard normal draws
+ * (two 3-vectors per input Gaussian; only the split ones are read).
+ * in and out must not overlap.  If out->n differs from the total of the
+ * preceding gs_densify_count on this scratch, nothing is written. */
+gs_status gs_densify_apply(const gs_scene_buf* in, int32_t storage_flags, const gs_densify_cfg* cfg,
+                           const float* eps, const void* scratch, gs_scene_buf* out, void* stream);
+
+/* Opacity reset of the default strategy: o = min(o, value) for every
+ * Gaussian, and the logit-opacity Adam moments (m and v) set to zero. */
+gs_status gs_reset_opacity(const gs_scene_buf* scene, int32_t storage_flags, float value, void* stream);
 
 #ifdef __cplusplus
 }

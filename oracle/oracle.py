@@ -443,3 +443,128 @@ def l1_ssim_loss_grad(images, targets, lam: float = 0.2):
         grads.append(d)
     loss = (1 - lam) * l1 / total + lam * (1 - ssim_sum / total)
     return loss, grads
+
+
+# --------------------------------------------------------------------------
+# Default densification (Sec. 4.6: the 3DGS default strategy, which the
+# paper follows) and its gradient statistic
+# --------------------------------------------------------------------------
+
+def densify_stats64(res: StepResult, cams) -> np.ndarray:
+    """Statistics one step adds, (n, 2): for every view in which a Gaussian
+    is listed (tile count > 0), x += |dL/d(mean2D)| with the x component
+    scaled by W/2, y by H/2, both by P_all / P_view (the gradient of that
+    view's own mean loss), and y += 1."""
+    n = res.grad.shape[0]
+    p_all = float(sum(c.width * c.height for c in cams))
+    st = np.zeros((n, 2), np.float64)
+    for cam, b, g2 in zip(cams, res.binnings, res.grad2d):
+        vis = b.count > 0
+        fac = p_all / float(cam.width * cam.height)
+        gx = g2[:, 0] * (0.5 * cam.width) * fac
+        gy = g2[:, 1] * (0.5 * cam.height) * fac
+        st[vis, 0] += np.hypot(gx, gy)[vis]
+        st[vis, 1] += 1.0
+    return st
+
+
+@dataclass
+class DenseScene:
+    """One scene in rows: means (n,3), quats (n,4), scales (n,3) and
+    opacities (n,) activated, sh (n,48) flat (index 3k + channel), Adam
+    moments m, v (n,60) in the chunk order (mean xyz + pad, quaternion,
+    log-scale xyz + logit-opacity, 48 SH), stats (n,2)."""
+    means: np.ndarray
+    quats: np.ndarray
+    scales: np.ndarray
+    opacities: np.ndarray
+    sh: np.ndarray
+    m: np.ndarray
+    v: np.ndarray
+    stats: np.ndarray
+
+    @property
+    def n(self):
+        return self.means.shape[0]
+
+    def take(self, idx):
+        return DenseScene(*(a[idx] for a in (self.means, self.quats, self.scales, self.opacities, self.sh,
+                                              self.m, self.v, self.stats)))
+
+
+def _rotation64(q):
+    """Rotation matrices (n,3,3) of quaternions (w, x, y, z), normalised."""
+    q = np.asarray(q, np.float64)
+    q = q / np.linalg.norm(q, axis=1, keepdims=True)
+    w, x, y, z = q[:, 0], q[:, 1], q[:, 2], q[:, 3]
+    return np.stack([
+        np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)], -1),
+        np.stack([2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)], -1),
+        np.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], -1)], 1)
+
+
+def densify64(sc: DenseScene, eps, scene_scale, grow_grad2d=2e-4, grow_scale3d=0.01, prune_opa=0.005,
+              prune_scale3d=0.1, split_factor=1.6, grow=True, prune_big=False):
+    """One refinement of the default strategy, in its three stages:
+      1. clone: Gaussians whose mean statistic x / max(y, 1) exceeds
+         grow_grad2d and whose largest scale is <= grow_scale3d * scene_scale
+         get a copy appended (zero moments);
+      2. split: the other high-statistic Gaussians of the original set are
+         removed and two products appended (first products of all, then
+         second products of all): mean + R(q) (scale * eps_k), scale /
+         split_factor, the rest copied, zero moments;
+      3. prune: Gaussians with opacity < prune_opa -- and with prune_big,
+         largest scale > prune_scale3d * scene_scale -- are removed.
+    The decisions compare binary32 stored values with binary32 thresholds
+    (as the parameters are stored), the new means are FP64.  Statistics of
+    the result are zero.  Returns (scene, (kept, clones, splits, total))."""
+    f32 = np.float32
+    n = sc.n
+    eps = np.asarray(eps, np.float64).reshape(n, 2, 3)
+    avg = sc.stats[:, 0].astype(f32) / np.maximum(sc.stats[:, 1].astype(f32), f32(1.0))
+    high = np.zeros(n, bool) if not grow else avg > f32(grow_grad2d)
+    smax = sc.scales.astype(f32).max(axis=1)
+    small = smax <= f32(grow_scale3d) * f32(scene_scale)
+    is_clone, is_split = high & small, high & ~small
+    # stage 1: clone
+    s1 = DenseScene(*(np.concatenate([a, a[is_clone]]) for a in (sc.means, sc.quats, sc.scales, sc.opacities,
+                                                                 sc.sh, sc.m, sc.v, sc.stats)))
+    s1.m[n:] = 0.0
+    s1.v[n:] = 0.0
+    split1 = np.concatenate([is_split, np.zeros(int(is_clone.sum()), bool)])
+    # stage 2: split
+    sel = np.nonzero(split1)[0]
+    rest = s1.take(np.nonzero(~split1)[0])
+    R = _rotation64(s1.quats[sel])
+    sv = s1.scales[sel].astype(np.float64)
+    prods = []
+    for k in range(2):
+        off = np.einsum("nij,nj->ni", R, sv * eps[sel, k])
+        p = s1.take(sel)
+        p.means = (p.means.astype(np.float64) + off)
+        p.scales = (p.scales.astype(f32) / f32(split_factor)).astype(f32)
+        p.m = np.zeros_like(p.m)
+        p.v = np.zeros_like(p.v)
+        prods.append(p)
+    s2 = DenseScene(*(np.concatenate([getattr(rest, f), getattr(prods[0], f), getattr(prods[1], f)])
+                      for f in ("means", "quats", "scales", "opacities", "sh", "m", "v", "stats")))
+    # stage 3: prune
+    prune = s2.opacities.astype(f32) < f32(prune_opa)
+    if prune_big:
+        prune |= s2.scales.astype(f32).max(axis=1) > f32(prune_scale3d) * f32(scene_scale)
+    out = s2.take(np.nonzero(~prune)[0])
+    out.stats = np.zeros_like(out.stats)
+    n_orig = rest.n - int(is_clone.sum())      # rest = [original non-split rows, clone rows]
+    kept = int((~prune[:n_orig]).sum())
+    clones = int((~prune[n_orig:rest.n]).sum())
+    splits = int((~prune[rest.n:rest.n + len(sel)]).sum())
+    return out, (kept, clones, splits, out.n)
+
+
+def reset_opacity64(sc: DenseScene, value=0.01) -> DenseScene:
+    """o = min(o, value) (binary32) and zero logit-opacity moments."""
+    out = sc.take(np.arange(sc.n))
+    out.opacities = np.minimum(sc.opacities.astype(np.float32), np.float32(value))
+    out.m[:, 11] = 0.0
+    out.v[:, 11] = 0.0
+    return out

@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* in, 
     }
 }
 
-static void scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* part, cudaStream_t st)
+void scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* part, cudaStream_t st)
 {
     const int64_t nparts = (n + kScanBlock - 1) / kScanBlock;
     k_scan_reduce<<<(unsigned)nparts, kScanThreads, 0, st>>>(in, n, part);

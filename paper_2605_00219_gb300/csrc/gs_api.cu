@@ -160,6 +160,7 @@ Scenes make_scenes(const Plan& P, const gs_scene_buf* scenes)
         S.s[s].sh = scenes[s].sh;
         S.s[s].m = scenes[s].m;
         S.s[s].v = scenes[s].v;
+        S.s[s].stats = static_cast<float2*>(scenes[s].stats);
     }
     return S;
 }
@@ -187,6 +188,11 @@ __global__ void k_adam_advance(WsHeader* hdr)
 }
 
 void launch_adam_advance(const WsPtrs& w, cudaStream_t st) { k_adam_advance<<<1, 32, 0, st>>>(w.hdr); }
+
+__global__ void k_set_step(WsHeader* hdr, int32_t step)
+{
+    if (threadIdx.x == 0) hdr->step = step;
+}
 
 static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
@@ -336,6 +342,14 @@ gs_status gs_adam_advance(const gs_plan* plan, void* ws, void* stream)
     if (!plan || !ws) return GS_ERR_INVALID_ARG;
     WsPtrs w = carve(plan->p, ws);
     launch_adam_advance(w, static_cast<cudaStream_t>(stream));
+    return launch_status();
+}
+
+gs_status gs_workspace_set_step(const gs_plan* plan, void* ws, int32_t step, void* stream)
+{
+    if (!plan || !ws || step < 0) return GS_ERR_INVALID_ARG;
+    WsPtrs w = carve(plan->p, ws);
+    k_set_step<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(w.hdr, step);
     return launch_status();
 }
 

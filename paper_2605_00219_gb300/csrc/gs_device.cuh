@@ -40,6 +40,7 @@ struct SceneDesc {
     void* sh;              // float4[12][n] or uint4[6][n]
     void* m;               // float4[15][n] or uint2[15][n]
     void* v;
+    float2* stats;         // NULL or densification statistics, float2[n]
 };
 
 struct Scenes {

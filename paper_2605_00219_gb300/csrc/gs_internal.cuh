@@ -97,6 +97,9 @@ void launch_bin_sort(const Plan& P, const WsPtrs& w, cudaStream_t st);
 void launch_raster_fwd(const Plan& P, const WsPtrs& w, const float* bg, float* image, cudaStream_t st);
 void launch_loss_l1(const Plan& P, const WsPtrs& w, const float* image, const float* target, float* dl,
                     cudaStream_t st);
+// Exclusive scan of n u32 (in place allowed); the grand total lands in
+// part[ceil(n / kScanBlock)].
+void scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* part, cudaStream_t st);
 int64_t ssim_tiles(const Views& V);  // 16x16 tiles of the fused L1 + SSIM loss
 void launch_loss_l1_ssim(const Plan& P, const WsPtrs& w, const float* image, const void* target_rgba8, float lam,
                          float* dl, cudaStream_t st);

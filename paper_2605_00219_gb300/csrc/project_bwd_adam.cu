@@ -317,6 +317,7 @@ __global__ void __launch_bounds__(kPbaThreads, 4) k_project_bwd_adam(Views V, Sc
         float4 q = sc.geom[n + g];
         float4 so = sc.geom[2 * n + g];
         float dmu[3] = {0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f}, ds[3] = {0.f, 0.f, 0.f}, dop = 0.f;
+        float st_sum = 0.f, st_cnt = 0.f;   // densification statistics of this step
         // the next view's count and offset are loaded while this view is
         // processed
         auto seek = [&](int u) {
@@ -347,6 +348,14 @@ __global__ void __launch_bounds__(kPbaThreads, 4) k_project_bwd_adam(Views V, Sc
                 g2[4] += r.b.x; g2[5] += r.b.y; g2[6] += r.b.z; g2[7] += r.b.w;
                 g2[8] += r.c.x;
             }
+            if (sc.stats) {
+                // dL/d(mean2D) in half-image units, as if this view's loss
+                // were the mean over its own pixels
+                const float fac = (float)V.pixels / ((float)vd.W * (float)vd.H);
+                const float gx = g2[0] * (0.5f * (float)vd.W) * fac, gy = g2[1] * (0.5f * (float)vd.H) * fac;
+                st_sum += sqrtf(gx * gx + gy * gy);
+                st_cnt += 1.0f;
+            }
             float cam[16];
 #pragma unroll
             for (int i = 0; i < 16; i++) cam[i] = __ldg(cams + 16 * v + i);
@@ -354,6 +363,12 @@ __global__ void __launch_bounds__(kPbaThreads, 4) k_project_bwd_adam(Views V, Sc
             proj_bwd_view(cam, vd.W, vd.H, mu, q, so, sc, SH16 ? 1 : 0, g, g2, dmu, dq, ds, dop, Y, draw);
 #pragma unroll
             for (int f = 0; f < 48; f++) sG[f][tid] = fmaf(Y[f / 3], draw[f % 3], sG[f][tid]);
+        }
+        if (sc.stats) {
+            float2 st = sc.stats[g];
+            st.x += st_sum;
+            st.y += st_cnt;
+            sc.stats[g] = st;
         }
         if (A.grad_only) {
             const int64_t N = S.total;

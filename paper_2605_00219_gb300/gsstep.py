@@ -31,7 +31,8 @@ STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_CAPACITY", 3: "G
 SYMBOLS = ["gs_plan_create", "gs_plan_destroy", "gs_workspace_bytes", "gs_plan_query", "gs_workspace_init",
            "gs_project_fwd", "gs_bin_sort", "gs_raster_fwd", "gs_loss_l1", "gs_raster_bwd",
            "gs_project_bwd_adam", "gs_adam_advance", "gs_read_stats", "gs_workspace_buffer", "gs_status_str",
-           "gs_loss_l1_noalloc", "gs_loss_l1_ssim"]
+           "gs_loss_l1_noalloc", "gs_loss_l1_ssim", "gs_densify_scratch_bytes", "gs_densify_count",
+           "gs_densify_counts", "gs_densify_apply", "gs_reset_opacity", "gs_workspace_set_step"]
 L1_NOALLOC_MAX_VALUES = 67108864
 
 
@@ -46,7 +47,7 @@ class gs_tuning(ctypes.Structure):
 
 class gs_scene_buf(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("geom", ctypes.c_void_p), ("sh", ctypes.c_void_p),
-                ("m", ctypes.c_void_p), ("v", ctypes.c_void_p)]
+                ("m", ctypes.c_void_p), ("v", ctypes.c_void_p), ("stats", ctypes.c_void_p)]
 
 
 class gs_adam(ctypes.Structure):
@@ -59,6 +60,12 @@ class gs_stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_uint32), ("step", ctypes.c_int32), ("k_required", ctypes.c_int64),
                 ("k_capacity", ctypes.c_int64), ("blended_pairs", ctypes.c_uint64), ("loss", ctypes.c_float),
                 ("reserved", ctypes.c_float)]
+
+
+class gs_densify_cfg(ctypes.Structure):
+    _fields_ = [("grow_grad2d", ctypes.c_float), ("grow_scale3d", ctypes.c_float), ("prune_opa", ctypes.c_float),
+                ("prune_scale3d", ctypes.c_float), ("scene_scale", ctypes.c_float), ("split_factor", ctypes.c_float),
+                ("grow", ctypes.c_int32), ("prune_big", ctypes.c_int32)]
 
 
 class GSError(RuntimeError):
@@ -94,15 +101,25 @@ def lib():
         L.gs_raster_bwd.argtypes = [vp, vp, vp, vp, vp]
         L.gs_project_bwd_adam.argtypes = [vp, vp, ctypes.POINTER(gs_scene_buf), vp, ctypes.POINTER(gs_adam), vp, vp]
         L.gs_adam_advance.argtypes = [vp, vp, vp]
+        L.gs_workspace_set_step.argtypes = [vp, vp, i32, vp]
         L.gs_read_stats.argtypes = [vp, vp, ctypes.POINTER(gs_stats), vp]
         L.gs_workspace_buffer.argtypes = [vp, vp, i32]
         L.gs_workspace_buffer.restype = vp
         L.gs_loss_l1_noalloc.argtypes = [vp, vp, vp, vp, i64, vp]
         L.gs_loss_l1_noalloc.restype = ctypes.c_int
+        L.gs_densify_scratch_bytes.argtypes = [i64]
+        L.gs_densify_scratch_bytes.restype = ctypes.c_size_t
+        L.gs_densify_count.argtypes = [ctypes.POINTER(gs_scene_buf), i32, ctypes.POINTER(gs_densify_cfg), vp, vp]
+        L.gs_densify_counts.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), vp]
+        L.gs_densify_apply.argtypes = [ctypes.POINTER(gs_scene_buf), i32, ctypes.POINTER(gs_densify_cfg), vp, vp,
+                                       ctypes.POINTER(gs_scene_buf), vp]
+        L.gs_reset_opacity.argtypes = [ctypes.POINTER(gs_scene_buf), i32, ctypes.c_float, vp]
         L.gs_status_str.argtypes = [ctypes.c_int]
         L.gs_status_str.restype = ctypes.c_char_p
         for name in ["gs_workspace_init", "gs_project_fwd", "gs_bin_sort", "gs_raster_fwd", "gs_loss_l1",
-                     "gs_loss_l1_ssim", "gs_raster_bwd", "gs_project_bwd_adam", "gs_adam_advance", "gs_read_stats"]:
+                     "gs_loss_l1_ssim", "gs_raster_bwd", "gs_project_bwd_adam", "gs_adam_advance", "gs_read_stats",
+                     "gs_densify_count", "gs_densify_counts", "gs_densify_apply", "gs_reset_opacity",
+                     "gs_workspace_set_step"]:
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -177,9 +194,11 @@ def scene_bufs(scenes):
     """gs_scene_buf array from a list of SceneBuffers."""
     arr = (gs_scene_buf * len(scenes))()
     for i, s in enumerate(scenes):
+        st = getattr(s, "stats", None)
         arr[i] = gs_scene_buf(s.n, s.geom.data_ptr(), s.sh.data_ptr(),
                               s.m.data_ptr() if s.m is not None else None,
-                              s.v.data_ptr() if s.v is not None else None)
+                              s.v.data_ptr() if s.v is not None else None,
+                              st.data_ptr() if st is not None else None)
     return arr
 
 
@@ -233,6 +252,10 @@ def gs_adam_advance(plan: Plan, ws, stream=None):
     _check(lib().gs_adam_advance(plan.handle, _ptr(ws), _stream(stream)), "gs_adam_advance")
 
 
+def gs_workspace_set_step(plan: Plan, ws, step: int, stream=None):
+    _check(lib().gs_workspace_set_step(plan.handle, _ptr(ws), int(step), _stream(stream)), "gs_workspace_set_step")
+
+
 def gs_read_stats(plan: Plan, ws, stream=None) -> gs_stats:
     st = gs_stats()
     _check(lib().gs_read_stats(plan.handle, _ptr(ws), ctypes.byref(st), _stream(stream)), "gs_read_stats")
@@ -257,3 +280,39 @@ def gs_loss_l1_noalloc(image, target, dl, loss, stream=None):
     device float tensor.  See include/gs_step.h for the shared-scratch rules."""
     _check(lib().gs_loss_l1_noalloc(_ptr(image), _ptr(target), _ptr(dl), _ptr(loss), int(image.numel()),
                                     _stream(stream)), "gs_loss_l1_noalloc")
+
+
+# ---------------------------------------------------------------------------
+# Default densification
+# ---------------------------------------------------------------------------
+
+def make_densify_cfg(scene_scale, grow_grad2d=2e-4, grow_scale3d=0.01, prune_opa=0.005, prune_scale3d=0.1,
+                     split_factor=1.6, grow=True, prune_big=False) -> gs_densify_cfg:
+    return gs_densify_cfg(float(grow_grad2d), float(grow_scale3d), float(prune_opa), float(prune_scale3d),
+                          float(scene_scale), float(split_factor), int(bool(grow)), int(bool(prune_big)))
+
+
+def gs_densify_scratch_bytes(n: int) -> int:
+    return int(lib().gs_densify_scratch_bytes(int(n)))
+
+
+def gs_densify_count(scene, storage_flags: int, cfg: gs_densify_cfg, scratch, stream=None):
+    _check(lib().gs_densify_count(scene_bufs([scene]), int(storage_flags), ctypes.byref(cfg), _ptr(scratch),
+                                  _stream(stream)), "gs_densify_count")
+
+
+def gs_densify_counts(scratch, stream=None):
+    """(kept, clones, splits, total) -- synchronises the stream."""
+    out = (ctypes.c_int64 * 4)()
+    _check(lib().gs_densify_counts(_ptr(scratch), out, _stream(stream)), "gs_densify_counts")
+    return tuple(int(x) for x in out)
+
+
+def gs_densify_apply(scene_in, storage_flags: int, cfg: gs_densify_cfg, eps, scratch, scene_out, stream=None):
+    _check(lib().gs_densify_apply(scene_bufs([scene_in]), int(storage_flags), ctypes.byref(cfg), _ptr(eps),
+                                  _ptr(scratch), scene_bufs([scene_out]), _stream(stream)), "gs_densify_apply")
+
+
+def gs_reset_opacity(scene, storage_flags: int, value: float, stream=None):
+    _check(lib().gs_reset_opacity(scene_bufs([scene]), int(storage_flags), float(value), _stream(stream)),
+           "gs_reset_opacity")

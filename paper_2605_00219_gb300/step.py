@@ -33,6 +33,22 @@ class SceneBuffers:
     sh: torch.Tensor            # (12, n, 4) float32 or (6, n, 8) bfloat16
     m: torch.Tensor | None      # (15, n, 4) float32 or bfloat16
     v: torch.Tensor | None
+    stats: torch.Tensor | None = None   # (n, 2) float32 densification statistics
+
+    @property
+    def storage_flags(self) -> int:
+        return ((gsstep.STORE_SH_BF16 if self.sh.dtype == torch.bfloat16 else 0) |
+                (gsstep.STORE_MOMENTS_BF16 if self.m is not None and self.m.dtype == torch.bfloat16 else 0))
+
+    @staticmethod
+    def empty_like_layout(ref: "SceneBuffers", n: int) -> "SceneBuffers":
+        """Uninitialised buffers for n Gaussians in ref's layout."""
+        dev = ref.geom.device
+        return SceneBuffers(n, torch.empty((3, n, 4), dtype=torch.float32, device=dev),
+                            torch.empty((ref.sh.shape[0], n, ref.sh.shape[2]), dtype=ref.sh.dtype, device=dev),
+                            torch.empty((15, n, 4), dtype=ref.m.dtype, device=dev),
+                            torch.empty((15, n, 4), dtype=ref.v.dtype, device=dev),
+                            None if ref.stats is None else torch.empty((n, 2), dtype=torch.float32, device=dev))
 
     @staticmethod
     def from_scene(scene: synth.Scene, device="cuda", sh_bf16=False, mom_bf16=False, moments=True):
@@ -175,3 +191,44 @@ class Trainer:
 
     def buffer(self, which: int, numel: int, dtype=torch.int32):
         return gsstep.gs_workspace_buffer(self.plan, self.ws, which, numel, dtype)
+
+    # -- default densification ----------------------------------------------
+    def enable_densify_stats(self):
+        """Let gs_project_bwd_adam accumulate the densification statistics."""
+        for sb in self.scenes:
+            if sb.stats is None:
+                sb.stats = torch.zeros((sb.n, 2), dtype=torch.float32, device=self.device)
+        self.graph = None
+
+    def densify(self, scene_scale, generator=None, **cfg):
+        """One refinement of the default strategy on every scene (clone /
+        split / prune, see gs_densify_apply), then a new plan and workspace for
+        the new sizes (the Adam step counter carries over; a captured graph is
+        dropped).  Returns [(kept, clones, splits, total)] per scene."""
+        t = int(self.stats().step)
+        out = []
+        for k, sb in enumerate(self.scenes):
+            c = gsstep.make_densify_cfg(scene_scale, **cfg)
+            scratch = torch.empty(gsstep.gs_densify_scratch_bytes(sb.n), dtype=torch.uint8, device=self.device)
+            gsstep.gs_densify_count(sb, sb.storage_flags, c, scratch)
+            counts = gsstep.gs_densify_counts(scratch)
+            eps = torch.randn((sb.n, 6), dtype=torch.float32, device=self.device, generator=generator)
+            nb = SceneBuffers.empty_like_layout(sb, counts[3])
+            gsstep.gs_densify_apply(sb, sb.storage_flags, c, eps, scratch, nb)
+            self.scenes[k] = nb
+            out.append(counts)
+        self._replan(t)
+        return out
+
+    def reset_opacity(self, value: float = 0.01):
+        for sb in self.scenes:
+            gsstep.gs_reset_opacity(sb, sb.storage_flags, value)
+
+    def _replan(self, step: int):
+        p = self.plan
+        self.plan = gsstep.Plan([s.n for s in self.scenes], p.views, 0, p.tile, p.bwd_batch, p.storage_flags,
+                                p.bwd_impl)
+        self.ws = torch.empty(self.plan.workspace_bytes(), dtype=torch.uint8, device=self.device)
+        gsstep.gs_workspace_init(self.plan, self.ws)
+        gsstep.gs_workspace_set_step(self.plan, self.ws, step)
+        self.graph = None
