@@ -206,7 +206,7 @@ gs_status gs_loss_l1_ssim(const gs_plan* plan, void* ws, const float* image,
  * tuning.bwd_impl = 1: the paper's first implementation -- Gaussians of the
  * tile in batches of S across threads, T recomputed front to back;
  * tuning.bwd_impl = 0: pixels across threads walking back from their last
- * blended pair (compensated division by 1 - alpha), per-Gaussian gradients
+ * blended pair (T recovered by division by 1 - alpha), per-Gaussian gradients
  * reduced across each warp's pixels with shuffles.
  * image is the gs_raster_fwd output, dL_dimage the loss gradient. */
 gs_status gs_raster_bwd(const gs_plan* plan, void* ws, const float* image,
