@@ -92,7 +92,7 @@ def _args():
     ap.add_argument("--tune-rounds", type=int, default=18)
     ap.add_argument("--psnr-steps", type=int, default=200)
     ap.add_argument("--tile", default=None, help="fix the tile shape (e.g. 16x16) instead of autotuning")
-    ap.add_argument("--bwd-impl", type=int, default=None, choices=[0, 1],
+    ap.add_argument("--bwd-impl", type=int, default=None, choices=[0, 1, 2],
                     help="fix the raster-backward implementation instead of autotuning")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")

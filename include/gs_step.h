@@ -92,7 +92,11 @@ typedef struct {
                                  threads with per-Gaussian warp-shuffle
                                  reductions, 1 = Gaussians across threads in
                                  batches of S (the paper's first
-                                 implementation, Sec. 4.2) */
+                                 implementation, Sec. 4.2), 2 = a pass over
+                                 pixels storing per-pair transmittance terms
+                                 in shared memory, then a pass over
+                                 (Gaussian, pixel block) pairs summing them
+                                 (the paper's second implementation) */
 } gs_tuning;
 
 typedef struct {
@@ -205,6 +209,10 @@ gs_status gs_loss_l1_ssim(const gs_plan* plan, void* ws, const float* image,
  * recomputed per tile (nothing per pair is kept from the forward).
  * tuning.bwd_impl = 1: the paper's first implementation -- Gaussians of the
  * tile in batches of S across threads, T recomputed front to back;
+ * tuning.bwd_impl = 2: the paper's second implementation -- per batch, a
+ * pass over pixels stores each (Gaussian, pixel) pair's weight and
+ * dL/dalpha terms in shared memory, then a pass over (Gaussian, pixel block)
+ * pairs sums them;
  * tuning.bwd_impl = 0: pixels across threads walking back from their last
  * blended pair (T recovered by division by 1 - alpha), per-Gaussian gradients
  * reduced across each warp's pixels with shuffles.

@@ -18,7 +18,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 TILES = [(8, 8), (16, 16), (16, 32)]
-BWD_IMPLS = [0, 1]
+BWD_IMPLS = [0, 1, 2]
 
 
 @dataclass

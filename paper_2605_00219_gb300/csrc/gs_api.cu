@@ -60,7 +60,7 @@ static bool plan_build(Plan& P, const int64_t* scene_n, int32_t n_scenes, const 
     if (!tile_ok) return false;
     if (!(t.bwd_batch == 0 || t.bwd_batch == 32 || t.bwd_batch == 64 || t.bwd_batch == 96 || t.bwd_batch == 128))
         return false;
-    if (t.bwd_impl != 0 && t.bwd_impl != 1) return false;
+    if (t.bwd_impl < 0 || t.bwd_impl > 2) return false;
     if (flags & ~(GS_STORE_SH_BF16 | GS_STORE_MOMENTS_BF16)) return false;
     P.tuning = t;
     P.sh_bf16 = (flags & GS_STORE_SH_BF16) ? 1 : 0;

@@ -298,9 +298,10 @@ void launch_raster_bwd_px(const Plan& P, const WsPtrs& w, const float* bg, const
 
 void launch_raster_bwd(const Plan& P, const WsPtrs& w, const float* image, const float* dl, cudaStream_t st)
 {
-    if (P.tuning.bwd_impl == 0) {
+    if (P.tuning.bwd_impl == 0 || P.tuning.bwd_impl == 2) {
         const float* bg = reinterpret_cast<const float*>(reinterpret_cast<const char*>(w.hdr) + offsetof(WsHeader, bg));
-        launch_raster_bwd_px(P, w, bg, dl, st);
+        if (P.tuning.bwd_impl == 0) launch_raster_bwd_px(P, w, bg, dl, st);
+        else launch_raster_bwd2(P, w, bg, dl, st);
         return;
     }
     const Views& V = P.views;

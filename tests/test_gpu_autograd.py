@@ -66,7 +66,7 @@ def _gpu_grads(n, dgeom, dsh):
     return np.concatenate([d[0, :, :3], d[1], d[2], s.transpose(1, 0, 2).reshape(n, 48)], axis=1)
 
 
-@pytest.mark.parametrize("bwd_impl", [0, 1])
+@pytest.mark.parametrize("bwd_impl", [0, 1, 2])
 def test_autograd_multi_scene_vs_oracle(mods, orc, bwd_impl):
     autograd, step = mods
     scenes, cams = _scenes()

@@ -79,7 +79,7 @@ def _check_grad(gpu, ref, mask, name, tol=1e-3):
     return worst
 
 
-@pytest.mark.parametrize("seed,bwd_impl", [(0, 0), (1, 0), (0, 1), (1, 1)])
+@pytest.mark.parametrize("seed,bwd_impl", [(0, 0), (1, 0), (0, 1), (1, 1), (0, 2), (1, 2)])
 def test_tiny_stages(gs, orc, seed, bwd_impl):
     """2,000 Gaussians, 128x128: every stage against the oracle (both
     raster-backward implementations)."""
@@ -181,7 +181,8 @@ def test_tiny_full_step_adam(gs, orc):
 
 @pytest.mark.parametrize("tile,bwd_batch,bwd_impl", [((16, 16), 0, 1), ((8, 8), 0, 1), ((16, 32), 0, 1),
                                                      ((16, 16), 32, 1), ((16, 16), 64, 1), ((16, 16), 96, 1),
-                                                     ((16, 16), 0, 0), ((8, 8), 0, 0), ((16, 32), 0, 0)])
+                                                     ((16, 16), 0, 0), ((8, 8), 0, 0), ((16, 32), 0, 0),
+                                                     ((16, 16), 0, 2), ((8, 8), 0, 2), ((16, 32), 0, 2)])
 def test_ragged_tiles_and_batches(gs, orc, tile, bwd_batch, bwd_impl):
     """Non-multiple image size (ragged tile tail), all tile shapes, fixed and
     adaptive backward batch sizes: keys bit-exact, images and gradients."""
@@ -210,7 +211,7 @@ def test_ragged_tiles_and_batches(gs, orc, tile, bwd_batch, bwd_impl):
     _check_grad(g2_gpu, g2_orc, good, f"grad2d {tile} S={bwd_batch} impl={bwd_impl}")
 
 
-@pytest.mark.parametrize("bwd_impl", [0, 1])
+@pytest.mark.parametrize("bwd_impl", [0, 1, 2])
 def test_background_colour(gs, orc, bwd_impl):
     """Non-black background: image, and gradients (the background enters
     every dL/d alpha through the colour still to come)."""
