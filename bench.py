@@ -57,12 +57,12 @@ LR = (1.6e-4 * 30.0, 1e-3, 5e-3, 5e-2, 2.5e-3, 2.5e-3 / 20)   # mean lr scaled b
 # raster backward; profiles/step_batched_bf16_3M_4x1080p_launch_list.md).
 # Valid only while the kernel sources hash to the recorded prefixes.
 MEASURED_TRAFFIC = {
-    "raster_bwd": (2155676160 + 1030893312, {"raster_bwd.cu": "f6f38f5977885d34"}),
-    "project_bwd_adam": (2128118016 + 1099712256, {"project_bwd_adam.cu": "3400fcbaf8be17f7"}),
-    "raster_fwd": (1059240960 + 166127616, {"raster_fwd.cu": "3f2b98cc012db5e7"}),
-    "project_fwd": (1869304064 + 666724096, {"project_fwd.cu": "182c89940c0d24b9"}),
+    "raster_bwd": (2106000000 + 976000000, {"raster_bwd.cu": "816a50647c3ae43f"}),
+    "project_bwd_adam": (2077000000 + 1099000000, {"project_bwd_adam.cu": "7e9c94ebada201bd"}),
+    "raster_fwd": (1031000000 + 155000000, {"raster_fwd.cu": "d92a368e13895eda"}),
+    "project_fwd": (1870000000 + 666000000, {"project_fwd.cu": "054b01e733416a04"}),
 }
-TRAFFIC_COMMON = {"gs_device.cuh": "f40b1e771be92640", "gs_internal.cuh": "33ad950b1776db18"}
+TRAFFIC_COMMON = {"gs_device.cuh": "02cf40e7d44ac4b5", "gs_internal.cuh": "6c2125d40657aed6"}
 
 
 def _measured_traffic(kernel: str, headline: bool):
