@@ -224,3 +224,19 @@ def loss_images(shapes, seed: int, smooth: bool = False):
         imgs.append(img.astype(np.float32))
         tgts.append(t8)
     return imgs, tgts
+
+
+MULTI_SIZES = (500_000, 500_000, 750_000, 750_000, 1_000_000, 1_250_000, 1_250_000, 6_000_000)
+
+
+def multi_scene_workload(sizes=MULTI_SIZES, radius: float = 36.0):
+    """Eight clustered scenes (seeds 0-7, 30 m box, about one cluster per
+    12,000 Gaussians) with two views each: even scenes 1920x1080 + 960x540,
+    odd scenes 1280x720 + 1600x900, on the r = 36 m orbit."""
+    scenes, cams = [], []
+    for k, n in enumerate(sizes):
+        scenes.append(cluster_scene(n, max(16, n // 12000), 30.0, seed=k))
+        res = [(1920, 1080), (960, 540)] if k % 2 == 0 else [(1280, 720), (1600, 900)]
+        for i, (w, h) in enumerate(res):
+            cams += orbit_cameras(1, radius, w, h, scene=k, phase_deg=45.0 * k + 60.0 * i)
+    return scenes, cams
