@@ -14,14 +14,17 @@ steps per second); the plain form's steps/s is reported beside it.  A short
 training run of both storage precisions on the same schedule gives the
 rendered-PSNR difference on a held-out 1080p view.  `--workload uneven`
 runs the batch of four uneven views (1920x1080, 1600x1064, 1280x720,
-960x540) instead, `--workload plain` the plain form alone.
+960x540) instead, `--workload plain` the plain form alone, `--workload
+multiscene` eight scenes of 0.5-6M Gaussians (12M in all) with two views
+each of mixed resolution (16 views per step, BF16 storage, 16x16 tiles;
+no plain comparison, PSNR or CPU baseline).
 
 Inputs (parameters, moments, targets, cameras) are resident in HBM when the
 timed region starts; the working set (about 1.5 GB of parameters and
 moments plus 2 GB of workspace) is far larger than L2, so no flush is used.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload batched|plain]
+                  [--workload batched|uneven|plain|multiscene]
 
 One JSON line on rank 0.  `--impl reference` times the CPU oracle (FP64, the
 plain restatement of the paper's step) on a bounded sample of the same
@@ -87,7 +90,7 @@ def _args():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="batched", choices=["batched", "uneven", "plain"])
+    ap.add_argument("--workload", default="batched", choices=["batched", "uneven", "plain", "multiscene"])
     ap.add_argument("--n", type=int, default=N_GAUSS)
     ap.add_argument("--tune-rounds", type=int, default=18)
     ap.add_argument("--psnr-steps", type=int, default=200)
@@ -336,11 +339,25 @@ def main():
     from paper_2605_00219_gb300 import step as stepmod
 
     stream = torch.cuda.current_stream()
-    scene = synth.large_scene(0, args.n)
-    tscene = synth.perturbed(scene, 1)
-    cams = _views(args.workload)
+    multi = args.workload == "multiscene"
+    if multi:
+        # eight scenes of 0.5-6M Gaussians with two views each, one step
+        import dataclasses
+        scenes, cams = synth.multi_scene_workload()
+        scene = scenes[-1]
+        targets = torch.cat([_render_targets(stepmod, synth.perturbed(sc, k + 1),
+                                             [dataclasses.replace(c, scene=0) for c in cams if c.scene == k])
+                             for k, sc in enumerate(scenes)])
+        args.no_plain, args.psnr_steps, args.no_cpu = True, 0, True
+        if args.tile is None:
+            args.tile = "16x16"
+    else:
+        scene = synth.large_scene(0, args.n)
+        tscene = synth.perturbed(scene, 1)
+        cams = _views(args.workload)
+        targets = _render_targets(stepmod, tscene, cams)
+        scenes = [scene]
     batched = args.workload != "plain"
-    targets = _render_targets(stepmod, tscene, cams)
     px = sum(c.width * c.height for c in cams)
     equiv = px / PX_1080
     nviews = len(cams)
@@ -362,7 +379,8 @@ def main():
 
     # ---- the measured form
     sh16 = batched
-    bufs = stepmod.SceneBuffers.from_scene(scene, sh_bf16=sh16, mom_bf16=sh16)
+    all_bufs = [stepmod.SceneBuffers.from_scene(sc, sh_bf16=sh16, mom_bf16=sh16) for sc in scenes]
+    bufs = all_bufs[0]
     fixed = args.tile is not None or args.bwd_impl is not None
     if batched and not fixed:
         best, tuner, trainers = autotune.tune_trainer([bufs], cams, rounds=args.tune_rounds, lr=LR, sh_bf16=True,
@@ -379,7 +397,7 @@ def main():
     else:
         tile = tuple(int(x) for x in args.tile.split("x")) if args.tile else (16, 16)
         impl = args.bwd_impl if args.bwd_impl is not None else 0
-        tr = stepmod.Trainer([bufs], cams, lr=LR, tile=tile, bwd_impl=impl, sh_bf16=sh16, mom_bf16=sh16)
+        tr = stepmod.Trainer(all_bufs, cams, lr=LR, tile=tile, bwd_impl=impl, sh_bf16=sh16, mom_bf16=sh16)
         tr.target.copy_(targets)
         tr.step(0)
         tune_info = None
@@ -442,7 +460,7 @@ def main():
     except OSError:
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    n = scene.n
+    n = sum(sc.n for sc in scenes)
     per_g = (240 + 480) * 2 if not sh16 else (48 + 96 + 240) * 2
     adam_bytes = n * per_g + K * 48 + n * 8 * len(cams)
     fwd_bytes = n * (48 + (96 if sh16 else 192)) + n * len(cams) * (48 + 16 + 4)
@@ -485,8 +503,10 @@ def main():
 
     if rank == 0:
         value = whole_job_rate(ws, nviews, ms)
-        desc = ("batched BF16: " if batched else "plain FP32: ") + \
-               f"{n / 1e6:.3g}M Gaussians (256 clusters, 30 m box), views per step " + \
+        desc = ("multi-scene BF16: 8 scenes of " + "/".join(f"{sc.n / 1e6:.3g}" for sc in scenes) +
+                f"M Gaussians ({n / 1e6:.3g}M in all), views per step " if multi else
+                ("batched BF16: " if batched else "plain FP32: ") +
+                f"{n / 1e6:.3g}M Gaussians (256 clusters, 30 m box), views per step ") + \
                "+".join(f"{c.width}x{c.height}" for c in cams) + \
                (", BF16 SH and Adam moments (FP32 math)" if sh16 else ", FP32 storage") + \
                f", tile {tile[0]}x{tile[1]}, raster_bwd impl {impl}, whole step in one CUDA graph; value = " + \
