@@ -1,0 +1,114 @@
+"""The mid-size workload: 200k Gaussians in 64 clusters, a 20-view orbit at
+1280x720.
+
+- Step 0 on a two-view batch against the FP64 oracle's step (post-Adam
+  parameters where the update is decided).
+- 200 graph-replayed steps cycling through the orbit four views at a time
+  (cameras and targets swapped in device memory between replays): the
+  held-out PSNR curve rises and the loss falls."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2605_00219_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+LR = (1.6e-4 * 10.0, 1e-3, 5e-3, 5e-2, 2.5e-3, 2.5e-3 / 20)
+MARGIN = 1e-3
+
+
+@pytest.fixture(scope="module")
+def mods():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_00219_gb300 import build
+    build.build()
+    from paper_2605_00219_gb300 import gsstep, step
+    return gsstep, step
+
+
+def test_step0_two_views_against_oracle(mods, orc):
+    gsstep, step_mod = mods
+    scene, tscene, cams = synth.mid_workload(0)
+    cams = cams[:2]
+    p_t = orc.Params64.from_scene(tscene)
+    targets = [orc.render64(c, orc.project64(p_t, c), orc.bin32(tscene, c)).image for c in cams]
+    res = orc.step(scene, cams, targets, LR, 1, margin=MARGIN)
+    tr = step_mod.Trainer([scene], cams, lr=LR)
+    tr.set_target([t.astype(np.float32) for t in targets])
+    tr.step(step=1)
+    torch.cuda.synchronize()
+    assert tr.stats().status == 0
+    assert tr.stats().loss == pytest.approx(res.loss, rel=1e-4)
+    bad = np.zeros(scene.n, bool)
+    for c, r, P, tg, b in zip(cams, res.renders, res.projs, targets, res.binnings):
+        r.unstable_px |= (np.abs(r.image - tg) < 1e-5).any(-1)
+        ys, xs = np.nonzero(r.unstable_px)
+        bad |= r.unstable_g
+        tiles = (ys // 16) * ((c.width + 15) // 16) + xs // 16
+        for t in np.unique(tiles):
+            sel = tiles == t
+            s0, e0 = b.ranges[t]
+            g = b.gidx[s0:e0].astype(np.int64)
+            dx = xs[sel][:, None] + 0.5 - P[g, 4][None, :]
+            dy = ys[sel][:, None] + 0.5 - P[g, 5][None, :]
+            d2 = P[g, 9] * dx * dx + 2 * P[g, 10] * dx * dy + P[g, 11] * dy * dy
+            bad[g[(d2 <= 9.0 * 1.001).any(0)]] = True
+    g = res.grad
+    rms = np.sqrt((g[~bad] ** 2).mean(0)) + 1e-30
+    decided = (np.abs(g) > 1e-2 * rms[None, :]) & ~bad[:, None]
+    assert decided.sum() > 100000          # values checked (flags exclude many Gaussians at 720p)
+    new = tr.scenes[0].to_scene()
+    th = np.concatenate([new.means, new.quats, np.log(new.scales), np.log(new.opacities / (1 - new.opacities))[:, None],
+                         new.sh.reshape(-1, 48)], axis=1).astype(np.float64)
+    tol = 1e-5 * np.abs(res.theta) + 1e-6
+    assert np.all(np.abs(th - res.theta)[decided] <= tol[decided])
+
+
+def _psnr(img, ref):
+    mse = float(((img.double() - ref.double()) ** 2).mean().item())
+    return 10.0 * math.log10(1.0 / max(mse, 1e-30))
+
+
+def test_200_steps_over_the_orbit(mods):
+    gsstep, step_mod = mods
+    scene, tscene, cams = synth.mid_workload(0)
+    held = synth.orbit_cameras(1, 12.0, 1280, 720, phase_deg=9.0)[0]      # between two training views
+
+    def render(x, cs):
+        t = step_mod.Trainer([x], cs, lr=LR)
+        t.forward()
+        torch.cuda.synchronize()
+        return t.image.clone()
+
+    targets = [render(tscene, cams[4 * k:4 * k + 4]) for k in range(5)]
+    held_tgt = render(tscene, [held])
+    from paper_2605_00219_gb300.step import camera_params
+    cam_params = [torch.from_numpy(camera_params(cams[4 * k:4 * k + 4])).cuda() for k in range(5)]
+    tr = step_mod.Trainer([scene], cams[:4], lr=LR, sh_bf16=True, mom_bf16=True)
+    tr.target.copy_(targets[0])
+    tr.step(0)
+    tr.capture()
+    curve = [(0, _psnr(render(scene, [held]), held_tgt))]
+    losses = []
+    for s in range(1, 200):
+        k = s % 5
+        tr.cams.copy_(cam_params[k])
+        tr.target.copy_(targets[k])
+        tr.replay()
+        if s % 5 == 4:
+            losses.append(float(tr.stats().loss))
+        if (s + 1) % 50 == 0:
+            tr.forward()
+            torch.cuda.synchronize()
+            ev = step_mod.Trainer([tr.scenes[0]], [held], lr=LR, sh_bf16=True, mom_bf16=True)
+            ev.forward()
+            torch.cuda.synchronize()
+            curve.append((s + 1, _psnr(ev.image, held_tgt)))
+    print("held-out PSNR (step, dB):", [(s, round(p, 2)) for s, p in curve])
+    assert tr.stats().status == 0 and tr.stats().step == 200
+    assert curve[-1][1] > curve[0][1] + 1.0
+    assert np.mean(losses[-5:]) < 0.8 * np.mean(losses[:5])
