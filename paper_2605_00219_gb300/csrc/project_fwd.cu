@@ -6,7 +6,9 @@
 
 namespace gs {
 
-__global__ void __launch_bounds__(256) k_project_fwd(Views V, Scenes S, const float* __restrict__ cams,
+// 3 CTAs per SM: the register cap (80) costs a few spills but raises occupancy
+// from 2 to 3 CTAs (0.88 -> 0.73 ms at 3M Gaussians x 4 views)
+__global__ void __launch_bounds__(256, 3) k_project_fwd(Views V, Scenes S, const float* __restrict__ cams,
                                                      uint32_t* __restrict__ count, ProjRec* __restrict__ rec,
                                                      float4* __restrict__ binrec, WsHeader* __restrict__ hdr)
 {
