@@ -71,10 +71,19 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* warp_s
     return before + x - v;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ in, int64_t n,
+// Effective scan length: n, or (*nb) * mul when the length is known only on
+// the device (the radix histograms: 256 digits x blocks holding keys).
+__device__ __forceinline__ int64_t scan_len(int64_t n, const uint32_t* nb, int mul)
+{
+    return nb ? min(n, (int64_t)(*nb) * mul) : n;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ in, int64_t n_max,
+                                                               const uint32_t* __restrict__ nb, int mul,
                                                                uint32_t* __restrict__ part)
 {
     __shared__ uint32_t ws[32];
+    const int64_t n = scan_len(n_max, nb, mul);
     const int64_t base = (int64_t)blockIdx.x * kScanBlock;
     uint32_t s = 0;
 #pragma unroll
@@ -104,12 +113,15 @@ __global__ void __launch_bounds__(1024) k_scan_part(uint32_t* __restrict__ part,
     if (threadIdx.x == 0) part[nparts] = carry;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* in, int64_t n,
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* in, int64_t n_max,
+                                                             const uint32_t* __restrict__ nb, int mul,
                                                              const uint32_t* __restrict__ part, uint32_t* out)
 {
     __shared__ uint32_t buf[kScanBlock];
     __shared__ uint32_t ws[32];
+    const int64_t n = scan_len(n_max, nb, mul);
     const int64_t base = (int64_t)blockIdx.x * kScanBlock;
+    if (base >= n) return;
 #pragma unroll
     for (int i = 0; i < kScanItems; i++) {
         int64_t idx = base + i * kScanThreads + threadIdx.x;
@@ -134,12 +146,18 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* in, 
     }
 }
 
+static void scan_u32_dyn(const uint32_t* in, uint32_t* out, int64_t n_max, const uint32_t* nb, int mul,
+                         uint32_t* part, cudaStream_t st)
+{
+    const int64_t nparts = (n_max + kScanBlock - 1) / kScanBlock;
+    k_scan_reduce<<<(unsigned)nparts, kScanThreads, 0, st>>>(in, n_max, nb, mul, part);
+    k_scan_part<<<1, 1024, 0, st>>>(part, nparts);
+    k_scan_down<<<(unsigned)nparts, kScanThreads, 0, st>>>(in, n_max, nb, mul, part, out);
+}
+
 void scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* part, cudaStream_t st)
 {
-    const int64_t nparts = (n + kScanBlock - 1) / kScanBlock;
-    k_scan_reduce<<<(unsigned)nparts, kScanThreads, 0, st>>>(in, n, part);
-    k_scan_part<<<1, 1024, 0, st>>>(part, nparts);
-    k_scan_down<<<(unsigned)nparts, kScanThreads, 0, st>>>(in, n, part, out);
+    scan_u32_dyn(in, out, n, nullptr, 1, part, st);
 }
 
 // Total, capacity check and view segment starts after the count scan.
@@ -150,6 +168,7 @@ __global__ void k_count_finalize(Views V, const uint32_t* __restrict__ part, int
     if (threadIdx.x == 0) {
         hdr->k_required = total;
         hdr->k_eff = total < cap ? total : cap;
+        hdr->hist_nblk = ((total < cap ? total : cap) + kRadixBlock - 1) / kRadixBlock;
         if (total > cap) atomicOr(&hdr->status, GS_STATUS_CAPACITY);
         offset[V.pairs] = total;
         hdr->seg[V.n] = total < cap ? total : cap;
@@ -211,11 +230,15 @@ template <int MODE>
 __global__ void __launch_bounds__(kRadixThreads) k_radix_up(const uint32_t* __restrict__ keys,
                                                              const uint32_t* __restrict__ vals, bool iota,
                                                              const WsHeader* __restrict__ hdr, int shift,
-                                                             uint32_t* __restrict__ hist, int64_t nblk, int nv)
+                                                             uint32_t* __restrict__ hist, int nv)
 {
     // digit counts of this block's 2048 keys: one private histogram per warp
-    // (plain shared-memory atomics), summed per digit at the end
+    // (plain shared-memory atomics), summed per digit at the end.  Only the
+    // blocks that hold keys take part; the histogram is [digit][block] over
+    // them, so its scan covers 256 x ceil(K / 2048) entries.
     constexpr int W = kRadixThreads / 32;
+    const uint32_t nb = hdr->hist_nblk;
+    if (blockIdx.x >= nb) return;
     __shared__ uint32_t h[W][kRadixDigits];
     __shared__ uint32_t seg[kMaxViews + 1];
     const int w = threadIdx.x >> 5;
@@ -249,7 +272,7 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_up(const uint32_t* __re
     uint32_t c = 0;
 #pragma unroll
     for (int i = 0; i < W; i++) c += h[i][threadIdx.x];
-    hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = c;
+    hist[(int64_t)threadIdx.x * nb + blockIdx.x] = c;
 }
 
 template <int MODE, bool IOTA, bool LAST>
@@ -257,7 +280,7 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_down(const uint32_t* __
                                                                const uint32_t* __restrict__ vals_in,
                                                                uint32_t* __restrict__ keys_out,
                                                                uint32_t* __restrict__ vals_out,
-                                                               const uint32_t* __restrict__ hist, int64_t nblk,
+                                                               const uint32_t* __restrict__ hist,
                                                                int shift, const WsHeader* __restrict__ hdr, int nv,
                                                                const uint32_t* __restrict__ pid,
                                                                uint32_t* __restrict__ pid_sorted)
@@ -320,7 +343,7 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_down(const uint32_t* __
         }
         uint32_t ex = block_excl_scan<kRadixThreads>(run, wsum, nullptr);
         bstart[d] = ex;
-        gbase[d] = hist[(int64_t)d * nblk + blockIdx.x];
+        gbase[d] = hist[(int64_t)d * hdr->hist_nblk + blockIdx.x];
     }
     __syncthreads();
 #pragma unroll
@@ -391,15 +414,14 @@ void launch_bin_sort(const Plan& P, const WsPtrs& w, cudaStream_t st)
         const bool first = pass == 0, last = pass == npass - 1;
         const int shift = 8 * pass;
         if (view)
-            k_radix_up<kDigitView><<<(unsigned)nblk, kRadixThreads, 0, st>>>(kin, vin, first, w.hdr, 0, w.hist, nblk,
-                                                                               V.n);
+            k_radix_up<kDigitView><<<(unsigned)nblk, kRadixThreads, 0, st>>>(kin, vin, first, w.hdr, 0, w.hist, V.n);
         else
             k_radix_up<kDigitKey><<<(unsigned)nblk, kRadixThreads, 0, st>>>(kin, vin, first, w.hdr, shift, w.hist,
-                                                                              nblk, V.n);
-        scan_u32(w.hist, w.hist, (int64_t)kRadixDigits * nblk, w.scan_part, st);
+                                                                              V.n);
+        scan_u32_dyn(w.hist, w.hist, (int64_t)kRadixDigits * nblk, &w.hdr->hist_nblk, kRadixDigits, w.scan_part, st);
 #define GS_DOWN(MODE, IOTA, LAST)                                                                          \
-    k_radix_down<MODE, IOTA, LAST><<<(unsigned)nblk, kRadixThreads, 0, st>>>(kin, vin, kout, vout, w.hist, nblk, \
-                                                                              shift, w.hdr, V.n, w.pid, w.pid_sorted)
+    k_radix_down<MODE, IOTA, LAST><<<(unsigned)nblk, kRadixThreads, 0, st>>>(kin, vin, kout, vout, w.hist, shift, \
+                                                                              w.hdr, V.n, w.pid, w.pid_sorted)
         if (view) {
             if (first) GS_DOWN(kDigitView, true, true);
             else GS_DOWN(kDigitView, false, true);

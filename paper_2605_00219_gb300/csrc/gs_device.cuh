@@ -60,7 +60,7 @@ struct WsHeader {
     uint32_t k_eff;            // min(k_required, capacity)
     uint32_t loss_counter;
     float loss;
-    uint32_t pad;
+    uint32_t hist_nblk;           // radix-sort blocks holding keys: ceil(k_eff / 2048)
     float bg[4];                  // background colour of the last raster_fwd
     uint32_t seg[kMaxViews + 1];  // sorted-segment start of each view
 };
