@@ -232,24 +232,25 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_up(const uint32_t* __re
                                                              const WsHeader* __restrict__ hdr, int shift,
                                                              uint32_t* __restrict__ hist, int nv)
 {
-    // digit counts of this block's 2048 keys: one private histogram per warp
+    // digit counts of each 2048-key block: one private histogram per warp
     // (plain shared-memory atomics), summed per digit at the end.  Only the
-    // blocks that hold keys take part; the histogram is [digit][block] over
-    // them, so its scan covers 256 x ceil(K / 2048) entries.
+    // blocks that hold keys take part (the grid strides over them); the
+    // histogram is [digit][block] over them, so its scan covers
+    // 256 x ceil(K / 2048) entries.
     constexpr int W = kRadixThreads / 32;
     const uint32_t nb = hdr->hist_nblk;
     if (blockIdx.x >= nb) return;
     __shared__ uint32_t h[W][kRadixDigits];
     __shared__ uint32_t seg[kMaxViews + 1];
     const int w = threadIdx.x >> 5;
-#pragma unroll
-    for (int i = 0; i < W; i++) h[i][threadIdx.x] = 0;
     if (MODE == kDigitView)
         for (int i = threadIdx.x; i <= nv; i += blockDim.x) seg[i] = hdr->seg[i];
-    __syncthreads();
     const uint32_t K = hdr->k_eff;
-    const int64_t base = (int64_t)blockIdx.x * kRadixBlock;
-    if (base < K) {
+    for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
+#pragma unroll
+        for (int i = 0; i < W; i++) h[i][threadIdx.x] = 0;
+        __syncthreads();
+        const int64_t base = (int64_t)b * kRadixBlock;
         uint32_t d[kRadixItems];
 #pragma unroll
         for (int i = 0; i < kRadixItems; i++) {   // all loads first, then the counts
@@ -267,12 +268,13 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_up(const uint32_t* __re
                 atomicAdd(&h[w][dg], 1u);
             }
         }
-    }
-    __syncthreads();
-    uint32_t c = 0;
+        __syncthreads();
+        uint32_t c = 0;
 #pragma unroll
-    for (int i = 0; i < W; i++) c += h[i][threadIdx.x];
-    hist[(int64_t)threadIdx.x * nb + blockIdx.x] = c;
+        for (int i = 0; i < W; i++) c += h[i][threadIdx.x];
+        hist[(int64_t)threadIdx.x * nb + b] = c;
+        __syncthreads();
+    }
 }
 
 template <int MODE, bool IOTA, bool LAST>
@@ -294,76 +296,80 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_down(const uint32_t* __
     __shared__ uint32_t seg[kMaxViews + 1];
     __shared__ uint32_t wsum[32];
     const uint32_t K = hdr->k_eff;
-    const int64_t base = (int64_t)blockIdx.x * kRadixBlock;
-    if (base >= K) return;
+    const uint32_t nb = hdr->hist_nblk;
+    if (blockIdx.x >= nb) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int i = 0; i < W; i++) wh[i][threadIdx.x] = 0;
     if (MODE == kDigitView)
         for (int i = threadIdx.x; i <= nv; i += blockDim.x) seg[i] = hdr->seg[i];
-    __syncthreads();
-
-    uint32_t key[kRadixItems], val[kRadixItems], dig[kRadixItems], rank[kRadixItems];
-#pragma unroll
-    for (int r = 0; r < kRadixItems; r++) {
-        const int64_t idx = base + w * (32 * kRadixItems) + r * 32 + lane;
-        const bool valid = idx < K;
-        key[r] = valid ? keys_in[idx] : 0u;
-        val[r] = IOTA ? (uint32_t)idx : (valid ? vals_in[idx] : 0u);
-        uint32_t d = 0xFFFFu;
-        if (valid) {
-            if (MODE == kDigitKey) d = (key[r] >> shift) & 0xFFu;
-            else d = (uint32_t)view_of_slot(seg, nv, val[r]);
-        }
-        dig[r] = d;
-    }
-    // stable rank within the warp's contiguous 256-key range, round by round
     const uint32_t lt = lanemask_lt();
+    for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {   // blocks holding keys
+        const int64_t base = (int64_t)b * kRadixBlock;
 #pragma unroll
-    for (int r = 0; r < kRadixItems; r++) {
-        const uint32_t d = dig[r];
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const bool valid = d != 0xFFFFu;
-        uint32_t cur = valid ? wh[w][d] : 0u;
-        rank[r] = cur + __popc(peers & lt);
-        __syncwarp();
-        if (valid && lane == __ffs(peers) - 1) wh[w][d] = cur + __popc(peers);
-        __syncwarp();
-    }
-    __syncthreads();
-    // per digit: exclusive offsets across warps, then across digits
-    {
-        const int d = threadIdx.x;
-        uint32_t run = 0;
+        for (int i = 0; i < W; i++) wh[i][threadIdx.x] = 0;
+        __syncthreads();
+
+        uint32_t key[kRadixItems], val[kRadixItems], dig[kRadixItems], rank[kRadixItems];
 #pragma unroll
-        for (int i = 0; i < W; i++) {
-            uint32_t c = wh[i][d];
-            wh[i][d] = run;
-            run += c;
+        for (int r = 0; r < kRadixItems; r++) {
+            const int64_t idx = base + w * (32 * kRadixItems) + r * 32 + lane;
+            const bool valid = idx < K;
+            key[r] = valid ? keys_in[idx] : 0u;
+            val[r] = IOTA ? (uint32_t)idx : (valid ? vals_in[idx] : 0u);
+            uint32_t d = 0xFFFFu;
+            if (valid) {
+                if (MODE == kDigitKey) d = (key[r] >> shift) & 0xFFu;
+                else d = (uint32_t)view_of_slot(seg, nv, val[r]);
+            }
+            dig[r] = d;
         }
-        uint32_t ex = block_excl_scan<kRadixThreads>(run, wsum, nullptr);
-        bstart[d] = ex;
-        gbase[d] = hist[(int64_t)d * hdr->hist_nblk + blockIdx.x];
-    }
-    __syncthreads();
+        // stable rank within the warp's contiguous 256-key range, round by round
 #pragma unroll
-    for (int r = 0; r < kRadixItems; r++) {
-        const uint32_t d = dig[r];
-        if (d != 0xFFFFu) {
-            const uint32_t lp = bstart[d] + wh[w][d] + rank[r];
-            sk[lp] = key[r];
-            sv[lp] = val[r];
+        for (int r = 0; r < kRadixItems; r++) {
+            const uint32_t d = dig[r];
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            const bool valid = d != 0xFFFFu;
+            uint32_t cur = valid ? wh[w][d] : 0u;
+            rank[r] = cur + __popc(peers & lt);
+            __syncwarp();
+            if (valid && lane == __ffs(peers) - 1) wh[w][d] = cur + __popc(peers);
+            __syncwarp();
         }
-    }
-    __syncthreads();
-    const int nvalid = (int)min((int64_t)kRadixBlock, (int64_t)K - base);
-    for (int i = threadIdx.x; i < nvalid; i += kRadixThreads) {
-        const uint32_t k = sk[i], v = sv[i];
-        const uint32_t d = MODE == kDigitKey ? ((k >> shift) & 0xFFu) : (uint32_t)view_of_slot(seg, nv, v);
-        const uint32_t pos = gbase[d] + (uint32_t)i - bstart[d];
-        keys_out[pos] = k;
-        vals_out[pos] = v;
-        if (LAST) pid_sorted[pos] = pid[v];
+        __syncthreads();
+        // per digit: exclusive offsets across warps, then across digits
+        {
+            const int d = threadIdx.x;
+            uint32_t run = 0;
+#pragma unroll
+            for (int i = 0; i < W; i++) {
+                uint32_t c = wh[i][d];
+                wh[i][d] = run;
+                run += c;
+            }
+            uint32_t ex = block_excl_scan<kRadixThreads>(run, wsum, nullptr);
+            bstart[d] = ex;
+            gbase[d] = hist[(int64_t)d * nb + b];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kRadixItems; r++) {
+            const uint32_t d = dig[r];
+            if (d != 0xFFFFu) {
+                const uint32_t lp = bstart[d] + wh[w][d] + rank[r];
+                sk[lp] = key[r];
+                sv[lp] = val[r];
+            }
+        }
+        __syncthreads();
+        const int nvalid = (int)min((int64_t)kRadixBlock, (int64_t)K - base);
+        for (int i = threadIdx.x; i < nvalid; i += kRadixThreads) {
+            const uint32_t k = sk[i], v = sv[i];
+            const uint32_t d = MODE == kDigitKey ? ((k >> shift) & 0xFFu) : (uint32_t)view_of_slot(seg, nv, v);
+            const uint32_t pos = gbase[d] + (uint32_t)i - bstart[d];
+            keys_out[pos] = k;
+            vals_out[pos] = v;
+            if (LAST) pid_sorted[pos] = pid[v];
+        }
+        __syncthreads();
     }
 }
 
@@ -405,8 +411,9 @@ void launch_bin_sort(const Plan& P, const WsPtrs& w, cudaStream_t st)
         const int64_t blocks = (V.pairs + 255) / 256;
         k_emit<<<(unsigned)blocks, 256, 0, st>>>(V, w.count, w.offset, w.rec, w.binrec, w.keysA, w.pid, cap);
     }
-    // sorting
-    const int64_t nblk = P.radix_blocks;
+    // sorting: the radix kernels stride over the blocks that hold keys, with
+    // a grid of at most 8 CTAs per SM
+    const int64_t nblk = std::min<int64_t>(P.radix_blocks, (int64_t)P.sm_count * 8);
     const int npass = P.key_passes + P.view_pass;
     uint32_t *kin = w.keysA, *vin = w.valsA, *kout = w.keysB, *vout = w.valsB;
     for (int pass = 0; pass < npass; pass++) {
@@ -418,7 +425,8 @@ void launch_bin_sort(const Plan& P, const WsPtrs& w, cudaStream_t st)
         else
             k_radix_up<kDigitKey><<<(unsigned)nblk, kRadixThreads, 0, st>>>(kin, vin, first, w.hdr, shift, w.hist,
                                                                               V.n);
-        scan_u32_dyn(w.hist, w.hist, (int64_t)kRadixDigits * nblk, &w.hdr->hist_nblk, kRadixDigits, w.scan_part, st);
+        scan_u32_dyn(w.hist, w.hist, (int64_t)kRadixDigits * P.radix_blocks, &w.hdr->hist_nblk, kRadixDigits,
+                     w.scan_part, st);
 #define GS_DOWN(MODE, IOTA, LAST)                                                                          \
     k_radix_down<MODE, IOTA, LAST><<<(unsigned)nblk, kRadixThreads, 0, st>>>(kin, vin, kout, vout, w.hist, shift, \
                                                                               w.hdr, V.n, w.pid, w.pid_sorted)

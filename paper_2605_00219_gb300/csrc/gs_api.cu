@@ -53,6 +53,15 @@ static bool plan_build(Plan& P, const int64_t* scene_n, int32_t n_scenes, const 
     if (!scene_n || !views || n_scenes < 1 || n_scenes > kMaxScenes || n_views < 1 || n_views > kMaxViews)
         return false;
     memset(&P, 0, sizeof(P));
+    {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+            P.sm_count = sms;
+        else
+            P.sm_count = 152;
+        cudaGetLastError();
+    }
     gs_tuning t = {16, 16, 0, 0};
     if (tuning) t = *tuning;
     const bool tile_ok = (t.tile_w == 8 && t.tile_h == 8) || (t.tile_w == 16 && t.tile_h == 16) ||

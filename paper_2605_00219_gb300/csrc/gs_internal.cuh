@@ -37,6 +37,7 @@ struct Plan {
     int64_t count_scan_parts;    // ceil((pairs + 1) / kScanBlock)
     int64_t hist_scan_parts;     // ceil(256 * radix_blocks / kScanBlock)
     int64_t raster_blocks;       // total tiles
+    int32_t sm_count;            // SMs of the device current at plan creation (152 if none)
     // workspace byte offsets
     size_t off_hdr, off_count, off_offset, off_rec, off_binrec;
     size_t off_keysA, off_valsA, off_keysB, off_valsB, off_pid, off_pid_sorted;
