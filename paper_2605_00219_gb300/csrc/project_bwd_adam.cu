@@ -342,6 +342,8 @@ __global__ void __launch_bounds__(kPbaThreads, 4) k_project_bwd_adam(Views V, Sc
             const ViewDesc& vd = V.v[v];
             const uint32_t end = min(off + cnt, cap);
             float g2[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            // two records' loads in flight at a time
+#pragma unroll 2
             for (uint32_t e = off; e < end; e++) {
                 const GradRec r = gradrec[e];
                 g2[0] += r.a.x; g2[1] += r.a.y; g2[2] += r.a.z; g2[3] += r.a.w;
