@@ -91,11 +91,12 @@ class Trainer:
 
     def __init__(self, scenes, cameras, capacity: int = 0, tile=(16, 16), bwd_batch: int = 0,
                  sh_bf16: bool = False, mom_bf16: bool = False, bg=None, lr=DEFAULT_LR, device="cuda",
-                 bwd_impl: int = 0, loss: str = "l1", ssim_lambda: float = 0.2):
+                 bwd_impl: int = 0, loss: str = "l1", ssim_lambda: float = 0.2, seed: int = 0):
         if loss not in ("l1", "l1_ssim"):
             raise ValueError(f"loss must be 'l1' or 'l1_ssim', not {loss!r}")
         self.loss = loss
         self.ssim_lambda = float(ssim_lambda)
+        self.seed = int(seed)         # stochastic rounding of BF16 storage
         self.device = torch.device(device)
         self.scenes = [s if isinstance(s, SceneBuffers) else
                        SceneBuffers.from_scene(s, device, sh_bf16, mom_bf16) for s in scenes]
@@ -160,7 +161,7 @@ class Trainer:
         else:
             gsstep.gs_loss_l1_ssim(self.plan, self.ws, self.image, self.target, self.ssim_lambda, self.dl, stream)
         gsstep.gs_raster_bwd(self.plan, self.ws, self.image, self.dl, stream)
-        adam = gsstep.make_adam(self.lr, step=step)
+        adam = gsstep.make_adam(self.lr, step=step, seed=self.seed)
         gsstep.gs_project_bwd_adam(self.plan, self.ws, self.scenes, self.cams, adam, None, stream)
         if step <= 0:
             gsstep.gs_adam_advance(self.plan, self.ws, stream)
@@ -223,6 +224,40 @@ class Trainer:
     def reset_opacity(self, value: float = 0.01):
         for sb in self.scenes:
             gsstep.gs_reset_opacity(sb, sb.storage_flags, value)
+
+    # -- checkpoints -----------------------------------------------------------
+    def state_dict(self) -> dict:
+        """Parameters, both Adam moments, densification statistics (when
+        kept) and the Adam step counter, as host tensors.  Every kernel of the
+        step is deterministic and the BF16 rounding is keyed by (seed, step,
+        Gaussian), so training resumed from a checkpoint repeats the
+        uninterrupted run bit for bit."""
+        scenes = []
+        for sb in self.scenes:
+            d = {"n": sb.n, "geom": sb.geom.cpu(), "sh": sb.sh.cpu(), "m": sb.m.cpu(), "v": sb.v.cpu()}
+            if sb.stats is not None:
+                d["stats"] = sb.stats.cpu()
+            scenes.append(d)
+        return {"scenes": scenes, "step": int(self.stats().step), "seed": self.seed, "lr": list(self.lr)}
+
+    def load_state_dict(self, state: dict):
+        """Restore a checkpoint of a trainer with the same views and scene
+        sizes (re-plans when the sizes differ, e.g. after densification)."""
+        self.seed = int(state["seed"])
+        self.lr = tuple(state["lr"])
+        new = []
+        for d in state["scenes"]:
+            sb = SceneBuffers(int(d["n"]), d["geom"].to(self.device), d["sh"].to(self.device),
+                              d["m"].to(self.device), d["v"].to(self.device),
+                              d["stats"].to(self.device) if "stats" in d else None)
+            new.append(sb)
+        same = [s.n for s in new] == [s.n for s in self.scenes]
+        self.scenes = new
+        if same:
+            gsstep.gs_workspace_set_step(self.plan, self.ws, int(state["step"]))
+            self.graph = None
+        else:
+            self._replan(int(state["step"]))
 
     def _replan(self, step: int):
         p = self.plan
