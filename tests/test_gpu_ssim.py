@@ -126,3 +126,19 @@ def test_trainer_step_with_ssim_loss(gs, orc):
     tie = np.abs(img.astype(np.float64) - orc.rgba8_to_float(t8)) < 1e-6
     assert np.abs(np.where(tie, 0.0, got - ref_g[0])).max() <= 1e-3 * np.abs(ref_g[0]).max()
     assert torch.isfinite(tr.scenes[0].geom).all() and torch.isfinite(tr.scenes[0].sh).all()
+
+
+def test_l1_ssim_full_size_four_views(gs, orc):
+    """The batched workload's size: four 1920x1080 views (smooth images with
+    flat regions), loss and every pixel's gradient against the oracle."""
+    gsstep, _ = gs
+    shapes = [(1920, 1080)] * 4
+    imgs, tgts = synth.loss_images(shapes, seed=21, smooth=True)
+    plan, ws = _plan(gsstep, shapes)
+    loss, dl = _run(gsstep, plan, ws, _flat(imgs, 3), _flat(tgts, 4), 0.2)
+    ref_loss, ref_g = orc.l1_ssim_loss_grad(imgs, [orc.rgba8_to_float(t) for t in tgts], 0.2)
+    assert abs(loss - ref_loss) <= 1e-5 * abs(ref_loss), (loss, ref_loss)
+    for got, ref, img, t in zip(_split(dl, shapes), ref_g, imgs, tgts):
+        tie = np.abs(img.astype(np.float64) - orc.rgba8_to_float(t)) < 1e-6
+        err = np.where(tie, 0.0, np.abs(got - ref))
+        assert err.max() <= 1e-3 * np.abs(ref).max(), err.max() / np.abs(ref).max()
