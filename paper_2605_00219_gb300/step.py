@@ -116,6 +116,7 @@ class Trainer:
         self.view_shapes = [(c.width, c.height) for c in cameras]
         self.lr = tuple(lr)
         self.graph = None
+        self._pair = None
         gsstep.gs_workspace_init(self.plan, self.ws)
 
     # -- inputs -------------------------------------------------------------
@@ -187,6 +188,52 @@ class Trainer:
     def replay(self):
         self.graph.replay()
 
+    def capture_pair(self):
+        """Two graphs of the step reading targets and cameras from two
+        buffer sets, so that the host copy of one step's inputs can overlap
+        the previous step (see run_from_host)."""
+        t2, c2 = torch.empty_like(self.target), torch.empty_like(self.cams)
+        ga = self.capture()
+        self.target, t2 = t2, self.target
+        self.cams, c2 = c2, self.cams
+        gb = self.capture()
+        bufs_b = (self.target, self.cams)
+        self.target, self.cams = t2, c2
+        self._pair = ((ga, (self.target, self.cams)), (gb, bufs_b))
+        self.graph = ga
+
+    def run_from_host(self, host_target, host_cams, steps: int):
+        """`steps` graph-replayed steps whose inputs come from host memory:
+        step k's targets and cameras (host_target(k), host_cams(k): pinned CPU
+        tensors) are copied on a side stream while step k - 1 runs, and each
+        step's statistics are read back after it.  Returns the losses."""
+        if getattr(self, "_pair", None) is None:
+            self.capture_pair()
+        main = torch.cuda.current_stream(self.device)
+        side = torch.cuda.Stream(device=self.device)
+        copied = [torch.cuda.Event(), torch.cuda.Event()]
+        free = [torch.cuda.Event(), torch.cuda.Event()]
+
+        def issue(k):
+            _, (tb, cb) = self._pair[k % 2]
+            with torch.cuda.stream(side):
+                if k >= 2:
+                    side.wait_event(free[k % 2])
+                tb.copy_(host_target(k), non_blocking=True)
+                cb.copy_(host_cams(k), non_blocking=True)
+                copied[k % 2].record(side)
+
+        losses = []
+        issue(0)
+        for k in range(steps):
+            if k + 1 < steps:
+                issue(k + 1)
+            main.wait_event(copied[k % 2])
+            self._pair[k % 2][0].replay()
+            free[k % 2].record(main)
+            losses.append(float(self.stats().loss))
+        return losses
+
     def stats(self) -> gsstep.gs_stats:
         return gsstep.gs_read_stats(self.plan, self.ws)
 
@@ -200,6 +247,7 @@ class Trainer:
             if sb.stats is None:
                 sb.stats = torch.zeros((sb.n, 2), dtype=torch.float32, device=self.device)
         self.graph = None
+        self._pair = None
 
     def densify(self, scene_scale, generator=None, **cfg):
         """One refinement of the default strategy on every scene (clone /
@@ -256,6 +304,7 @@ class Trainer:
         if same:
             gsstep.gs_workspace_set_step(self.plan, self.ws, int(state["step"]))
             self.graph = None
+            self._pair = None
         else:
             self._replan(int(state["step"]))
 
@@ -267,3 +316,4 @@ class Trainer:
         gsstep.gs_workspace_init(self.plan, self.ws)
         gsstep.gs_workspace_set_step(self.plan, self.ws, step)
         self.graph = None
+        self._pair = None

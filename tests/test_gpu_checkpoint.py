@@ -85,3 +85,24 @@ def test_resume_after_densification(step_mod):
     _run(resumed, 3)
     assert resumed.stats().step == full.stats().step == 8
     _same(full, resumed)
+
+
+def test_host_fed_replays_equal_device_steps(step_mod):
+    """run_from_host (two graphs over two input buffer sets, host copies
+    overlapping the previous step) computes the same steps as plain graph
+    replays with the inputs already on the device."""
+    scene = synth.cluster_scene(20000, 8, 2.5, seed=5, log_scale=(-3.0, 0.6), logit_opacity=(-0.5, 1.5))
+    cams = synth.orbit_cameras(2, 5.0, 160, 120, hfov_deg=55.0)
+    g = torch.Generator(device="cuda").manual_seed(3)
+    target = torch.rand((sum(c.width * c.height for c in cams), 3), device="cuda", generator=g)
+    a = _trainer(step_mod, scene, cams, target)
+    a.capture()
+    for _ in range(5):
+        a.replay()
+    torch.cuda.synchronize()
+    b = _trainer(step_mod, scene, cams, target)
+    host_t = target.cpu().pin_memory()
+    host_c = b.cams.cpu().pin_memory()
+    losses = b.run_from_host(lambda k: host_t, lambda k: host_c, 5)
+    assert len(losses) == 5 and b.stats().step == a.stats().step == 5
+    _same(a, b)
