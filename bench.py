@@ -468,6 +468,14 @@ def main():
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     alu_peak = sm_count * 128 * 2 * 2.070e9 / 1e12
     FLOP_BWD, FLOP_FWD = 90.0, 28.0   # FP32 FLOP (FMA = 2) per evaluated pair
+    # sort: count scan (4 B in, 4 B out per pair), emission (8 B written per
+    # intersection, 32 B of records read per emitting pair), per radix pass
+    # 4 B read (histogram) + 8 B read + 8 B written per intersection, and the
+    # last pass's gather of the pair index (4 B read + 4 B written)
+    pairs = n * len(cams) if not multi else sum(scenes[c.scene].n for c in cams)
+    npass = 4 + (1 if len(cams) > 1 else 0)
+    sort_bytes = pairs * 8 + K * 8 + pairs * 32 + npass * K * 20 + K * 8
+    loss_bytes = px * 3 * 12          # image, target, gradient (FP32)
     rooflines = {
         "project_bwd_adam": {"bound": "hbm", "achieved": adam_bytes / (acc["project_bwd_adam"] * 1e-3) / 1e9,
                              "peak": hbm_peak, "unit": "GB/s", "traffic": None},
@@ -477,6 +485,10 @@ def main():
                        "peak": alu_peak, "unit": "TFLOP/s", "traffic": None},
         "raster_fwd": {"bound": "alu", "achieved": evaluated * FLOP_FWD / (acc["raster_fwd"] * 1e-3) / 1e12,
                        "peak": alu_peak, "unit": "TFLOP/s", "traffic": None},
+        "bin_sort": {"bound": "hbm", "achieved": sort_bytes / (acc["bin_sort"] * 1e-3) / 1e9, "peak": hbm_peak,
+                     "unit": "GB/s", "traffic": None},
+        "loss_l1": {"bound": "hbm", "achieved": loss_bytes / (acc["loss_l1"] * 1e-3) / 1e9, "peak": hbm_peak,
+                    "unit": "GB/s", "traffic": None},
     }
     headline = args.workload == "batched" and args.n == N_GAUSS and tuple(tile) == (16, 16) and impl == 0
     for k, r in rooflines.items():
