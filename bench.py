@@ -98,6 +98,9 @@ def _args():
     ap.add_argument("--bwd-impl", type=int, default=None, choices=[0, 1, 2],
                     help="fix the raster-backward implementation instead of autotuning")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison")
+    ap.add_argument("--fp32", action="store_true",
+                    help="FP32 storage for the batched form too (the batched-and-autotuned configuration with "
+                         "--workload uneven)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--cpu-sample-tiles", type=int, default=16,
                     help="oracle renders 1 in this many tiles (bounded CPU sample)")
@@ -378,13 +381,13 @@ def main():
         del plain
 
     # ---- the measured form
-    sh16 = batched
+    sh16 = batched and not args.fp32
     all_bufs = [stepmod.SceneBuffers.from_scene(sc, sh_bf16=sh16, mom_bf16=sh16) for sc in scenes]
     bufs = all_bufs[0]
     fixed = args.tile is not None or args.bwd_impl is not None
     if batched and not fixed:
-        best, tuner, trainers = autotune.tune_trainer([bufs], cams, rounds=args.tune_rounds, lr=LR, sh_bf16=True,
-                                                      mom_bf16=True, target=targets)
+        best, tuner, trainers = autotune.tune_trainer([bufs], cams, rounds=args.tune_rounds, lr=LR, sh_bf16=sh16,
+                                                      mom_bf16=sh16, target=targets)
         tr = trainers[best]
         for c, t in list(trainers.items()):
             if c != best:
@@ -518,7 +521,7 @@ def main():
         value = whole_job_rate(ws, nviews, ms)
         desc = ("multi-scene BF16: 8 scenes of " + "/".join(f"{sc.n / 1e6:.3g}" for sc in scenes) +
                 f"M Gaussians ({n / 1e6:.3g}M in all), views per step " if multi else
-                ("batched BF16: " if batched else "plain FP32: ") +
+                (("batched BF16: " if sh16 else "batched FP32: ") if batched else "plain FP32: ") +
                 f"{n / 1e6:.3g}M Gaussians (256 clusters, 30 m box), views per step ") + \
                "+".join(f"{c.width}x{c.height}" for c in cams) + \
                (", BF16 SH and Adam moments (FP32 math)" if sh16 else ", FP32 storage") + \
