@@ -106,3 +106,29 @@ def test_fullsize_four_view_batch_keys(big, orc):
         np.testing.assert_array_equal(keys[o:o + b.K], b.keys)
         np.testing.assert_array_equal(pids[o:o + b.K], b.gidx + v * scene.n)
         o += b.K
+
+
+def test_fullsize_uneven_batch_500_fp32_steps(big):
+    """The batched configuration's own form: four views of uneven resolution
+    (1920x1080, 1600x1064, 1280x720, 960x540), FP32 storage, 500
+    graph-replayed steps: status clear, loss falls, parameters finite."""
+    gsstep, step, scene = big
+    cams = synth.large_views(4)
+    tscene = synth.perturbed(scene, 1)
+    t = step.Trainer([tscene], cams, lr=(1e-3,) * 6)
+    t.forward()
+    torch.cuda.synchronize()
+    target = t.image.clone()
+    del t
+    tr = step.Trainer([scene], cams, lr=(1.6e-4 * 30.0, 1e-3, 5e-3, 5e-2, 2.5e-3, 2.5e-3 / 20))
+    tr.target.copy_(target)
+    tr.step(0)
+    first = float(tr.stats().loss)
+    tr.capture()
+    for _ in range(499):
+        tr.replay()
+    torch.cuda.synchronize()
+    st = tr.stats()
+    assert st.status == 0 and st.step == 500
+    assert float(st.loss) < 0.5 * first
+    assert bool(torch.isfinite(tr.scenes[0].geom).all()) and bool(torch.isfinite(tr.scenes[0].sh).all())
