@@ -554,6 +554,12 @@ def main():
             "blended_pairs_per_s": blended * 1e3 / ms,
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
+            "memory_gib": {
+                "workspace": tr.ws.numel() / 2 ** 30,
+                "scene_buffers": sum(t.numel() * t.element_size() for sb in tr.scenes
+                                     for t in (sb.geom, sb.sh, sb.m, sb.v) if t is not None) / 2 ** 30,
+                "images_targets_gradients": 3 * tr.image.numel() * 4 / 2 ** 30,
+            },
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
