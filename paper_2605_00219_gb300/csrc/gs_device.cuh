@@ -421,6 +421,26 @@ __device__ __forceinline__ void accurate_mean2d(const float* cam, float4 mu, flo
     }
 }
 
+// Transmittance before a list entry from the one after it, as a compensated
+// FP32 pair (Th + Tl) / (1 - alpha): 1 - alpha is split exactly into
+// om + om_err (Fast2Sum, 1 >= alpha), the quotient q = Th r uses the hardware
+// reciprocal r, the remainder Th - q om is exact (one FMA), and the low part
+// (remainder + Tl - q om_err) r carries what q misses, so the pair stays close
+// to the exact quotient through hundreds of divisions.  Returns r.
+__device__ __forceinline__ float div_one_minus(float alpha, float& Th, float& Tl)
+{
+    const float om = __fsub_rn(1.0f, alpha);
+    const float om_err = __fsub_rn(-alpha, __fsub_rn(om, 1.0f));
+    const float r = __fdividef(1.0f, om);
+    const float q = __fmul_rn(Th, r);
+    const float rem = __fmaf_rn(-q, om, Th);
+    const float lo = (rem + Tl - q * om_err) * r;
+    const float hi = q + lo;
+    Tl = lo - (hi - q);
+    Th = hi;
+    return r;
+}
+
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTMin = 1e-4f;

@@ -334,10 +334,9 @@ void launch_raster_bwd(const Plan& P, const WsPtrs& w, const float* image, const
 // One CTA per tile, one thread per pixel, each warp an 8x4 pixel block (so a
 // small Gaussian touches few warps).  Every pixel walks its own list prefix
 // back to front from its last blended entry: T before an entry is recovered
-// as T after it times the hardware reciprocal of (1 - alpha) (about 2 ulp of
-// relative error per entry, so a few 1e-5 after hundreds of entries, far
-// inside the gradient tolerance), and the colour still to come S grows from
-// T_final * bg without cancellation.  The list is
+// by a compensated division of T after it by (1 - alpha) (div_one_minus:
+// hardware reciprocal, exact remainder, carried low part), and the colour
+// still to come S grows from T_final * bg without cancellation.  The list is
 // staged BB entries at a time with a mask of the warp blocks each entry's
 // 3-sigma box touches; a warp visits only its entries, and for an entry that
 // at least one of its pixels blended it sums the nine gradients over its 32
@@ -427,7 +426,7 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint2* __re
     const int vi = bfly_index(lane);
 
     uint32_t nl = 0;
-    float Th = 1.f, d0 = 0.f, d1 = 0.f, d2 = 0.f;
+    float Th = 1.f, Tl = 0.f, d0 = 0.f, d1 = 0.f, d2 = 0.f;
     if (inside) {
         const int64_t pix = vd.pix_base + (int64_t)py * vd.W + px;
         nl = nlast[pix];
@@ -514,9 +513,8 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint2* __re
                             hit = true;
                             const float4 cd = cD[j];
                             const float cb = cd.w;
-                            // T before this entry = T after it / (1 - alpha)
-                            const float rom = __fdividef(1.0f, 1.0f - alpha);
-                            Th *= rom;
+                            // compensated T before this entry
+                            const float rom = div_one_minus(alpha, Th, Tl);
                             const float wgt = alpha * Th;
                             g[6] = wgt * d0;
                             g[7] = wgt * d1;

@@ -11,8 +11,8 @@
 // (Gaussian, block) pair is one unit of work.  A staged chunk is cut from its
 // back into sub-batches of at most NP pairs:
 //   phase 1 (pixels): each warp walks its entries of the sub-batch back to
-//     front, continuing its pixels' state (T recovered by division by
-//     1 - alpha, colour still to come S), and stores per pixel the blend
+//     front, continuing its pixels' state (T recovered by a compensated
+//     division by 1 - alpha, colour still to come S), and stores per pixel the blend
 //     weight w = alpha T and A = dL/dalpha * G (zero where the 0.99 clamp
 //     holds) at [pixel][pair] (odd row stride: no bank conflicts);
 //   phase 2 (pairs): TPP threads per pair each sum PPT pixels of the pair's
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(BS) k_raster_bwd2(Views V, const uint2* __rest
     const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
 
     uint32_t nl = 0;
-    float Th = 1.f, d0 = 0.f, d1 = 0.f, d2 = 0.f;
+    float Th = 1.f, Tl = 0.f, d0 = 0.f, d1 = 0.f, d2 = 0.f;
     if (inside) {
         const int64_t pix = vd.pix_base + (int64_t)py * vd.W + px;
         nl = nlast[pix];
@@ -212,9 +212,8 @@ __global__ void __launch_bounds__(BS) k_raster_bwd2(Views V, const uint2* __rest
                             const float alpha = fminf(kAlphaMax, araw);
                             if (alpha >= kAlphaMin) {
                                 const float cb = cD[j].w;
-                                // T before this entry = T after it / (1 - alpha)
-                                const float rom = __fdividef(1.0f, 1.0f - alpha);
-                                Th *= rom;
+                                // compensated T before this entry
+                                const float rom = div_one_minus(alpha, Th, Tl);
                                 wv = alpha * Th;
                                 float da = d0 * fmaf(b.z, Th, -S0 * rom);
                                 da = fmaf(d1, fmaf(b.w, Th, -S1 * rom), da);
