@@ -397,6 +397,38 @@ __global__ void __launch_bounds__(256) k_ranges(Views V, const uint32_t* __restr
     }
 }
 
+// Launch order of the raster kernels: tiles by decreasing list length,
+// bucketed by floor(log2(length + 1)).  Blocks are dispatched roughly in
+// index order, so the longest tiles start first and the short ones fill the
+// tail (longest-processing-time scheduling).  Within a bucket the order
+// follows shared-memory atomics; it decides only when a tile runs, never its
+// result.
+__global__ void __launch_bounds__(1024) k_tile_order(int64_t tiles, const uint2* __restrict__ ranges,
+                                                     uint32_t* __restrict__ order)
+{
+    __shared__ uint32_t cnt[32];
+    if (threadIdx.x < 32) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (int64_t t = threadIdx.x; t < tiles; t += blockDim.x) {
+        const uint2 r = ranges[t];
+        atomicAdd(&cnt[31 - __clz(r.y - r.x + 1u)], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int b = 31; b >= 0; b--) {
+            const uint32_t c = cnt[b];
+            cnt[b] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (int64_t t = threadIdx.x; t < tiles; t += blockDim.x) {
+        const uint2 r = ranges[t];
+        order[atomicAdd(&cnt[31 - __clz(r.y - r.x + 1u)], 1u)] = (uint32_t)t;
+    }
+}
+
 // ---------------------------------------------------------------------------
 
 void launch_bin_sort(const Plan& P, const WsPtrs& w, cudaStream_t st)
@@ -453,6 +485,7 @@ void launch_bin_sort(const Plan& P, const WsPtrs& w, cudaStream_t st)
         if (blocks < 1) blocks = 1;
         k_ranges<<<(unsigned)blocks, 256, 0, st>>>(V, w.keys_sorted, w.hdr, w.ranges, cap);
     }
+    k_tile_order<<<1, 1024, 0, st>>>(V.tiles, w.ranges, w.tile_order);
 }
 
 }  // namespace gs

@@ -35,6 +35,7 @@ WsPtrs carve(const Plan& P, void* ws)
     w.pid = reinterpret_cast<uint32_t*>(b + P.off_pid);
     w.pid_sorted = reinterpret_cast<uint32_t*>(b + P.off_pid_sorted);
     w.ranges = reinterpret_cast<uint2*>(b + P.off_ranges);
+    w.tile_order = reinterpret_cast<uint32_t*>(b + P.off_order);
     w.nlast = reinterpret_cast<uint32_t*>(b + P.off_nlast);
     w.tfinal = reinterpret_cast<float*>(b + P.off_tfinal);
     w.gradrec = reinterpret_cast<GradRec*>(b + P.off_gradrec);
@@ -144,6 +145,7 @@ static bool plan_build(Plan& P, const int64_t* scene_n, int32_t n_scenes, const 
     P.off_pid = take(4 * (size_t)cap);
     P.off_pid_sorted = take(4 * (size_t)cap);
     P.off_ranges = take(8 * (size_t)tiles);
+    P.off_order = take(4 * (size_t)tiles);
     P.off_nlast = take(4 * (size_t)pixels);
     P.off_tfinal = take(4 * (size_t)pixels);
     P.off_gradrec = take(sizeof(GradRec) * (size_t)cap);

@@ -41,7 +41,7 @@ struct Plan {
     // workspace byte offsets
     size_t off_hdr, off_count, off_offset, off_rec, off_binrec;
     size_t off_keysA, off_valsA, off_keysB, off_valsB, off_pid, off_pid_sorted;
-    size_t off_ranges, off_nlast, off_tfinal, off_gradrec, off_scan_part, off_hist, off_loss_part;
+    size_t off_ranges, off_nlast, off_tfinal, off_gradrec, off_scan_part, off_hist, off_loss_part, off_order;
     size_t ws_bytes;
 };
 
@@ -55,6 +55,7 @@ struct WsPtrs {
     uint32_t* pid;
     uint32_t* pid_sorted;
     uint2* ranges;
+    uint32_t* tile_order;      // tiles by decreasing list length (raster launch order)
     uint32_t* nlast;
     float* tfinal;
     GradRec* gradrec;

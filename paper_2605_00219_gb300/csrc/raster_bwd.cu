@@ -54,7 +54,8 @@ __device__ __forceinline__ void neumaier_add(float& s, float& c, float x)
 }
 
 template <int P>
-__global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(Views V, const uint2* __restrict__ ranges,
+__global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(Views V, const uint32_t* __restrict__ order,
+                                                            const uint2* __restrict__ ranges,
                                                             const uint32_t* __restrict__ vals_sorted,
                                                             const uint32_t* __restrict__ pid_sorted,
                                                             const ProjRec* __restrict__ rec,
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(Views V, const uint2
     sm.misc = reinterpret_cast<int*>(sm.red + 128 * 9);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t gt = blockIdx.x;
+    const int64_t gt = order[blockIdx.x];   // longest lists first
     const int v = view_of_tile(V, gt);
     const ViewDesc& vd = V.v[v];
     const int lt = (int)(gt - vd.tile_base);
@@ -316,7 +317,7 @@ void launch_raster_bwd(const Plan& P, const WsPtrs& w, const float* image, const
             cudaFuncSetAttribute(k_raster_bwd<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);   \
             attr_set = true;                                                                                \
         }                                                                                                   \
-        k_raster_bwd<NP><<<grid, kBwdThreads, sb, st>>>(V, w.ranges, w.vals_sorted, w.pid_sorted, w.rec, image, \
+        k_raster_bwd<NP><<<grid, kBwdThreads, sb, st>>>(V, w.tile_order, w.ranges, w.vals_sorted, w.pid_sorted, w.rec, image, \
                                                         dl, w.nlast, w.gradrec, fixed);                     \
     } while (0)
     if (np == 64) GS_RB(64);
@@ -387,7 +388,8 @@ __device__ __forceinline__ int bfly_index(int lane)
 }
 
 template <int BS, int TW>
-__global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint2* __restrict__ ranges,
+__global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* __restrict__ order,
+                                                      const uint2* __restrict__ ranges,
                                                       const uint32_t* __restrict__ vals_sorted,
                                                       const uint32_t* __restrict__ pid_sorted,
                                                       const ProjRec* __restrict__ rec,
@@ -412,7 +414,7 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint2* __re
     __shared__ int smax[NW];
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int64_t gt = blockIdx.x;
+    const int64_t gt = order[blockIdx.x];   // longest lists first
     const int v = view_of_tile(V, gt);
     const ViewDesc& vd = V.v[v];
     const int lt = (int)(gt - vd.tile_base);
@@ -576,7 +578,7 @@ void launch_raster_bwd_px(const Plan& P, const WsPtrs& w, const float* bg, const
 {
     const Views& V = P.views;
     const unsigned grid = (unsigned)V.tiles;
-#define GS_RBP(BS, TW) k_raster_bwd_px<BS, TW><<<grid, BS, 0, st>>>(V, w.ranges, w.vals_sorted, w.pid_sorted, \
+#define GS_RBP(BS, TW) k_raster_bwd_px<BS, TW><<<grid, BS, 0, st>>>(V, w.tile_order, w.ranges, w.vals_sorted, w.pid_sorted, \
                                                                    w.rec, w.tfinal, bg, dl, w.nlast, w.gradrec)
     if (V.tw == 8) GS_RBP(64, 8);
     else if (V.th == 16) GS_RBP(256, 16);

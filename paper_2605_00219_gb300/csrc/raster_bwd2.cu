@@ -93,7 +93,8 @@ __device__ __forceinline__ int bwd2_sub_lo(const int* __restrict__ pbase, int hi
 }
 
 template <int BS, int TW>
-__global__ void __launch_bounds__(BS) k_raster_bwd2(Views V, const uint2* __restrict__ ranges,
+__global__ void __launch_bounds__(BS) k_raster_bwd2(Views V, const uint32_t* __restrict__ order,
+                                                    const uint2* __restrict__ ranges,
                                                     const uint32_t* __restrict__ vals_sorted,
                                                     const uint32_t* __restrict__ pid_sorted,
                                                     const ProjRec* __restrict__ rec,
@@ -111,7 +112,7 @@ __global__ void __launch_bounds__(BS) k_raster_bwd2(Views V, const uint2* __rest
     Bwd2Smem<BS>& S = *reinterpret_cast<Bwd2Smem<BS>*>(bwd2_raw);
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int64_t gt = blockIdx.x;
+    const int64_t gt = order[blockIdx.x];   // longest lists first
     const int v = view_of_tile(V, gt);
     const ViewDesc& vd = V.v[v];
     const int lt = (int)(gt - vd.tile_base);
@@ -310,7 +311,7 @@ void launch_raster_bwd2(const Plan& P, const WsPtrs& w, const float* bg, const f
             cudaFuncSetAttribute(k_raster_bwd2<BS, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb); \
             attr_set = true;                                                                                  \
         }                                                                                                     \
-        k_raster_bwd2<BS, TW><<<grid, BS, sb, st>>>(V, w.ranges, w.vals_sorted, w.pid_sorted, w.rec, w.tfinal, \
+        k_raster_bwd2<BS, TW><<<grid, BS, sb, st>>>(V, w.tile_order, w.ranges, w.vals_sorted, w.pid_sorted, w.rec, w.tfinal, \
                                                      bg, dl, w.nlast, w.gradrec);                             \
     } while (0)
     if (V.tw == 8) GS_RB2(64, 8);

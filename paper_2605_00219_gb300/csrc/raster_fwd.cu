@@ -18,7 +18,8 @@ namespace gs {
 // more resident warps hide the chunk barriers (2.23 -> 2.01 ms at 3M Gaussians,
 // 4x1080p; 7 CTAs spill and lose)
 template <int BS, int TW>
-__global__ void __launch_bounds__(BS, (BS == 256 ? 6 : 1)) k_raster_fwd(Views V, const uint2* __restrict__ ranges,
+__global__ void __launch_bounds__(BS, (BS == 256 ? 6 : 1)) k_raster_fwd(Views V, const uint32_t* __restrict__ order,
+                                                                       const uint2* __restrict__ ranges,
                                                    const uint32_t* __restrict__ pid_sorted,
                                                    const ProjRec* __restrict__ rec, const float* __restrict__ bg,
                                                    float* __restrict__ image, float* __restrict__ tfinal,
@@ -33,7 +34,7 @@ __global__ void __launch_bounds__(BS, (BS == 256 ? 6 : 1)) k_raster_fwd(Views V,
     constexpr int WPR = TW / 8, RPB = BS / TW / 4;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t wbit = 1u << w;
-    const int64_t gt = blockIdx.x;
+    const int64_t gt = order[blockIdx.x];   // longest lists first
     const int v = view_of_tile(V, gt);
     const ViewDesc& vd = V.v[v];
     const int lt = (int)(gt - vd.tile_base);
@@ -144,7 +145,7 @@ void launch_raster_fwd(const Plan& P, const WsPtrs& w, const float* bg, float* i
     const Views& V = P.views;
     const int bs = V.tw * V.th;
     const unsigned grid = (unsigned)V.tiles;
-#define GS_RF(BS, TW) k_raster_fwd<BS, TW><<<grid, BS, 0, st>>>(V, w.ranges, w.pid_sorted, w.rec, bg, image, \
+#define GS_RF(BS, TW) k_raster_fwd<BS, TW><<<grid, BS, 0, st>>>(V, w.tile_order, w.ranges, w.pid_sorted, w.rec, bg, image, \
                                                                 w.tfinal, w.nlast, w.hdr)
     if (bs == 64) GS_RF(64, 8);
     else if (bs == 256) GS_RF(256, 16);
