@@ -426,7 +426,9 @@ __device__ __forceinline__ void accurate_mean2d(const float* cam, float4 mu, flo
 // om + om_err (Fast2Sum, 1 >= alpha), the quotient q = Th r uses the hardware
 // reciprocal r, the remainder Th - q om is exact (one FMA), and the low part
 // (remainder + Tl - q om_err) r carries what q misses, so the pair stays close
-// to the exact quotient through hundreds of divisions.  Returns r.
+// to the exact quotient through hundreds of divisions.  The pair is not
+// renormalised: Th is always the last quotient and Tl stays near its ulp,
+// since each step's remainder is at most about an ulp of Th.  Returns r.
 __device__ __forceinline__ float div_one_minus(float alpha, float& Th, float& Tl)
 {
     const float om = __fsub_rn(1.0f, alpha);
@@ -434,10 +436,8 @@ __device__ __forceinline__ float div_one_minus(float alpha, float& Th, float& Tl
     const float r = __fdividef(1.0f, om);
     const float q = __fmul_rn(Th, r);
     const float rem = __fmaf_rn(-q, om, Th);
-    const float lo = (rem + Tl - q * om_err) * r;
-    const float hi = q + lo;
-    Tl = lo - (hi - q);
-    Th = hi;
+    Tl = __fmul_rn(__fmaf_rn(-q, om_err, __fadd_rn(rem, Tl)), r);
+    Th = q;
     return r;
 }
 
