@@ -8,7 +8,7 @@
 // gathers); with each entry the loader stores a mask of the warp blocks its
 // 3-sigma box touches, and each warp walks only its entries (ballot over 32
 // entries, then the set bits in order).  Transmittance is a compensated FP32 pair
-// (TwoProduct with fmaf, Fast2Sum renormalisation), so the product over
+// (TwoProduct with fmaf, the low part carried alongside), so the product over
 // hundreds of factors keeps close to full FP32 accuracy.
 #include "gs_internal.cuh"
 
@@ -86,14 +86,15 @@ __global__ void __launch_bounds__(BS, (BS == 256 ? 6 : 1)) k_raster_fwd(Views V,
                 const float G = ex2_approx(p2);
                 const float alpha = fminf(kAlphaMax, __fmul_rn(b.y, G));
                 if (alpha < kAlphaMin) continue;
-                // compensated T * (1 - alpha)
+                // compensated T * (1 - alpha); the pair is carried without
+                // renormalising (Th the rounded product, Tl its low part),
+                // and the stop test takes their sum
                 const float om = __fsub_rn(1.0f, alpha);
                 const float om_err = __fsub_rn(-alpha, __fsub_rn(om, 1.0f));
                 const float pr = __fmul_rn(Th, om);
                 const float pe = __fmaf_rn(Th, om, -pr);
                 const float lo = __fmaf_rn(Th, om_err, __fmaf_rn(Tl, om, pe));
-                const float hi = __fadd_rn(pr, lo);
-                if (hi < kTMin) {
+                if (__fadd_rn(pr, lo) < kTMin) {
                     done = 1;
                     break;
                 }
@@ -101,8 +102,8 @@ __global__ void __launch_bounds__(BS, (BS == 256 ? 6 : 1)) k_raster_fwd(Views V,
                 C0 = fmaf(b.z, wgt, C0);
                 C1 = fmaf(b.w, wgt, C1);
                 C2 = fmaf(cl.x, wgt, C2);
-                Tl = __fsub_rn(lo, __fsub_rn(hi, pr));
-                Th = hi;
+                Tl = lo;
+                Th = pr;
                 last = base - r.x + j + 1;
                 nbl++;
             }
