@@ -490,8 +490,10 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
             }
         }
         for (int c = (cnt - 1) >> 5; c >= 0; c--) {
-            // entries of this chunk whose 3-sigma box touches this warp's block
-            uint32_t bits = __ballot_sync(0xffffffffu, 32 * c + lane < cnt && (cM[32 * c + lane] & wbit));
+            // entries of this chunk whose 3-sigma box touches this warp's block,
+            // before the last pair any of the warp's pixels blended
+            const int jl = 32 * c + lane;
+            uint32_t bits = __ballot_sync(0xffffffffu, jl < cnt && bb + jl < mx_nl && (cM[jl] & wbit));
             uint32_t done_bits = 0;
             while (bits) {
                 const int jj = 31 - __clz(bits);

@@ -145,20 +145,28 @@ __global__ void __launch_bounds__(BS) k_raster_bwd2(Views V, const uint32_t* __r
     for (int i = 0; i < NW; i++) L = max(L, S.smax[i]);
     L = min(L, (int)(r.y - r.x));
 
-    auto stage = [&](int buf, int i, const ProjRec& q, uint32_t e) {
+    // warps whose pixels blended past list position pos (a pair is only
+    // formed for those)
+    auto live = [&](int pos) {
+        uint32_t m = 0;
+#pragma unroll
+        for (int i = 0; i < NW; i++) m |= (pos < S.smax[i] ? 1u : 0u) << i;
+        return m;
+    };
+    auto stage = [&](int buf, int i, int pos, const ProjRec& q, uint32_t e) {
         S.sA[buf][i] = pair_coefs(q.a.x, q.a.y, q.a.z, q.a.w, q.b.x);
         S.sB[buf][i] = make_float4(pair_c2(q.b.x), q.b.y, q.b.z, q.b.w);
         S.sD[buf][i] = make_float4(q.a.z, q.a.w, q.b.x, q.c.x);
         S.sL[buf][i] = make_float2(q.c.z, q.c.w);
         S.sE[buf][i] = e;
-        S.sM[buf][i] = warp_block_mask(q.a.x, q.a.y, q.a.z, q.a.w, q.b.x, q.b.y, ox, oy, WPR, RPB);
+        S.sM[buf][i] = warp_block_mask(q.a.x, q.a.y, q.a.z, q.a.w, q.b.x, q.b.y, ox, oy, WPR, RPB) & live(pos);
     };
     int bb = ((L + BB - 1) / BB - 1) * BB;
     if (bb >= 0) {
         const int cnt0 = min(BB, L - bb);
         for (int i = tid; i < cnt0; i += BS) {
             const uint32_t k = r.x + bb + i;
-            stage(0, i, rec[pid_sorted[k]], vals_sorted[k]);
+            stage(0, i, bb + i, rec[pid_sorted[k]], vals_sorted[k]);
         }
     }
     __syncthreads();
@@ -286,7 +294,7 @@ __global__ void __launch_bounds__(BS) k_raster_bwd2(Views V, const uint32_t* __r
 #pragma unroll
             for (int u = 0; u < IPT; u++) {
                 const int i = tid + u * BS;
-                if (i < BB) stage(cur ^ 1, i, qn[u], en[u]);
+                if (i < BB) stage(cur ^ 1, i, bb - BB + i, qn[u], en[u]);
             }
         }
         __syncthreads();
