@@ -310,13 +310,22 @@ __device__ __forceinline__ uint32_t scanline_tiles(const BinGeom& g, int tw, int
 // --------------------------------------------------------------------------
 
 
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Conservative mask of the 8x4-pixel warp blocks of a tile (WPR blocks per
-// row, RPB rows of blocks) that a Gaussian (mean, conic, opacity) can
-// contribute to.  A pair needs d^2 <= 9 and o exp(-d^2/2) >= 1/255, i.e.
-// d^2 <= r^2 = min(9, 2 ln(255 o)); the box of that ellipse, widened by 0.1%
-// and 0.01 px, is intersected with each block.  (ox, oy) is the tile's first
-// pixel.  Pairs in a masked-out block would be skipped by the raster's own
-// tests, so skipping them changes no result.
+// row, RPB rows of blocks; WPR * RPB <= 16) that a Gaussian (mean, conic,
+// opacity) can contribute to.  A pair needs d^2 <= 9 and
+// o exp(-d^2/2) >= 1/255, i.e. d^2 <= r^2 = min(9, 2 ln(255 o)); the
+// half-extents sqrt(r^2 c / det), sqrt(r^2 a / det) of that ellipse, widened
+// by 0.1% of r^2, 1e-5 relative and 0.01 px (which also cover the hardware
+// divide and square root), give a box that is intersected with the blocks.
+// (ox, oy) is the tile's first pixel.  Pairs in a masked-out block would be
+// skipped by the raster's own tests, so skipping them changes no result.
 __device__ __forceinline__ uint32_t warp_block_mask(float mx, float my, float ca, float cb, float cc, float op,
                                                     int ox, int oy, int WPR, int RPB)
 {
@@ -324,20 +333,23 @@ __device__ __forceinline__ uint32_t warp_block_mask(float mx, float my, float ca
     const float det = ca * cc - cb * cb;
     if (!(det > 0.0f)) return 0xffffffffu;
     const float r2 = fminf(9.0f, 2.0f * __logf(op * 255.0f)) * 1.002f + 1e-3f;
-    const float rr = sqrtf(r2);
-    const float ex = fmaf(rr, sqrtf(cc / det), 0.01f);
-    const float ey = fmaf(rr, sqrtf(ca / det), 0.01f);
+    const float s = __fdividef(r2, det);
+    const float ex = fmaf(sqrt_approx(s * cc), 1.00001f, 0.01f);
+    const float ey = fmaf(sqrt_approx(s * ca), 1.00001f, 0.01f);
     // pixel-centre coordinates relative to the tile's first centre
-    const float xl = fminf(fmaxf(mx - ex - ((float)ox + 0.5f), -1e4f), 1e4f);
-    const float xh = fminf(fmaxf(mx + ex - ((float)ox + 0.5f), -1e4f), 1e4f);
-    const float yl = fminf(fmaxf(my - ey - ((float)oy + 0.5f), -1e4f), 1e4f);
-    const float yh = fminf(fmaxf(my + ey - ((float)oy + 0.5f), -1e4f), 1e4f);
+    const float mxr = mx - ((float)ox + 0.5f), myr = my - ((float)oy + 0.5f);
+    const float xl = fminf(fmaxf(mxr - ex, -1e4f), 1e4f);
+    const float xh = fminf(fmaxf(mxr + ex, -1e4f), 1e4f);
+    const float yl = fminf(fmaxf(myr - ey, -1e4f), 1e4f);
+    const float yh = fminf(fmaxf(myr + ey, -1e4f), 1e4f);
     const int bx0 = max(0, (int)ceilf((xl - 7.0f) * 0.125f)), bx1 = min(WPR - 1, (int)floorf(xh * 0.125f));
     const int by0 = max(0, (int)ceilf((yl - 3.0f) * 0.25f)), by1 = min(RPB - 1, (int)floorf(yh * 0.25f));
-    uint32_t m = 0;
-    for (int by = by0; by <= by1; by++)
-        for (int bx = bx0; bx <= bx1; bx++) m |= 1u << (by * WPR + bx);
-    return m;
+    if (bx0 > bx1 || by0 > by1) return 0u;
+    // columns bx0..bx1 of one row, times one bit per row by0..by1
+    uint32_t rows = 0;
+    for (int by = 0; by < RPB; by++) rows |= 1u << (by * WPR);
+    rows &= ~((1u << (by0 * WPR)) - 1u) & ((1u << ((by1 + 1) * WPR)) - 1u);
+    return ((2u << bx1) - (1u << bx0)) * rows;
 }
 
 // Exponent in base 2: power2 = log2(e) * power = dx (A dx + B dy) + C dy^2

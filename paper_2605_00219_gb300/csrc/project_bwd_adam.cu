@@ -37,13 +37,6 @@ struct AdamConst {
     float epsp, b1, b2, omb1, omb2;
 };
 
-__device__ __forceinline__ float sqrt_approx(float x)
-{
-    float y;
-    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
 __device__ __forceinline__ void adam1(float& th, float& m, float& v, float g, float alpha, const AdamConst& K)
 {
     m = fmaf(K.b1, m, K.omb1 * g);
