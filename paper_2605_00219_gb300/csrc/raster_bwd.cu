@@ -340,9 +340,12 @@ void launch_raster_bwd(const Plan& P, const WsPtrs& w, const float* image, const
 // still to come S grows from T_final * bg without cancellation.  The list is
 // staged BB entries at a time with a mask of the warp blocks each entry's
 // 3-sigma box touches; a warp visits only its entries, and for an entry that
-// at least one of its pixels blended it sums the nine gradients over its 32
-// pixels with a halving butterfly (12 shuffles; afterwards nine lanes each
-// hold one fully reduced value) into its own shared-memory slot.  After each
+// at least one of its pixels blended it sums nine values over its 32 pixels
+// with a halving butterfly (12 shuffles; afterwards nine lanes each hold one
+// fully reduced value) into its own shared-memory slot: the opacity and
+// colour gradients and the moments dx dp, dy dp, dx^2 dp, dx dy dp, dy^2 dp
+// of dp = dL/dpower, from which the mean and conic gradients follow per
+// entry (the mean gradient is the conic times the first two).  After each
 // batch the warps' slots are added in warp order and written to each entry's
 // emission slot, so the result does not depend on scheduling.
 // ===========================================================================
@@ -515,8 +518,7 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
                         const float alpha = fminf(kAlphaMax, araw);
                         if (alpha >= kAlphaMin) {
                             hit = true;
-                            const float4 cd = cD[j];
-                            const float cb = cd.w;
+                            const float cb = cD[j].w;
                             // compensated T before this entry
                             const float rom = div_one_minus(alpha, Th, Tl);
                             const float wgt = alpha * Th;
@@ -530,13 +532,16 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
                             S1 = fmaf(b.w, wgt, S1);
                             S2 = fmaf(cb, wgt, S2);
                             if (araw <= kAlphaMax) {
+                                // moments of dp = dL/dpower; the conic and
+                                // the constant factors are applied per entry
+                                // after the reduction
                                 g[5] = da * G;
                                 const float dp = da * araw;
-                                g[2] = -0.5f * dx * dx * dp;
-                                g[3] = -dx * dy * dp;
-                                g[4] = -0.5f * dy * dy * dp;
-                                g[0] = fmaf(cd.x, dx, cd.y * dy) * dp;
-                                g[1] = fmaf(cd.y, dx, cd.z * dy) * dp;
+                                g[0] = dx * dp;
+                                g[1] = dy * dp;
+                                g[2] = dx * g[0];
+                                g[3] = dx * g[1];
+                                g[4] = dy * g[1];
                             }
                         }
                     }
@@ -550,14 +555,28 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
             if (lane == 0) pmask[w][c] = done_bits;
         }
         __syncthreads();
-        // add the warps' partial sums in warp order; write each entry's record
+        // add the warps' partial sums in warp order; write each entry's
+        // record.  Slots 0-4 hold sums of dp (dx, dy, dx^2, dx dy, dy^2):
+        // dL/dmean = conic (sum dx dp, sum dy dp) and dL/dconic =
+        // -(sum dx^2 dp / 2, sum dx dy dp, sum dy^2 dp / 2).
         for (int t = tid; t < cnt * 9; t += BS) {
             const int j = t / 9, comp = t - 9 * j;
-            float s = 0.f;
+            const int comp2 = comp < 2 ? comp ^ 1 : comp;
+            float s = 0.f, s2 = 0.f;
 #pragma unroll
             for (int i = 0; i < NW; i++)
-                if ((pmask[i][j >> 5] >> (j & 31)) & 1u) s += part[i][j][comp];
-            reinterpret_cast<float*>(gradrec + sE[cur][j])[comp] = s;
+                if ((pmask[i][j >> 5] >> (j & 31)) & 1u) {
+                    s += part[i][j][comp];
+                    s2 += part[i][j][comp2];
+                }
+            float out = s;
+            if (comp < 2) {
+                const float4 cd = sD[cur][j];
+                out = comp == 0 ? fmaf(cd.x, s, cd.y * s2) : fmaf(cd.y, s2, cd.z * s);
+            } else if (comp < 5) {
+                out = comp == 3 ? -s : -0.5f * s;
+            }
+            reinterpret_cast<float*>(gradrec + sE[cur][j])[comp] = out;
         }
         if (bb > 0) {
 #pragma unroll

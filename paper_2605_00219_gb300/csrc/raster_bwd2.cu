@@ -254,7 +254,6 @@ __global__ void __launch_bounds__(BS) k_raster_bwd2(Views V, const uint32_t* __r
                     const int j = S.pj[pq], b = S.pb[pq];
                     const float4 a = cA[j];
                     const float2 ml = cL[j];
-                    const float4 cd = cD[j];
                     const float op = cB[j].y;
                     const float bx = (float)(ox + (b % WPR) * 8) + 0.5f, by = (float)(oy + (b / WPR) * 4) + 0.5f;
 #pragma unroll
@@ -268,25 +267,42 @@ __global__ void __launch_bounds__(BS) k_raster_bwd2(Views V, const uint32_t* __r
                         acc[7] = fmaf(wv, dv.y, acc[7]);
                         acc[8] = fmaf(wv, dv.z, acc[8]);
                         acc[5] += av;
+                        // moments of dp = dL/dpower (conic and constant
+                        // factors applied per entry in the combine)
                         const float dp = av * op;
-                        acc[0] = fmaf(fmaf(cd.x, dx, cd.y * dy), dp, acc[0]);
-                        acc[1] = fmaf(fmaf(cd.y, dx, cd.z * dy), dp, acc[1]);
-                        acc[2] = fmaf(-0.5f * dx * dx, dp, acc[2]);
-                        acc[3] = fmaf(-dx * dy, dp, acc[3]);
-                        acc[4] = fmaf(-0.5f * dy * dy, dp, acc[4]);
+                        const float ex = dx * dp, ey = dy * dp;
+                        acc[0] += ex;
+                        acc[1] += ey;
+                        acc[2] = fmaf(dx, ex, acc[2]);
+                        acc[3] = fmaf(dx, ey, acc[3]);
+                        acc[4] = fmaf(dy, ey, acc[4]);
                     }
                 }
 #pragma unroll
                 for (int i = 0; i < 9; i++) S.pr[i][tid] = acc[i];
             }
             __syncthreads();
-            // ---- combine: each entry's pairs in block order (deterministic)
+            // ---- combine: each entry's pairs in block order (deterministic).
+            // Slots 0-4 hold sums of dp (dx, dy, dx^2, dx dy, dy^2):
+            // dL/dmean = conic (sum dx dp, sum dy dp), dL/dconic =
+            // -(sum dx^2 dp / 2, sum dx dy dp, sum dy^2 dp / 2).
             for (int t = tid; t < (hi - lo) * 9; t += BS) {
                 const int e = lo + t / 9, comp = t - 9 * (t / 9);
-                float s = 0.f;
+                const int comp2 = comp < 2 ? comp ^ 1 : comp;
+                float s = 0.f, s2 = 0.f;
                 const int q1 = (S.pbase[e + 1] - p0) * TPP;
-                for (int q = (S.pbase[e] - p0) * TPP; q < q1; q++) s += S.pr[comp][q];
-                reinterpret_cast<float*>(gradrec + S.sE[cur][e])[comp] = s;
+                for (int q = (S.pbase[e] - p0) * TPP; q < q1; q++) {
+                    s += S.pr[comp][q];
+                    s2 += S.pr[comp2][q];
+                }
+                float out = s;
+                if (comp < 2) {
+                    const float4 cd = cD[e];
+                    out = comp == 0 ? fmaf(cd.x, s, cd.y * s2) : fmaf(cd.y, s2, cd.z * s);
+                } else if (comp < 5) {
+                    out = comp == 3 ? -s : -0.5f * s;
+                }
+                reinterpret_cast<float*>(gradrec + S.sE[cur][e])[comp] = out;
             }
             hi = lo;
         }
