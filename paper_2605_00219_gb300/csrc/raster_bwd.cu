@@ -337,9 +337,11 @@ void launch_raster_bwd(const Plan& P, const WsPtrs& w, const float* image, const
 // back to front from its last blended entry: T before an entry is recovered
 // by a compensated division of T after it by (1 - alpha) (div_one_minus:
 // hardware reciprocal, exact remainder, carried low part), and the colour
-// still to come S grows from T_final * bg without cancellation.  The list is
-// staged BB entries at a time with a mask of the warp blocks each entry's
-// 3-sigma box touches; a warp visits only its entries, and for an entry that
+// still to come S grows from T_final * bg without cancellation; only its
+// projection U = dL/dC . S is carried, since dL/dalpha needs no more.  The
+// list is staged BB entries at a time with a mask of the warp blocks each
+// entry's 3-sigma box touches; a warp visits only its entries, and for an
+// entry that
 // at least one of its pixels blended it sums nine values over its 32 pixels
 // with a halving butterfly (12 shuffles; afterwards nine lanes each hold one
 // fully reduced value) into its own shared-memory slot: the opacity and
@@ -438,8 +440,10 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
         Th = tfinal[pix];
         d0 = dl[3 * pix]; d1 = dl[3 * pix + 1]; d2 = dl[3 * pix + 2];
     }
-    float S0 = 0.f, S1 = 0.f, S2 = 0.f;
-    if (bg) { S0 = Th * bg[0]; S1 = Th * bg[1]; S2 = Th * bg[2]; }
+    // U = sum_c dL/dC_c S_c, S_c the colour still to come behind an entry
+    // (from T_final bg_c): dL/dalpha = T sum_c dL/dC_c col_c - U / (1 - alpha)
+    float U = 0.f;
+    if (bg) U = Th * fmaf(d0, bg[0], fmaf(d1, bg[1], d2 * bg[2]));
     int mx_nl = (int)nl;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx_nl = max(mx_nl, __shfl_xor_sync(0xffffffffu, mx_nl, o));
@@ -525,12 +529,9 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
                             g[6] = wgt * d0;
                             g[7] = wgt * d1;
                             g[8] = wgt * d2;
-                            float da = d0 * fmaf(b.z, Th, -S0 * rom);
-                            da = fmaf(d1, fmaf(b.w, Th, -S1 * rom), da);
-                            da = fmaf(d2, fmaf(cb, Th, -S2 * rom), da);
-                            S0 = fmaf(b.z, wgt, S0);
-                            S1 = fmaf(b.w, wgt, S1);
-                            S2 = fmaf(cb, wgt, S2);
+                            const float dcol = fmaf(d0, b.z, fmaf(d1, b.w, d2 * cb));
+                            const float da = fmaf(Th, dcol, -U * rom);
+                            U = fmaf(wgt, dcol, U);
                             if (araw <= kAlphaMax) {
                                 // moments of dp = dL/dpower; the conic and
                                 // the constant factors are applied per entry

@@ -12,7 +12,8 @@
 // back into sub-batches of at most NP pairs:
 //   phase 1 (pixels): each warp walks its entries of the sub-batch back to
 //     front, continuing its pixels' state (T recovered by a compensated
-//     division by 1 - alpha, colour still to come S), and stores per pixel the blend
+//     division by 1 - alpha, colour still to come S carried as its
+//     projection dL/dC . S), and stores per pixel the blend
 //     weight w = alpha T and A = dL/dalpha * G (zero where the 0.99 clamp
 //     holds) at [pixel][pair] (odd row stride: no bank conflicts);
 //   phase 2 (pairs): TPP threads per pair each sum PPT pixels of the pair's
@@ -133,8 +134,10 @@ __global__ void __launch_bounds__(BS) k_raster_bwd2(Views V, const uint32_t* __r
         d0 = dl[3 * pix]; d1 = dl[3 * pix + 1]; d2 = dl[3 * pix + 2];
     }
     S.sd[lane][w] = make_float4(d0, d1, d2, 0.f);
-    float S0 = 0.f, S1 = 0.f, S2 = 0.f;
-    if (bg) { S0 = Th * bg[0]; S1 = Th * bg[1]; S2 = Th * bg[2]; }
+    // U = sum_c dL/dC_c S_c, S_c the colour still to come behind an entry
+    // (from T_final bg_c): dL/dalpha = T sum_c dL/dC_c col_c - U / (1 - alpha)
+    float U = 0.f;
+    if (bg) U = Th * fmaf(d0, bg[0], fmaf(d1, bg[1], d2 * bg[2]));
     int mx_nl = (int)nl;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx_nl = max(mx_nl, __shfl_xor_sync(0xffffffffu, mx_nl, o));
@@ -224,12 +227,9 @@ __global__ void __launch_bounds__(BS) k_raster_bwd2(Views V, const uint32_t* __r
                                 // compensated T before this entry
                                 const float rom = div_one_minus(alpha, Th, Tl);
                                 wv = alpha * Th;
-                                float da = d0 * fmaf(b.z, Th, -S0 * rom);
-                                da = fmaf(d1, fmaf(b.w, Th, -S1 * rom), da);
-                                da = fmaf(d2, fmaf(cb, Th, -S2 * rom), da);
-                                S0 = fmaf(b.z, wv, S0);
-                                S1 = fmaf(b.w, wv, S1);
-                                S2 = fmaf(cb, wv, S2);
+                                const float dcol = fmaf(d0, b.z, fmaf(d1, b.w, d2 * cb));
+                                const float da = fmaf(Th, dcol, -U * rom);
+                                U = fmaf(wv, dcol, U);
                                 if (araw <= kAlphaMax) av = da * G;
                             }
                         }
