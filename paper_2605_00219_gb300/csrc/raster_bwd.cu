@@ -415,7 +415,6 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
     __shared__ uint32_t sE[2][BB];
     __shared__ uint32_t sM[2][BB];
     __shared__ float part[NW][BB][9];
-    __shared__ uint32_t pmask[NW][BB / 32];
     __shared__ int smax[NW];
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -456,15 +455,19 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
 
     // Batches from the back; the batch below the current one is gathered into
     // registers while the current one is processed, then stored to the other
-    // buffer: two barriers per batch.
+    // buffer: two barriers per batch.  An entry's mask keeps the warps whose
+    // block its box touches and one of whose pixels blended at or past it:
+    // exactly the warps that visit it.
     auto stage = [&](int bbx, int buf, int i, const ProjRec& q, uint32_t e) {
-        (void)bbx;
+        uint32_t live = 0;
+#pragma unroll
+        for (int k = 0; k < NW; k++) live |= (bbx + i < smax[k] ? 1u : 0u) << k;
         sA[buf][i] = pair_coefs(q.a.x, q.a.y, q.a.z, q.a.w, q.b.x);
         sB[buf][i] = make_float4(pair_c2(q.b.x), q.b.y, q.b.z, q.b.w);
         sD[buf][i] = make_float4(q.a.z, q.a.w, q.b.x, q.c.x);
         sL[buf][i] = make_float2(q.c.z, q.c.w);
         sE[buf][i] = e;
-        sM[buf][i] = warp_block_mask(q.a.x, q.a.y, q.a.z, q.a.w, q.b.x, q.b.y, ox, oy, WPR, RPB);
+        sM[buf][i] = warp_block_mask(q.a.x, q.a.y, q.a.z, q.a.w, q.b.x, q.b.y, ox, oy, WPR, RPB) & live;
     };
     int bb = ((L + BB - 1) / BB - 1) * BB;
     if (bb >= 0) {
@@ -500,8 +503,7 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
             // entries of this chunk whose 3-sigma box touches this warp's block,
             // before the last pair any of the warp's pixels blended
             const int jl = 32 * c + lane;
-            uint32_t bits = __ballot_sync(0xffffffffu, jl < cnt && bb + jl < mx_nl && (cM[jl] & wbit));
-            uint32_t done_bits = 0;
+            uint32_t bits = __ballot_sync(0xffffffffu, jl < cnt && (cM[jl] & wbit));
             while (bits) {
                 const int jj = 31 - __clz(bits);
                 bits &= ~(1u << jj);
@@ -547,13 +549,12 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
                         }
                     }
                 }
-                if (__any_sync(0xffffffffu, hit)) {
-                    const float x = bfly9(g, lane);
-                    if (vi >= 0) part[w][j][vi] = x;
-                    done_bits |= 1u << jj;
-                }
+                // every visiting warp fills its slot (zeros when none of its
+                // pixels blended the entry)
+                float x = 0.f;
+                if (__any_sync(0xffffffffu, hit)) x = bfly9(g, lane);
+                if (vi >= 0) part[w][j][vi] = x;
             }
-            if (lane == 0) pmask[w][c] = done_bits;
         }
         __syncthreads();
         // add the warps' partial sums in warp order; write each entry's
@@ -564,12 +565,11 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
             const int j = t / 9, comp = t - 9 * j;
             const int comp2 = comp < 2 ? comp ^ 1 : comp;
             float s = 0.f, s2 = 0.f;
-#pragma unroll
-            for (int i = 0; i < NW; i++)
-                if ((pmask[i][j >> 5] >> (j & 31)) & 1u) {
-                    s += part[i][j][comp];
-                    s2 += part[i][j][comp2];
-                }
+            for (uint32_t m = sM[cur][j]; m; m &= m - 1u) {     // visiting warps, in warp order
+                const int i = __ffs(m) - 1;
+                s += part[i][j][comp];
+                s2 += part[i][j][comp2];
+            }
             float out = s;
             if (comp < 2) {
                 const float4 cd = sD[cur][j];
