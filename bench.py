@@ -102,6 +102,10 @@ def _args():
                     help="FP32 storage for the batched form too (the batched-and-autotuned configuration with "
                          "--workload uneven)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--loss", default="l1", choices=["l1", "l1_ssim"],
+                    help="photometric loss of the step: L1 against FP32 targets, or (1 - lambda) L1 + lambda "
+                         "(1 - SSIM) with lambda = 0.2 against 8-bit RGBA targets (fixed tile and implementation; "
+                         "no plain, PSNR or CPU legs)")
     ap.add_argument("--cpu-sample-tiles", type=int, default=16,
                     help="oracle renders 1 in this many tiles (bounded CPU sample)")
     return ap.parse_args()
@@ -283,8 +287,15 @@ def _time_replays(torch, tr, steps, stream):
     return e0.elapsed_time(e1) / steps
 
 
+def _rgba8(torch, flat):
+    """FP32 (P, 3) images in [0, 1] -> 8-bit RGBA (P, 4), alpha 255."""
+    rgb = (flat * 255.0).round().clamp(0, 255).to(torch.uint8)
+    return torch.cat([rgb, torch.full_like(rgb[:, :1], 255)], dim=1)
+
+
 def _stage_times(torch, gsstep, tr, reps, stream):
-    stages = ["project_fwd", "bin_sort", "raster_fwd", "loss_l1", "raster_bwd", "project_bwd_adam"]
+    loss_stage = "loss_l1" if tr.loss == "l1" else "loss_l1_ssim"
+    stages = ["project_fwd", "bin_sort", "raster_fwd", loss_stage, "raster_bwd", "project_bwd_adam"]
     acc = {s: 0.0 for s in stages}
     for _ in range(reps):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)]
@@ -295,7 +306,10 @@ def _stage_times(torch, gsstep, tr, reps, stream):
         ev[2].record(stream)
         gsstep.gs_raster_fwd(tr.plan, tr.ws, tr.bg, tr.image)
         ev[3].record(stream)
-        gsstep.gs_loss_l1(tr.plan, tr.ws, tr.image, tr.target, tr.dl)
+        if tr.loss == "l1":
+            gsstep.gs_loss_l1(tr.plan, tr.ws, tr.image, tr.target, tr.dl)
+        else:
+            gsstep.gs_loss_l1_ssim(tr.plan, tr.ws, tr.image, tr.target, tr.ssim_lambda, tr.dl)
         ev[4].record(stream)
         gsstep.gs_raster_bwd(tr.plan, tr.ws, tr.image, tr.dl)
         ev[5].record(stream)
@@ -342,6 +356,10 @@ def main():
     from paper_2605_00219_gb300 import step as stepmod
 
     stream = torch.cuda.current_stream()
+    if args.loss != "l1":
+        args.no_plain, args.psnr_steps, args.no_cpu = True, 0, True
+        if args.tile is None and args.bwd_impl is None:
+            args.tile = "16x16"
     multi = args.workload == "multiscene"
     if multi:
         # eight scenes of 0.5-6M Gaussians with two views each, one step
@@ -400,8 +418,9 @@ def main():
     else:
         tile = tuple(int(x) for x in args.tile.split("x")) if args.tile else (16, 16)
         impl = args.bwd_impl if args.bwd_impl is not None else 0
-        tr = stepmod.Trainer(all_bufs, cams, lr=LR, tile=tile, bwd_impl=impl, sh_bf16=sh16, mom_bf16=sh16)
-        tr.target.copy_(targets)
+        tr = stepmod.Trainer(all_bufs, cams, lr=LR, tile=tile, bwd_impl=impl, sh_bf16=sh16, mom_bf16=sh16,
+                             loss=args.loss)
+        tr.target.copy_(targets if args.loss == "l1" else _rgba8(torch, targets))
         tr.step(0)
         tune_info = None
     tr.capture()
@@ -428,9 +447,9 @@ def main():
     evaluated = int(tr.buffer(5, tr.plan.pixels).to(torch.int64).sum().item())
 
     # ---- end to end: host targets and cameras in, statistics out, every step
-    pinned_tgt = targets.cpu().pin_memory()
+    pinned_tgt = tr.target.cpu().pin_memory()
     pinned_cam = tr.cams.cpu().pin_memory()
-    h2d = pinned_tgt.numel() * 4 + pinned_cam.numel() * 4
+    h2d = pinned_tgt.numel() * pinned_tgt.element_size() + pinned_cam.numel() * pinned_cam.element_size()
     # two graphs over two input buffer sets: step k's host copy runs on a side
     # stream while step k - 1 computes; every step still copies its own inputs
     # from pinned host memory and reads its statistics back
@@ -478,7 +497,9 @@ def main():
     pairs = n * len(cams) if not multi else sum(scenes[c.scene].n for c in cams)
     npass = 4 + (1 if len(cams) > 1 else 0)
     sort_bytes = pairs * 8 + K * 8 + pairs * 32 + npass * K * 20 + K * 8
-    loss_bytes = px * 3 * 12          # image, target, gradient (FP32)
+    loss_stage = "loss_l1" if args.loss == "l1" else "loss_l1_ssim"
+    # image and gradient (FP32 RGB) and the target (FP32 RGB or 8-bit RGBA)
+    loss_bytes = px * (12 + 12 + (12 if args.loss == "l1" else 4))
     rooflines = {
         "project_bwd_adam": {"bound": "hbm", "achieved": adam_bytes / (acc["project_bwd_adam"] * 1e-3) / 1e9,
                              "peak": hbm_peak, "unit": "GB/s", "traffic": None},
@@ -490,10 +511,11 @@ def main():
                        "peak": alu_peak, "unit": "TFLOP/s", "traffic": None},
         "bin_sort": {"bound": "hbm", "achieved": sort_bytes / (acc["bin_sort"] * 1e-3) / 1e9, "peak": hbm_peak,
                      "unit": "GB/s", "traffic": None},
-        "loss_l1": {"bound": "hbm", "achieved": loss_bytes / (acc["loss_l1"] * 1e-3) / 1e9, "peak": hbm_peak,
-                    "unit": "GB/s", "traffic": None},
+        loss_stage: {"bound": "hbm", "achieved": loss_bytes / (acc[loss_stage] * 1e-3) / 1e9, "peak": hbm_peak,
+                     "unit": "GB/s", "traffic": None},
     }
-    headline = args.workload == "batched" and args.n == N_GAUSS and tuple(tile) == (16, 16) and impl == 0
+    headline = (args.workload == "batched" and args.n == N_GAUSS and tuple(tile) == (16, 16) and impl == 0
+                and args.loss == "l1")
     for k, r in rooflines.items():
         r["frac"] = r["achieved"] / r["peak"]
         r["traffic"] = _measured_traffic(k, headline)
@@ -525,7 +547,9 @@ def main():
                 f"{n / 1e6:.3g}M Gaussians (256 clusters, 30 m box), views per step ") + \
                "+".join(f"{c.width}x{c.height}" for c in cams) + \
                (", BF16 SH and Adam moments (FP32 math)" if sh16 else ", FP32 storage") + \
-               f", tile {tile[0]}x{tile[1]}, raster_bwd impl {impl}, whole step in one CUDA graph; value = " + \
+               f", tile {tile[0]}x{tile[1]}, raster_bwd impl {impl}, " + \
+               ("L1 loss" if args.loss == "l1" else "0.8 L1 + 0.2 (1 - SSIM) loss against 8-bit RGBA targets") + \
+               ", whole step in one CUDA graph; value = " + \
                f"view-steps/s ({nviews} views per step x steps/s; {equiv:.3f} 1080p-equivalents of pixels per step)"
         line = {
             "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
@@ -576,7 +600,7 @@ def launches_per_step(plan) -> int:
         key_bits = max(key_bits, 32 if tb >= 9 else 23 + tb)
     passes = (key_bits + 7) // 8 + (1 if views > 1 else 0)
     project = 2                                        # header reset + projection
-    binsort = 3 + 1 + 1 + passes * (1 + 3 + 1) + 1 + 1  # scan, finalize, emit, passes, fill, ranges
+    binsort = 3 + 1 + 1 + passes * (1 + 3 + 1) + 1 + 1 + 1  # scan, finalize, emit, passes, fill, ranges, order
     return project + binsort + 1 + 1 + 1 + 1 + 1       # raster fwd, loss, raster bwd, proj bwd+adam, advance
 
 

@@ -1,42 +1,28 @@
 // project_fwd.cu -- projection forward fused with the exact tile count
 // (VkSplat Sec. 4.1: the number of intersected tiles is computed in the
-// projection-forward pass).  One thread per (view, Gaussian) pair; SoA float4
-// parameter loads, SH read only for Gaussians that survive culling.
+// projection-forward pass).  One thread per Gaussian, looping over the views
+// of its scene: the parameters are read from HBM once, the SH coefficients
+// once per surviving (view, Gaussian) pair from the first read's cached
+// lines; SoA float4 loads; the outputs of pair (v, g) go to pair
+// pair_base[v] + g, so consecutive threads write consecutive records.
 #include "gs_internal.cuh"
 
 namespace gs {
 
-// 3 CTAs per SM: the register cap (80) costs a few spills but raises occupancy
-// from 2 to 3 CTAs (0.88 -> 0.73 ms at 3M Gaussians x 4 views)
-__global__ void __launch_bounds__(256, 3) k_project_fwd(Views V, Scenes S, const float* __restrict__ cams,
-                                                     uint32_t* __restrict__ count, ProjRec* __restrict__ rec,
-                                                     float4* __restrict__ binrec, WsHeader* __restrict__ hdr)
+// One (view, Gaussian) pair: tile count, and for a pair that meets a tile its
+// projected record and binning geometry.
+__device__ __forceinline__ void project_pair(const ViewDesc& vd, int tw, int th, const SceneDesc& sc, int sh_bf16,
+                                             const float* __restrict__ camp, int64_t g, int64_t p, const float4& mu,
+                                             const float4& q, const float4& so, uint32_t* __restrict__ count,
+                                             ProjRec* __restrict__ rec, float4* __restrict__ binrec)
 {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= V.pairs) return;
-    const int v = view_of_pair(V, p);
-    const ViewDesc& vd = V.v[v];
-    const int64_t g = p - vd.pair_base;
-    const SceneDesc& sc = S.s[vd.scene];
-    const int64_t n = sc.n;
     float cam[16];
 #pragma unroll
-    for (int i = 0; i < 16; i++) cam[i] = __ldg(cams + 16 * v + i);
-    const float4 mu = sc.geom[g];
-    const float4 q = sc.geom[n + g];
-    const float4 so = sc.geom[2 * n + g];
-    const bool finite = isfinite(mu.x) && isfinite(mu.y) && isfinite(mu.z) && isfinite(q.x) && isfinite(q.y) &&
-                        isfinite(q.z) && isfinite(q.w) && isfinite(so.x) && isfinite(so.y) && isfinite(so.z) &&
-                        isfinite(so.w);
-    if (!finite) {
-        atomicOr(&hdr->status, GS_STATUS_NONFINITE);
-        count[p] = 0;
-        return;
-    }
+    for (int i = 0; i < 16; i++) cam[i] = __ldg(camp + i);
     BinGeom bg;
     bin_project(mu, q, so, cam, vd.W, vd.H, bg);
     uint32_t cnt = 0;
-    if (bg.valid) cnt = scanline_tiles(bg, V.tw, V.th, vd.TX, vd.TY, [](uint32_t, uint32_t) {});
+    if (bg.valid) cnt = scanline_tiles(bg, tw, th, vd.TX, vd.TY, [](uint32_t, uint32_t) {});
     count[p] = cnt;
     if (cnt == 0) return;
 
@@ -53,7 +39,7 @@ __global__ void __launch_bounds__(256, 3) k_project_fwd(Views V, Scenes S, const
     float Y[16];
     sh_basis(dx, dy, dz, Y);
     float shv[48];
-    load_sh(sc, S.sh_bf16, g, shv);
+    load_sh(sc, sh_bf16, g, shv);
     float col[3];
 #pragma unroll
     for (int c = 0; c < 3; c++) {
@@ -74,10 +60,43 @@ __global__ void __launch_bounds__(256, 3) k_project_fwd(Views V, Scenes S, const
     binrec[p] = make_float4(bg.a, bg.b, bg.c, __uint_as_float(bg.mant));
 }
 
+// 3 CTAs per SM: the register cap (80) costs a few spills but raises occupancy
+// from 2 to 3 CTAs
+__global__ void __launch_bounds__(256, 3) k_project_fwd(Views V, Scenes S, const float* __restrict__ cams,
+                                                     uint32_t* __restrict__ count, ProjRec* __restrict__ rec,
+                                                     float4* __restrict__ binrec, WsHeader* __restrict__ hdr)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= S.total) return;
+    int s = 0;
+    while (s + 1 < S.n && t >= S.s[s + 1].base) s++;
+    const SceneDesc& sc = S.s[s];
+    const int64_t g = t - sc.base;
+    const int64_t n = sc.n;
+    const float4 mu = sc.geom[g];
+    const float4 q = sc.geom[n + g];
+    const float4 so = sc.geom[2 * n + g];
+    const bool finite = isfinite(mu.x) && isfinite(mu.y) && isfinite(mu.z) && isfinite(q.x) && isfinite(q.y) &&
+                        isfinite(q.z) && isfinite(q.w) && isfinite(so.x) && isfinite(so.y) && isfinite(so.z) &&
+                        isfinite(so.w);
+    if (!finite) atomicOr(&hdr->status, GS_STATUS_NONFINITE);
+    for (int v = 0; v < V.n; v++) {
+        const ViewDesc& vd = V.v[v];
+        if (vd.scene != s) continue;
+        const int64_t p = vd.pair_base + g;
+        if (!finite) {
+            count[p] = 0;
+            continue;
+        }
+        project_pair(vd, V.tw, V.th, sc, S.sh_bf16, cams + 16 * v, g, p, mu, q, so, count, rec, binrec);
+    }
+}
+
 void launch_project_fwd(const Plan& P, const Scenes& S, const float* cams, const WsPtrs& w, cudaStream_t st)
 {
     const int T = 256;
-    const int64_t blocks = (P.views.pairs + T - 1) / T;
+    const int64_t blocks = (S.total + T - 1) / T;
+    if (blocks == 0) return;
     k_project_fwd<<<(unsigned)blocks, T, 0, st>>>(P.views, S, cams, w.count, w.rec, w.binrec, w.hdr);
 }
 
