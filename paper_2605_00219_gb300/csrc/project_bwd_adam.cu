@@ -53,15 +53,74 @@ __device__ __forceinline__ float4 sh_chunk(const SceneDesc& sc, int bf16, int64_
     return make_float4(bf16_lo(u0), bf16_hi(u0), bf16_lo(u1), bf16_hi(u1));
 }
 
+// Rotation R of the normalised quaternion q = (w, x, y, z) and
+// M = R diag(s); returns 1 / |q|.
+__device__ __forceinline__ float rot_scale(float4 q, float4 so, float* R, float* M, float& w, float& x, float& y,
+                                           float& z)
+{
+    const float qn_r = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+    w = q.x * qn_r; x = q.y * qn_r; y = q.z * qn_r; z = q.w * qn_r;
+    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z);       R[2] = 2.f * (x * z + w * y);
+    R[3] = 2.f * (x * y + w * z);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+    R[6] = 2.f * (x * z - w * y);       R[7] = 2.f * (y * z + w * x);       R[8] = 1.f - 2.f * (x * x + y * y);
+    const float sv[3] = {so.x, so.y, so.z};
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) M[3 * i + j] = R[3 * i + j] * sv[j];
+    return qn_r;
+}
+
+// 3D covariance Sigma = M M^T as (S00, S01, S02, S11, S12, S22); it does
+// not depend on the view, so it is formed once per Gaussian.
+__device__ __forceinline__ void covariance3d(float4 q, float4 so, float* Sg)
+{
+    float R[9], M[9], w, x, y, z;
+    rot_scale(q, so, R, M, w, x, y, z);
+    auto dot = [&](int i, int j) { return M[3 * i] * M[3 * j] + M[3 * i + 1] * M[3 * j + 1] + M[3 * i + 2] * M[3 * j + 2]; };
+    Sg[0] = dot(0, 0); Sg[1] = dot(0, 1); Sg[2] = dot(0, 2);
+    Sg[3] = dot(1, 1); Sg[4] = dot(1, 2); Sg[5] = dot(2, 2);
+}
+
+// Backward of Sigma = M M^T, M = R(q) diag(s), once per Gaussian from the
+// sum over views of dL/dSigma (symmetric, as stored by covariance3d):
+// accumulates dq (raw quaternion) and ds (activated scale).
+__device__ __forceinline__ void covariance3d_bwd(float4 q, float4 so, const float* dSg, float* dq, float* ds)
+{
+    float R[9], M[9], w, x, y, z;
+    const float qn_r = rot_scale(q, so, R, M, w, x, y, z);
+    const float dS[9] = {dSg[0], dSg[1], dSg[2], dSg[1], dSg[3], dSg[4], dSg[2], dSg[4], dSg[5]};
+    const float sv[3] = {so.x, so.y, so.z};
+    float dR[9];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            const float dM = 2.f * (dS[3 * i] * M[j] + dS[3 * i + 1] * M[3 + j] + dS[3 * i + 2] * M[6 + j]);
+            dR[3 * i + j] = dM * sv[j];
+            ds[j] += dM * R[3 * i + j];
+        }
+    float dqn[4];
+    dqn[0] = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
+    dqn[1] = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - w * dR[5] + z * dR[6] + w * dR[7]) - 4.f * x * (dR[4] + dR[8]);
+    dqn[2] = 2.f * (x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] + z * dR[7]) - 4.f * y * (dR[0] + dR[8]);
+    dqn[3] = 2.f * (-w * dR[1] + x * dR[2] + w * dR[3] + y * dR[5] + x * dR[6] + y * dR[7]) - 4.f * z * (dR[0] + dR[4]);
+    const float dqq = dqn[0] * w + dqn[1] * x + dqn[2] * y + dqn[3] * z;
+    dq[0] += (dqn[0] - w * dqq) * qn_r;
+    dq[1] += (dqn[1] - x * dqq) * qn_r;
+    dq[2] += (dqn[2] - y * dqq) * qn_r;
+    dq[3] += (dqn[3] - z * dqq) * qn_r;
+}
+
 // Per-view backward of one Gaussian through projection and colour:
-// accumulates dmu, dq, ds (activated scale) and dop (activated opacity), and
-// returns the SH basis at the view direction (Y) and dL/d(raw colour) (draw)
-// so that the SH gradient sum_v Y_v[k] draw_v[c] can be formed later.  The
-// SH coefficients are streamed twice (clamp test, then the direction
+// accumulates dmu, dSg (dL/dSigma, symmetric) and dop (activated opacity),
+// and returns the SH basis at the view direction (Y) and dL/d(raw colour)
+// (draw) so that the SH gradient sum_v Y_v[k] draw_v[c] can be formed later.
+// The SH coefficients are streamed twice (clamp test, then the direction
 // gradient) instead of being held in registers.
-__device__ __forceinline__ void proj_bwd_view(const float* cam, int W, int H, float4 mu, float4 q, float4 so,
+__device__ __forceinline__ void proj_bwd_view(const float* cam, int W, int H, float4 mu, const float* Sg,
                                               const SceneDesc& sc, int bf16, int64_t g, const float* g2,
-                                              float* dmu, float* dq, float* ds, float& dop, float* Y, float* draw)
+                                              float* dmu, float* dSg, float& dop, float* Y, float* draw)
 {
     const float fx = cam[12], fy = cam[13];
     const float* C = cam;
@@ -108,24 +167,6 @@ __device__ __forceinline__ void proj_bwd_view(const float* cam, int W, int H, fl
     // ---- opacity
     dop += g2[5];
 
-    // ---- rotation, scale, 3D covariance
-    const float qn_r = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
-    const float w = q.x * qn_r, x = q.y * qn_r, y = q.z * qn_r, z = q.w * qn_r;
-    float R[9];
-    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z);       R[2] = 2.f * (x * z + w * y);
-    R[3] = 2.f * (x * y + w * z);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
-    R[6] = 2.f * (x * z - w * y);       R[7] = 2.f * (y * z + w * x);       R[8] = 1.f - 2.f * (x * x + y * y);
-    const float sv[3] = {so.x, so.y, so.z};
-    float M[9], Sg[9];
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) M[3 * i + j] = R[3 * i + j] * sv[j];
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) Sg[3 * i + j] = M[3 * i] * M[3 * j] + M[3 * i + 1] * M[3 * j + 1] + M[3 * i + 2] * M[3 * j + 2];
-
     // ---- EWA Jacobian (with the 1.3x FOV clamp) and T = J C
     const float limx = 1.3f * (0.5f * (float)W / fx), limy = 1.3f * (0.5f * (float)H / fy);
     const float ux = tx * itz, uy = ty * itz;
@@ -138,35 +179,44 @@ __device__ __forceinline__ void proj_bwd_view(const float* cam, int W, int H, fl
         T[k] = j00 * C[k] + j02 * C[6 + k];
         T[3 + k] = j11 * C[3 + k] + j12 * C[6 + k];
     }
+    const float Sf[9] = {Sg[0], Sg[1], Sg[2], Sg[1], Sg[3], Sg[4], Sg[2], Sg[4], Sg[5]};
     float TS[6];
 #pragma unroll
     for (int i = 0; i < 2; i++)
 #pragma unroll
-        for (int l = 0; l < 3; l++) TS[3 * i + l] = T[3 * i] * Sg[l] + T[3 * i + 1] * Sg[3 + l] + T[3 * i + 2] * Sg[6 + l];
+        for (int l = 0; l < 3; l++) TS[3 * i + l] = T[3 * i] * Sf[l] + T[3 * i + 1] * Sf[3 + l] + T[3 * i + 2] * Sf[6 + l];
     const float va = TS[0] * T[0] + TS[1] * T[1] + TS[2] * T[2] + 0.3f;
     const float vb = TS[0] * T[3] + TS[1] * T[4] + TS[2] * T[5];
     const float vc = TS[3] * T[3] + TS[4] * T[4] + TS[5] * T[5] + 0.3f;
     const float idet = 1.0f / (va * vc - vb * vb);
     const float qa = vc * idet, qb = -vb * idet, qc = va * idet;
-    // dL/dV = -Q G Q, G = [[dca, dcb/2], [dcb/2, dcc]]
+    // dL/dV = -Q G Q, G = [[dca, dcb/2], [dcb/2, dcc]] (symmetric)
     const float ga = g2[2], gb = 0.5f * g2[3], gc = g2[4];
     const float m00 = qa * ga + qb * gb, m01 = qa * gb + qb * gc;
-    const float m10 = qb * ga + qc * gb, m11 = qb * gb + qc * gc;
+    const float m11 = qb * gb + qc * gc;
     const float dV00 = -(m00 * qa + m01 * qb), dV01 = -(m00 * qb + m01 * qc);
-    const float dV10 = -(m10 * qa + m11 * qb), dV11 = -(m10 * qb + m11 * qc);
-    // dSigma = T^T dV T
-    float dS[9];
+    const float dV11 = -((qb * ga + qc * gb) * qb + m11 * qc);
+    // dSigma += T^T dV T (upper triangle)
+    {
+        float U0[3], U1[3];     // rows of dV T
 #pragma unroll
-    for (int k = 0; k < 3; k++)
-#pragma unroll
-        for (int l = 0; l < 3; l++)
-            dS[3 * k + l] = T[k] * (dV00 * T[l] + dV01 * T[3 + l]) + T[3 + k] * (dV10 * T[l] + dV11 * T[3 + l]);
+        for (int l = 0; l < 3; l++) {
+            U0[l] = dV00 * T[l] + dV01 * T[3 + l];
+            U1[l] = dV01 * T[l] + dV11 * T[3 + l];
+        }
+        dSg[0] += T[0] * U0[0] + T[3] * U1[0];
+        dSg[1] += T[0] * U0[1] + T[3] * U1[1];
+        dSg[2] += T[0] * U0[2] + T[3] * U1[2];
+        dSg[3] += T[1] * U0[1] + T[4] * U1[1];
+        dSg[4] += T[1] * U0[2] + T[4] * U1[2];
+        dSg[5] += T[2] * U0[2] + T[5] * U1[2];
+    }
     // dT = 2 dV T Sigma, dJ = dT C^T
     float dT[6];
 #pragma unroll
     for (int l = 0; l < 3; l++) {
         dT[l] = 2.f * (dV00 * TS[l] + dV01 * TS[3 + l]);
-        dT[3 + l] = 2.f * (dV10 * TS[l] + dV11 * TS[3 + l]);
+        dT[3 + l] = 2.f * (dV01 * TS[l] + dV11 * TS[3 + l]);
     }
     const float dJ00 = dT[0] * C[0] + dT[1] * C[1] + dT[2] * C[2];
     const float dJ02 = dT[0] * C[6] + dT[1] * C[7] + dT[2] * C[8];
@@ -188,33 +238,15 @@ __device__ __forceinline__ void proj_bwd_view(const float* cam, int W, int H, fl
     dmu[0] += C[0] * dtx + C[3] * dty + C[6] * dtz;
     dmu[1] += C[1] * dtx + C[4] * dty + C[7] * dtz;
     dmu[2] += C[2] * dtx + C[5] * dty + C[8] * dtz;
-
-    // ---- Sigma = M M^T, M = R diag(s)
-    float dR[9];
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) {
-            const float dM = 2.f * (dS[3 * i] * M[j] + dS[3 * i + 1] * M[3 + j] + dS[3 * i + 2] * M[6 + j]);
-            dR[3 * i + j] = dM * sv[j];
-            ds[j] += dM * R[3 * i + j];
-        }
-    float dqn[4];
-    dqn[0] = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
-    dqn[1] = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - w * dR[5] + z * dR[6] + w * dR[7]) - 4.f * x * (dR[4] + dR[8]);
-    dqn[2] = 2.f * (x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] + z * dR[7]) - 4.f * y * (dR[0] + dR[8]);
-    dqn[3] = 2.f * (-w * dR[1] + x * dR[2] + w * dR[3] + y * dR[5] + x * dR[6] + y * dR[7]) - 4.f * z * (dR[0] + dR[4]);
-    const float dqq = dqn[0] * w + dqn[1] * x + dqn[2] * y + dqn[3] * z;
-    dq[0] += (dqn[0] - w * dqq) * qn_r;
-    dq[1] += (dqn[1] - x * dqq) * qn_r;
-    dq[2] += (dqn[2] - y * dqq) * qn_r;
-    dq[3] += (dqn[3] - z * dqq) * qn_r;
 }
 
-// Stochastic rounding to bf16 (storage form of SH and Adam moments): add a
-// 16-bit random number below the kept bits, then truncate.  The random bits
-// come from the MurmurHash3 32-bit finaliser applied to a counter built from
-// (seed, step, element), so the rounding is reproducible.
+// Stochastic rounding to bf16 (storage form of SH and Adam moments): each
+// value becomes one of its two neighbouring bf16 values with probabilities
+// proportional to closeness, by the conversion instruction with stochastic
+// rounding (cvt.rs, saturating to the largest finite value), two values per
+// instruction from 32 random bits.  The random bits come from the
+// MurmurHash3 32-bit finaliser applied to a counter built from (seed, step,
+// element), so the rounding is reproducible.
 __device__ __forceinline__ uint32_t fmix32(uint32_t x)
 {
     x ^= x >> 16;
@@ -225,11 +257,12 @@ __device__ __forceinline__ uint32_t fmix32(uint32_t x)
     return x;
 }
 
-__device__ __forceinline__ uint32_t bf16_sr(float f, uint32_t rnd)
+// bf16 pair (lo in bits 0-15, hi in bits 16-31) by stochastic rounding
+__device__ __forceinline__ uint32_t bf16x2_sr(float lo, float hi, uint32_t rbits)
 {
-    uint32_t u = __float_as_uint(f);
-    if ((u & 0x7f800000u) != 0x7f800000u) u += rnd & 0xFFFFu;
-    return u >> 16;
+    uint32_t d;
+    asm("cvt.rs.satfinite.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
+    return d;
 }
 
 // Per-thread stream key: one hash of (seed, step, Gaussian); each stored
@@ -259,9 +292,7 @@ __device__ __forceinline__ void store_mom(void* base, int64_t idx, float4 m, uin
         return;
     }
     const uint32_t r0 = sr_bits(key, 2u * ctr), r1 = sr_bits(key, 2u * ctr + 1u);
-    const uint32_t a = bf16_sr(m.x, r0), b = bf16_sr(m.y, r0 >> 16);
-    const uint32_t c = bf16_sr(m.z, r1), d = bf16_sr(m.w, r1 >> 16);
-    reinterpret_cast<uint2*>(base)[idx] = make_uint2(a | (b << 16), c | (d << 16));
+    reinterpret_cast<uint2*>(base)[idx] = make_uint2(bf16x2_sr(m.x, m.y, r0), bf16x2_sr(m.z, m.w, r1));
 }
 
 constexpr int kPbaThreads = 128;
@@ -309,7 +340,9 @@ __global__ void __launch_bounds__(kPbaThreads, 4) k_project_bwd_adam(Views V, Sc
         float4 mu = sc.geom[g];
         float4 q = sc.geom[n + g];
         float4 so = sc.geom[2 * n + g];
-        float dmu[3] = {0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f}, ds[3] = {0.f, 0.f, 0.f}, dop = 0.f;
+        float dmu[3] = {0.f, 0.f, 0.f}, dSg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, dop = 0.f;
+        float Sg[6];
+        covariance3d(q, so, Sg);
         float st_sum = 0.f, st_cnt = 0.f;   // densification statistics of this step
         // the next view's count and offset are loaded while this view is
         // processed
@@ -355,10 +388,12 @@ __global__ void __launch_bounds__(kPbaThreads, 4) k_project_bwd_adam(Views V, Sc
 #pragma unroll
             for (int i = 0; i < 16; i++) cam[i] = __ldg(cams + 16 * v + i);
             float Y[16], draw[3];
-            proj_bwd_view(cam, vd.W, vd.H, mu, q, so, sc, SH16 ? 1 : 0, g, g2, dmu, dq, ds, dop, Y, draw);
+            proj_bwd_view(cam, vd.W, vd.H, mu, Sg, sc, SH16 ? 1 : 0, g, g2, dmu, dSg, dop, Y, draw);
 #pragma unroll
             for (int f = 0; f < 48; f++) sG[f][tid] = fmaf(Y[f / 3], draw[f % 3], sG[f][tid]);
         }
+        float dq[4] = {0.f, 0.f, 0.f, 0.f}, ds[3] = {0.f, 0.f, 0.f};
+        covariance3d_bwd(q, so, dSg, dq, ds);
         if (sc.stats) {
             float2 st = sc.stats[g];
             st.x += st_sum;
@@ -452,15 +487,10 @@ __global__ void __launch_bounds__(kPbaThreads, 4) k_project_bwd_adam(Views V, Sc
             reinterpret_cast<float4*>(sc.sh)[(int64_t)(2 * jp) * n + g] = make_float4(th[0], th[1], th[2], th[3]);
             reinterpret_cast<float4*>(sc.sh)[(int64_t)(2 * jp + 1) * n + g] = make_float4(th[4], th[5], th[6], th[7]);
         } else {
-            uint32_t u[8];
+            uint32_t u[4];
 #pragma unroll
-            for (int i = 0; i < 8; i += 2) {
-                const uint32_t r = sr_bits(key, 64u + 8u * jp + i);
-                u[i] = bf16_sr(th[i], r);
-                u[i + 1] = bf16_sr(th[i + 1], r >> 16);
-            }
-            reinterpret_cast<uint4*>(sc.sh)[(int64_t)jp * n + g] =
-                make_uint4(u[0] | (u[1] << 16), u[2] | (u[3] << 16), u[4] | (u[5] << 16), u[6] | (u[7] << 16));
+            for (int i = 0; i < 4; i++) u[i] = bf16x2_sr(th[2 * i], th[2 * i + 1], sr_bits(key, 64u + 8u * jp + 2 * i));
+            reinterpret_cast<uint4*>(sc.sh)[(int64_t)jp * n + g] = make_uint4(u[0], u[1], u[2], u[3]);
         }
     }
 }
