@@ -244,9 +244,8 @@ __device__ __forceinline__ void proj_bwd_view(const float* cam, int W, int H, fl
 // value becomes one of its two neighbouring bf16 values with probabilities
 // proportional to closeness, by the conversion instruction with stochastic
 // rounding (cvt.rs, saturating to the largest finite value), two values per
-// instruction from 32 random bits.  The random bits come from the
-// MurmurHash3 32-bit finaliser applied to a counter built from (seed, step,
-// element), so the rounding is reproducible.
+// instruction from 32 random bits.  The random bits are a function of
+// (seed, step, Gaussian, element), so the rounding is reproducible.
 __device__ __forceinline__ uint32_t fmix32(uint32_t x)
 {
     x ^= x >> 16;
@@ -265,15 +264,23 @@ __device__ __forceinline__ uint32_t bf16x2_sr(float lo, float hi, uint32_t rbits
     return d;
 }
 
-// Per-thread stream key: one hash of (seed, step, Gaussian); each stored
-// group of values then takes fmix32(key ^ group counter), whose 32 bits serve
-// two bf16 roundings.
+// Per-thread stream key: one hash of (seed, step, Gaussian), uniform over
+// 32 bits.  Draw ctr of the stream is one multiply-xorshift round of
+// key + ctr * 0x9E3779B9: for each ctr a bijection of the key, hence uniform
+// as well, which is what unbiased stochastic rounding needs; its 32 bits
+// serve two bf16 roundings.
 __device__ __forceinline__ uint32_t sr_key(uint32_t seed, int step, int64_t gi)
 {
     return fmix32(seed ^ fmix32((uint32_t)step * 0x9E3779B9u ^ (uint32_t)gi ^ (uint32_t)(gi >> 32) * 0xc2b2ae35u));
 }
 
-__device__ __forceinline__ uint32_t sr_bits(uint32_t key, uint32_t ctr) { return fmix32(key ^ (ctr * 0x9E3779B9u)); }
+__device__ __forceinline__ uint32_t sr_bits(uint32_t key, uint32_t ctr)
+{
+    uint32_t x = key + ctr * 0x9E3779B9u;
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    return x ^ (x >> 15);
+}
 
 // Moment chunk ci (4 values) of Gaussian g: FP32 float4 or 4 x bf16.
 template <bool MOM16>
@@ -310,7 +317,9 @@ __global__ void __launch_bounds__(kPbaThreads, 4) k_project_bwd_adam(Views V, Sc
                                                                   float4* __restrict__ grads_out,
                                                                   const WsHeader* __restrict__ hdr, uint32_t cap)
 {
-    __shared__ float sG[48][kPbaThreads];
+    // SH gradients, 12 float4 per thread (row stride 13 float4: the 16-byte
+    // accesses of 8 consecutive threads cover all 32 banks once)
+    __shared__ float4 sG[kPbaThreads][13];
     __shared__ AdamConst sK;
     const int tid = threadIdx.x;
     const int64_t gi = (int64_t)blockIdx.x * kPbaThreads + tid;
@@ -328,7 +337,7 @@ __global__ void __launch_bounds__(kPbaThreads, 4) k_project_bwd_adam(Views V, Sc
         sK.omb2 = 1.0f - A.b2;
     }
 #pragma unroll
-    for (int f = 0; f < 48; f++) sG[f][tid] = 0.f;
+    for (int j = 0; j < 12; j++) sG[tid][j] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
 
     if (gi < S.total) {
@@ -390,7 +399,14 @@ __global__ void __launch_bounds__(kPbaThreads, 4) k_project_bwd_adam(Views V, Sc
             float Y[16], draw[3];
             proj_bwd_view(cam, vd.W, vd.H, mu, Sg, sc, SH16 ? 1 : 0, g, g2, dmu, dSg, dop, Y, draw);
 #pragma unroll
-            for (int f = 0; f < 48; f++) sG[f][tid] = fmaf(Y[f / 3], draw[f % 3], sG[f][tid]);
+            for (int j = 0; j < 12; j++) {
+                float4 a = sG[tid][j];
+                a.x = fmaf(Y[(4 * j) / 3], draw[(4 * j) % 3], a.x);
+                a.y = fmaf(Y[(4 * j + 1) / 3], draw[(4 * j + 1) % 3], a.y);
+                a.z = fmaf(Y[(4 * j + 2) / 3], draw[(4 * j + 2) % 3], a.z);
+                a.w = fmaf(Y[(4 * j + 3) / 3], draw[(4 * j + 3) % 3], a.w);
+                sG[tid][j] = a;
+            }
         }
         float dq[4] = {0.f, 0.f, 0.f, 0.f}, ds[3] = {0.f, 0.f, 0.f};
         covariance3d_bwd(q, so, dSg, dq, ds);
@@ -451,8 +467,7 @@ __global__ void __launch_bounds__(kPbaThreads, 4) k_project_bwd_adam(Views V, Sc
         const int64_t N = S.total;
 #pragma unroll
         for (int j = 0; j < 12; j++)
-            grads_out[(3 + j) * N + gi] = make_float4(sG[4 * j][tid], sG[4 * j + 1][tid], sG[4 * j + 2][tid],
-                                                      sG[4 * j + 3][tid]);
+            grads_out[(3 + j) * N + gi] = sG[tid][j];
         return;
     }
     const AdamConst K = sK;
@@ -473,12 +488,14 @@ __global__ void __launch_bounds__(kPbaThreads, 4) k_project_bwd_adam(Views V, Sc
             const int j = 2 * jp + h;
             const int64_t ci = (int64_t)(3 + j) * n + g;
             float4 m = load_mom<MOM16>(sc.m, ci), vv = load_mom<MOM16>(sc.v, ci);
+            const float4 g4 = sG[tid][j];
             float* mp = &m.x;
             float* vp = &vv.x;
+            const float* gp = &g4.x;
 #pragma unroll
             for (int i = 0; i < 4; i++) {
                 const int f = 4 * j + i;
-                adam1(th[4 * h + i], mp[i], vp[i], sG[f][tid], f < 3 ? K.alpha[4] : K.alpha[5], K);
+                adam1(th[4 * h + i], mp[i], vp[i], gp[i], f < 3 ? K.alpha[4] : K.alpha[5], K);
             }
             store_mom<MOM16>(sc.m, ci, m, key, 6u + 2u * j);
             store_mom<MOM16>(sc.v, ci, vv, key, 7u + 2u * j);
