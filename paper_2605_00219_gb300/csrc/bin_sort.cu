@@ -226,6 +226,17 @@ __device__ __forceinline__ int view_of_slot(const uint32_t* seg, int nv, uint32_
     return v;
 }
 
+// 16-byte asynchronous global -> shared copy (bypassing L1), and its group
+// commit / wait (hardware waits: no spinning in this code)
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 template <int MODE>
 __global__ void __launch_bounds__(kRadixThreads) k_radix_up(const uint32_t* __restrict__ keys,
                                                              const uint32_t* __restrict__ vals, bool iota,
@@ -234,9 +245,10 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_up(const uint32_t* __re
 {
     // digit counts of each 2048-key block: one private histogram per warp
     // (plain shared-memory atomics), summed per digit at the end.  Only the
-    // blocks that hold keys take part (the grid strides over them); the
-    // histogram is [digit][block] over them, so its scan covers
-    // 256 x ceil(K / 2048) entries.
+    // blocks that hold keys take part (the grid strides over them, the next
+    // block's keys loaded while this one is counted); the histogram is
+    // [digit][block] over them, so its scan covers 256 x ceil(K / 2048)
+    // entries.  Key arrays are padded to whole blocks.
     constexpr int W = kRadixThreads / 32;
     const uint32_t nb = hdr->hist_nblk;
     if (blockIdx.x >= nb) return;
@@ -246,25 +258,32 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_up(const uint32_t* __re
     if (MODE == kDigitView)
         for (int i = threadIdx.x; i <= nv; i += blockDim.x) seg[i] = hdr->seg[i];
     const uint32_t K = hdr->k_eff;
+    const uint32_t* src = MODE == kDigitKey ? keys : vals;
+    const bool load = MODE == kDigitKey || !iota;
+    uint32_t d[kRadixItems];
+    auto fetch = [&](uint32_t b) {
+        const int64_t base = (int64_t)b * kRadixBlock;
+#pragma unroll
+        for (int i = 0; i < kRadixItems; i++) {
+            const int64_t idx = base + i * kRadixThreads + threadIdx.x;
+            d[i] = load ? src[idx] : (uint32_t)idx;
+        }
+    };
+    fetch(blockIdx.x);
     for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
+        uint32_t cur[kRadixItems];
+#pragma unroll
+        for (int i = 0; i < kRadixItems; i++) cur[i] = d[i];
+        if (b + gridDim.x < nb) fetch(b + gridDim.x);
 #pragma unroll
         for (int i = 0; i < W; i++) h[i][threadIdx.x] = 0;
         __syncthreads();
         const int64_t base = (int64_t)b * kRadixBlock;
-        uint32_t d[kRadixItems];
-#pragma unroll
-        for (int i = 0; i < kRadixItems; i++) {   // all loads first, then the counts
-            const int64_t idx = base + i * kRadixThreads + threadIdx.x;
-            d[i] = 0xFFFFFFFFu;
-            if (idx < K) {
-                if (MODE == kDigitKey) d[i] = keys[idx];
-                else d[i] = iota ? (uint32_t)idx : vals[idx];
-            }
-        }
 #pragma unroll
         for (int i = 0; i < kRadixItems; i++) {
             if (base + i * kRadixThreads + threadIdx.x < K) {
-                const uint32_t dg = MODE == kDigitKey ? (d[i] >> shift) & 0xFFu : (uint32_t)view_of_slot(seg, nv, d[i]);
+                const uint32_t dg = MODE == kDigitKey ? (cur[i] >> shift) & 0xFFu
+                                                      : (uint32_t)view_of_slot(seg, nv, cur[i]);
                 atomicAdd(&h[w][dg], 1u);
             }
         }
@@ -287,12 +306,16 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_down(const uint32_t* __
                                                                const uint32_t* __restrict__ pid,
                                                                uint32_t* __restrict__ pid_sorted)
 {
+    // Blocks are double-buffered in shared memory: the next block's keys and
+    // payload are copied asynchronously while this one is ranked, and this
+    // block's buffer then holds its locally reordered keys for the coalesced
+    // write-out.  Key arrays are padded to whole blocks.
     constexpr int W = kRadixThreads / 32;
     __shared__ uint32_t wh[W][kRadixDigits];
     __shared__ uint32_t bstart[kRadixDigits];
     __shared__ uint32_t gbase[kRadixDigits];
-    __shared__ uint32_t sk[kRadixBlock];
-    __shared__ uint32_t sv[kRadixBlock];
+    __shared__ __align__(16) uint32_t sk[2][kRadixBlock];
+    __shared__ __align__(16) uint32_t sv[2][kRadixBlock];
     __shared__ uint32_t seg[kMaxViews + 1];
     __shared__ uint32_t wsum[32];
     const uint32_t K = hdr->k_eff;
@@ -302,19 +325,33 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_down(const uint32_t* __
     if (MODE == kDigitView)
         for (int i = threadIdx.x; i <= nv; i += blockDim.x) seg[i] = hdr->seg[i];
     const uint32_t lt = lanemask_lt();
-    for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {   // blocks holding keys
+    auto issue = [&](uint32_t b, int buf) {
         const int64_t base = (int64_t)b * kRadixBlock;
+        for (int c = threadIdx.x; c < kRadixBlock / 4; c += kRadixThreads) {
+            cp_async16(&sk[buf][4 * c], keys_in + base + 4 * c);
+            if (!IOTA) cp_async16(&sv[buf][4 * c], vals_in + base + 4 * c);
+        }
+        cp_async_commit();
+    };
+    issue(blockIdx.x, 0);
+    int cur = 0;
+    for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x, cur ^= 1) {   // blocks holding keys
+        const int64_t base = (int64_t)b * kRadixBlock;
+        if (b + gridDim.x < nb) issue(b + gridDim.x, cur ^ 1);
+        else cp_async_commit();                 // empty group: the wait below stays one behind
 #pragma unroll
         for (int i = 0; i < W; i++) wh[i][threadIdx.x] = 0;
+        cp_async_wait<1>();
         __syncthreads();
 
         uint32_t key[kRadixItems], val[kRadixItems], dig[kRadixItems], rank[kRadixItems];
 #pragma unroll
         for (int r = 0; r < kRadixItems; r++) {
-            const int64_t idx = base + w * (32 * kRadixItems) + r * 32 + lane;
+            const int li = w * (32 * kRadixItems) + r * 32 + lane;
+            const int64_t idx = base + li;
             const bool valid = idx < K;
-            key[r] = valid ? keys_in[idx] : 0u;
-            val[r] = IOTA ? (uint32_t)idx : (valid ? vals_in[idx] : 0u);
+            key[r] = valid ? sk[cur][li] : 0u;
+            val[r] = IOTA ? (uint32_t)idx : (valid ? sv[cur][li] : 0u);
             uint32_t d = 0xFFFFu;
             if (valid) {
                 if (MODE == kDigitKey) d = (key[r] >> shift) & 0xFFu;
@@ -328,10 +365,10 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_down(const uint32_t* __
             const uint32_t d = dig[r];
             const uint32_t peers = __match_any_sync(0xffffffffu, d);
             const bool valid = d != 0xFFFFu;
-            uint32_t cur = valid ? wh[w][d] : 0u;
-            rank[r] = cur + __popc(peers & lt);
+            uint32_t c = valid ? wh[w][d] : 0u;
+            rank[r] = c + __popc(peers & lt);
             __syncwarp();
-            if (valid && lane == __ffs(peers) - 1) wh[w][d] = cur + __popc(peers);
+            if (valid && lane == __ffs(peers) - 1) wh[w][d] = c + __popc(peers);
             __syncwarp();
         }
         __syncthreads();
@@ -350,19 +387,20 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_down(const uint32_t* __
             gbase[d] = hist[(int64_t)d * nb + b];
         }
         __syncthreads();
+        // every thread has its items in registers: reorder into this block's buffer
 #pragma unroll
         for (int r = 0; r < kRadixItems; r++) {
             const uint32_t d = dig[r];
             if (d != 0xFFFFu) {
                 const uint32_t lp = bstart[d] + wh[w][d] + rank[r];
-                sk[lp] = key[r];
-                sv[lp] = val[r];
+                sk[cur][lp] = key[r];
+                sv[cur][lp] = val[r];
             }
         }
         __syncthreads();
         const int nvalid = (int)min((int64_t)kRadixBlock, (int64_t)K - base);
         for (int i = threadIdx.x; i < nvalid; i += kRadixThreads) {
-            const uint32_t k = sk[i], v = sv[i];
+            const uint32_t k = sk[cur][i], v = sv[cur][i];
             const uint32_t d = MODE == kDigitKey ? ((k >> shift) & 0xFFu) : (uint32_t)view_of_slot(seg, nv, v);
             const uint32_t pos = gbase[d] + (uint32_t)i - bstart[d];
             keys_out[pos] = k;
@@ -371,6 +409,7 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_down(const uint32_t* __
         }
         __syncthreads();
     }
+    cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
@@ -444,8 +483,10 @@ void launch_bin_sort(const Plan& P, const WsPtrs& w, cudaStream_t st)
         k_emit<<<(unsigned)blocks, 256, 0, st>>>(V, w.count, w.offset, w.rec, w.binrec, w.keysA, w.pid, cap);
     }
     // sorting: the radix kernels stride over the blocks that hold keys, with
-    // a grid of at most 8 CTAs per SM
+    // grids of the resident CTAs (8 per SM for the counts, 4 for the
+    // double-buffered reorder)
     const int64_t nblk = std::min<int64_t>(P.radix_blocks, (int64_t)P.sm_count * 8);
+    const int64_t nblk_down = std::min<int64_t>(P.radix_blocks, (int64_t)P.sm_count * 4);
     const int npass = P.key_passes + P.view_pass;
     uint32_t *kin = w.keysA, *vin = w.valsA, *kout = w.keysB, *vout = w.valsB;
     for (int pass = 0; pass < npass; pass++) {
@@ -460,7 +501,7 @@ void launch_bin_sort(const Plan& P, const WsPtrs& w, cudaStream_t st)
         scan_u32_dyn(w.hist, w.hist, (int64_t)kRadixDigits * P.radix_blocks, &w.hdr->hist_nblk, kRadixDigits,
                      w.scan_part, st);
 #define GS_DOWN(MODE, IOTA, LAST)                                                                          \
-    k_radix_down<MODE, IOTA, LAST><<<(unsigned)nblk, kRadixThreads, 0, st>>>(kin, vin, kout, vout, w.hist, shift, \
+    k_radix_down<MODE, IOTA, LAST><<<(unsigned)nblk_down, kRadixThreads, 0, st>>>(kin, vin, kout, vout, w.hist, shift, \
                                                                               w.hdr, V.n, w.pid, w.pid_sorted)
         if (view) {
             if (first) GS_DOWN(kDigitView, true, true);
