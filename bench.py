@@ -55,17 +55,20 @@ BATCH_RES = [(1920, 1080), (1600, 1064), (1280, 720), (960, 540)]
 PX_1080 = 1920 * 1080
 LR = (1.6e-4 * 30.0, 1e-3, 5e-3, 5e-2, 2.5e-3, 2.5e-3 / 20)   # mean lr scaled by the 30 m scene extent
 
-# DRAM bytes (read + write) of one launch, from one ncu capture of the
-# headline workload (batched BF16, 4 x 1920x1080, 16x16 tiles, pixel-parallel
-# raster backward; profiles/step_batched_bf16_3M_4x1080p_launch_list.md).
-# Valid only while the kernel sources hash to the recorded prefixes.
+# DRAM bytes (read + write) of one launch (for the sort: of its launches in
+# one step), from one ncu capture of the headline workload (batched BF16,
+# 4 x 1920x1080, 16x16 tiles, pixel-parallel raster backward;
+# profiles/step_batched_bf16_3M_4x1080p_launch_list.md).  Valid only while
+# the kernel sources hash to the recorded prefixes.
 MEASURED_TRAFFIC = {
-    "raster_bwd": (2106000000 + 976000000, {"raster_bwd.cu": "816a50647c3ae43f"}),
-    "project_bwd_adam": (2077000000 + 1099000000, {"project_bwd_adam.cu": "7e9c94ebada201bd"}),
-    "raster_fwd": (1031000000 + 155000000, {"raster_fwd.cu": "d92a368e13895eda"}),
-    "project_fwd": (1870000000 + 666000000, {"project_fwd.cu": "054b01e733416a04"}),
+    "raster_bwd": (3678310400, {"raster_bwd.cu": "4e93ffce6fe0f042"}),
+    "project_bwd_adam": (3192167936, {"project_bwd_adam.cu": "332d8b12f0eadb8c"}),
+    "raster_fwd": (1706953984, {"raster_fwd.cu": "eb796557894a3910"}),
+    "project_fwd": (1260378624, {"project_fwd.cu": "1653c497900428cc"}),
+    "bin_sort": (3071833600, {"bin_sort.cu": "85f6dcb4f9cf70b1"}),
+    "loss_l1": (266785792, {"raster_fwd.cu": "eb796557894a3910"}),
 }
-TRAFFIC_COMMON = {"gs_device.cuh": "02cf40e7d44ac4b5", "gs_internal.cuh": "6c2125d40657aed6"}
+TRAFFIC_COMMON = {"gs_device.cuh": "aaffbe874e2f2481", "gs_internal.cuh": "9999e81ae0e203c9"}
 
 
 def _measured_traffic(kernel: str, headline: bool):
