@@ -304,6 +304,8 @@ __device__ __forceinline__ void store_mom(void* base, int64_t idx, float4 m, uin
 
 constexpr int kPbaThreads = 128;
 
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 // Phase 1 (one thread per Gaussian): sum the intersection records per view,
 // back-propagate through projection and colour, apply Adam to mean,
 // quaternion and (log-scale, logit-opacity); the 48 SH gradients accumulate
@@ -349,6 +351,19 @@ __global__ void __launch_bounds__(kPbaThreads, 4) k_project_bwd_adam(Views V, Sc
         float4 mu = sc.geom[g];
         float4 q = sc.geom[n + g];
         float4 so = sc.geom[2 * n + g];
+        if (!A.grad_only) {
+            // the moments and the SH chunks are read only after the
+            // projection backward of every view: request their lines into L2
+            // now (no registers held)
+#pragma unroll
+            for (int ci = 0; ci < 15; ci++) {
+                prefetch_l2(reinterpret_cast<const char*>(sc.m) + ((int64_t)ci * n + g) * (MOM16 ? 8 : 16));
+                prefetch_l2(reinterpret_cast<const char*>(sc.v) + ((int64_t)ci * n + g) * (MOM16 ? 8 : 16));
+            }
+#pragma unroll
+            for (int j = 0; j < (SH16 ? 6 : 12); j++)
+                prefetch_l2(reinterpret_cast<const char*>(sc.sh) + ((int64_t)j * n + g) * 16);
+        }
         float dmu[3] = {0.f, 0.f, 0.f}, dSg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, dop = 0.f;
         float Sg[6];
         covariance3d(q, so, Sg);
