@@ -424,15 +424,25 @@ __global__ void __launch_bounds__(256) k_ranges(Views V, const uint32_t* __restr
     for (int i = threadIdx.x; i <= V.n; i += blockDim.x) seg[i] = hdr->seg[i];
     __syncthreads();
     const uint32_t K = hdr->k_eff;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < K; k += (int64_t)gridDim.x * blockDim.x) {
-        const int v = view_of_slot(seg, V.n, (uint32_t)k);
-        const ViewDesc& vd = V.v[v];
-        const uint32_t tile = keys[k] >> vd.shift;
-        const int64_t gt = vd.tile_base + tile;
-        const bool first = (k == seg[v]) || ((keys[k - 1] >> vd.shift) != tile);
-        const bool last = (k + 1 == seg[v + 1]) || ((keys[k + 1] >> vd.shift) != tile);
-        if (first) ranges[gt].x = (uint32_t)k;
-        if (last) ranges[gt].y = (uint32_t)(k + 1);
+    // four consecutive keys per thread (one 16-byte load; the capacity is a
+    // multiple of 4) and their two neighbours
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
+    for (int64_t k0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; k0 < K; k0 += stride) {
+        const uint4 q = *reinterpret_cast<const uint4*>(keys + k0);
+        const uint32_t kk[6] = {k0 > 0 ? keys[k0 - 1] : 0u, q.x, q.y, q.z, q.w, k0 + 4 < K ? keys[k0 + 4] : 0u};
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const int64_t k = k0 + i;
+            if (k >= K) break;
+            const int v = view_of_slot(seg, V.n, (uint32_t)k);
+            const ViewDesc& vd = V.v[v];
+            const uint32_t tile = kk[i + 1] >> vd.shift;
+            const int64_t gt = vd.tile_base + tile;
+            const bool first = (k == seg[v]) || ((kk[i] >> vd.shift) != tile);
+            const bool last = (k + 1 == seg[v + 1]) || ((kk[i + 2] >> vd.shift) != tile);
+            if (first) ranges[gt].x = (uint32_t)k;
+            if (last) ranges[gt].y = (uint32_t)(k + 1);
+        }
     }
 }
 
