@@ -27,6 +27,19 @@ constexpr int kSsR = 5;                  // window radius
 constexpr int kSsQ = kSsT + 2 * kSsR;    // 26: positions whose window reaches the tile
 constexpr int kSsX = kSsT + 4 * kSsR;    // 36: staged pixels per side
 constexpr float kSsC1 = 0.01f * 0.01f;
+
+// Window tap k (0..10): exp(-(k - 5)^2 / (2 * 1.5^2)) normalised to unit sum,
+// evaluated in FP64 and rounded to FP32; with unrolled tap loops these become
+// immediate operands of the FMAs.
+__host__ __device__ constexpr float ssim_w(int k)
+{
+    return (k == 0 || k == 10) ? 0.0010283801f
+         : (k == 1 || k == 9)  ? 0.0075987582f
+         : (k == 2 || k == 8)  ? 0.036000773f
+         : (k == 3 || k == 7)  ? 0.10936069f
+         : (k == 4 || k == 6)  ? 0.21300554f
+                               : 0.26601171f;
+}
 constexpr float kSsC2 = 0.03f * 0.03f;
 
 __device__ __forceinline__ int ssim_view_of_tile(const Views& V, int64_t t, int64_t& first)
@@ -59,7 +72,6 @@ __global__ void __launch_bounds__(256) k_loss_l1_ssim(Views V, const float* __re
     __shared__ float hm[5][kSsX][kSsQ];
     __shared__ float abc[3][kSsQ][kSsQ + 1];
     __shared__ float habc[3][kSsQ][kSsT];
-    __shared__ float wg[2 * kSsR + 1];
     __shared__ float red[2][8];
     __shared__ bool is_last;
 
@@ -70,11 +82,6 @@ __global__ void __launch_bounds__(256) k_loss_l1_ssim(Views V, const float* __re
     const int lt = (int)(blockIdx.x - first);
     const int TX = (vd.W + kSsT - 1) / kSsT;
     const int ox = (lt % TX) * kSsT, oy = (lt / TX) * kSsT;
-    if (tid < 2 * kSsR + 1) {
-        float s = 0.f;
-        for (int i = 0; i <= 2 * kSsR; i++) s += expf(-(float)((i - kSsR) * (i - kSsR)) / (2.f * 1.5f * 1.5f));
-        wg[tid] = expf(-(float)((tid - kSsR) * (tid - kSsR)) / (2.f * 1.5f * 1.5f)) / s;
-    }
     const int pc = tid % kSsT, pr = tid / kSsT;
     const int px = ox + pc, py = oy + pr;
     const bool pin = px < vd.W && py < vd.H;
@@ -104,7 +111,7 @@ __global__ void __launch_bounds__(256) k_loss_l1_ssim(Views V, const float* __re
             float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, m4 = 0.f;
 #pragma unroll
             for (int k = 0; k <= 2 * kSsR; k++) {
-                const float w = wg[k], a = sx[r][q + k], b = sy[r][q + k];
+                const float w = ssim_w(k), a = sx[r][q + k], b = sy[r][q + k];
                 m0 = fmaf(w, a, m0);
                 m1 = fmaf(w, b, m1);
                 m2 = fmaf(w, a * a, m2);
@@ -120,7 +127,7 @@ __global__ void __launch_bounds__(256) k_loss_l1_ssim(Views V, const float* __re
             float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int k = 0; k <= 2 * kSsR; k++) {
-                const float w = wg[k];
+                const float w = ssim_w(k);
 #pragma unroll
                 for (int j = 0; j < 5; j++) m[j] = fmaf(w, hm[j][qr + k][qc], m[j]);
             }
@@ -147,7 +154,7 @@ __global__ void __launch_bounds__(256) k_loss_l1_ssim(Views V, const float* __re
             float a = 0.f, b = 0.f, d = 0.f;
 #pragma unroll
             for (int k = 0; k <= 2 * kSsR; k++) {
-                const float w = wg[k];
+                const float w = ssim_w(k);
                 a = fmaf(w, abc[0][r][q + k], a);
                 b = fmaf(w, abc[1][r][q + k], b);
                 d = fmaf(w, abc[2][r][q + k], d);
@@ -159,7 +166,7 @@ __global__ void __launch_bounds__(256) k_loss_l1_ssim(Views V, const float* __re
         float wa = 0.f, wb = 0.f, wc = 0.f;
 #pragma unroll
         for (int k = 0; k <= 2 * kSsR; k++) {
-            const float w = wg[k];
+            const float w = ssim_w(k);
             wa = fmaf(w, habc[0][pr + k][pc], wa);
             wb = fmaf(w, habc[1][pr + k][pc], wb);
             wc = fmaf(w, habc[2][pr + k][pc], wc);
