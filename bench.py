@@ -61,12 +61,12 @@ LR = (1.6e-4 * 30.0, 1e-3, 5e-3, 5e-2, 2.5e-3, 2.5e-3 / 20)   # mean lr scaled b
 # profiles/step_batched_bf16_3M_4x1080p_launch_list.md).  Valid only while
 # the kernel sources hash to the recorded prefixes.
 MEASURED_TRAFFIC = {
-    "raster_bwd": (3678310400, {"raster_bwd.cu": "4e93ffce6fe0f042"}),
-    "project_bwd_adam": (3192167936, {"project_bwd_adam.cu": "332d8b12f0eadb8c"}),
-    "raster_fwd": (1706953984, {"raster_fwd.cu": "eb796557894a3910"}),
-    "project_fwd": (1260378624, {"project_fwd.cu": "1653c497900428cc"}),
-    "bin_sort": (3071833600, {"bin_sort.cu": "85f6dcb4f9cf70b1"}),
-    "loss_l1": (266785792, {"raster_fwd.cu": "eb796557894a3910"}),
+    "raster_bwd": (3637729536, {"raster_bwd.cu": "4e93ffce6fe0f042"}),
+    "project_bwd_adam": (3304814080, {"project_bwd_adam.cu": "92b38a842cbd145f"}),
+    "raster_fwd": (1685828096, {"raster_fwd.cu": "eb796557894a3910"}),
+    "project_fwd": (1259325184, {"project_fwd.cu": "1653c497900428cc"}),
+    "bin_sort": (3072882176, {"bin_sort.cu": "49d33c937ce3d28f"}),
+    "loss_l1": (266700800, {"raster_fwd.cu": "eb796557894a3910"}),
 }
 TRAFFIC_COMMON = {"gs_device.cuh": "aaffbe874e2f2481", "gs_internal.cuh": "9999e81ae0e203c9"}
 
@@ -488,8 +488,10 @@ def main():
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     n = sum(sc.n for sc in scenes)
     per_g = (240 + 480) * 2 if not sh16 else (48 + 96 + 240) * 2
-    adam_bytes = n * per_g + K * 48 + n * 8 * len(cams)
-    fwd_bytes = n * (48 + (96 if sh16 else 192)) + n * len(cams) * (48 + 16 + 4)
+    # (view, Gaussian) pairs: each view pairs with the Gaussians of its own scene
+    pairs = n * len(cams) if not multi else sum(scenes[c.scene].n for c in cams)
+    adam_bytes = n * per_g + K * 48 + pairs * 8
+    fwd_bytes = n * (48 + (96 if sh16 else 192)) + pairs * (48 + 16 + 4)
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     alu_peak = sm_count * 128 * 2 * 2.070e9 / 1e12
     FLOP_BWD, FLOP_FWD = 90.0, 28.0   # FP32 FLOP (FMA = 2) per evaluated pair
@@ -497,12 +499,15 @@ def main():
     # intersection, 32 B of records read per emitting pair), per radix pass
     # 4 B read (histogram) + 8 B read + 8 B written per intersection, and the
     # last pass's gather of the pair index (4 B read + 4 B written)
-    pairs = n * len(cams) if not multi else sum(scenes[c.scene].n for c in cams)
     npass = 4 + (1 if len(cams) > 1 else 0)
     sort_bytes = pairs * 8 + K * 8 + pairs * 32 + npass * K * 20 + K * 8
     loss_stage = "loss_l1" if args.loss == "l1" else "loss_l1_ssim"
     # image and gradient (FP32 RGB) and the target (FP32 RGB or 8-bit RGBA)
     loss_bytes = px * (12 + 12 + (12 if args.loss == "l1" else 4))
+    # L1 + SSIM is ALU-bound: per pixel and channel, 11 taps of the horizontal
+    # pass (5 moment FMAs + 3 products) and of the vertical pass (5 FMAs), and
+    # 11 taps of both passes of the 3 partials (3 FMAs each): 209 FP32
+    # operations, the window halo not counted
     rooflines = {
         "project_bwd_adam": {"bound": "hbm", "achieved": adam_bytes / (acc["project_bwd_adam"] * 1e-3) / 1e9,
                              "peak": hbm_peak, "unit": "GB/s", "traffic": None},
@@ -514,8 +519,10 @@ def main():
                        "peak": alu_peak, "unit": "TFLOP/s", "traffic": None},
         "bin_sort": {"bound": "hbm", "achieved": sort_bytes / (acc["bin_sort"] * 1e-3) / 1e9, "peak": hbm_peak,
                      "unit": "GB/s", "traffic": None},
-        loss_stage: {"bound": "hbm", "achieved": loss_bytes / (acc[loss_stage] * 1e-3) / 1e9, "peak": hbm_peak,
-                     "unit": "GB/s", "traffic": None},
+        loss_stage: ({"bound": "hbm", "achieved": loss_bytes / (acc[loss_stage] * 1e-3) / 1e9, "peak": hbm_peak,
+                      "unit": "GB/s", "traffic": None} if args.loss == "l1" else
+                     {"bound": "alu", "achieved": px * 3 * 209 * 2 / (acc[loss_stage] * 1e-3) / 1e12,
+                      "peak": alu_peak, "unit": "TFLOP/s", "traffic": None}),
     }
     headline = (args.workload == "batched" and args.n == N_GAUSS and tuple(tile) == (16, 16) and impl == 0
                 and args.loss == "l1")
