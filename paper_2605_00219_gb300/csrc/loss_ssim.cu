@@ -69,9 +69,16 @@ __global__ void __launch_bounds__(256) k_loss_l1_ssim(Views V, const float* __re
 {
     __shared__ float sx[kSsX][kSsX + 1];
     __shared__ float sy[kSsX][kSsX + 1];
-    __shared__ float hm[5][kSsX][kSsQ];
-    __shared__ float abc[3][kSsQ][kSsQ + 1];
-    __shared__ float habc[3][kSsQ][kSsT];
+    // moments and partials interleaved in pairs, so each tap of the next pass
+    // reads them with 64-bit loads: (mu_x, mu_y), (E[x^2], E[y^2]), E[xy];
+    // (A, B), Cc
+    __shared__ float2 hm01[kSsX][kSsQ];
+    __shared__ float2 hm23[kSsX][kSsQ];
+    __shared__ float hm4[kSsX][kSsQ];
+    __shared__ float2 abc01[kSsQ][kSsQ];
+    __shared__ float abc2[kSsQ][kSsQ + 1];
+    __shared__ float2 habc01[kSsQ][kSsT];
+    __shared__ float habc2[kSsQ][kSsT];
     __shared__ float red[2][8];
     __shared__ bool is_last;
 
@@ -118,7 +125,9 @@ __global__ void __launch_bounds__(256) k_loss_l1_ssim(Views V, const float* __re
                 m3 = fmaf(w, b * b, m3);
                 m4 = fmaf(w, a * b, m4);
             }
-            hm[0][r][q] = m0; hm[1][r][q] = m1; hm[2][r][q] = m2; hm[3][r][q] = m3; hm[4][r][q] = m4;
+            hm01[r][q] = make_float2(m0, m1);
+            hm23[r][q] = make_float2(m2, m3);
+            hm4[r][q] = m4;
         }
         __syncthreads();
         // vertical pass, SSIM and its partials at 26 x 26 positions
@@ -128,8 +137,12 @@ __global__ void __launch_bounds__(256) k_loss_l1_ssim(Views V, const float* __re
 #pragma unroll
             for (int k = 0; k <= 2 * kSsR; k++) {
                 const float w = ssim_w(k);
-#pragma unroll
-                for (int j = 0; j < 5; j++) m[j] = fmaf(w, hm[j][qr + k][qc], m[j]);
+                const float2 a = hm01[qr + k][qc], b = hm23[qr + k][qc];
+                m[0] = fmaf(w, a.x, m[0]);
+                m[1] = fmaf(w, a.y, m[1]);
+                m[2] = fmaf(w, b.x, m[2]);
+                m[3] = fmaf(w, b.y, m[3]);
+                m[4] = fmaf(w, hm4[qr + k][qc], m[4]);
             }
             const int x = ox - kSsR + qc, y = oy - kSsR + qr;
             float A = 0.f, B = 0.f, Cc = 0.f;
@@ -145,7 +158,8 @@ __global__ void __launch_bounds__(256) k_loss_l1_ssim(Views V, const float* __re
                 Cc = 2.f * a1 * ib;
                 if (qr >= kSsR && qr < kSsR + kSsT && qc >= kSsR && qc < kSsR + kSsT) ss += s;
             }
-            abc[0][qr][qc] = A; abc[1][qr][qc] = B; abc[2][qr][qc] = Cc;
+            abc01[qr][qc] = make_float2(A, B);
+            abc2[qr][qc] = Cc;
         }
         __syncthreads();
         // horizontal pass of A, B, Cc: 26 rows x 16 columns
@@ -155,11 +169,13 @@ __global__ void __launch_bounds__(256) k_loss_l1_ssim(Views V, const float* __re
 #pragma unroll
             for (int k = 0; k <= 2 * kSsR; k++) {
                 const float w = ssim_w(k);
-                a = fmaf(w, abc[0][r][q + k], a);
-                b = fmaf(w, abc[1][r][q + k], b);
-                d = fmaf(w, abc[2][r][q + k], d);
+                const float2 ab = abc01[r][q + k];
+                a = fmaf(w, ab.x, a);
+                b = fmaf(w, ab.y, b);
+                d = fmaf(w, abc2[r][q + k], d);
             }
-            habc[0][r][q] = a; habc[1][r][q] = b; habc[2][r][q] = d;
+            habc01[r][q] = make_float2(a, b);
+            habc2[r][q] = d;
         }
         __syncthreads();
         // vertical pass at the tile's pixel; combine with the L1 term
@@ -167,9 +183,10 @@ __global__ void __launch_bounds__(256) k_loss_l1_ssim(Views V, const float* __re
 #pragma unroll
         for (int k = 0; k <= 2 * kSsR; k++) {
             const float w = ssim_w(k);
-            wa = fmaf(w, habc[0][pr + k][pc], wa);
-            wb = fmaf(w, habc[1][pr + k][pc], wb);
-            wc = fmaf(w, habc[2][pr + k][pc], wc);
+            const float2 ab = habc01[pr + k][pc];
+            wa = fmaf(w, ab.x, wa);
+            wb = fmaf(w, ab.y, wb);
+            wc = fmaf(w, habc2[pr + k][pc], wc);
         }
         if (pin) {
             const float x = image[3 * ppix + c], y = target_channel(target[ppix], c);
