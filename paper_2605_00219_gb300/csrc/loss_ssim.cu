@@ -67,8 +67,7 @@ __global__ void __launch_bounds__(256) k_loss_l1_ssim(Views V, const float* __re
                                                       float inv_n, float* __restrict__ dl,
                                                       float* __restrict__ part, WsHeader* __restrict__ hdr)
 {
-    __shared__ float sx[kSsX][kSsX + 1];
-    __shared__ float sy[kSsX][kSsX + 1];
+    __shared__ float2 sxy[kSsX][kSsX + 1];   // (x, y) about the shift
     // moments and partials interleaved in pairs, so each tap of the next pass
     // reads them with 64-bit loads: (mu_x, mu_y), (E[x^2], E[y^2]), E[xy];
     // (A, B), Cc
@@ -108,8 +107,7 @@ __global__ void __launch_bounds__(256) k_loss_l1_ssim(Views V, const float* __re
                 a = image[3 * pix + c];
                 b = target_channel(target[pix], c);
             }
-            sx[r][col] = a - shx;
-            sy[r][col] = b - shy;
+            sxy[r][col] = make_float2(a - shx, b - shy);
         }
         __syncthreads();
         // horizontal pass: 5 moments at 36 rows x 26 columns
@@ -118,7 +116,9 @@ __global__ void __launch_bounds__(256) k_loss_l1_ssim(Views V, const float* __re
             float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, m4 = 0.f;
 #pragma unroll
             for (int k = 0; k <= 2 * kSsR; k++) {
-                const float w = ssim_w(k), a = sx[r][q + k], b = sy[r][q + k];
+                const float w = ssim_w(k);
+                const float2 xy = sxy[r][q + k];
+                const float a = xy.x, b = xy.y;
                 m0 = fmaf(w, a, m0);
                 m1 = fmaf(w, b, m1);
                 m2 = fmaf(w, a * a, m2);
