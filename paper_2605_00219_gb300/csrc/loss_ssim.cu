@@ -68,11 +68,9 @@ __global__ void __launch_bounds__(256) k_loss_l1_ssim(Views V, const float* __re
                                                       float* __restrict__ part, WsHeader* __restrict__ hdr)
 {
     __shared__ float2 sxy[kSsX][kSsX + 1];   // (x, y) about the shift
-    // moments and partials interleaved in pairs, so each tap of the next pass
-    // reads them with 64-bit loads: (mu_x, mu_y), (E[x^2], E[y^2]), E[xy];
-    // (A, B), Cc
-    __shared__ float2 hm01[kSsX][kSsQ];
-    __shared__ float2 hm23[kSsX][kSsQ];
+    // moments and partials interleaved, so each tap of the next pass reads
+    // them with vector loads: (mu_x, mu_y, E[x^2], E[y^2]), E[xy]; (A, B), Cc
+    __shared__ float4 hm03[kSsX][kSsQ];
     __shared__ float hm4[kSsX][kSsQ];
     __shared__ float2 abc01[kSsQ][kSsQ];
     __shared__ float abc2[kSsQ][kSsQ + 1];
@@ -125,8 +123,7 @@ __global__ void __launch_bounds__(256) k_loss_l1_ssim(Views V, const float* __re
                 m3 = fmaf(w, b * b, m3);
                 m4 = fmaf(w, a * b, m4);
             }
-            hm01[r][q] = make_float2(m0, m1);
-            hm23[r][q] = make_float2(m2, m3);
+            hm03[r][q] = make_float4(m0, m1, m2, m3);
             hm4[r][q] = m4;
         }
         __syncthreads();
@@ -137,11 +134,11 @@ __global__ void __launch_bounds__(256) k_loss_l1_ssim(Views V, const float* __re
 #pragma unroll
             for (int k = 0; k <= 2 * kSsR; k++) {
                 const float w = ssim_w(k);
-                const float2 a = hm01[qr + k][qc], b = hm23[qr + k][qc];
+                const float4 a = hm03[qr + k][qc];
                 m[0] = fmaf(w, a.x, m[0]);
                 m[1] = fmaf(w, a.y, m[1]);
-                m[2] = fmaf(w, b.x, m[2]);
-                m[3] = fmaf(w, b.y, m[3]);
+                m[2] = fmaf(w, a.z, m[2]);
+                m[3] = fmaf(w, a.w, m[3]);
                 m[4] = fmaf(w, hm4[qr + k][qc], m[4]);
             }
             const int x = ox - kSsR + qc, y = oy - kSsR + qr;
