@@ -487,47 +487,13 @@ def main():
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     n = sum(sc.n for sc in scenes)
-    per_g = (240 + 480) * 2 if not sh16 else (48 + 96 + 240) * 2
-    # (view, Gaussian) pairs: each view pairs with the Gaussians of its own scene
-    pairs = n * len(cams) if not multi else sum(scenes[c.scene].n for c in cams)
-    adam_bytes = n * per_g + K * 48 + pairs * 8
-    fwd_bytes = n * (48 + (96 if sh16 else 192)) + pairs * (48 + 16 + 4)
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     alu_peak = sm_count * 128 * 2 * 2.070e9 / 1e12
-    FLOP_BWD, FLOP_FWD = 90.0, 28.0   # FP32 FLOP (FMA = 2) per evaluated pair
-    # sort: count scan (4 B in, 4 B out per pair), emission (8 B written per
-    # intersection, 32 B of records read per emitting pair), per radix pass
-    # 4 B read (histogram) + 8 B read + 8 B written per intersection, and the
-    # last pass's gather of the pair index (4 B read + 4 B written)
-    npass = 4 + (1 if len(cams) > 1 else 0)
-    sort_bytes = pairs * 8 + K * 8 + pairs * 32 + npass * K * 20 + K * 8
-    loss_stage = "loss_l1" if args.loss == "l1" else "loss_l1_ssim"
-    # image and gradient (FP32 RGB) and the target (FP32 RGB or 8-bit RGBA)
-    loss_bytes = px * (12 + 12 + (12 if args.loss == "l1" else 4))
-    # L1 + SSIM is ALU-bound: per pixel and channel, 11 taps of the horizontal
-    # pass (5 moment FMAs + 3 products) and of the vertical pass (5 FMAs), and
-    # 11 taps of both passes of the 3 partials (3 FMAs each): 209 FP32
-    # operations, the window halo not counted
-    rooflines = {
-        "project_bwd_adam": {"bound": "hbm", "achieved": adam_bytes / (acc["project_bwd_adam"] * 1e-3) / 1e9,
-                             "peak": hbm_peak, "unit": "GB/s", "traffic": None},
-        "project_fwd": {"bound": "hbm", "achieved": fwd_bytes / (acc["project_fwd"] * 1e-3) / 1e9, "peak": hbm_peak,
-                        "unit": "GB/s", "traffic": None},
-        "raster_bwd": {"bound": "alu", "achieved": evaluated * FLOP_BWD / (acc["raster_bwd"] * 1e-3) / 1e12,
-                       "peak": alu_peak, "unit": "TFLOP/s", "traffic": None},
-        "raster_fwd": {"bound": "alu", "achieved": evaluated * FLOP_FWD / (acc["raster_fwd"] * 1e-3) / 1e12,
-                       "peak": alu_peak, "unit": "TFLOP/s", "traffic": None},
-        "bin_sort": {"bound": "hbm", "achieved": sort_bytes / (acc["bin_sort"] * 1e-3) / 1e9, "peak": hbm_peak,
-                     "unit": "GB/s", "traffic": None},
-        loss_stage: ({"bound": "hbm", "achieved": loss_bytes / (acc[loss_stage] * 1e-3) / 1e9, "peak": hbm_peak,
-                      "unit": "GB/s", "traffic": None} if args.loss == "l1" else
-                     {"bound": "alu", "achieved": px * 3 * 209 * 2 / (acc[loss_stage] * 1e-3) / 1e12,
-                      "peak": alu_peak, "unit": "TFLOP/s", "traffic": None}),
-    }
+    work = stage_work([sc.n for sc in scenes], [c.scene for c in cams], K, evaluated, px, sh16, args.loss)
+    rooflines = stage_rooflines(work, acc, hbm_peak, alu_peak)
     headline = (args.workload == "batched" and args.n == N_GAUSS and tuple(tile) == (16, 16) and impl == 0
                 and args.loss == "l1")
     for k, r in rooflines.items():
-        r["frac"] = r["achieved"] / r["peak"]
         r["traffic"] = _measured_traffic(k, headline)
     dom = max(rooflines, key=lambda k: acc[k])
     roof = dict(rooflines[dom])
@@ -598,6 +564,67 @@ def main():
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+FLOP_BWD, FLOP_FWD = 90.0, 28.0   # FP32 FLOP (FMA = 2) per evaluated pair
+SSIM_OPS = 209                    # FP32 operations per pixel and channel of the L1 + SSIM loss
+
+
+def stage_work(scene_sizes, view_scenes, K, evaluated, px, sh16, loss="l1"):
+    """Algorithmic work of each stage of one step, as (bound, amount): bytes
+    for the HBM-bound stages, FP32 FLOP for the ALU-bound ones.
+
+    scene_sizes: Gaussians per scene; view_scenes: the scene of each view (a
+    view pairs with the Gaussians of its own scene); K: intersections;
+    evaluated: pairs within every pixel's n_last; px: pixels of all views."""
+    n = sum(scene_sizes)
+    pairs = sum(scene_sizes[s] for s in view_scenes)
+    # projection: parameters (48 B) and SH (96 B BF16, 192 B FP32) read once,
+    # 68 B written per pair (record, binning record, count)
+    fwd_bytes = n * (48 + (96 if sh16 else 192)) + pairs * (48 + 16 + 4)
+    # fused Adam: parameters, SH and both moments read and written, a 48-byte
+    # gradient record per intersection, a count and an offset per pair
+    per_g = (240 + 480) * 2 if not sh16 else (48 + 96 + 240) * 2
+    adam_bytes = n * per_g + K * 48 + pairs * 8
+    # sort: count scan (4 B in, 4 B out per pair), emission (8 B written per
+    # intersection, 32 B of records read per emitting pair), per radix pass
+    # 4 B read (histogram) + 8 B read + 8 B written per intersection, and the
+    # last pass's gather of the pair index (4 B read + 4 B written)
+    npass = 4 + (1 if len(view_scenes) > 1 else 0)
+    sort_bytes = pairs * 8 + K * 8 + pairs * 32 + npass * K * 20 + K * 8
+    work = {
+        "project_bwd_adam": ("hbm", adam_bytes),
+        "project_fwd": ("hbm", fwd_bytes),
+        "raster_bwd": ("alu", evaluated * FLOP_BWD),
+        "raster_fwd": ("alu", evaluated * FLOP_FWD),
+        "bin_sort": ("hbm", sort_bytes),
+    }
+    if loss == "l1":
+        # image and gradient (FP32 RGB) and the FP32 RGB target
+        work["loss_l1"] = ("hbm", px * (12 + 12 + 12))
+    else:
+        # ALU-bound: per pixel and channel, 11 taps of the horizontal pass
+        # (5 moment FMAs + 3 products) and of the vertical pass (5 FMAs), and
+        # 11 taps of both passes of the 3 partials (3 FMAs each): 209 FP32
+        # operations, the window halo not counted
+        work["loss_l1_ssim"] = ("alu", px * 3 * SSIM_OPS * 2)
+    return work
+
+
+def stage_rooflines(work, stage_ms, hbm_peak_gbs, alu_peak_tflops):
+    """Roofline record of each stage: its algorithmic work (stage_work) over
+    its measured time in ms, against the HBM or FP32 peak."""
+    out = {}
+    for k, (bound, amount) in work.items():
+        sec = stage_ms[k] * 1e-3
+        if bound == "hbm":
+            r = {"bound": "hbm", "achieved": amount / sec / 1e9, "peak": hbm_peak_gbs, "unit": "GB/s"}
+        else:
+            r = {"bound": "alu", "achieved": amount / sec / 1e12, "peak": alu_peak_tflops, "unit": "TFLOP/s"}
+        r["frac"] = r["achieved"] / r["peak"]
+        r["traffic"] = None
+        out[k] = r
+    return out
 
 
 def launches_per_step(plan) -> int:

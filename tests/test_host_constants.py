@@ -6,6 +6,8 @@
   profiles/).
 - The compile-time window taps of the L1 + SSIM kernel are the oracle's
   normalised Gaussian window (11 taps, sigma 1.5) rounded to FP32.
+- The algorithmic work per stage behind the bench's rooflines, and the
+  roofline records built from it.
 """
 import os
 import re
@@ -47,3 +49,45 @@ def test_ssim_window_constants_are_the_oracle_window_in_fp32(orc):
     ref = orc.ssim_window(11, 1.5).astype(np.float32)
     assert np.array_equal(taps, ref), (taps, ref)
     assert abs(float(taps.astype(np.float64).sum()) - 1.0) < 1e-7
+
+
+def test_stage_work_headline_figures():
+    """Algorithmic bytes of the 3M-Gaussian, 4 x 1920x1080 BF16 step (the
+    figures of the launch-list profile's bandwidth table)."""
+    K, px = 17_269_857, 4 * 1920 * 1080
+    w = bench.stage_work([3_000_000], [0, 0, 0, 0], K, 3_715_163_821, px, sh16=True)
+    pairs = 12_000_000
+    assert w["project_fwd"] == ("hbm", 3_000_000 * 144 + pairs * 68)
+    assert abs(w["project_fwd"][1] / 1e9 - 1.248) < 5e-4
+    assert abs(w["project_bwd_adam"][1] / 1e9 - 3.229) < 5e-4
+    assert abs(w["bin_sort"][1] / 1e9 - 2.483) < 5e-4
+    assert w["loss_l1"] == ("hbm", px * 36)
+    assert w["raster_bwd"] == ("alu", 3_715_163_821 * 90.0)
+    assert set(w) == {"project_fwd", "bin_sort", "raster_fwd", "loss_l1", "raster_bwd", "project_bwd_adam"}
+
+
+def test_stage_work_counts_each_views_own_scene():
+    """Eight scenes with two views each: a view pairs only with the Gaussians
+    of its own scene (24M pairs, not 12M x 16)."""
+    sizes = [500_000, 500_000, 750_000, 750_000, 1_000_000, 1_250_000, 1_250_000, 6_000_000]
+    views = [s for s in range(8) for _ in range(2)]
+    w = bench.stage_work(sizes, views, 30_000_000, 1, 1, sh16=True)
+    n = sum(sizes)
+    assert w["project_fwd"][1] == n * 144 + 2 * n * 68
+    assert w["project_bwd_adam"][1] == n * 768 + 30_000_000 * 48 + 2 * n * 8
+
+
+def test_stage_work_ssim_loss_is_alu_work():
+    w = bench.stage_work([1000], [0], 10, 10, 100, sh16=False, loss="l1_ssim")
+    assert "loss_l1" not in w and w["loss_l1_ssim"] == ("alu", 100 * 3 * 209 * 2)
+    assert w["project_fwd"][1] == 1000 * 240 + 1000 * 68     # FP32 SH
+
+
+def test_stage_rooflines_units_and_fractions():
+    work = {"project_fwd": ("hbm", 1.248e9), "raster_bwd": ("alu", 3.7e9 * 90.0)}
+    r = bench.stage_rooflines(work, {"project_fwd": 0.729, "raster_bwd": 5.273}, 6777.0, 80.54784)
+    assert r["project_fwd"]["unit"] == "GB/s" and abs(r["project_fwd"]["achieved"] - 1.248e9 / 0.729e-3 / 1e9) < 1e-9
+    assert abs(r["project_fwd"]["frac"] - r["project_fwd"]["achieved"] / 6777.0) < 1e-12
+    assert r["raster_bwd"]["bound"] == "alu" and r["raster_bwd"]["unit"] == "TFLOP/s"
+    assert abs(r["raster_bwd"]["achieved"] - 63.15) < 0.01
+    assert all(x["traffic"] is None for x in r.values())
