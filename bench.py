@@ -62,7 +62,7 @@ LR = (1.6e-4 * 30.0, 1e-3, 5e-3, 5e-2, 2.5e-3, 2.5e-3 / 20)   # mean lr scaled b
 # the kernel sources hash to the recorded prefixes.
 MEASURED_TRAFFIC = {
     "raster_bwd": (3637729536, {"raster_bwd.cu": "4e93ffce6fe0f042"}),
-    "project_bwd_adam": (3304814080, {"project_bwd_adam.cu": "92b38a842cbd145f"}),
+    "project_bwd_adam": (3304814080, {"project_bwd_adam.cu": "542274191b8e2688"}),
     "raster_fwd": (1685828096, {"raster_fwd.cu": "eb796557894a3910"}),
     "project_fwd": (1259325184, {"project_fwd.cu": "1653c497900428cc"}),
     "bin_sort": (3072882176, {"bin_sort.cu": "49d33c937ce3d28f"}),

@@ -4,9 +4,10 @@
 // One thread per Gaussian.  For every view of its scene the thread sums the
 // Gaussian's intersection gradient records (contiguous at its emission
 // offset), back-propagates through the SH colour (with the clamp), the view
-// direction, the conic inverse, the EWA Jacobian (with the FOV clamp), the
-// camera transform and the covariance (scale, quaternion with its
-// normalisation), accumulating the parameter gradient in registers.  Then one
+// direction, the conic inverse, the EWA Jacobian (with the FOV clamp) and the
+// camera transform, accumulating dL/dmean and the symmetric dL/dSigma of the
+// 3D covariance in registers; the covariance backward (scale, quaternion with
+// its normalisation) then runs once on the sum over views.  Then one
 // Adam step per parameter group; scale and opacity move to log / logit space
 // inside the optimiser and are written back activated, SH degree 0 and
 // degrees 1-3 take their own learning rates.  No gradient tensor is stored.
@@ -309,8 +310,8 @@ __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefe
 // Phase 1 (one thread per Gaussian): sum the intersection records per view,
 // back-propagate through projection and colour, apply Adam to mean,
 // quaternion and (log-scale, logit-opacity); the 48 SH gradients accumulate
-// in the thread's own column of shared memory.  Phase 2: Adam on the SH
-// chunks, streaming coefficients and moments with few live registers.
+// in the thread's own row of shared memory.  Phase 2: Adam on the SH chunks,
+// streaming coefficients and moments with few live registers.
 template <bool SH16, bool MOM16>
 __global__ void __launch_bounds__(kPbaThreads, 4) k_project_bwd_adam(Views V, Scenes S, const float* __restrict__ cams,
                                                                   const uint32_t* __restrict__ count,
