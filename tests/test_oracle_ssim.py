@@ -70,3 +70,46 @@ def test_rgba8_target():
     from oracle import oracle as orc
     t = np.array([[[255, 0, 51, 7]]], np.uint8)
     np.testing.assert_allclose(orc.rgba8_to_float(t), [[[1.0, 0.0, 0.2]]])
+
+
+def test_loss_equals_direct_window_sums():
+    """The loss against SSIM written out with plain loops: per pixel and
+    channel, sums over the 11x11 window of w_a w_b times x, y, x^2, y^2, xy
+    with zero outside the image, w_k = exp(-(k - 5)^2 / (2 * 1.5^2)) / sum;
+    SSIM = (2 mx my + C1)(2 cov + C2) / ((mx^2 + my^2 + C1)(vx + vy + C2));
+    the mean over 3 x all pixels of two ragged views."""
+    import math
+    from oracle import oracle as orc
+    rng = np.random.default_rng(7)
+    xs = [rng.uniform(0, 1, size=(9, 7, 3)), rng.uniform(0, 1, size=(5, 12, 3))]
+    ys = [rng.uniform(0, 1, size=x.shape) for x in xs]
+    e = [math.exp(-(k - 5) ** 2 / (2 * 1.5 ** 2)) for k in range(11)]
+    w = [v / sum(e) for v in e]
+    C1, C2 = 0.01 ** 2, 0.03 ** 2
+    ssim_sum = l1_sum = 0.0
+    cnt = 0
+    for x, y in zip(xs, ys):
+        H, W, _ = x.shape
+        for c in range(3):
+            for i in range(H):
+                for j in range(W):
+                    m = [0.0] * 5
+                    for a in range(11):
+                        for b in range(11):
+                            ii, jj = i + a - 5, j + b - 5
+                            if 0 <= ii < H and 0 <= jj < W:
+                                ww = w[a] * w[b]
+                                xv, yv = float(x[ii, jj, c]), float(y[ii, jj, c])
+                                m[0] += ww * xv
+                                m[1] += ww * yv
+                                m[2] += ww * xv * xv
+                                m[3] += ww * yv * yv
+                                m[4] += ww * xv * yv
+                    mx, my = m[0], m[1]
+                    vx, vy, cov = m[2] - mx * mx, m[3] - my * my, m[4] - mx * my
+                    ssim_sum += (2 * mx * my + C1) * (2 * cov + C2) / ((mx * mx + my * my + C1) * (vx + vy + C2))
+                    l1_sum += abs(float(x[i, j, c]) - float(y[i, j, c]))
+                    cnt += 1
+    for lam in (0.0, 0.2, 1.0):
+        loss, _ = orc.l1_ssim_loss_grad(xs, ys, lam)
+        assert loss == pytest.approx((1 - lam) * l1_sum / cnt + lam * (1 - ssim_sum / cnt), rel=1e-12)
