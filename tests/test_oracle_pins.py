@@ -509,6 +509,31 @@ def test_adam_step1_closed_form(orc):
     np.testing.assert_allclose(th1, th - lr[grp][None, :] * g / (np.abs(g) + 1e-15), rtol=1e-12, atol=1e-15)
 
 
+def test_adam_five_steps_equal_torch_adam(orc):
+    """Five Adam steps with changing gradients equal torch.optim.Adam (FP64,
+    one parameter group per learning-rate group): bias corrections and the
+    moment recurrences past the first step."""
+    import torch
+    rng = np.random.default_rng(5)
+    th0 = rng.normal(size=(6, 59))
+    grads = [rng.normal(size=(6, 59)) * 10.0 ** rng.uniform(-6, 1, size=(6, 59)) for _ in range(5)]
+    lr = np.array([1e-3, 2e-3, 3e-3, 4e-3, 5e-3, 6e-3])
+    grp = np.array([0] * 3 + [1] * 4 + [2] * 3 + [3] + [4] * 3 + [5] * 45)
+    th, m, v = th0.copy(), np.zeros_like(th0), np.zeros_like(th0)
+    for t, g in enumerate(grads, 1):
+        orc.adam64(th, m, v, g.copy(), lr, t)
+    cols = [np.nonzero(grp == k)[0] for k in range(6)]
+    params = [torch.tensor(th0[:, c], dtype=torch.float64, requires_grad=True) for c in cols]
+    opt = torch.optim.Adam([{"params": [p], "lr": float(lr[k])} for k, p in enumerate(params)],
+                           betas=(0.9, 0.999), eps=1e-15)
+    for g in grads:
+        for k, p in enumerate(params):
+            p.grad = torch.tensor(g[:, cols[k]], dtype=torch.float64)
+        opt.step()
+    for k, p in enumerate(params):
+        np.testing.assert_allclose(th[:, cols[k]], p.detach().numpy(), rtol=1e-10, atol=1e-14)
+
+
 def test_l1_gradient_closed_form(orc):
     a = np.array([[[0.5, 0.2, 0.0]]]); t = np.array([[[0.4, 0.2, 0.1]]])
     loss, (g,) = orc.l1_loss_grad([a], [t])
