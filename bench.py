@@ -56,10 +56,9 @@ PX_1080 = 1920 * 1080
 LR = (1.6e-4 * 30.0, 1e-3, 5e-3, 5e-2, 2.5e-3, 2.5e-3 / 20)   # mean lr scaled by the 30 m scene extent
 
 # DRAM bytes (read + write) of one launch (for the sort: of its launches in
-# one step), from one ncu capture of the headline workload (batched BF16,
-# 4 x 1920x1080, 16x16 tiles, pixel-parallel raster backward;
-# profiles/step_batched_bf16_3M_4x1080p_launch_list.md).  Valid only while
-# the kernel sources hash to the recorded prefixes.
+# one step), from ncu DRAM counters of the headline step (3M Gaussians, BF16,
+# 4 x 1920x1080, 16x16 tiles, pixel-parallel raster backward).  Valid only
+# while the kernel sources hash to the recorded prefixes.
 MEASURED_TRAFFIC = {
     "raster_bwd": (3637729536, {"raster_bwd.cu": "4e93ffce6fe0f042"}),
     "project_bwd_adam": (3304814080, {"project_bwd_adam.cu": "542274191b8e2688"}),
@@ -109,8 +108,6 @@ def _args():
                     help="photometric loss of the step: L1 against FP32 targets, or (1 - lambda) L1 + lambda "
                          "(1 - SSIM) with lambda = 0.2 against 8-bit RGBA targets (fixed tile and implementation; "
                          "no plain, PSNR or CPU legs)")
-    ap.add_argument("--cpu-sample-tiles", type=int, default=16,
-                    help="oracle renders 1 in this many tiles (bounded CPU sample)")
     return ap.parse_args()
 
 
@@ -146,37 +143,53 @@ def _views(workload):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms from the
+    moment the first sample has arrived (entered before the warm-up, left
+    after the timed region)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
-        self.gpu, self.proc, self.out = gpu_index, None, None
+    def __init__(self, gpu_index: int, period_ms: int = 50):
+        self.gpu, self.period, self.proc, self.lines = gpu_index, period_ms, None, []
+        self.reader = None
 
     def __enter__(self):
+        import threading
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.period)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+            return self
+        first = threading.Event()
+
+        def read():
+            for line in self.proc.stdout:
+                self.lines.append(line)
+                first.set()
+        self.reader = threading.Thread(target=read, daemon=True)
+        self.reader.start()
+        first.wait(5.0)
         return self
 
     def __exit__(self, *exc):
         if self.proc is not None:
             self.proc.terminate()
             try:
-                self.out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
-                self.out, _ = self.proc.communicate()
+                self.proc.wait()
+            if self.reader is not None:
+                self.reader.join(timeout=5)
         return False
 
     def summary(self):
         rows = []
-        for line in (self.out or "").strip().splitlines():
+        for line in self.lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -189,82 +202,104 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
         return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(rows), "period_ms": self.period,
+                "window": "warm-up and timed replays"}
 
 
 # ----------------------------------------------------------------------------
 # CPU oracle (bounded sample)
 # ----------------------------------------------------------------------------
 
-def run_cpu_oracle(scene, targets, cams, sample_tiles: int):
-    """One oracle step over `cams` on a bounded sample: projection, FP32
-    binning and Adam over everything; compositing and its backward on 1 in
-    `sample_tiles` tiles.  Returns (seconds for the full step with the
-    tile-bound part scaled up, details)."""
+def _oracle_target(orc, tscene, cam):
+    """Target image of one view rendered by the oracle from the target scene
+    (no input of the oracle comes from the CUDA path)."""
+    return orc.render64(cam, orc.project64(orc.Params64.from_scene(tscene), cam), orc.bin32(tscene, cam)).image
+
+
+def time_oracle_step(orc, scene, cams, targets, lr):
+    """Wall-clock seconds of one full, un-sampled oracle step over `cams`
+    (FP32 binning, FP64 projection, compositing, L1 gradient, compositing and
+    projection backward, one Adam update over every Gaussian)."""
+    t0 = time.perf_counter()
+    r = orc.step(scene, cams, targets, lr)
+    return time.perf_counter() - t0, sum(x.blended for x in r.renders)
+
+
+def cpu_baseline_leg(scene, tscene, cams):
+    """The oracle timed on this host: one full step over the first view of
+    the measured workload (all Gaussians, every tile), on all cores; and the
+    tiny and mid-size configurations (2,000 Gaussians at 128x128; 200k at
+    1280x720, one orbit view per step) on one thread and on all cores."""
     from oracle import oracle as orc
-    t_fixed = t_tiles = 0.0
-    tiles = sampled = 0
-    p = orc.Params64.from_scene(scene)
-    grad = np.zeros((scene.n, orc.NTHETA))
-    total_px = sum(c.width * c.height for c in cams)
-    for cam, tgt in zip(cams, targets):
-        t0 = time.perf_counter()
-        b = orc.bin32(scene, cam)
-        P = orc.project64(p, cam)
-        t1 = time.perf_counter()
-        keep = np.zeros(b.ranges.shape[0], bool)
-        keep[::sample_tiles] = True
-        bs = orc.Binning(b.count, b.bin, b.mant, b.offset, b.keys_emit, b.gidx_emit, b.keys, b.gidx, b.perm,
-                         np.where(keep[:, None], b.ranges, 0))
-        r = orc.render64(cam, P, bs)
-        dl = np.sign(r.image - tgt) / (3 * total_px)
-        g2 = orc.raster_bwd64(cam, P, bs, dl)
-        t2 = time.perf_counter()
-        orc.project_bwd64(p, cam, P, g2, out=grad)
-        t3 = time.perf_counter()
-        t_fixed += (t1 - t0) + (t3 - t2)
-        t_tiles += t2 - t1
-        tiles += int(keep.size)
-        sampled += int(keep.sum())
-    t4 = time.perf_counter()
-    th = p.theta()
-    orc.adam64(th, np.zeros_like(th), np.zeros_like(th), grad, LR, 1)
-    t_fixed += time.perf_counter() - t4
-    full = t_fixed + t_tiles * sample_tiles
-    return full, {"measured_s": t_fixed + t_tiles, "tiles_sampled": sampled, "tiles": tiles}
+    from paper_2605_00219_gb300 import synth
+    orc.build()
+    cores = orc.set_threads(os.cpu_count() or 1)
+    cam = cams[0]
+    tgt = _oracle_target(orc, tscene, cam)
+    t, blended = time_oracle_step(orc, scene, [cam], [tgt], LR)
+    out = {"value": 1.0 / t, "unit": "view-steps/s", "cores": cores, "kind": "oracle",
+           "sample": f"one full oracle step over 1 of the {len(cams)} views ({cam.width}x{cam.height}, all "
+                     f"{scene.n} Gaussians, every tile, L1 against an oracle-rendered target, Adam over every "
+                     f"Gaussian): {t:.1f} s measured, not scaled",
+           "blended_pairs_per_s": blended / t, "configs": {}}
+    small = {"tiny: 2,000 Gaussians, 128x128": synth.tiny_workload(0),
+             "mid: 200k Gaussians, 1280x720": synth.mid_workload(0)}
+    for name, (sc, tsc, cs) in small.items():
+        c = cs[0]
+        tg = _oracle_target(orc, tsc, c)
+        lr = (1e-3,) * 6 if sc.n < 10000 else LR
+        row = {}
+        for label, threads in (("1_thread", 1), ("all_cores", cores)):
+            orc.set_threads(threads)
+            reps = 5 if sc.n < 10000 else 1
+            best = min(time_oracle_step(orc, sc, [c], [tg], lr)[0] for _ in range(reps))
+            row[label] = {"s_per_step": best, "steps_per_s": 1.0 / best, "threads": threads}
+        out["configs"][name] = row
+    orc.set_threads(cores)
+    return out
 
 
 def reference_arm(args):
+    """The oracle on this host's cores, as the reference arm: each step is one
+    full, un-sampled oracle step over one view of the workload (rotating
+    through its views), against oracle-rendered targets from the same target
+    scene.  A step takes tens of seconds, so at most 3 timed steps and 1
+    warm-up step run; the line reports the counts that ran."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
     from oracle import oracle as orc
     from paper_2605_00219_gb300 import synth
     orc.build()
+    cores = orc.set_threads(os.cpu_count() or 1)
     scene = synth.large_scene(0, args.n)
+    tscene = synth.perturbed(scene, 1)
     cams = _views(args.workload)
-    targets = [np.zeros((c.height, c.width, 3)) for c in cams]
     steps = max(1, min(args.steps, 3))
     warm = min(args.warmup, 1)
-    times = []
-    for i in range(warm + steps):
-        t, info = run_cpu_oracle(scene, targets, cams, args.cpu_sample_tiles)
+    used = [cams[i % len(cams)] for i in range(warm + steps)]
+    targets = {id(c): _oracle_target(orc, tscene, c) for c in used}
+    times, blended = [], 0
+    for i, c in enumerate(used):
+        t, b = time_oracle_step(orc, scene, [c], [targets[id(c)]], LR)
         if i >= warm:
             times.append(t)
+            blended += b
     mean = sum(times) / len(times)
-    value = len(cams) / mean
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
+    value = 1.0 / mean
+    sample = (f"{steps} timed and {warm} warm-up steps (of the requested {args.steps} and {args.warmup}); each "
+              f"one full oracle step over one of the {len(cams)} views, all {scene.n} Gaussians, every tile, "
+              f"not scaled")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "view-steps/s", "n_gpus": args.gpus,
             "steps": steps, "warmup": warm, "ms_per_step": mean * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"{args.workload}: {args.n / 1e6:.3g}M Gaussians, views "
-                                   f"{[f'{c.width}x{c.height}' for c in cams]}, FP64 CPU oracle; value in "
-                                   "view-steps/s", "global_batch": len(cams), "seq_len": 0,
+                                   f"{[f'{c.width}x{c.height}' for c in cams]}, one view per oracle step; FP64 "
+                                   "CPU oracle; value in view-steps/s", "global_batch": 1, "seq_len": 0,
                        "parallelism": "none"},
-            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"compositing and its backward on 1 in {args.cpu_sample_tiles} tiles, "
-                                       "scaled to the full images; projection, binning and Adam over all "
-                                       "Gaussians"},
-            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "cpu_baseline": {"value": value, "unit": "view-steps/s", "cores": cores, "kind": "oracle",
+                             "sample": sample, "blended_pairs_per_s": blended / sum(times)},
+            "e2e": {"value": value, "unit": "view-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -427,17 +462,17 @@ def main():
         tr.step(0)
         tune_info = None
     tr.capture()
-    for _ in range(args.warmup):
-        tr.replay()
-    torch.cuda.synchronize()
-    st = tr.stats()
-    if st.status:
-        raise RuntimeError(f"device status {st.status:#x} (k_required={st.k_required}, capacity={st.k_capacity})")
-
-    if ws > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
     with ClockSampler(local) as clk:
+        for _ in range(args.warmup):
+            tr.replay()
+        torch.cuda.synchronize()
+        st = tr.stats()
+        if st.status:
+            raise RuntimeError(f"device status {st.status:#x} (k_required={st.k_required}, "
+                               f"capacity={st.k_capacity})")
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
         ms = _time_replays(torch, tr, args.steps, stream)
     if ws > 1:
         ms = max_over_ranks(ms, "cuda")
@@ -489,7 +524,8 @@ def main():
     n = sum(sc.n for sc in scenes)
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     alu_peak = sm_count * 128 * 2 * 2.070e9 / 1e12
-    work = stage_work([sc.n for sc in scenes], [c.scene for c in cams], K, evaluated, px, sh16, args.loss)
+    work = stage_work([sc.n for sc in scenes], [c.scene for c in cams], K, evaluated, blended, px,
+                      int(tr.plan.tiles), sh16, args.loss)
     rooflines = stage_rooflines(work, acc, hbm_peak, alu_peak)
     headline = (args.workload == "batched" and args.n == N_GAUSS and tuple(tile) == (16, 16) and impl == 0
                 and args.loss == "l1")
@@ -501,19 +537,7 @@ def main():
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        from oracle import oracle as orc
-        orc.build()
-        tg = []
-        o = 0
-        tnp = targets.cpu().numpy().astype(np.float64)
-        for c in cams:
-            tg.append(tnp[o:o + c.width * c.height].reshape(c.height, c.width, 3))
-            o += c.width * c.height
-        t_full, info = run_cpu_oracle(scene, tg, cams, args.cpu_sample_tiles)
-        cpu = {"value": nviews / t_full, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"one oracle step over the same views: projection, binning and Adam over all {n} "
-                         f"Gaussians, compositing and its backward on {info['tiles_sampled']} of {info['tiles']} "
-                         f"tiles, scaled to the full images ({info['measured_s']:.1f} s measured)"}
+        cpu = cpu_baseline_leg(scene, tscene, cams)
 
     if rank == 0:
         value = whole_job_rate(ws, nviews, ms)
@@ -528,13 +552,15 @@ def main():
                ", whole step in one CUDA graph; value = " + \
                f"view-steps/s ({nviews} views per step x steps/s; {equiv:.3f} 1080p-equivalents of pixels per step)"
         line = {
-            "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
+            "metric": METRIC, "value": value, "unit": "view-steps/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": desc, "global_batch": ws * len(cams), "seq_len": 0,
                        "parallelism": f"replicas{ws}" if ws > 1 else "none",
-                       "l2": "inputs larger than L2 (no flush)"},
-            "e2e": {"value": ws * nviews * 1e3 / e2e_ms, "unit": "steps/s", "h2d_bytes_per_step": int(h2d),
+                       "l2": "inputs larger than L2 (no flush)",
+                       "storage": "BF16 SH and Adam moments, FP32 geometry" if sh16 else "FP32",
+                       "views_per_step": nviews},
+            "e2e": {"value": ws * nviews * 1e3 / e2e_ms, "unit": "view-steps/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": int(args.steps * launches_per_step(tr.plan)),
             "roofline": roof,
@@ -551,6 +577,9 @@ def main():
             "stage_ms": acc,
             "intersections": K,
             "evaluated_pairs": evaluated,
+            "blended_pairs": blended,
+            "tiles": int(tr.plan.tiles),
+            "pixels": int(px),
             "blended_pairs_per_s": blended * 1e3 / ms,
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
@@ -566,37 +595,53 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-FLOP_BWD, FLOP_FWD = 90.0, 28.0   # FP32 FLOP (FMA = 2) per evaluated pair
+# FP32 operations per pair of the raster kernels.  Every pair inside a
+# pixel's n_last is evaluated (pixel offset, exponent, the 3-sigma and 1/255
+# tests: 14 operations and one ex2); a blended pair costs more on top: the
+# forward's compensated transmittance product, stop test and colour FMAs (13),
+# the backward's compensated division, dL/dalpha and the nine gradient terms
+# with their accumulation (31, the rest of the backward's 45 per pair).  An
+# operation occupies one FP32-pipe lane slot; it is counted as 2 FLOP, like
+# the FMA in the peak (SMs x 128 lanes x 2 x clock).
+OPS_TEST, OPS_BLEND_FWD, OPS_BLEND_BWD = 14, 13, 31
 SSIM_OPS = 209                    # FP32 operations per pixel and channel of the L1 + SSIM loss
 
 
-def stage_work(scene_sizes, view_scenes, K, evaluated, px, sh16, loss="l1"):
+def stage_work(scene_sizes, view_scenes, K, evaluated, blended, px, tiles, sh16, loss="l1"):
     """Algorithmic work of each stage of one step, as (bound, amount): bytes
-    for the HBM-bound stages, FP32 FLOP for the ALU-bound ones.
+    for the HBM-bound stages, FP32 FLOP (2 per operation) for the ALU-bound
+    ones.  Per-unit figures are the method's, not this layout's: padding,
+    the separate binning record and record gathers wider than the data are
+    not counted.
 
     scene_sizes: Gaussians per scene; view_scenes: the scene of each view (a
     view pairs with the Gaussians of its own scene); K: intersections;
-    evaluated: pairs within every pixel's n_last; px: pixels of all views."""
+    evaluated: pairs within every pixel's n_last; blended: pairs composited;
+    px: pixels of all views; tiles: tiles of all views."""
     n = sum(scene_sizes)
     pairs = sum(scene_sizes[s] for s in view_scenes)
-    # projection: parameters (48 B) and SH (96 B BF16, 192 B FP32) read once,
-    # 68 B written per pair (record, binning record, count)
-    fwd_bytes = n * (48 + (96 if sh16 else 192)) + pairs * (48 + 16 + 4)
-    # fused Adam: parameters, SH and both moments read and written, a 48-byte
-    # gradient record per intersection, a count and an offset per pair
-    per_g = (240 + 480) * 2 if not sh16 else (48 + 96 + 240) * 2
-    adam_bytes = n * per_g + K * 48 + pairs * 8
-    # sort: count scan (4 B in, 4 B out per pair), emission (8 B written per
-    # intersection, 32 B of records read per emitting pair), per radix pass
-    # 4 B read (histogram) + 8 B read + 8 B written per intersection, and the
-    # last pass's gather of the pair index (4 B read + 4 B written)
+    # projection: parameters read once per step for all views (44 B of
+    # geometry + 48 SH coefficients: 236 B FP32, 140 B with BF16 SH); 48 B
+    # written per (view, Gaussian) pair (mean, conic, opacity, colour, depth,
+    # tile count)
+    fwd_bytes = n * (140 if sh16 else 236) + pairs * 48
+    # fused Adam: the 59 parameters and both moments read and written
+    # (2 x (236 + 472) = 1416 B FP32; 2 x (140 + 236) = 752 B with BF16 SH
+    # and moments), a 36-byte gradient (9 floats) read per intersection, and
+    # each pair's count and offset
+    adam_bytes = n * (752 if sh16 else 1416) + K * 36 + pairs * 8
+    # sort: the count scan (4 B in, 4 B out per pair), emission (count and
+    # offset read per pair, key and value written per intersection), one key
+    # and value read and written per radix pass (4 digit passes of the 32-bit
+    # key, one more ordering the views when there are several), the ranges
+    # (one key read per intersection, 8 B written per tile)
     npass = 4 + (1 if len(view_scenes) > 1 else 0)
-    sort_bytes = pairs * 8 + K * 8 + pairs * 32 + npass * K * 20 + K * 8
+    sort_bytes = pairs * 8 + pairs * 8 + K * 8 + npass * K * 16 + K * 4 + tiles * 8
     work = {
         "project_bwd_adam": ("hbm", adam_bytes),
         "project_fwd": ("hbm", fwd_bytes),
-        "raster_bwd": ("alu", evaluated * FLOP_BWD),
-        "raster_fwd": ("alu", evaluated * FLOP_FWD),
+        "raster_bwd": ("alu", 2.0 * (evaluated * OPS_TEST + blended * OPS_BLEND_BWD)),
+        "raster_fwd": ("alu", 2.0 * (evaluated * OPS_TEST + blended * OPS_BLEND_FWD)),
         "bin_sort": ("hbm", sort_bytes),
     }
     if loss == "l1":

@@ -28,6 +28,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_PSTRIDE 24     /* doubles per projected Gaussian record */
 #define ORC_NTHETA 59      /* optimised scalars per Gaussian */
@@ -856,4 +859,18 @@ void orc_adam64(int64_t n, double* theta, double* m, double* v, const double* gr
             theta[i] -= lr[grp] * mh / (sqrt(vh) + eps);
         }
     }
+}
+
+/* Thread count of the OpenMP loops above, for timing the oracle on one core
+ * or on all of them; no result depends on it.  n <= 0 leaves it unchanged.
+ * Returns the count in effect. */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }

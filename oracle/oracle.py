@@ -92,8 +92,16 @@ def lib():
         L.orc_project_bwd64.restype = None
         L.orc_adam64.argtypes = [i64, vp, vp, vp, vp, vp, dbl, dbl, dbl, i32]
         L.orc_adam64.restype = None
+        L.orc_set_threads.argtypes = [i32]
+        L.orc_set_threads.restype = i32
         _lib = L
     return _lib
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads of the oracle's parallel loops (0: leave as is); returns the
+    count in effect.  For timing only: results do not depend on it."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 def make_cam(cam, tile_w: int = 16, tile_h: int = 16) -> OrcCam:

@@ -52,17 +52,23 @@ def test_ssim_window_constants_are_the_oracle_window_in_fp32(orc):
 
 
 def test_stage_work_headline_figures():
-    """Algorithmic bytes of the 3M-Gaussian, 4 x 1920x1080 BF16 step (the
-    figures of the launch-list profile's bandwidth table)."""
-    K, px = 17_269_857, 4 * 1920 * 1080
-    w = bench.stage_work([3_000_000], [0, 0, 0, 0], K, 3_715_163_821, px, sh16=True)
+    """Algorithmic work of the 3M-Gaussian, 4 x 1920x1080 BF16 step from the
+    per-unit figures of the method: 140 B of parameters read per Gaussian and
+    48 B written per pair by the projection; 752 B per Gaussian and 36 B per
+    intersection for the fused Adam; the raster kernels charged 14 operations
+    per evaluated pair and 13 (forward) or 31 (backward) per blended one."""
+    K, px, ev, bl, tiles = 17_269_857, 4 * 1920 * 1080, 3_715_163_821, 358_000_000, 4 * 8160
+    w = bench.stage_work([3_000_000], [0, 0, 0, 0], K, ev, bl, px, tiles, sh16=True)
     pairs = 12_000_000
-    assert w["project_fwd"] == ("hbm", 3_000_000 * 144 + pairs * 68)
-    assert abs(w["project_fwd"][1] / 1e9 - 1.248) < 5e-4
-    assert abs(w["project_bwd_adam"][1] / 1e9 - 3.229) < 5e-4
-    assert abs(w["bin_sort"][1] / 1e9 - 2.483) < 5e-4
+    assert w["project_fwd"] == ("hbm", 3_000_000 * 140 + pairs * 48)
+    assert w["project_bwd_adam"] == ("hbm", 3_000_000 * 752 + K * 36 + pairs * 8)
+    assert w["bin_sort"] == ("hbm", pairs * 16 + K * 8 + 5 * K * 16 + K * 4 + tiles * 8)
     assert w["loss_l1"] == ("hbm", px * 36)
-    assert w["raster_bwd"] == ("alu", 3_715_163_821 * 90.0)
+    assert w["raster_bwd"] == ("alu", 2.0 * (ev * 14 + bl * 31))
+    assert w["raster_fwd"] == ("alu", 2.0 * (ev * 14 + bl * 13))
+    # the backward at the recorded 5.28 ms: about 0.30 of the FP32 peak
+    r = bench.stage_rooflines(w, {k: 1.0 for k in w} | {"raster_bwd": 5.28}, 6777.0, 80.54784)
+    assert abs(r["raster_bwd"]["frac"] - 0.30) < 0.01
     assert set(w) == {"project_fwd", "bin_sort", "raster_fwd", "loss_l1", "raster_bwd", "project_bwd_adam"}
 
 
@@ -71,16 +77,18 @@ def test_stage_work_counts_each_views_own_scene():
     of its own scene (24M pairs, not 12M x 16)."""
     sizes = [500_000, 500_000, 750_000, 750_000, 1_000_000, 1_250_000, 1_250_000, 6_000_000]
     views = [s for s in range(8) for _ in range(2)]
-    w = bench.stage_work(sizes, views, 30_000_000, 1, 1, sh16=True)
+    w = bench.stage_work(sizes, views, 30_000_000, 1, 1, 1, 1, sh16=True)
     n = sum(sizes)
-    assert w["project_fwd"][1] == n * 144 + 2 * n * 68
-    assert w["project_bwd_adam"][1] == n * 768 + 30_000_000 * 48 + 2 * n * 8
+    assert w["project_fwd"][1] == n * 140 + 2 * n * 48
+    assert w["project_bwd_adam"][1] == n * 752 + 30_000_000 * 36 + 2 * n * 8
 
 
 def test_stage_work_ssim_loss_is_alu_work():
-    w = bench.stage_work([1000], [0], 10, 10, 100, sh16=False, loss="l1_ssim")
+    w = bench.stage_work([1000], [0], 10, 10, 5, 100, 4, sh16=False, loss="l1_ssim")
     assert "loss_l1" not in w and w["loss_l1_ssim"] == ("alu", 100 * 3 * 209 * 2)
-    assert w["project_fwd"][1] == 1000 * 240 + 1000 * 68     # FP32 SH
+    assert w["project_fwd"][1] == 1000 * 236 + 1000 * 48     # FP32 SH
+    assert w["project_bwd_adam"][1] == 1000 * 1416 + 10 * 36 + 1000 * 8
+    assert w["bin_sort"][1] == 1000 * 16 + 10 * 8 + 4 * 10 * 16 + 10 * 4 + 4 * 8   # one view: no view pass
 
 
 def test_stage_rooflines_units_and_fractions():
