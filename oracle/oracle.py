@@ -200,6 +200,23 @@ def bin32(scene, cam, tile_w=16, tile_h=16) -> Binning:
                    slot.astype(np.int64), ranges)
 
 
+def sort64(b: Binning, cam, tile_w=16, tile_h=16) -> Binning:
+    """The same tile lists ordered by 64-bit keys instead of the 32-bit keys
+    of Sec. 4.4: tile id in the high 32 bits, the full binary32 depth t_z in
+    the low 32 (its bit pattern orders like the value, t_z > 0), stable, so
+    equal depths keep ascending Gaussian order.  The 32-bit key keeps only
+    the top (32 - tile bits) bits of the depth code; the two orders differ
+    only among entries of a tile whose truncated codes are equal."""
+    tx, ty = tiles_of(cam, tile_w, tile_h)
+    shift = key_shift(tx * ty)
+    tile = (b.keys_emit >> np.uint32(shift)).astype(np.uint64)
+    tz = np.ascontiguousarray(b.bin[b.gidx_emit.astype(np.int64), 7], np.float32)
+    key64 = (tile << np.uint64(32)) | tz.view(np.uint32).astype(np.uint64)
+    perm = np.argsort(key64, kind="stable")
+    return Binning(b.count, b.bin, b.mant, b.offset, b.keys_emit, b.gidx_emit, b.keys_emit[perm],
+                   b.gidx_emit[perm], perm.astype(np.int64), b.ranges)
+
+
 # --------------------------------------------------------------------------
 # FP64 forward / backward / Adam
 # --------------------------------------------------------------------------

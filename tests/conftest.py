@@ -18,3 +18,21 @@ def orc():
     from oracle import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def report():
+    """report(name, record): prints a parity record (measured errors, counts
+    of checked and skipped items) and, when GS_PARITY_REPORT names a file,
+    appends it there as one JSON line."""
+    import json
+
+    path = os.environ.get("GS_PARITY_REPORT")
+
+    def _report(name, record):
+        line = json.dumps({"test": name, **record}, default=float)
+        print(line)
+        if path:
+            with open(path, "a") as f:
+                f.write(line + "\n")
+    return _report

@@ -2,8 +2,8 @@
 Adam moments in BF16 (FP32 arithmetic).
 
 - One step with the L1 loss restricted to a 64x64 tile-aligned crop, against
-  the FP64 oracle: the image on the crop, and the post-Adam parameters of
-  every Gaussian listed in the crop's tiles.
+  the FP64 oracle: the image on the crop, the gradients and the post-Adam
+  parameters of every Gaussian listed in the crop's tiles.
 - The rendered PSNR of BF16 against FP32 storage after 2000 steps of the
   same schedule: |delta| < 0.05 dB on the training view and a held-out view."""
 import math
@@ -50,7 +50,7 @@ def _crop_binning(orc, b):
     return keep, bs
 
 
-def test_crop_step_against_oracle(mods, orc):
+def test_crop_step_against_oracle(mods, orc, report):
     gsstep, step_mod = mods
     scene = synth.large_scene(0)
     scene.sh = _bf16_round(scene.sh)               # what BF16 storage holds
@@ -82,6 +82,8 @@ def test_crop_step_against_oracle(mods, orc):
     mask = torch.from_numpy(crop.reshape(-1, 1).astype(np.float32)).cuda()
     tr.dl.mul_(mask * float(1920 * 1080) / float(CW * CW))
     gsstep.gs_raster_bwd(tr.plan, tr.ws, tr.image, tr.dl)
+    go = torch.empty((15, scene.n, 4), dtype=torch.float32, device="cuda")
+    gsstep.gs_project_bwd_adam(tr.plan, tr.ws, tr.scenes, tr.cams, None, go)     # gradient only
     gsstep.gs_project_bwd_adam(tr.plan, tr.ws, tr.scenes, tr.cams, gsstep.make_adam(LR, step=1))
     torch.cuda.synchronize()
     assert tr.stats().status == 0
@@ -106,6 +108,15 @@ def test_crop_step_against_oracle(mods, orc):
         bad[g[d2 <= 9.0 * 1.001]] = True
     sel = listed & ~bad
     assert sel.sum() > 0.5 * listed.sum() and sel.sum() > 200
+    # gradients with respect to the stored parameters (scales and opacity
+    # activated), relative 1e-3 with an absolute floor of 1e-3 x the RMS
+    gg = go.cpu().numpy()
+    gpu_g = np.concatenate([gg[0, :, :3], gg[1], gg[2], gg[3:15].transpose(1, 0, 2).reshape(-1, 48)], axis=1)[sel]
+    ref_g = np.concatenate([grad[:, 0:3], grad[:, 3:7], grad[:, 7:10] / p.scales,
+                            (grad[:, 10] / (p.opacities * (1 - p.opacities)))[:, None], grad[:, 11:]], axis=1)[sel]
+    grms = np.sqrt((ref_g ** 2).mean(0)) + 1e-30
+    gerr = np.abs(gpu_g - ref_g) / np.maximum(np.abs(ref_g), grms[None, :])
+    assert gerr.max() <= 1e-3, gerr.max()
     rms = np.sqrt((grad[sel] ** 2).mean(0)) + 1e-30
     decided = (np.abs(grad[sel]) > 1e-2 * rms[None, :])
     new = tr.scenes[0].to_scene()
@@ -116,6 +127,14 @@ def test_crop_step_against_oracle(mods, orc):
     tol[:, 11:] += _bf16_ulp(ref[:, 11:])
     assert decided.sum() > 0.3 * decided.size
     assert np.all(np.abs(th - ref)[decided] <= tol[decided]), np.abs(th - ref)[decided].max()
+    sh_ulps = (np.abs(th - ref)[:, 11:] / _bf16_ulp(ref[:, 11:]))[decided[:, 11:]]
+    report("config3_bf16_1080p_crop_step",
+           {"image_max_abs_err": float(np.abs(img - r.image)[stable].max()), "crop_pixels": int(crop.sum()),
+            "excluded_pixels": int((crop & ~stable).sum()), "grad3d_max_rel_err": float(gerr.max()),
+            "post_adam_geometry_err_over_bound": float((np.abs(th - ref)[:, :11] / tol[:, :11])[decided[:, :11]].max()),
+            "post_adam_sh_max_err_bf16_ulps": float(sh_ulps.max()),
+            "listed_gaussians": int(listed.sum()), "excluded_gaussians": int(listed.sum() - sel.sum()),
+            "decided_values": int(decided.sum())})
     # Gaussians with no listed intersection in the crop keep their parameters
     far = ~listed
     sh_before = scene.sh.reshape(-1, 48)[far][:1000]
@@ -128,7 +147,7 @@ def _psnr(img, ref):
     return 10.0 * math.log10(1.0 / max(mse, 1e-30))
 
 
-def test_bf16_psnr_after_2000_steps(mods):
+def test_bf16_psnr_after_2000_steps(mods, report):
     gsstep, step_mod = mods
     scene = synth.large_scene(0)
     tscene = synth.perturbed(scene, 1)
@@ -156,6 +175,8 @@ def test_bf16_psnr_after_2000_steps(mods):
         torch.cuda.synchronize()
         out[bf16] = (_psnr(tr.image, tgt), _psnr(render(tr.scenes[0], held, bf16), held_tgt))
     print("PSNR after 2000 steps (train, held-out): FP32", out[False], "BF16", out[True])
+    report("config3_psnr_2000_steps", {"fp32_train_db": out[False][0], "fp32_heldout_db": out[False][1],
+                                       "bf16_train_db": out[True][0], "bf16_heldout_db": out[True][1]})
     assert abs(out[True][0] - out[False][0]) < 0.05
     assert abs(out[True][1] - out[False][1]) < 0.05
     assert out[False][0] > _psnr(render(scene, cam), tgt) + 1.0      # training improved the fit

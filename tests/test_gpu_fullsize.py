@@ -30,7 +30,7 @@ def big():
     return gsstep, step, synth.large_scene(0, N)
 
 
-def test_fullsize_single_view_keys_image_gradients(big, orc):
+def test_fullsize_single_view_keys_image_gradients(big, orc, report):
     gsstep, step, scene = big
     cam = synth.large_views(1, resolutions=[(1920, 1080)])[0]
     tr = step.Trainer([scene], [cam], lr=(1e-3,) * 6)
@@ -85,6 +85,11 @@ def test_fullsize_single_view_keys_image_gradients(big, orc):
     rms = np.sqrt((ref ** 2).mean(0)) + 1e-30
     err = np.abs(got - ref) / np.maximum(np.abs(ref), rms[None, :])
     assert err.max() <= 1e-3, err.max()
+    report("config2_1080p_sampled_tiles",
+           {"keys": int(K), "keys_bit_exact": True, "image_max_abs_err": float(np.abs(img - r.image)[ok].max()),
+            "sampled_pixels": int(sampled_px.sum()), "excluded_pixels": int(sampled_px.sum() - ok.sum()),
+            "grad2d_max_rel_err": float(err.max()), "gaussians_touched": int(touched.sum()),
+            "excluded_gaussians": int(touched.sum() - good.sum())})
 
 
 def test_fullsize_four_view_batch_keys(big, orc):

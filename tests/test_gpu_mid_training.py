@@ -30,7 +30,7 @@ def mods():
     return gsstep, step
 
 
-def test_step0_two_views_against_oracle(mods, orc):
+def test_step0_two_views_against_oracle(mods, orc, report):
     gsstep, step_mod = mods
     scene, tscene, cams = synth.mid_workload(0)
     cams = cams[:2]
@@ -44,7 +44,11 @@ def test_step0_two_views_against_oracle(mods, orc):
     assert tr.stats().status == 0
     assert tr.stats().loss == pytest.approx(res.loss, rel=1e-4)
     bad = np.zeros(scene.n, bool)
-    for c, r, P, tg, b in zip(cams, res.renders, res.projs, targets, res.binnings):
+    img_err, excl_px = 0.0, 0
+    for c, r, P, tg, b, im in zip(cams, res.renders, res.projs, targets, res.binnings, tr.image_views()):
+        got = im.cpu().numpy().astype(np.float64)
+        img_err = max(img_err, float(np.abs(got - r.image)[~r.unstable_px].max()))
+        excl_px += int(r.unstable_px.sum())
         r.unstable_px |= (np.abs(r.image - tg) < 1e-5).any(-1)
         ys, xs = np.nonzero(r.unstable_px)
         bad |= r.unstable_g
@@ -66,6 +70,12 @@ def test_step0_two_views_against_oracle(mods, orc):
                          new.sh.reshape(-1, 48)], axis=1).astype(np.float64)
     tol = 1e-5 * np.abs(res.theta) + 1e-6
     assert np.all(np.abs(th - res.theta)[decided] <= tol[decided])
+    assert img_err <= 1e-5, img_err
+    report("config1_step0_two_views",
+           {"image_max_abs_err": img_err, "excluded_pixels": excl_px, "pixels": 2 * 1280 * 720,
+            "loss_rel_err": abs(tr.stats().loss - res.loss) / res.loss,
+            "post_adam_err_over_bound": float((np.abs(th - res.theta)[decided] / tol[decided]).max()),
+            "decided_values": int(decided.sum()), "excluded_gaussians": int(bad.sum()), "gaussians": int(scene.n)})
 
 
 def _psnr(img, ref):

@@ -80,7 +80,7 @@ def _check_grad(gpu, ref, mask, name, tol=1e-3):
 
 
 @pytest.mark.parametrize("seed,bwd_impl", [(0, 0), (1, 0), (0, 1), (1, 1), (0, 2), (1, 2)])
-def test_tiny_stages(gs, orc, seed, bwd_impl):
+def test_tiny_stages(gs, orc, report, seed, bwd_impl):
     """2,000 Gaussians, 128x128: every stage against the oracle (both
     raster-backward implementations)."""
     gsstep, step_mod = gs
@@ -131,7 +131,7 @@ def test_tiny_stages(gs, orc, seed, bwd_impl):
     g2_gpu = _sum_slots(gr, off, count)
     good = vis & ~_unstable_gaussians(P, r, cam)
     assert good.sum() > 0.7 * vis.sum()
-    _check_grad(g2_gpu, g2_orc, good, "grad2d")
+    w2 = _check_grad(g2_gpu, g2_orc, good, "grad2d")
     # --- projection backward, gradient-only mode (activated parameters)
     grads = torch.zeros((15, n, 4), dtype=torch.float32, device="cuda")
     gsstep.gs_project_bwd_adam(tr.plan, tr.ws, tr.scenes, tr.cams, None, grads)
@@ -141,10 +141,17 @@ def test_tiny_stages(gs, orc, seed, bwd_impl):
     ref = np.concatenate([gth[:, 0:3], gth[:, 3:7], gth[:, 7:10] / p.scales,
                           (gth[:, 10] / (p.opacities * (1 - p.opacities)))[:, None], gth[:, 11:]], axis=1)
     gpu = np.concatenate([g[0, :, :3], g[1], g[2], g[3:].transpose(1, 0, 2).reshape(n, 48)], axis=1)
-    _check_grad(gpu, ref, good, "grad3d")
+    w3 = _check_grad(gpu, ref, good, "grad3d")
+    report(f"config0_stages_seed{seed}_impl{bwd_impl}",
+           {"image_max_abs_err": float(err), "excluded_pixels": int(r.unstable_px.sum()), "pixels": int(ok.size),
+            "conic_max_rel_err": float((np.abs(con_g - con_o) / scale).max()),
+            "colour_max_abs_err": float(np.abs(rec[vis][:, [6, 7, 8]] - P[vis][:, [16, 17, 18]]).max()),
+            "grad2d_max_rel_err": float(w2), "grad3d_max_rel_err": float(w3),
+            "excluded_gaussians": int(vis.sum() - good.sum()), "visible_gaussians": int(vis.sum()),
+            "keys": int(b.K), "keys_bit_exact": True})
 
 
-def test_tiny_full_step_adam(gs, orc):
+def test_tiny_full_step_adam(gs, orc, report):
     """Whole step (device L1 gradient, fused Adam) vs the oracle's step."""
     gsstep, step_mod = gs
     scene, tscene, cams = synth.tiny_workload(0)
@@ -177,6 +184,13 @@ def test_tiny_full_step_adam(gs, orc):
     tol = 1e-5 * np.abs(res.theta) + 1e-6
     assert np.all(diff[decided] <= tol[decided]), diff[decided].max()
     assert np.all(diff[zero] <= tol[zero])
+    report("config0_full_step_adam",
+           {"loss_rel_err": abs(st.loss - res.loss) / res.loss,
+            "post_adam_err_over_bound": float((diff[decided] / tol[decided]).max()),
+            "post_adam_max_abs_err": float(diff[decided].max()),
+            "decided_values": int(decided.sum()), "values": int(g.size),
+            "excluded_gaussians": int(bad.sum()), "gaussians": int(scene.n),
+            "excluded_pixels": int(r.unstable_px.sum())})
 
 
 @pytest.mark.parametrize("tile,bwd_batch,bwd_impl", [((16, 16), 0, 1), ((8, 8), 0, 1), ((16, 32), 0, 1),
@@ -317,7 +331,7 @@ def _bf16_ulp(x):
     return 2.0 ** (np.floor(np.log2(ax)) - 7)
 
 
-def test_bf16_storage_step(gs, orc):
+def test_bf16_storage_step(gs, orc, report):
     """SH and both Adam moments stored in BF16 (FP32 arithmetic): image and
     post-Adam geometry as in FP32; post-Adam SH and moments within one BF16
     ulp (stochastic rounding) of the FP64 oracle fed the same stored SH."""
@@ -352,6 +366,7 @@ def test_bf16_storage_step(gs, orc):
     tol = _bf16_ulp(sh_orc) + 1e-6
     d = decided[:, 11:]
     assert np.all(np.abs(sh_gpu - sh_orc)[d] <= tol[d])
+    sh_ulps = float((np.abs(sh_gpu - sh_orc)[d] / _bf16_ulp(sh_orc)[d]).max())
     # geometry stays FP32
     geo_gpu = np.concatenate([new.means, new.quats, np.log(new.scales)], axis=1).astype(np.float64)
     dg = decided[:, :10]
@@ -366,6 +381,11 @@ def test_bf16_storage_step(gs, orc):
         # one bf16 ulp of rounding plus the FP32 gradient's own 1e-3 (x2 for v)
         bound = _bf16_ulp(orc_a) + 2e-3 * np.abs(orc_a)
         assert np.all(np.abs(mg - orc_a)[ok] <= bound[ok]), name
+    report("config0_bf16_storage_step",
+           {"image_max_abs_err": float(np.abs(img - r.image)[~r.unstable_px].max()),
+            "sh_max_err_bf16_ulps": sh_ulps,
+            "geometry_max_abs_err": float(np.abs(geo_gpu - res.theta[:, :10])[dg].max()),
+            "decided_values": int(decided.sum()), "excluded_gaussians": int(bad.sum())})
 
 
 @pytest.mark.parametrize("bf16", [False, True])

@@ -1,10 +1,10 @@
 """Parity of the fused L1 + SSIM loss kernel (Sec. 4.5, 8-bit RGBA reference)
 with the FP64 oracle, through the C ABI.
 
-Tolerances: loss within 1e-5 relative; per-pixel gradient within 1e-3 of the
-view's largest |dL/dC| (the gradient tolerance of the step), pixels whose
-L1 sign is within 1e-6 of a tie excluded; lambda = 0 reproduces gs_loss_l1's
-gradient bit for bit.
+Tolerances: loss within 1e-5 relative; every pixel's gradient within 1e-3
+relative, with an absolute floor of 1e-3 x the RMS of the view's gradient
+(the gradient tolerance of the step), pixels whose L1 sign is within 1e-6 of
+a tie excluded; lambda = 0 reproduces gs_loss_l1's gradient bit for bit.
 """
 import numpy as np
 import pytest
@@ -48,6 +48,12 @@ def _split(flat, shapes):
     return out
 
 
+def _grad_err(got, ref, tie):
+    """Per-element error |got - ref| / max(|ref|, RMS of ref), ties excluded."""
+    rms = np.sqrt((ref ** 2).mean()) + 1e-30
+    return np.where(tie, 0.0, np.abs(got - ref) / np.maximum(np.abs(ref), rms))
+
+
 def _run(gsstep, plan, ws, img_d, tgt_d, lam):
     dl = torch.full_like(img_d, np.nan)
     gsstep.gs_loss_l1_ssim(plan, ws, img_d, tgt_d, lam, dl)
@@ -57,7 +63,7 @@ def _run(gsstep, plan, ws, img_d, tgt_d, lam):
 
 @pytest.mark.parametrize("smooth", [False, True])
 @pytest.mark.parametrize("lam", [0.2, 1.0])
-def test_l1_ssim_matches_oracle(gs, orc, smooth, lam):
+def test_l1_ssim_matches_oracle(gs, orc, report, smooth, lam):
     gsstep, _ = gs
     imgs, tgts = synth.loss_images(SHAPES, seed=11 + int(smooth), smooth=smooth)
     plan, ws = _plan(gsstep, SHAPES)
@@ -67,12 +73,12 @@ def test_l1_ssim_matches_oracle(gs, orc, smooth, lam):
     worst = 0.0
     for got, ref, img, t in zip(_split(dl, SHAPES), ref_g, imgs, tgts):
         tie = np.abs(img.astype(np.float64) - orc.rgba8_to_float(t)) < 1e-6
-        err = np.where(tie, 0.0, np.abs(got - ref))
-        scale = np.abs(ref).max()
+        err = _grad_err(got, ref, tie)
         assert np.isfinite(got).all()
-        assert err.max() <= 1e-3 * scale, (err.max(), scale)
-        worst = max(worst, err.max() / scale)
-    print(f"max gradient error / view max |g|: {worst:.2e}")
+        assert err.max() <= 1e-3, err.max()
+        worst = max(worst, err.max())
+    report(f"l1_ssim_small_lambda{lam}_smooth{int(smooth)}",
+           {"loss_rel_err": abs(loss - ref_loss) / abs(ref_loss), "grad_max_err": worst})
 
 
 def test_lambda_zero_is_l1(gs):
@@ -124,11 +130,11 @@ def test_trainer_step_with_ssim_loss(gs, orc):
     assert abs(tr.stats().loss - ref_loss) <= 1e-5 * ref_loss
     got = tr.dl.cpu().numpy().reshape(img.shape)
     tie = np.abs(img.astype(np.float64) - orc.rgba8_to_float(t8)) < 1e-6
-    assert np.abs(np.where(tie, 0.0, got - ref_g[0])).max() <= 1e-3 * np.abs(ref_g[0]).max()
+    assert _grad_err(got, ref_g[0], tie).max() <= 1e-3
     assert torch.isfinite(tr.scenes[0].geom).all() and torch.isfinite(tr.scenes[0].sh).all()
 
 
-def test_l1_ssim_full_size_four_views(gs, orc):
+def test_l1_ssim_full_size_four_views(gs, orc, report):
     """The batched workload's size: four 1920x1080 views (smooth images with
     flat regions), loss and every pixel's gradient against the oracle."""
     gsstep, _ = gs
@@ -138,7 +144,10 @@ def test_l1_ssim_full_size_four_views(gs, orc):
     loss, dl = _run(gsstep, plan, ws, _flat(imgs, 3), _flat(tgts, 4), 0.2)
     ref_loss, ref_g = orc.l1_ssim_loss_grad(imgs, [orc.rgba8_to_float(t) for t in tgts], 0.2)
     assert abs(loss - ref_loss) <= 1e-5 * abs(ref_loss), (loss, ref_loss)
+    worst = 0.0
     for got, ref, img, t in zip(_split(dl, shapes), ref_g, imgs, tgts):
         tie = np.abs(img.astype(np.float64) - orc.rgba8_to_float(t)) < 1e-6
-        err = np.where(tie, 0.0, np.abs(got - ref))
-        assert err.max() <= 1e-3 * np.abs(ref).max(), err.max() / np.abs(ref).max()
+        err = _grad_err(got, ref, tie)
+        assert err.max() <= 1e-3, err.max()
+        worst = max(worst, err.max())
+    report("l1_ssim_4x1080p", {"loss_rel_err": abs(loss - ref_loss) / abs(ref_loss), "grad_max_err": worst})
