@@ -94,9 +94,11 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batched", choices=["batched", "uneven", "plain", "multiscene"])
     ap.add_argument("--n", type=int, default=N_GAUSS)
-    ap.add_argument("--tune-rounds", type=int, default=18)
+    ap.add_argument("--tune-rounds", type=int, default=24)
     ap.add_argument("--psnr-steps", type=int, default=200)
     ap.add_argument("--tile", default=None, help="fix the tile shape (e.g. 16x16) instead of autotuning")
+    ap.add_argument("--threads-per-tile", type=int, default=0,
+                    help="fix the raster threads per tile (0: one per pixel) when the shape is fixed")
     ap.add_argument("--bwd-impl", type=int, default=None, choices=[0, 1, 2],
                     help="fix the raster-backward implementation instead of autotuning")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison")
@@ -365,14 +367,16 @@ def _psnr(torch, img, ref):
     return 10.0 * math.log10(1.0 / max(mse, 1e-30))
 
 
-def _psnr_run(torch, stepmod, synth, scene, cams, targets, tile, impl, bf16, steps, heldout_cam, heldout_tgt):
+def _psnr_run(torch, stepmod, synth, scene, cams, targets, tile, impl, tpt, bf16, steps, heldout_cam,
+              heldout_tgt):
     """Train `steps` steps from `scene` and return the held-out view's PSNR."""
-    tr = stepmod.Trainer([scene], cams, lr=LR, tile=tile, bwd_impl=impl, sh_bf16=bf16, mom_bf16=bf16)
+    tr = stepmod.Trainer([scene], cams, lr=LR, tile=tile, bwd_impl=impl, sh_bf16=bf16, mom_bf16=bf16,
+                         threads_per_tile=tpt)
     tr.target.copy_(targets)
     for _ in range(steps):
         tr.step(0)
-    ev = stepmod.Trainer([tr.scenes[0]], [heldout_cam], lr=LR, tile=tile, bwd_impl=impl, sh_bf16=bf16,
-                         mom_bf16=bf16)
+    ev = stepmod.Trainer([tr.scenes[0]], [heldout_cam], lr=LR, tile=tile, bwd_impl=impl, threads_per_tile=tpt,
+                         sh_bf16=bf16, mom_bf16=bf16)
     ev.forward()
     torch.cuda.synchronize()
     return _psnr(torch, ev.image, heldout_tgt), float(tr.stats().loss)
@@ -448,16 +452,17 @@ def main():
         for c, t in list(trainers.items()):
             if c != best:
                 del trainers[c]
-        tile, impl = best
-        tune_info = {"chosen": {"tile": list(tile), "bwd_impl": impl},
-                     "pulls": {f"{c[0][0]}x{c[0][1]}/impl{c[1]}": n for c, n in zip(tuner.candidates, tuner.pulls)},
-                     "mean_ms": {f"{c[0][0]}x{c[0][1]}/impl{c[1]}": round(p.mean, 3)
+        tile, impl, tpt = best
+        tune_info = {"chosen": {"tile": list(tile), "bwd_impl": impl, "threads_per_tile": tpt},
+                     "pulls": {autotune.describe(c): n for c, n in zip(tuner.candidates, tuner.pulls)},
+                     "mean_ms": {autotune.describe(c): round(p.mean, 3)
                                  for c, p in zip(tuner.candidates, tuner.post) if p.n}}
     else:
         tile = tuple(int(x) for x in args.tile.split("x")) if args.tile else (16, 16)
         impl = args.bwd_impl if args.bwd_impl is not None else 0
+        tpt = args.threads_per_tile or tile[0] * tile[1]
         tr = stepmod.Trainer(all_bufs, cams, lr=LR, tile=tile, bwd_impl=impl, sh_bf16=sh16, mom_bf16=sh16,
-                             loss=args.loss)
+                             loss=args.loss, threads_per_tile=tpt)
         tr.target.copy_(targets if args.loss == "l1" else _rgba8(torch, targets))
         tr.step(0)
         tune_info = None
@@ -507,9 +512,9 @@ def main():
     if args.psnr_steps > 0 and rank == 0:
         held = synth.large_views(1, resolutions=[RES_1080], phase_deg=45.0)[0]
         held_tgt = _render_targets(stepmod, tscene, [held])
-        p32, l32 = _psnr_run(torch, stepmod, synth, scene, cams, targets, tile, impl, False, args.psnr_steps, held,
+        p32, l32 = _psnr_run(torch, stepmod, synth, scene, cams, targets, tile, impl, tpt, False, args.psnr_steps, held,
                              held_tgt)
-        p16, l16 = _psnr_run(torch, stepmod, synth, scene, cams, targets, tile, impl, True, args.psnr_steps, held,
+        p16, l16 = _psnr_run(torch, stepmod, synth, scene, cams, targets, tile, impl, tpt, True, args.psnr_steps, held,
                              held_tgt)
         psnr = {"steps": args.psnr_steps, "fp32_db": p32, "bf16_db": p16, "delta_db": abs(p16 - p32),
                 "loss_fp32": l32, "loss_bf16": l16, "heldout": "1920x1080 orbit view at +45 deg"}
@@ -528,6 +533,7 @@ def main():
                       int(tr.plan.tiles), sh16, args.loss)
     rooflines = stage_rooflines(work, acc, hbm_peak, alu_peak)
     headline = (args.workload == "batched" and args.n == N_GAUSS and tuple(tile) == (16, 16) and impl == 0
+                and tpt == 256
                 and args.loss == "l1")
     for k, r in rooflines.items():
         r["traffic"] = _measured_traffic(k, headline)
@@ -547,7 +553,7 @@ def main():
                 f"{n / 1e6:.3g}M Gaussians (256 clusters, 30 m box), views per step ") + \
                "+".join(f"{c.width}x{c.height}" for c in cams) + \
                (", BF16 SH and Adam moments (FP32 math)" if sh16 else ", FP32 storage") + \
-               f", tile {tile[0]}x{tile[1]}, raster_bwd impl {impl}, " + \
+               f", tile {tile[0]}x{tile[1]}, raster_bwd impl {impl}, {tpt} threads per tile, " + \
                ("L1 loss" if args.loss == "l1" else "0.8 L1 + 0.2 (1 - SSIM) loss against 8-bit RGBA targets") + \
                ", whole step in one CUDA graph; value = " + \
                f"view-steps/s ({nviews} views per step x steps/s; {equiv:.3f} 1080p-equivalents of pixels per step)"

@@ -97,6 +97,15 @@ typedef struct {
                                  in shared memory, then a pass over
                                  (Gaussian, pixel block) pairs summing them
                                  (the paper's second implementation) */
+    int32_t threads_per_tile; /* threads of a raster_bwd thread block
+                                 (bwd_impl 0): 0 or tile_w x tile_h = one per
+                                 pixel; half or (16-wide tiles) a quarter of
+                                 that = 2 or 4 pixels per thread, each warp
+                                 covering 8 x 8 or 8 x 16 pixels (Sec. 4.2: the
+                                 scheduler's threads per tile).  Pixels per
+                                 thread other than 1 need bwd_impl 0.  The
+                                 raster forward always runs one thread per
+                                 pixel. */
 } gs_tuning;
 
 typedef struct {

@@ -22,11 +22,11 @@ from .step import camera_params
 
 class Renderer:
     def __init__(self, scene_sizes, cameras, capacity: int = 0, tile=(16, 16), bwd_impl: int = 0,
-                 bwd_batch: int = 0, sh_bf16: bool = False, bg=None, device="cuda"):
+                 bwd_batch: int = 0, sh_bf16: bool = False, bg=None, device="cuda", threads_per_tile: int = 0):
         self.device = torch.device(device)
         flags = gsstep.STORE_SH_BF16 if sh_bf16 else 0
         self.plan = gsstep.Plan(list(scene_sizes), [(c.width, c.height, c.scene) for c in cameras], capacity,
-                                tile, bwd_batch, flags, bwd_impl)
+                                tile, bwd_batch, flags, bwd_impl, threads_per_tile)
         self.ws = torch.empty(self.plan.workspace_bytes(), dtype=torch.uint8, device=self.device)
         gsstep.gs_workspace_init(self.plan, self.ws)
         self.cams = torch.from_numpy(camera_params(cameras)).to(self.device)

@@ -1,7 +1,12 @@
 """Autotuner for the step's launch shape: tile size x raster-backward
-implementation, chosen by Thompson sampling over measured step latencies
-(the scheduler the paper uses to pick between its two rasterization-backward
-implementations, Sec. 4.2).
+implementation x threads per tile, chosen by Thompson sampling over measured
+step latencies (the scheduler the paper uses to pick between its two
+rasterization-backward implementations, Sec. 4.2).
+
+A candidate is (tile, bwd_impl, threads_per_tile).  The pixel-parallel
+backward (impl 0) runs with one, two or (16-wide tiles) four pixels per
+thread; the other two backward implementations, and the raster forward, with
+one thread per pixel.
 
 Each candidate keeps a Normal-Inverse-Gamma posterior over its latency.  A
 round samples one latency per candidate from its posterior, runs the
@@ -19,6 +24,26 @@ import numpy as np
 
 TILES = [(8, 8), (16, 16), (16, 32)]
 BWD_IMPLS = [0, 1, 2]
+
+
+def pixels_per_thread_options(tile) -> list:
+    """Pixels per raster thread a tile shape supports (warps of 8 x 4, 8 x 8
+    or 8 x 16 pixels; an 8x8 tile needs at least one full warp)."""
+    return [1, 2] if tile[0] == 8 else [1, 2, 4]
+
+
+def default_candidates(tiles=TILES, impls=BWD_IMPLS) -> list:
+    """(tile, bwd_impl, threads_per_tile) for every supported combination."""
+    out = []
+    for t in tiles:
+        for b in impls:
+            ppts = pixels_per_thread_options(t) if b == 0 else [1]
+            out += [(tuple(t), b, t[0] * t[1] // k) for k in ppts]
+    return out
+
+
+def describe(c) -> str:
+    return f"{c[0][0]}x{c[0][1]}/impl{c[1]}/tpt{c[2]}"
 
 
 @dataclass
@@ -83,19 +108,20 @@ class ThompsonTuner:
 
 def tune_trainer(scenes, cameras, rounds: int = 24, steps_per_pull: int = 2, lr=None, sh_bf16=False,
                  mom_bf16=False, target=None, capacity: int = 0, candidates=None, seed: int = 0):
-    """Pick (tile, bwd_impl) for a workload by Thompson sampling over eager
-    training steps (CUDA events on the current stream).  `scenes` are
-    SceneBuffers shared by all candidates.  Returns (best, tuner, trainers)."""
+    """Pick (tile, bwd_impl, threads_per_tile) for a workload by Thompson
+    sampling over eager training steps (CUDA events on the current stream).
+    `scenes` are SceneBuffers shared by all candidates.  Returns (best,
+    tuner, trainers)."""
     import torch
     from .step import DEFAULT_LR, Trainer
 
-    cands = candidates or [(t, b) for t in TILES for b in BWD_IMPLS]
+    cands = candidates or default_candidates()
     trainers = {}
 
     def get(c):
         if c not in trainers:
             tr = Trainer(scenes, cameras, capacity=capacity, tile=c[0], bwd_impl=c[1], lr=lr or DEFAULT_LR,
-                         sh_bf16=sh_bf16, mom_bf16=mom_bf16)
+                         sh_bf16=sh_bf16, mom_bf16=mom_bf16, threads_per_tile=c[2])
             if target is not None:
                 tr.target.copy_(target)
             tr.step(0)               # first call sets kernel attributes

@@ -63,7 +63,7 @@ static bool plan_build(Plan& P, const int64_t* scene_n, int32_t n_scenes, const 
             P.sm_count = 152;
         cudaGetLastError();
     }
-    gs_tuning t = {16, 16, 0, 0};
+    gs_tuning t = {16, 16, 0, 0, 0};
     if (tuning) t = *tuning;
     const bool tile_ok = (t.tile_w == 8 && t.tile_h == 8) || (t.tile_w == 16 && t.tile_h == 16) ||
                          (t.tile_w == 16 && t.tile_h == 32);
@@ -71,6 +71,14 @@ static bool plan_build(Plan& P, const int64_t* scene_n, int32_t n_scenes, const 
     if (!(t.bwd_batch == 0 || t.bwd_batch == 32 || t.bwd_batch == 64 || t.bwd_batch == 96 || t.bwd_batch == 128))
         return false;
     if (t.bwd_impl < 0 || t.bwd_impl > 2) return false;
+    {
+        const int np = t.tile_w * t.tile_h;
+        const int tpt = t.threads_per_tile;
+        const bool ok = tpt == 0 || tpt == np || tpt == np / 2 || (t.tile_w == 16 && tpt == np / 4);
+        if (!ok) return false;
+        if (tpt != 0 && tpt != np && t.bwd_impl != 0) return false;
+        if (tpt == np) t.threads_per_tile = 0;
+    }
     if (flags & ~(GS_STORE_SH_BF16 | GS_STORE_MOMENTS_BF16)) return false;
     P.tuning = t;
     P.sh_bf16 = (flags & GS_STORE_SH_BF16) ? 1 : 0;

@@ -317,9 +317,9 @@ __device__ __forceinline__ float sqrt_approx(float x)
     return y;
 }
 
-// Conservative mask of the 8x4-pixel warp blocks of a tile (WPR blocks per
-// row, RPB rows of blocks; WPR * RPB <= 16) that a Gaussian (mean, conic,
-// opacity) can contribute to.  A pair needs d^2 <= 9 and
+// Conservative mask of the warp blocks (8 x BH pixels; BH = 4 x the pixels
+// each lane owns) of a tile (WPR blocks per row, RPB rows of blocks;
+// WPR * RPB <= 16) that a Gaussian (mean, conic, opacity) can contribute to.  A pair needs d^2 <= 9 and
 // o exp(-d^2/2) >= 1/255, i.e. d^2 <= r^2 = min(9, 2 ln(255 o)); the
 // half-extents sqrt(r^2 c / det), sqrt(r^2 a / det) of that ellipse, widened
 // by 0.1% of r^2, 1e-5 relative and 0.01 px (which also cover the hardware
@@ -327,7 +327,7 @@ __device__ __forceinline__ float sqrt_approx(float x)
 // (ox, oy) is the tile's first pixel.  Pairs in a masked-out block would be
 // skipped by the raster's own tests, so skipping them changes no result.
 __device__ __forceinline__ uint32_t warp_block_mask(float mx, float my, float ca, float cb, float cc, float op,
-                                                    int ox, int oy, int WPR, int RPB)
+                                                    int ox, int oy, int WPR, int RPB, int BH = 4)
 {
     if (!(op * 255.0f > 1.0f)) return 0u;  // alpha never reaches 1/255
     const float det = ca * cc - cb * cb;
@@ -343,7 +343,8 @@ __device__ __forceinline__ uint32_t warp_block_mask(float mx, float my, float ca
     const float yl = fminf(fmaxf(myr - ey, -1e4f), 1e4f);
     const float yh = fminf(fmaxf(myr + ey, -1e4f), 1e4f);
     const int bx0 = max(0, (int)ceilf((xl - 7.0f) * 0.125f)), bx1 = min(WPR - 1, (int)floorf(xh * 0.125f));
-    const int by0 = max(0, (int)ceilf((yl - 3.0f) * 0.25f)), by1 = min(RPB - 1, (int)floorf(yh * 0.25f));
+    const float ibh = 1.0f / (float)BH;   // BH a power of two: exact
+    const int by0 = max(0, (int)ceilf((yl - (float)(BH - 1)) * ibh)), by1 = min(RPB - 1, (int)floorf(yh * ibh));
     if (bx0 > bx1 || by0 > by1) return 0u;
     // columns bx0..bx1 of one row, times one bit per row by0..by1
     uint32_t rows = 0;

@@ -69,6 +69,13 @@ struct WsPtrs {
 
 WsPtrs carve(const Plan& P, void* ws);
 
+// Pixels each raster thread owns (1, 2 or 4; validated by the plan).
+inline int tile_ppt(const Plan& P)
+{
+    const int np = P.views.tw * P.views.th;
+    return P.tuning.threads_per_tile > 0 ? np / P.tuning.threads_per_tile : 1;
+}
+
 // Degree-3 SH of Gaussian g (48 floats, flat index 3*k + channel).
 __device__ __forceinline__ void load_sh(const SceneDesc& sc, int bf16, int64_t g, float* shv)
 {

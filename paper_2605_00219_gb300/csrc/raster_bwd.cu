@@ -392,7 +392,10 @@ __device__ __forceinline__ int bfly_index(int lane)
     return (lane & 16) ? (ki < 4 ? 5 + ki : -1) : ki;
 }
 
-template <int BS, int TW>
+// BS threads per tile, each owning PPT pixels of its warp's 8 x (4 PPT)
+// block (lane (x, y) holds rows y, y + 4, ...): the PPT pixels' nine values
+// are summed in the lane before one butterfly per visit.
+template <int BS, int TW, int PPT>
 __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* __restrict__ order,
                                                       const uint2* __restrict__ ranges,
                                                       const uint32_t* __restrict__ vals_sorted,
@@ -404,8 +407,10 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
                                                       GradRec* __restrict__ gradrec)
 {
     constexpr int NW = BS / 32;
-    constexpr int WPR = TW / 8;            // 8x4 warp blocks per tile row
-    constexpr int RPB = BS / TW / 4;       // rows of warp blocks
+    constexpr int BH = 4 * PPT;            // warp block height, pixels
+    constexpr int TH = BS * PPT / TW;      // tile height, pixels
+    constexpr int WPR = TW / 8;            // warp blocks per tile row
+    constexpr int RPB = TH / BH;           // rows of warp blocks
     constexpr int BB = NW <= 8 ? 96 : 64;  // list entries per staged batch
     constexpr int IPT = (BB + BS - 1) / BS;   // staged entries per thread
     __shared__ float4 sA[2][BB];
@@ -422,28 +427,36 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
     const int v = view_of_tile(V, gt);
     const ViewDesc& vd = V.v[v];
     const int lt = (int)(gt - vd.tile_base);
-    const int ox = (lt % vd.TX) * TW, oy = (lt / vd.TX) * (BS / TW);
+    const int ox = (lt % vd.TX) * TW, oy = (lt / vd.TX) * TH;
     const int px = ox + (w % WPR) * 8 + (lane & 7);
-    const int py = oy + (w / WPR) * 4 + (lane >> 3);
+    const int py0 = oy + (w / WPR) * BH + (lane >> 3);
     const uint32_t wbit = 1u << w;
-    const bool inside = px < vd.W && py < vd.H;
     const uint2 r = ranges[gt];
-    const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+    const float fx = (float)px + 0.5f;
     const int vi = bfly_index(lane);
 
-    uint32_t nl = 0;
-    float Th = 1.f, Tl = 0.f, d0 = 0.f, d1 = 0.f, d2 = 0.f;
-    if (inside) {
-        const int64_t pix = vd.pix_base + (int64_t)py * vd.W + px;
-        nl = nlast[pix];
-        Th = tfinal[pix];
-        d0 = dl[3 * pix]; d1 = dl[3 * pix + 1]; d2 = dl[3 * pix + 2];
+    // per pixel k (row py0 + 4k): last blended entry, compensated T after
+    // it, dL/dC, and U = sum_c dL/dC_c S_c with S_c the colour still to come
+    // behind an entry (from T_final bg_c): dL/dalpha = T dL/dC . col -
+    // U / (1 - alpha)
+    uint32_t nl[PPT];
+    float Th[PPT], Tl[PPT], d0[PPT], d1[PPT], d2[PPT], U[PPT], fy[PPT];
+    int mx_nl = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; k++) {
+        const int py = py0 + 4 * k;
+        fy[k] = (float)py + 0.5f;
+        nl[k] = 0;
+        Th[k] = 1.f; Tl[k] = 0.f; d0[k] = 0.f; d1[k] = 0.f; d2[k] = 0.f; U[k] = 0.f;
+        if (px < vd.W && py < vd.H) {
+            const int64_t pix = vd.pix_base + (int64_t)py * vd.W + px;
+            nl[k] = nlast[pix];
+            Th[k] = tfinal[pix];
+            d0[k] = dl[3 * pix]; d1[k] = dl[3 * pix + 1]; d2[k] = dl[3 * pix + 2];
+        }
+        if (bg) U[k] = Th[k] * fmaf(d0[k], bg[0], fmaf(d1[k], bg[1], d2[k] * bg[2]));
+        mx_nl = max(mx_nl, (int)nl[k]);
     }
-    // U = sum_c dL/dC_c S_c, S_c the colour still to come behind an entry
-    // (from T_final bg_c): dL/dalpha = T sum_c dL/dC_c col_c - U / (1 - alpha)
-    float U = 0.f;
-    if (bg) U = Th * fmaf(d0, bg[0], fmaf(d1, bg[1], d2 * bg[2]));
-    int mx_nl = (int)nl;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx_nl = max(mx_nl, __shfl_xor_sync(0xffffffffu, mx_nl, o));
     if (lane == 0) smax[w] = mx_nl;
@@ -467,7 +480,7 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
         sD[buf][i] = make_float4(q.a.z, q.a.w, q.b.x, q.c.x);
         sL[buf][i] = make_float2(q.c.z, q.c.w);
         sE[buf][i] = e;
-        sM[buf][i] = warp_block_mask(q.a.x, q.a.y, q.a.z, q.a.w, q.b.x, q.b.y, ox, oy, WPR, RPB) & live;
+        sM[buf][i] = warp_block_mask(q.a.x, q.a.y, q.a.z, q.a.w, q.b.x, q.b.y, ox, oy, WPR, RPB, BH) & live;
     };
     int bb = ((L + BB - 1) / BB - 1) * BB;
     if (bb >= 0) {
@@ -500,7 +513,7 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
             }
         }
         for (int c = (cnt - 1) >> 5; c >= 0; c--) {
-            // entries of this chunk whose 3-sigma box touches this warp's block,
+            // entries of this chunk whose box touches this warp's block,
             // before the last pair any of the warp's pixels blended
             const int jl = 32 * c + lane;
             uint32_t bits = __ballot_sync(0xffffffffu, jl < cnt && (cM[jl] & wbit));
@@ -512,39 +525,44 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
 #pragma unroll
                 for (int i = 0; i < 9; i++) g[i] = 0.f;
                 bool hit = false;
-                if (bb + j < (int)nl) {
-                    const float4 a = cA[j];
-                    const float4 b = cB[j];
-                    const float2 ml = cL[j];
-                    const float dx = pix_offset(fx, a.x, ml.x), dy = pix_offset(fy, a.y, ml.y);
-                    const float p2 = pair_power2(dx, dy, a.z, a.w, b.x);
-                    if (p2 >= kPow2Min) {
-                        const float G = ex2_approx(p2);
-                        const float araw = __fmul_rn(b.y, G);
-                        const float alpha = fminf(kAlphaMax, araw);
-                        if (alpha >= kAlphaMin) {
-                            hit = true;
-                            const float cb = cD[j].w;
-                            // compensated T before this entry
-                            const float rom = div_one_minus(alpha, Th, Tl);
-                            const float wgt = alpha * Th;
-                            g[6] = wgt * d0;
-                            g[7] = wgt * d1;
-                            g[8] = wgt * d2;
-                            const float dcol = fmaf(d0, b.z, fmaf(d1, b.w, d2 * cb));
-                            const float da = fmaf(Th, dcol, -U * rom);
-                            U = fmaf(wgt, dcol, U);
-                            if (araw <= kAlphaMax) {
-                                // moments of dp = dL/dpower; the conic and
-                                // the constant factors are applied per entry
-                                // after the reduction
-                                g[5] = da * G;
-                                const float dp = da * araw;
-                                g[0] = dx * dp;
-                                g[1] = dy * dp;
-                                g[2] = dx * g[0];
-                                g[3] = dx * g[1];
-                                g[4] = dy * g[1];
+                const float4 a = cA[j];
+                const float4 b = cB[j];
+                const float2 ml = cL[j];
+                const float dx = pix_offset(fx, a.x, ml.x);
+#pragma unroll
+                for (int k = 0; k < PPT; k++) {
+                    if (bb + j < (int)nl[k]) {
+                        const float dy = pix_offset(fy[k], a.y, ml.y);
+                        const float p2 = pair_power2(dx, dy, a.z, a.w, b.x);
+                        if (p2 >= kPow2Min) {
+                            const float G = ex2_approx(p2);
+                            const float araw = __fmul_rn(b.y, G);
+                            const float alpha = fminf(kAlphaMax, araw);
+                            if (alpha >= kAlphaMin) {
+                                hit = true;
+                                const float cb = cD[j].w;
+                                // compensated T before this entry
+                                const float rom = div_one_minus(alpha, Th[k], Tl[k]);
+                                const float wgt = alpha * Th[k];
+                                g[6] = fmaf(wgt, d0[k], g[6]);
+                                g[7] = fmaf(wgt, d1[k], g[7]);
+                                g[8] = fmaf(wgt, d2[k], g[8]);
+                                const float dcol = fmaf(d0[k], b.z, fmaf(d1[k], b.w, d2[k] * cb));
+                                const float da = fmaf(Th[k], dcol, -U[k] * rom);
+                                U[k] = fmaf(wgt, dcol, U[k]);
+                                if (araw <= kAlphaMax) {
+                                    // moments of dp = dL/dpower; the conic
+                                    // and the constant factors are applied
+                                    // per entry after the reduction
+                                    g[5] = fmaf(da, G, g[5]);
+                                    const float dp = da * araw;
+                                    const float xdp = dx * dp, ydp = dy * dp;
+                                    g[0] += xdp;
+                                    g[1] += ydp;
+                                    g[2] = fmaf(dx, xdp, g[2]);
+                                    g[3] = fmaf(dx, ydp, g[3]);
+                                    g[4] = fmaf(dy, ydp, g[4]);
+                                }
                             }
                         }
                     }
@@ -600,11 +618,22 @@ void launch_raster_bwd_px(const Plan& P, const WsPtrs& w, const float* bg, const
 {
     const Views& V = P.views;
     const unsigned grid = (unsigned)V.tiles;
-#define GS_RBP(BS, TW) k_raster_bwd_px<BS, TW><<<grid, BS, 0, st>>>(V, w.tile_order, w.ranges, w.vals_sorted, w.pid_sorted, \
-                                                                   w.rec, w.tfinal, bg, dl, w.nlast, w.gradrec)
-    if (V.tw == 8) GS_RBP(64, 8);
-    else if (V.th == 16) GS_RBP(256, 16);
-    else GS_RBP(512, 16);
+    const int ppt = tile_ppt(P);
+#define GS_RBP(BS, TW, PPT)                                                                                  \
+    k_raster_bwd_px<BS, TW, PPT><<<grid, BS, 0, st>>>(V, w.tile_order, w.ranges, w.vals_sorted, w.pid_sorted, \
+                                                      w.rec, w.tfinal, bg, dl, w.nlast, w.gradrec)
+    if (V.tw == 8) {
+        if (ppt == 1) GS_RBP(64, 8, 1);
+        else GS_RBP(32, 8, 2);
+    } else if (V.th == 16) {
+        if (ppt == 1) GS_RBP(256, 16, 1);
+        else if (ppt == 2) GS_RBP(128, 16, 2);
+        else GS_RBP(64, 16, 4);
+    } else {
+        if (ppt == 1) GS_RBP(512, 16, 1);
+        else if (ppt == 2) GS_RBP(256, 16, 2);
+        else GS_RBP(128, 16, 4);
+    }
 #undef GS_RBP
 }
 

@@ -42,7 +42,7 @@ class gs_view(ctypes.Structure):
 
 class gs_tuning(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("bwd_batch", ctypes.c_int32),
-                ("bwd_impl", ctypes.c_int32)]
+                ("bwd_impl", ctypes.c_int32), ("threads_per_tile", ctypes.c_int32)]
 
 
 class gs_scene_buf(ctypes.Structure):
@@ -145,13 +145,13 @@ class Plan:
     """Static shape of a step (host object wrapping gs_plan)."""
 
     def __init__(self, scene_sizes, views, capacity: int = 0, tile=(16, 16), bwd_batch: int = 0,
-                 storage_flags: int = 0, bwd_impl: int = 0):
+                 storage_flags: int = 0, bwd_impl: int = 0, threads_per_tile: int = 0):
         L = lib()
         n_arr = (ctypes.c_int64 * len(scene_sizes))(*[int(x) for x in scene_sizes])
         v_arr = (gs_view * len(views))()
         for i, (w, h, s) in enumerate(views):
             v_arr[i] = gs_view(int(w), int(h), int(s))
-        tun = gs_tuning(int(tile[0]), int(tile[1]), int(bwd_batch), int(bwd_impl))
+        tun = gs_tuning(int(tile[0]), int(tile[1]), int(bwd_batch), int(bwd_impl), int(threads_per_tile))
         err = ctypes.c_int(0)
         h = L.gs_plan_create(n_arr, len(scene_sizes), v_arr, len(views), int(capacity), ctypes.byref(tun),
                              int(storage_flags), ctypes.byref(err))
@@ -164,6 +164,7 @@ class Plan:
         self.storage_flags = storage_flags
         self.bwd_impl = int(bwd_impl)
         self.bwd_batch = int(bwd_batch)
+        self.threads_per_tile = int(threads_per_tile) or int(tile[0]) * int(tile[1])
 
     def __del__(self):
         h = getattr(self, "handle", None)

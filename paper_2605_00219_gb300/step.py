@@ -91,7 +91,8 @@ class Trainer:
 
     def __init__(self, scenes, cameras, capacity: int = 0, tile=(16, 16), bwd_batch: int = 0,
                  sh_bf16: bool = False, mom_bf16: bool = False, bg=None, lr=DEFAULT_LR, device="cuda",
-                 bwd_impl: int = 0, loss: str = "l1", ssim_lambda: float = 0.2, seed: int = 0):
+                 bwd_impl: int = 0, loss: str = "l1", ssim_lambda: float = 0.2, seed: int = 0,
+                 threads_per_tile: int = 0):
         if loss not in ("l1", "l1_ssim"):
             raise ValueError(f"loss must be 'l1' or 'l1_ssim', not {loss!r}")
         self.loss = loss
@@ -102,7 +103,7 @@ class Trainer:
                        SceneBuffers.from_scene(s, device, sh_bf16, mom_bf16) for s in scenes]
         flags = (gsstep.STORE_SH_BF16 if sh_bf16 else 0) | (gsstep.STORE_MOMENTS_BF16 if mom_bf16 else 0)
         self.plan = gsstep.Plan([s.n for s in self.scenes], [(c.width, c.height, c.scene) for c in cameras],
-                                capacity, tile, bwd_batch, flags, bwd_impl)
+                                capacity, tile, bwd_batch, flags, bwd_impl, threads_per_tile)
         self.ws = torch.empty(self.plan.workspace_bytes(), dtype=torch.uint8, device=self.device)
         self.cams = torch.from_numpy(camera_params(cameras)).to(self.device)
         P = self.plan.pixels

@@ -53,9 +53,35 @@ def test_plan_validation(gslib):
                 dict(scene_sizes=[5], views=[(0, 8, 0)]),
                 dict(scene_sizes=[5], views=[(8, 8, 0)], tile=(12, 12)),
                 dict(scene_sizes=[5], views=[(8, 8, 0)], bwd_batch=48),
+                dict(scene_sizes=[5], views=[(8, 8, 0)], threads_per_tile=100),
+                dict(scene_sizes=[5], views=[(8, 8, 0)], tile=(8, 8), threads_per_tile=16),
+                dict(scene_sizes=[5], views=[(8, 8, 0)], threads_per_tile=128, bwd_impl=1),
+                dict(scene_sizes=[5], views=[(8, 8, 0)], threads_per_tile=64, bwd_impl=2),
                 dict(scene_sizes=[5], views=[(8, 8, 0)] * 65)]:
         with pytest.raises(gslib.GSError):
             gslib.Plan(**bad)
+
+
+def test_threads_per_tile_choices(gslib):
+    """One, two or (16-wide tiles) four pixels per raster thread; the
+    autotuner's candidates are exactly the accepted combinations."""
+    from paper_2605_00219_gb300 import autotune
+    for tile in autotune.TILES:
+        np_ = tile[0] * tile[1]
+        for tpt in (0, np_, np_ // 2, np_ // 4, np_ // 8):
+            ok = tpt in (0, np_, np_ // 2) or (tile[0] == 16 and tpt == np_ // 4)
+            for impl in (0, 1, 2):
+                accept = ok and (impl == 0 or tpt in (0, np_))
+                try:
+                    gslib.Plan([5], [(40, 40, 0)], tile=tile, bwd_impl=impl, threads_per_tile=tpt)
+                    got = True
+                except gslib.GSError:
+                    got = False
+                assert got == accept, (tile, tpt, impl)
+    cands = autotune.default_candidates()
+    assert len(cands) == len(set(cands)) == 14
+    for tile, impl, tpt in cands:
+        gslib.Plan([5], [(40, 40, 0)], tile=tile, bwd_impl=impl, threads_per_tile=tpt)
 
 
 def test_status_strings(gslib):

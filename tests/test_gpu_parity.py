@@ -51,9 +51,9 @@ def _unstable_gaussians(P, r, cam):
     return bad
 
 
-def _run_forward(step_mod, scene, cams, tile=(16, 16), bwd_batch=0, bg=None, capacity=0, bwd_impl=0):
+def _run_forward(step_mod, scene, cams, tile=(16, 16), bwd_batch=0, bg=None, capacity=0, bwd_impl=0, tpt=0):
     tr = step_mod.Trainer([scene], cams, capacity=capacity, tile=tile, bwd_batch=bwd_batch, bg=bg, lr=LR,
-                          bwd_impl=bwd_impl)
+                          bwd_impl=bwd_impl, threads_per_tile=tpt)
     tr.forward()
     torch.cuda.synchronize()
     return tr
@@ -223,6 +223,44 @@ def test_ragged_tiles_and_batches(gs, orc, tile, bwd_batch, bwd_impl):
     g2_gpu = _sum_slots(gr, off, count)
     good = (b.count > 0) & ~_unstable_gaussians(P, r, cam)
     _check_grad(g2_gpu, g2_orc, good, f"grad2d {tile} S={bwd_batch} impl={bwd_impl}")
+
+
+@pytest.mark.parametrize("tile,tpt,bg", [((16, 16), 128, None), ((16, 16), 64, None), ((8, 8), 32, None),
+                                         ((16, 32), 256, None), ((16, 32), 128, None),
+                                         ((16, 16), 128, (0.25, 0.5, 0.75)), ((16, 16), 64, (0.3, 0.1, 0.9))])
+def test_pixels_per_thread(gs, orc, report, tile, tpt, bg):
+    """The pixel-parallel raster backward with 2 or 4 pixels per thread
+    (warps of 8 x 8 or 8 x 16 pixels) on a ragged image: the forward is
+    unchanged (bit for bit), gradients within 1e-3 of the oracle, with and
+    without a background."""
+    gsstep, step_mod = gs
+    scene = synth.cluster_scene(20000, 16, 3.0, seed=7, log_scale=(-3.5, 0.5), logit_opacity=(0.0, 1.5))
+    cam = synth.look_at([0, -6, 2], [0, 0, 0], 203, 149, 180.0)
+    bgo = bg or (0.0, 0.0, 0.0)
+    b, p, P, r = _oracle_all(orc, scene, cam, tile, bg=bgo)
+    ref = _run_forward(step_mod, scene, [cam], tile=tile, bg=bg)
+    tr = _run_forward(step_mod, scene, [cam], tile=tile, bg=bg, tpt=tpt)
+    n = scene.n
+    assert torch.equal(tr.image, ref.image)
+    assert torch.equal(tr.buffer(5, 149 * 203), ref.buffer(5, 149 * 203))          # n_last
+    assert torch.equal(tr.buffer(6, 149 * 203, torch.float32), ref.buffer(6, 149 * 203, torch.float32))
+    assert tr.stats().blended_pairs == ref.stats().blended_pairs
+    img = tr.image.view(149, 203, 3).cpu().numpy().astype(np.float64)
+    ok = ~r.unstable_px
+    ierr = np.abs(img - r.image)[ok].max()
+    assert ierr <= 1e-5
+    rng = np.random.default_rng(4)
+    dl64 = rng.normal(size=(149, 203, 3)).astype(np.float32).astype(np.float64) / (3 * 149 * 203)
+    tr.dl.copy_(torch.from_numpy(dl64.astype(np.float32).reshape(-1, 3)))
+    gsstep.gs_raster_bwd(tr.plan, tr.ws, tr.image, tr.dl)
+    g2_orc = orc.raster_bwd64(cam, P, b, dl64, bgo, *tile)
+    count = tr.buffer(0, n).cpu().numpy().view(np.uint32)
+    off = tr.buffer(1, n + 1).cpu().numpy().view(np.uint32).astype(np.int64)
+    gr = tr.buffer(8, b.K * 12, torch.float32).cpu().numpy().reshape(b.K, 12)
+    good = (b.count > 0) & ~_unstable_gaussians(P, r, cam)
+    w = _check_grad(_sum_slots(gr, off, count), g2_orc, good, f"grad2d {tile} tpt={tpt} bg={bg}")
+    report(f"pixels_per_thread {tile} tpt={tpt} bg={bg}", {"image_max_abs_err": float(ierr),
+                                                          "grad2d_max_rel_err": float(w)})
 
 
 @pytest.mark.parametrize("bwd_impl", [0, 1, 2])
