@@ -680,15 +680,8 @@ def stage_rooflines(work, stage_ms, hbm_peak_gbs, alu_peak_tflops):
 
 def launches_per_step(plan) -> int:
     """Kernels of this library launched by one step (see the launchers)."""
-    views = len(plan.views)
-    key_bits = 0
-    for (w, h, _) in plan.views:
-        tx, ty = (w + plan.tile[0] - 1) // plan.tile[0], (h + plan.tile[1] - 1) // plan.tile[1]
-        tb = max(0, int(np.ceil(np.log2(tx * ty))))
-        key_bits = max(key_bits, 32 if tb >= 9 else 23 + tb)
-    passes = (key_bits + 7) // 8 + (1 if views > 1 else 0)
     project = 2                                        # header reset + projection
-    binsort = 3 + 1 + 1 + passes * (1 + 3 + 1) + 1 + 1 + 1  # scan, finalize, emit, passes, fill, ranges, order
+    binsort = 3 + 1 + 3 + 1 + 1 + 1 + 1                # count scan, finalize, tile scan, ranges, order, emit, sort
     return project + binsort + 1 + 1 + 1 + 1 + 1       # raster fwd, loss, raster bwd, proj bwd+adam, advance
 
 

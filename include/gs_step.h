@@ -175,12 +175,15 @@ gs_status gs_project_fwd(const gs_plan* plan, void* ws, const gs_scene_buf* scen
                          const float* cams, void* stream);
 
 /* Tiling and sorting (Sec. 4.1, Sec. 4.4, Table 2 "Tiling/Sorting"):
- * exclusive scan of the counts ("index offset"), a second scan-line pass
- * emitting (key, pair) for every intersected tile ("generate keys"), a stable
- * LSD radix sort of the 32-bit keys (tile id in the top ceil(log2 tiles)
- * bits, depth code (2z+1)/(z+1) mantissa below; one extra pass orders the
- * views when there are several) and per-tile [start, end) ranges.  K stays
- * on the device; intersections beyond the capacity set GS_STATUS_CAPACITY. */
+ * exclusive scan of the counts ("index offset"), per-tile [start, end)
+ * ranges from the per-tile counts of the projection's traversal, a second
+ * scan-line pass emitting every intersected tile into its tile's list
+ * ("generate keys"), and a sort of each tile's list, so that the lists hold
+ * the 32-bit keys (tile id in the top ceil(log2 tiles) bits, depth code
+ * (2z+1)/(z+1) mantissa below) in the order of a stable sort of the keys,
+ * view by view (ties in emission order, i.e. by Gaussian).  K stays on the
+ * device; if it exceeds the capacity, GS_STATUS_CAPACITY is set and every
+ * tile list is left empty. */
 gs_status gs_bin_sort(const gs_plan* plan, void* ws, void* stream);
 
 /* Front-to-back compositing per tile (Sec. 2): alpha = min(0.99, o exp(-d^2/2))
@@ -254,11 +257,14 @@ gs_status gs_workspace_set_step(const gs_plan* plan, void* ws, int32_t step, voi
 gs_status gs_read_stats(const gs_plan* plan, const void* ws, gs_stats* out, void* stream);
 
 /* Device views of intermediate buffers (for tests and tools): 0 counts
- * u32[pairs], 1 offsets u32[pairs+1], 2 sorted keys u32[cap], 3 sorted pair
- * index u32[cap], 4 tile ranges u32[tiles][2], 5 n_last u32[pixels],
- * 6 final transmittance f32[pixels], 7 projected records float4[pairs][3],
- * 8 gradient records float4[cap][3], 9 sorted emission slot u32[cap].
- * Returns NULL for an unknown buffer. */
+ * u32[pairs] and 1 offsets u32[pairs+1] (its exclusive scan: each pair's
+ * first emission slot), both in Gaussian-major pair order (scene by scene,
+ * Gaussian by Gaussian, the scene's views in plan order), 2 sorted keys
+ * u32[cap], 3 sorted pair index u32[cap] (view-major: the view's first pair
+ * + Gaussian), 4 tile ranges u32[tiles][2], 5 n_last u32[pixels], 6 final
+ * transmittance f32[pixels], 7 projected records float4[pairs][3]
+ * (view-major), 8 gradient records float4[cap][3] (at emission slots),
+ * 9 sorted emission slot u32[cap].  Returns NULL for an unknown buffer. */
 void* gs_workspace_buffer(const gs_plan* plan, void* ws, int32_t which);
 
 const char* gs_status_str(gs_status s);
@@ -278,7 +284,10 @@ const char* gs_status_str(gs_status s);
  * is a static array inside the library, held by every GPU that loads the
  * library until the process exits.  The first call on a device looks up that
  * array's device address (with the device current) and caches it; make that
- * first call before any stream capture.  The array is shared by every call on
+ * first call before any stream capture.  The cached address is the one in
+ * the device's primary context (the context the CUDA runtime uses): call
+ * this entry point only with that context current, and not after the
+ * process has reset the device (cudaDeviceReset), which invalidates it.  The array is shared by every call on
  * the device and keeps the last call's contents (the counter is cleared at
  * the start of each call), so calls whose executions overlap on the GPU race
  * and must be ordered by the caller.

@@ -1,30 +1,36 @@
 // bin_sort.cu -- tiling and sorting (VkSplat Sec. 4.1, Sec. 4.4; Table 2
 // "Tiling/Sorting": index offset, generate keys, sorting, tile ranges).
 //
-//   index offset : exclusive scan of the per-pair tile counts (reduce-then-
-//                  scan, three launches, no inter-block waiting)
-//   generate keys: second scan-line pass writing 32-bit keys
-//                  (tile << shift | depth code >> drop) and the pair of each
-//                  emitted intersection
-//   sorting      : stable LSD radix sort, 8-bit digits, 2048 keys per block,
-//                  warp-level match_any ranking, scatter through shared memory
-//                  so that global writes are coalesced runs per digit; the
-//                  payload starts as the implicit emission index; when there
-//                  are several views a final pass orders the view segments;
-//                  the last pass also gathers the sorted pair indices
-//   tile ranges  : [start, end) per tile from key boundaries
+// The sorted lists are the 32-bit keys (tile << shift | depth code >> drop)
+// of Sec. 4.4 in stable order, i.e. ordered by (view, tile, depth code,
+// emission slot): the tile is the key's leading part, so the sort is done
+// as a bucketing by tile followed by a sort of each tile's short list.
+//
+//   index offset : exclusive scan of the per-pair tile counts, in
+//                  Gaussian-major pair order (reduce-then-scan, three
+//                  launches, no inter-block waiting): a Gaussian's
+//                  intersections in all views are consecutive emission slots
+//   tile ranges  : the projection's traversal already counted the entries of
+//                  every tile; their exclusive scan gives each tile's
+//                  [start, end) in the sorted arrays and its scatter cursor
+//   generate keys: second scan-line pass; each intersection takes the next
+//                  slot of its tile (an atomic cursor) and stores its depth
+//                  code and emission slot there, and its pair at the
+//                  emission slot
+//   sorting      : one thread block per tile sorts the tile's entries by
+//                  (depth code, emission slot) -- unique, so the arrival
+//                  order of the atomics does not matter -- and writes the
+//                  keys, emission slots and pairs: bitonic sort in shared
+//                  memory up to kTileSortMax entries; longer lists are sorted
+//                  in chunks of that size and merged in global memory by
+//                  rank (each entry's position in the other run by binary
+//                  search)
 // K never leaves the device: every kernel reads it from the workspace header
-// and grids are sized by the capacity.
+// and grids are sized by the plan.  When K exceeds the capacity nothing is
+// emitted and every tile list is empty (GS_STATUS_CAPACITY reports it).
 #include "gs_internal.cuh"
 
 namespace gs {
-
-__device__ __forceinline__ uint32_t lanemask_lt()
-{
-    uint32_t m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
-}
 
 __global__ void k_fill_u32(uint32_t* __restrict__ p, int64_t n, uint32_t value)
 {
@@ -160,289 +166,196 @@ void scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* part, cuda
     scan_u32_dyn(in, out, n, nullptr, 1, part, st);
 }
 
-// Total, capacity check and view segment starts after the count scan.
-__global__ void k_count_finalize(Views V, const uint32_t* __restrict__ part, int64_t nparts,
+// Total and capacity check after the count scan: k_eff = K when it fits the
+// capacity, else 0 (nothing is emitted).
+__global__ void k_count_finalize(const uint32_t* __restrict__ part, int64_t nparts, int64_t pairs,
                                  uint32_t* __restrict__ offset, WsHeader* __restrict__ hdr, uint32_t cap)
 {
-    const uint32_t total = part[nparts];
     if (threadIdx.x == 0) {
+        const uint32_t total = part[nparts];
         hdr->k_required = total;
-        hdr->k_eff = total < cap ? total : cap;
-        hdr->hist_nblk = ((total < cap ? total : cap) + kRadixBlock - 1) / kRadixBlock;
+        hdr->k_eff = total <= cap ? total : 0u;
         if (total > cap) atomicOr(&hdr->status, GS_STATUS_CAPACITY);
-        offset[V.pairs] = total;
-        hdr->seg[V.n] = total < cap ? total : cap;
+        offset[pairs] = total;
     }
-    for (int v = threadIdx.x; v < V.n; v += blockDim.x) {
-        uint32_t s = offset[V.v[v].pair_base];
-        hdr->seg[v] = s < cap ? s : cap;
+}
+
+// Tile ranges from the scanned tile counts (start in tile_cur, which stays
+// as the tile's scatter cursor); an empty list is [0, 0), and every list is
+// empty when K exceeds the capacity.
+__global__ void k_tile_setup(int64_t tiles, const uint32_t* __restrict__ tile_cnt,
+                             const uint32_t* __restrict__ tile_start, const WsHeader* __restrict__ hdr,
+                             uint2* __restrict__ ranges)
+{
+    const bool fits = hdr->k_eff == hdr->k_required;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tiles; t += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t s0 = tile_start[t], c = tile_cnt[t];
+        ranges[t] = fits && c ? make_uint2(s0, s0 + c) : make_uint2(0u, 0u);
     }
 }
 
 // ---------------------------------------------------------------------------
-// Generate keys
+// Generate keys into tile buckets
 // ---------------------------------------------------------------------------
 
+// One thread per Gaussian-major pair q: its intersections take emission
+// slots offset[q] + i in traversal order; each is placed at the next free
+// slot of its tile's list (depth code and emission slot), and the view-major
+// pair index is recorded at its emission slot.
 __global__ void __launch_bounds__(256) k_emit(Views V, const uint32_t* __restrict__ count,
                                               const uint32_t* __restrict__ offset, const ProjRec* __restrict__ rec,
-                                              const float4* __restrict__ binrec, uint32_t* __restrict__ keys,
-                                              uint32_t* __restrict__ pid, uint32_t cap)
+                                              const float4* __restrict__ binrec, uint32_t* tile_cur,
+                                              uint32_t* __restrict__ bkey, uint32_t* __restrict__ bval,
+                                              uint32_t* __restrict__ pid, const WsHeader* __restrict__ hdr)
 {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= V.pairs) return;
-    const uint32_t cnt = count[p];
+    const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (qi >= V.pairs) return;
+    if (hdr->k_eff != hdr->k_required) return;     // over capacity: nothing is emitted
+    const uint32_t cnt = count[qi];
     if (cnt == 0) return;
-    const ViewDesc& vd = V.v[view_of_pair(V, p)];
-    const uint32_t off = offset[p];
+    int s = 0;
+    while (s + 1 < V.n_scenes && V.qbase[s + 1] <= qi) s++;
+    const int nv = V.nv[s];
+    const int64_t local = qi - V.qbase[s];
+    const int64_t g = local / nv;
+    const int v = V.view_of[s][(int)(local - g * nv)];
+    const ViewDesc& vd = V.v[v];
+    const int64_t p = vd.pair_base + g;
+    const uint32_t off = offset[qi];
     const float4 ra = rec[p].a;
     const float4 bb = binrec[p];
-    BinGeom g;
-    g.mx = ra.x; g.my = ra.y; g.a = bb.x; g.b = bb.y; g.c = bb.z;
-    g.det = FS(FM(g.a, g.c), FM(g.b, g.b));
-    g.r2 = cull_r2(rec[p].b.y);   // same bits as in the projection pass
-    g.mant = __float_as_uint(bb.w);
-    g.valid = 1;
-    const uint32_t low = g.mant >> vd.drop;
-    const int shift = vd.shift;
-    scanline_tiles(g, V.tw, V.th, vd.TX, vd.TY, [&](uint32_t i, uint32_t tile) {
-        uint32_t e = off + i;
-        if (e < cap) {
-            keys[e] = (tile << shift) | low;
-            pid[e] = (uint32_t)p;
-        }
+    BinGeom gm;
+    gm.mx = ra.x; gm.my = ra.y; gm.a = bb.x; gm.b = bb.y; gm.c = bb.z;
+    gm.det = FS(FM(gm.a, gm.c), FM(gm.b, gm.b));
+    gm.r2 = cull_r2(rec[p].b.y);   // same bits as in the projection pass
+    gm.mant = __float_as_uint(bb.w);
+    gm.valid = 1;
+    const uint32_t low = gm.mant >> vd.drop;
+    uint32_t* cur = tile_cur + vd.tile_base;
+    scanline_tiles(gm, V.tw, V.th, vd.TX, vd.TY, [&](uint32_t i, uint32_t tile) {
+        const uint32_t e = off + i;
+        const uint32_t slot = atomicAdd(cur + tile, 1u);
+        bkey[slot] = low;
+        bval[slot] = e;
+        pid[e] = (uint32_t)p;
     });
 }
 
 // ---------------------------------------------------------------------------
-// Radix sort passes
+// Per-tile sort
 // ---------------------------------------------------------------------------
 
-enum { kDigitKey = 0, kDigitView = 1 };
-
-__device__ __forceinline__ int view_of_slot(const uint32_t* seg, int nv, uint32_t e)
+__device__ __forceinline__ unsigned long long sort_key(uint32_t low, uint32_t e)
 {
-    int v = 0;
-    while (v + 1 < nv && seg[v + 1] <= e) v++;
-    return v;
+    return ((unsigned long long)low << 32) | e;
 }
 
-// 16-byte asynchronous global -> shared copy (bypassing L1), and its group
-// commit / wait (hardware waits: no spinning in this code)
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+// Ascending bitonic sort of N (a power of two) 64-bit keys in shared memory.
+__device__ void bitonic_sort_smem(unsigned long long* a, int N)
 {
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-template <int MODE>
-__global__ void __launch_bounds__(kRadixThreads) k_radix_up(const uint32_t* __restrict__ keys,
-                                                             const uint32_t* __restrict__ vals, bool iota,
-                                                             const WsHeader* __restrict__ hdr, int shift,
-                                                             uint32_t* __restrict__ hist, int nv)
-{
-    // digit counts of each 2048-key block: one private histogram per warp
-    // (plain shared-memory atomics), summed per digit at the end.  Only the
-    // blocks that hold keys take part (the grid strides over them, the next
-    // block's keys loaded while this one is counted); the histogram is
-    // [digit][block] over them, so its scan covers 256 x ceil(K / 2048)
-    // entries.  Key arrays are padded to whole blocks.
-    constexpr int W = kRadixThreads / 32;
-    const uint32_t nb = hdr->hist_nblk;
-    if (blockIdx.x >= nb) return;
-    __shared__ uint32_t h[W][kRadixDigits];
-    __shared__ uint32_t seg[kMaxViews + 1];
-    const int w = threadIdx.x >> 5;
-    if (MODE == kDigitView)
-        for (int i = threadIdx.x; i <= nv; i += blockDim.x) seg[i] = hdr->seg[i];
-    const uint32_t K = hdr->k_eff;
-    const uint32_t* src = MODE == kDigitKey ? keys : vals;
-    const bool load = MODE == kDigitKey || !iota;
-    uint32_t d[kRadixItems];
-    auto fetch = [&](uint32_t b) {
-        const int64_t base = (int64_t)b * kRadixBlock;
-#pragma unroll
-        for (int i = 0; i < kRadixItems; i++) {
-            const int64_t idx = base + i * kRadixThreads + threadIdx.x;
-            d[i] = load ? src[idx] : (uint32_t)idx;
-        }
-    };
-    fetch(blockIdx.x);
-    for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
-        uint32_t cur[kRadixItems];
-#pragma unroll
-        for (int i = 0; i < kRadixItems; i++) cur[i] = d[i];
-        if (b + gridDim.x < nb) fetch(b + gridDim.x);
-#pragma unroll
-        for (int i = 0; i < W; i++) h[i][threadIdx.x] = 0;
-        __syncthreads();
-        const int64_t base = (int64_t)b * kRadixBlock;
-#pragma unroll
-        for (int i = 0; i < kRadixItems; i++) {
-            if (base + i * kRadixThreads + threadIdx.x < K) {
-                const uint32_t dg = MODE == kDigitKey ? (cur[i] >> shift) & 0xFFu
-                                                      : (uint32_t)view_of_slot(seg, nv, cur[i]);
-                atomicAdd(&h[w][dg], 1u);
+    for (int k = 2; k <= N; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < (N >> 1); i += blockDim.x) {
+                const int lo = ((i & ~(j - 1)) << 1) | (i & (j - 1));
+                const int hi = lo | j;
+                const unsigned long long x = a[lo], y = a[hi];
+                const bool up = (lo & k) == 0;
+                if ((x > y) == up) {
+                    a[lo] = y;
+                    a[hi] = x;
+                }
             }
+            __syncthreads();
         }
-        __syncthreads();
-        uint32_t c = 0;
-#pragma unroll
-        for (int i = 0; i < W; i++) c += h[i][threadIdx.x];
-        hist[(int64_t)threadIdx.x * nb + b] = c;
-        __syncthreads();
     }
 }
 
-template <int MODE, bool IOTA, bool LAST>
-__global__ void __launch_bounds__(kRadixThreads) k_radix_down(const uint32_t* __restrict__ keys_in,
-                                                               const uint32_t* __restrict__ vals_in,
-                                                               uint32_t* __restrict__ keys_out,
-                                                               uint32_t* __restrict__ vals_out,
-                                                               const uint32_t* __restrict__ hist,
-                                                               int shift, const WsHeader* __restrict__ hdr, int nv,
-                                                               const uint32_t* __restrict__ pid,
-                                                               uint32_t* __restrict__ pid_sorted)
+// Entries of a run [b, b + len) below key x (binary search; keys unique).
+__device__ __forceinline__ uint32_t rank_in_run(const uint32_t* k, const uint32_t* v, uint32_t b, uint32_t len,
+                                                unsigned long long x)
 {
-    // Blocks are double-buffered in shared memory: the next block's keys and
-    // payload are copied asynchronously while this one is ranked, and this
-    // block's buffer then holds its locally reordered keys for the coalesced
-    // write-out.  Key arrays are padded to whole blocks.
-    constexpr int W = kRadixThreads / 32;
-    __shared__ uint32_t wh[W][kRadixDigits];
-    __shared__ uint32_t bstart[kRadixDigits];
-    __shared__ uint32_t gbase[kRadixDigits];
-    __shared__ __align__(16) uint32_t sk[2][kRadixBlock];
-    __shared__ __align__(16) uint32_t sv[2][kRadixBlock];
-    __shared__ uint32_t seg[kMaxViews + 1];
-    __shared__ uint32_t wsum[32];
-    const uint32_t K = hdr->k_eff;
-    const uint32_t nb = hdr->hist_nblk;
-    if (blockIdx.x >= nb) return;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (MODE == kDigitView)
-        for (int i = threadIdx.x; i <= nv; i += blockDim.x) seg[i] = hdr->seg[i];
-    const uint32_t lt = lanemask_lt();
-    auto issue = [&](uint32_t b, int buf) {
-        const int64_t base = (int64_t)b * kRadixBlock;
-        for (int c = threadIdx.x; c < kRadixBlock / 4; c += kRadixThreads) {
-            cp_async16(&sk[buf][4 * c], keys_in + base + 4 * c);
-            if (!IOTA) cp_async16(&sv[buf][4 * c], vals_in + base + 4 * c);
-        }
-        cp_async_commit();
-    };
-    issue(blockIdx.x, 0);
-    int cur = 0;
-    for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x, cur ^= 1) {   // blocks holding keys
-        const int64_t base = (int64_t)b * kRadixBlock;
-        if (b + gridDim.x < nb) issue(b + gridDim.x, cur ^ 1);
-        else cp_async_commit();                 // empty group: the wait below stays one behind
-#pragma unroll
-        for (int i = 0; i < W; i++) wh[i][threadIdx.x] = 0;
-        cp_async_wait<1>();
-        __syncthreads();
+    uint32_t lo = 0, hi = len;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (sort_key(k[b + mid], v[b + mid]) < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
 
-        uint32_t key[kRadixItems], val[kRadixItems], dig[kRadixItems], rank[kRadixItems];
-#pragma unroll
-        for (int r = 0; r < kRadixItems; r++) {
-            const int li = w * (32 * kRadixItems) + r * 32 + lane;
-            const int64_t idx = base + li;
-            const bool valid = idx < K;
-            key[r] = valid ? sk[cur][li] : 0u;
-            val[r] = IOTA ? (uint32_t)idx : (valid ? sv[cur][li] : 0u);
-            uint32_t d = 0xFFFFu;
-            if (valid) {
-                if (MODE == kDigitKey) d = (key[r] >> shift) & 0xFFu;
-                else d = (uint32_t)view_of_slot(seg, nv, val[r]);
-            }
-            dig[r] = d;
-        }
-        // stable rank within the warp's contiguous 256-key range, round by round
-#pragma unroll
-        for (int r = 0; r < kRadixItems; r++) {
-            const uint32_t d = dig[r];
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
-            const bool valid = d != 0xFFFFu;
-            uint32_t c = valid ? wh[w][d] : 0u;
-            rank[r] = c + __popc(peers & lt);
-            __syncwarp();
-            if (valid && lane == __ffs(peers) - 1) wh[w][d] = c + __popc(peers);
-            __syncwarp();
-        }
+// One thread block per tile (launched longest lists first).  Input: the
+// tile's bucket [s0, s1) in (bkey, bval), in atomic arrival order.  Output at
+// the same positions: keys_sorted = tile << shift | depth code, vals_sorted
+// = emission slot, pid_sorted = the slot's pair.
+__global__ void __launch_bounds__(kTileSortThreads) k_tile_sort(Views V, const uint32_t* __restrict__ order,
+                                                                 const uint2* __restrict__ ranges, uint32_t* bkey,
+                                                                 uint32_t* bval, const uint32_t* __restrict__ pid,
+                                                                 uint32_t* keys_sorted, uint32_t* vals_sorted,
+                                                                 uint32_t* __restrict__ pid_sorted)
+{
+    extern __shared__ unsigned long long sk[];
+    const int64_t gt = order[blockIdx.x];
+    const uint2 r = ranges[gt];
+    const uint32_t s0 = r.x, n = r.y - r.x;
+    if (n == 0) return;
+    const ViewDesc& vd = V.v[view_of_tile(V, gt)];
+    const uint32_t hi_bits = (uint32_t)(gt - vd.tile_base) << vd.shift;
+    if (n <= (uint32_t)kTileSortMax) {
+        int N = 1;
+        while (N < (int)n) N <<= 1;
+        for (int i = threadIdx.x; i < N; i += blockDim.x)
+            sk[i] = i < (int)n ? sort_key(bkey[s0 + i], bval[s0 + i]) : ~0ull;
         __syncthreads();
-        // per digit: exclusive offsets across warps, then across digits
-        {
-            const int d = threadIdx.x;
-            uint32_t run = 0;
-#pragma unroll
-            for (int i = 0; i < W; i++) {
-                uint32_t c = wh[i][d];
-                wh[i][d] = run;
-                run += c;
-            }
-            uint32_t ex = block_excl_scan<kRadixThreads>(run, wsum, nullptr);
-            bstart[d] = ex;
-            gbase[d] = hist[(int64_t)d * nb + b];
+        bitonic_sort_smem(sk, N);
+        for (int i = threadIdx.x; i < (int)n; i += blockDim.x) {
+            const unsigned long long x = sk[i];
+            const uint32_t e = (uint32_t)x;
+            keys_sorted[s0 + i] = hi_bits | (uint32_t)(x >> 32);
+            vals_sorted[s0 + i] = e;
+            pid_sorted[s0 + i] = pid[e];
         }
+        return;
+    }
+    // long list: sorted chunks of kTileSortMax into (keys_sorted,
+    // vals_sorted), then merges by rank, alternating with (bkey, bval)
+    const uint32_t M = kTileSortMax;
+    for (uint32_t c0 = 0; c0 < n; c0 += M) {
+        const uint32_t len = min(M, n - c0);
+        for (uint32_t i = threadIdx.x; i < M; i += blockDim.x)
+            sk[i] = i < len ? sort_key(bkey[s0 + c0 + i], bval[s0 + c0 + i]) : ~0ull;
         __syncthreads();
-        // every thread has its items in registers: reorder into this block's buffer
-#pragma unroll
-        for (int r = 0; r < kRadixItems; r++) {
-            const uint32_t d = dig[r];
-            if (d != 0xFFFFu) {
-                const uint32_t lp = bstart[d] + wh[w][d] + rank[r];
-                sk[cur][lp] = key[r];
-                sv[cur][lp] = val[r];
-            }
-        }
-        __syncthreads();
-        const int nvalid = (int)min((int64_t)kRadixBlock, (int64_t)K - base);
-        for (int i = threadIdx.x; i < nvalid; i += kRadixThreads) {
-            const uint32_t k = sk[cur][i], v = sv[cur][i];
-            const uint32_t d = MODE == kDigitKey ? ((k >> shift) & 0xFFu) : (uint32_t)view_of_slot(seg, nv, v);
-            const uint32_t pos = gbase[d] + (uint32_t)i - bstart[d];
-            keys_out[pos] = k;
-            vals_out[pos] = v;
-            if (LAST) pid_sorted[pos] = pid[v];
+        bitonic_sort_smem(sk, (int)M);
+        for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
+            keys_sorted[s0 + c0 + i] = (uint32_t)(sk[i] >> 32);
+            vals_sorted[s0 + c0 + i] = (uint32_t)sk[i];
         }
         __syncthreads();
     }
-    cp_async_wait<0>();
-}
-
-// ---------------------------------------------------------------------------
-// Tile ranges
-// ---------------------------------------------------------------------------
-
-__global__ void __launch_bounds__(256) k_ranges(Views V, const uint32_t* __restrict__ keys,
-                                                const WsHeader* __restrict__ hdr, uint2* __restrict__ ranges,
-                                                uint32_t cap)
-{
-    __shared__ uint32_t seg[kMaxViews + 1];
-    for (int i = threadIdx.x; i <= V.n; i += blockDim.x) seg[i] = hdr->seg[i];
-    __syncthreads();
-    const uint32_t K = hdr->k_eff;
-    // four consecutive keys per thread (one 16-byte load; the capacity is a
-    // multiple of 4) and their two neighbours
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
-    for (int64_t k0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; k0 < K; k0 += stride) {
-        const uint4 q = *reinterpret_cast<const uint4*>(keys + k0);
-        const uint32_t kk[6] = {k0 > 0 ? keys[k0 - 1] : 0u, q.x, q.y, q.z, q.w, k0 + 4 < K ? keys[k0 + 4] : 0u};
-#pragma unroll
-        for (int i = 0; i < 4; i++) {
-            const int64_t k = k0 + i;
-            if (k >= K) break;
-            const int v = view_of_slot(seg, V.n, (uint32_t)k);
-            const ViewDesc& vd = V.v[v];
-            const uint32_t tile = kk[i + 1] >> vd.shift;
-            const int64_t gt = vd.tile_base + tile;
-            const bool first = (k == seg[v]) || ((kk[i] >> vd.shift) != tile);
-            const bool last = (k + 1 == seg[v + 1]) || ((kk[i + 2] >> vd.shift) != tile);
-            if (first) ranges[gt].x = (uint32_t)k;
-            if (last) ranges[gt].y = (uint32_t)(k + 1);
+    uint32_t *sk_in = keys_sorted, *sv_in = vals_sorted, *sk_out = bkey, *sv_out = bval;
+    for (uint32_t run = M; run < n; run <<= 1) {
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+            const uint32_t ri = i / run, b = (ri & ~1u) * run;
+            const unsigned long long x = sort_key(sk_in[s0 + i], sv_in[s0 + i]);
+            uint32_t pos;
+            if ((ri & 1u) == 0) {   // left run: rank among the right run
+                const uint32_t pb = b + run, plen = pb < n ? min(run, n - pb) : 0u;
+                pos = i + (plen ? rank_in_run(sk_in, sv_in, s0 + pb, plen, x) : 0u);
+            } else {                // right run: rank among the left run
+                pos = b + (i - ri * run) + rank_in_run(sk_in, sv_in, s0 + b, run, x);
+            }
+            sk_out[s0 + pos] = sk_in[s0 + i];
+            sv_out[s0 + pos] = sv_in[s0 + i];
         }
+        __syncthreads();
+        uint32_t* t = sk_in; sk_in = sk_out; sk_out = t;
+        t = sv_in; sv_in = sv_out; sv_out = t;
+    }
+    // sk_in / sv_in hold the sorted list; each thread rewrites its own index
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const uint32_t low = sk_in[s0 + i], e = sv_in[s0 + i];
+        keys_sorted[s0 + i] = hi_bits | low;
+        vals_sorted[s0 + i] = e;
+        pid_sorted[s0 + i] = pid[e];
     }
 }
 
@@ -484,59 +397,29 @@ void launch_bin_sort(const Plan& P, const WsPtrs& w, cudaStream_t st)
 {
     const Views& V = P.views;
     const uint32_t cap = (uint32_t)P.cap;
-    // index offset
+    // index offset (Gaussian-major pair order)
     scan_u32(w.count, w.offset, V.pairs, w.scan_part, st);
-    k_count_finalize<<<1, 64, 0, st>>>(V, w.scan_part, P.count_scan_parts, w.offset, w.hdr, cap);
-    // generate keys
+    k_count_finalize<<<1, 32, 0, st>>>(w.scan_part, P.count_scan_parts, V.pairs, w.offset, w.hdr, cap);
+    // tile ranges and scatter cursors from the per-tile counts
+    scan_u32(w.tile_cnt, w.tile_cur, V.tiles, w.scan_part, st);
     {
-        const int64_t blocks = (V.pairs + 255) / 256;
-        k_emit<<<(unsigned)blocks, 256, 0, st>>>(V, w.count, w.offset, w.rec, w.binrec, w.keysA, w.pid, cap);
-    }
-    // sorting: the radix kernels stride over the blocks that hold keys, with
-    // grids of the resident CTAs (8 per SM for the counts, 4 for the
-    // double-buffered reorder)
-    const int64_t nblk = std::min<int64_t>(P.radix_blocks, (int64_t)P.sm_count * 8);
-    const int64_t nblk_down = std::min<int64_t>(P.radix_blocks, (int64_t)P.sm_count * 4);
-    const int npass = P.key_passes + P.view_pass;
-    uint32_t *kin = w.keysA, *vin = w.valsA, *kout = w.keysB, *vout = w.valsB;
-    for (int pass = 0; pass < npass; pass++) {
-        const bool view = pass >= P.key_passes;
-        const bool first = pass == 0, last = pass == npass - 1;
-        const int shift = 8 * pass;
-        if (view)
-            k_radix_up<kDigitView><<<(unsigned)nblk, kRadixThreads, 0, st>>>(kin, vin, first, w.hdr, 0, w.hist, V.n);
-        else
-            k_radix_up<kDigitKey><<<(unsigned)nblk, kRadixThreads, 0, st>>>(kin, vin, first, w.hdr, shift, w.hist,
-                                                                              V.n);
-        scan_u32_dyn(w.hist, w.hist, (int64_t)kRadixDigits * P.radix_blocks, &w.hdr->hist_nblk, kRadixDigits,
-                     w.scan_part, st);
-#define GS_DOWN(MODE, IOTA, LAST)                                                                          \
-    k_radix_down<MODE, IOTA, LAST><<<(unsigned)nblk_down, kRadixThreads, 0, st>>>(kin, vin, kout, vout, w.hist, shift, \
-                                                                              w.hdr, V.n, w.pid, w.pid_sorted)
-        if (view) {
-            if (first) GS_DOWN(kDigitView, true, true);
-            else GS_DOWN(kDigitView, false, true);
-        } else if (first) {
-            if (last) GS_DOWN(kDigitKey, true, true);
-            else GS_DOWN(kDigitKey, true, false);
-        } else {
-            if (last) GS_DOWN(kDigitKey, false, true);
-            else GS_DOWN(kDigitKey, false, false);
-        }
-#undef GS_DOWN
-        uint32_t* t;
-        t = kin; kin = kout; kout = t;
-        t = vin; vin = vout; vout = t;
-    }
-    // tile ranges
-    launch_fill_u32(reinterpret_cast<uint32_t*>(w.ranges), 2 * V.tiles, 0u, st);
-    {
-        int64_t blocks = ((int64_t)cap + 255) / 256;
-        if (blocks > 152 * 32) blocks = 152 * 32;
-        if (blocks < 1) blocks = 1;
-        k_ranges<<<(unsigned)blocks, 256, 0, st>>>(V, w.keys_sorted, w.hdr, w.ranges, cap);
+        const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((V.tiles + 255) / 256, (int64_t)P.sm_count * 8));
+        k_tile_setup<<<(unsigned)blocks, 256, 0, st>>>(V.tiles, w.tile_cnt, w.tile_cur, w.hdr, w.ranges);
     }
     k_tile_order<<<1, 1024, 0, st>>>(V.tiles, w.ranges, w.tile_order);
+    // generate keys into the tile buckets
+    {
+        const int64_t blocks = (V.pairs + 255) / 256;
+        k_emit<<<(unsigned)blocks, 256, 0, st>>>(V, w.count, w.offset, w.rec, w.binrec, w.tile_cur, w.bkey, w.bval,
+                                                 w.pid, w.hdr);
+    }
+    // sort each tile's list
+    {
+        const size_t smem = sizeof(unsigned long long) * kTileSortMax;   // 32 KB: no opt-in needed
+        k_tile_sort<<<(unsigned)V.tiles, kTileSortThreads, smem, st>>>(V, w.tile_order, w.ranges, w.bkey, w.bval,
+                                                                       w.pid, w.keys_sorted, w.vals_sorted,
+                                                                       w.pid_sorted);
+    }
 }
 
 }  // namespace gs

@@ -28,23 +28,21 @@ WsPtrs carve(const Plan& P, void* ws)
     w.offset = reinterpret_cast<uint32_t*>(b + P.off_offset);
     w.rec = reinterpret_cast<ProjRec*>(b + P.off_rec);
     w.binrec = reinterpret_cast<float4*>(b + P.off_binrec);
-    w.keysA = reinterpret_cast<uint32_t*>(b + P.off_keysA);
-    w.valsA = reinterpret_cast<uint32_t*>(b + P.off_valsA);
-    w.keysB = reinterpret_cast<uint32_t*>(b + P.off_keysB);
-    w.valsB = reinterpret_cast<uint32_t*>(b + P.off_valsB);
+    w.bkey = reinterpret_cast<uint32_t*>(b + P.off_bkey);
+    w.bval = reinterpret_cast<uint32_t*>(b + P.off_bval);
+    w.keys_sorted = reinterpret_cast<uint32_t*>(b + P.off_keys);
+    w.vals_sorted = reinterpret_cast<uint32_t*>(b + P.off_vals);
     w.pid = reinterpret_cast<uint32_t*>(b + P.off_pid);
     w.pid_sorted = reinterpret_cast<uint32_t*>(b + P.off_pid_sorted);
+    w.tile_cnt = reinterpret_cast<uint32_t*>(b + P.off_tile_cnt);
+    w.tile_cur = reinterpret_cast<uint32_t*>(b + P.off_tile_cur);
     w.ranges = reinterpret_cast<uint2*>(b + P.off_ranges);
     w.tile_order = reinterpret_cast<uint32_t*>(b + P.off_order);
     w.nlast = reinterpret_cast<uint32_t*>(b + P.off_nlast);
     w.tfinal = reinterpret_cast<float*>(b + P.off_tfinal);
     w.gradrec = reinterpret_cast<GradRec*>(b + P.off_gradrec);
     w.scan_part = reinterpret_cast<uint32_t*>(b + P.off_scan_part);
-    w.hist = reinterpret_cast<uint32_t*>(b + P.off_hist);
     w.loss_part = reinterpret_cast<float*>(b + P.off_loss_part);
-    const bool odd = ((P.key_passes + P.view_pass) & 1) != 0;
-    w.keys_sorted = odd ? w.keysB : w.keysA;
-    w.vals_sorted = odd ? w.valsB : w.valsA;
     return w;
 }
 
@@ -96,6 +94,7 @@ static bool plan_build(Plan& P, const int64_t* scene_n, int32_t n_scenes, const 
     V.n = n_views;
     V.tw = t.tile_w;
     V.th = t.tile_h;
+    V.n_scenes = n_scenes;
     int64_t pairs = 0, tiles = 0, pixels = 0;
     int max_bits = 0;
     for (int v = 0; v < n_views; v++) {
@@ -108,6 +107,9 @@ static bool plan_build(Plan& P, const int64_t* scene_n, int32_t n_scenes, const 
         d.TX = (gv.width + t.tile_w - 1) / t.tile_w;
         d.TY = (gv.height + t.tile_h - 1) / t.tile_h;
         d.scene = gv.scene;
+        d.rank = V.nv[gv.scene];
+        V.view_of[gv.scene][d.rank] = (uint8_t)v;
+        V.nv[gv.scene] += 1;
         const int tb = ceil_log2((int64_t)d.TX * d.TY);
         d.shift = tb >= 9 ? 32 - tb : 23;
         d.drop = tb >= 9 ? tb - 9 : 0;
@@ -122,16 +124,22 @@ static bool plan_build(Plan& P, const int64_t* scene_n, int32_t n_scenes, const 
     V.pairs = pairs;
     V.tiles = tiles;
     V.pixels = pixels;
-    if (pairs >= ((int64_t)1 << 31)) return false;
+    (void)max_bits;
+    {
+        int64_t q = 0;
+        for (int sc = 0; sc < n_scenes; sc++) {
+            V.qbase[sc] = q;
+            q += scene_n[sc] * V.nv[sc];
+        }
+        V.qbase[n_scenes] = q;
+    }
+    if (pairs >= ((int64_t)1 << 31) || tiles >= ((int64_t)1 << 31)) return false;
     if (cap <= 0) cap = std::max<int64_t>(4096, 8 * pairs);
-    cap = align_up((size_t)cap, kRadixBlock);
+    cap = align_up((size_t)cap, kCapGranule);
     if (cap >= ((int64_t)1 << 31)) return false;
     P.cap = cap;
-    P.key_passes = (max_bits + 7) / 8;
-    P.view_pass = n_views > 1 ? 1 : 0;
-    P.radix_blocks = cap / kRadixBlock;
     P.count_scan_parts = (pairs + kScanBlock - 1) / kScanBlock;
-    P.hist_scan_parts = (kRadixDigits * P.radix_blocks + kScanBlock - 1) / kScanBlock;
+    P.tile_scan_parts = (tiles + kScanBlock - 1) / kScanBlock;
     P.raster_blocks = tiles;
     const int64_t loss_blocks = std::max<int64_t>((3 * pixels + 2047) / 2048, 2 * ssim_tiles(V));
 
@@ -146,19 +154,20 @@ static bool plan_build(Plan& P, const int64_t* scene_n, int32_t n_scenes, const 
     P.off_offset = take(4 * (size_t)(pairs + 1));
     P.off_rec = take(sizeof(ProjRec) * (size_t)pairs);
     P.off_binrec = take(16 * (size_t)pairs);
-    P.off_keysA = take(4 * (size_t)cap);
-    P.off_valsA = take(4 * (size_t)cap);
-    P.off_keysB = take(4 * (size_t)cap);
-    P.off_valsB = take(4 * (size_t)cap);
+    P.off_bkey = take(4 * (size_t)cap);
+    P.off_bval = take(4 * (size_t)cap);
+    P.off_keys = take(4 * (size_t)cap);
+    P.off_vals = take(4 * (size_t)cap);
     P.off_pid = take(4 * (size_t)cap);
     P.off_pid_sorted = take(4 * (size_t)cap);
+    P.off_tile_cnt = take(4 * (size_t)tiles);
+    P.off_tile_cur = take(4 * (size_t)(tiles + 1));
     P.off_ranges = take(8 * (size_t)tiles);
     P.off_order = take(4 * (size_t)tiles);
     P.off_nlast = take(4 * (size_t)pixels);
     P.off_tfinal = take(4 * (size_t)pixels);
     P.off_gradrec = take(sizeof(GradRec) * (size_t)cap);
-    P.off_scan_part = take(4 * (size_t)(std::max(P.count_scan_parts, P.hist_scan_parts) + 1));
-    P.off_hist = take(4 * (size_t)kRadixDigits * (size_t)P.radix_blocks);
+    P.off_scan_part = take(4 * (size_t)(std::max(P.count_scan_parts, P.tile_scan_parts) + 1));
     P.off_loss_part = take(4 * (size_t)loss_blocks);
     P.ws_bytes = o;
     return true;
@@ -184,9 +193,11 @@ Scenes make_scenes(const Plan& P, const gs_scene_buf* scenes)
     return S;
 }
 
-__global__ void k_ws_init(WsHeader* hdr, int full)
+// Header reset (and, with `full`, the Adam step counter); the per-tile
+// counters that the projection adds to start from zero.
+__global__ void k_ws_init(WsHeader* hdr, int full, uint32_t* __restrict__ tile_cnt, int64_t tiles)
 {
-    if (threadIdx.x == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         hdr->status = 0;
         hdr->k_required = 0;
         hdr->blended = 0;
@@ -195,11 +206,24 @@ __global__ void k_ws_init(WsHeader* hdr, int full)
         hdr->loss = 0.f;
         if (full) hdr->step = 0;
     }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tiles; i += (int64_t)gridDim.x * blockDim.x)
+        tile_cnt[i] = 0u;
 }
 
-void launch_ws_init(const Plan&, const WsPtrs& w, cudaStream_t st) { k_ws_init<<<1, 32, 0, st>>>(w.hdr, 1); }
+static unsigned init_blocks(const Plan& P)
+{
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((P.views.tiles + 255) / 256, (int64_t)P.sm_count * 8));
+}
 
-static void launch_step_begin(const WsPtrs& w, cudaStream_t st) { k_ws_init<<<1, 32, 0, st>>>(w.hdr, 0); }
+void launch_ws_init(const Plan& P, const WsPtrs& w, cudaStream_t st)
+{
+    k_ws_init<<<init_blocks(P), 256, 0, st>>>(w.hdr, 1, w.tile_cnt, P.views.tiles);
+}
+
+static void launch_step_begin(const Plan& P, const WsPtrs& w, cudaStream_t st)
+{
+    k_ws_init<<<init_blocks(P), 256, 0, st>>>(w.hdr, 0, w.tile_cnt, P.views.tiles);
+}
 
 __global__ void k_adam_advance(WsHeader* hdr)
 {
@@ -293,7 +317,7 @@ gs_status gs_project_fwd(const gs_plan* plan, void* ws, const gs_scene_buf* scen
     if (e != GS_OK) return e;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     WsPtrs w = carve(P, ws);
-    launch_step_begin(w, st);
+    launch_step_begin(P, w, st);
     launch_project_fwd(P, make_scenes(P, scenes), cams, w, st);
     return launch_status();
 }

@@ -19,18 +19,27 @@ struct ViewDesc {
     int32_t scene;
     int32_t shift;         // key >> shift = tile id
     int32_t drop;          // depth code >> drop = low key bits
-    int32_t pad;
+    int32_t rank;          // index of this view among its scene's views
     int64_t pair_base;     // first (view, Gaussian) pair of this view
     int64_t tile_base;     // first global tile of this view
     int64_t pix_base;      // first pixel of this view
 };
 
+// Two orders of the (view, Gaussian) pairs:
+//  - view-major pair index p = pair_base[v] + g (projected records, the
+//    pair index the sorted lists carry);
+//  - Gaussian-major index q = qbase[s] + g * nv[s] + rank[v] (tile counts,
+//    their offsets and so the emission slots of the intersections): a
+//    Gaussian's intersections in all views of its scene are contiguous.
 struct Views {
     int32_t n;
     int32_t tw, th;        // tile size, pixels
-    int32_t pad;
+    int32_t n_scenes;
     int64_t pairs, tiles, pixels;
     ViewDesc v[kMaxViews];
+    int64_t qbase[kMaxScenes + 1];
+    int32_t nv[kMaxScenes];             // views of each scene
+    uint8_t view_of[kMaxScenes][kMaxViews];   // view of each (scene, rank)
 };
 
 struct SceneDesc {
@@ -57,12 +66,11 @@ struct WsHeader {
     int32_t step;
     unsigned long long k_required;
     unsigned long long blended;
-    uint32_t k_eff;            // min(k_required, capacity)
+    uint32_t k_eff;            // k_required if it fits the capacity, else 0
     uint32_t loss_counter;
     float loss;
-    uint32_t hist_nblk;           // radix-sort blocks holding keys: ceil(k_eff / 2048)
+    uint32_t pad;
     float bg[4];                  // background colour of the last raster_fwd
-    uint32_t seg[kMaxViews + 1];  // sorted-segment start of each view
 };
 
 // Projected record of one (view, Gaussian) pair, read by the raster kernels.

@@ -9,11 +9,14 @@
 
 namespace gs {
 
-// Radix sort geometry: 256 threads x 8 keys per block, 8-bit digits.
-constexpr int kRadixThreads = 256;
-constexpr int kRadixItems = 8;
-constexpr int kRadixBlock = kRadixThreads * kRadixItems;
-constexpr int kRadixDigits = 256;
+// Intersection capacity granule (the capacity is rounded up to it).
+constexpr int kCapGranule = 2048;
+
+// Per-tile sort: lists of up to kTileSortMax entries are sorted in shared
+// memory by one thread block; longer lists are sorted in chunks of that size
+// and merged in global memory by the same block.
+constexpr int kTileSortThreads = 256;
+constexpr int kTileSortMax = 4096;
 
 // Exclusive scan geometry: 512 threads x 8 values per block.
 constexpr int kScanThreads = 512;
@@ -31,40 +34,39 @@ struct Plan {
     int64_t cap;                 // intersection capacity
     gs_tuning tuning;
     int32_t sh_bf16, mom_bf16;
-    int32_t key_passes;          // 8-bit LSD passes over the key
-    int32_t view_pass;           // one more pass ordering the views
-    int64_t radix_blocks;        // ceil(cap / kRadixBlock)
-    int64_t count_scan_parts;    // ceil((pairs + 1) / kScanBlock)
-    int64_t hist_scan_parts;     // ceil(256 * radix_blocks / kScanBlock)
+    int64_t count_scan_parts;    // ceil(pairs / kScanBlock)
+    int64_t tile_scan_parts;     // ceil(tiles / kScanBlock)
     int64_t raster_blocks;       // total tiles
     int32_t sm_count;            // SMs of the device current at plan creation (152 if none)
     // workspace byte offsets
     size_t off_hdr, off_count, off_offset, off_rec, off_binrec;
-    size_t off_keysA, off_valsA, off_keysB, off_valsB, off_pid, off_pid_sorted;
-    size_t off_ranges, off_nlast, off_tfinal, off_gradrec, off_scan_part, off_hist, off_loss_part, off_order;
+    size_t off_bkey, off_bval, off_keys, off_vals, off_pid, off_pid_sorted;
+    size_t off_tile_cnt, off_tile_cur;
+    size_t off_ranges, off_nlast, off_tfinal, off_gradrec, off_scan_part, off_loss_part, off_order;
     size_t ws_bytes;
 };
 
 struct WsPtrs {
     WsHeader* hdr;
-    uint32_t* count;
-    uint32_t* offset;
-    ProjRec* rec;
+    uint32_t* count;           // tiles per pair, Gaussian-major order
+    uint32_t* offset;          // its exclusive scan: first emission slot of each pair
+    ProjRec* rec;              // projected records, view-major pair order
     float4* binrec;
-    uint32_t *keysA, *valsA, *keysB, *valsB;
-    uint32_t* pid;
-    uint32_t* pid_sorted;
+    uint32_t* bkey;            // tile buckets: depth code of each entry
+    uint32_t* bval;            // tile buckets: emission slot of each entry
+    uint32_t* pid;             // view-major pair of each emission slot
+    uint32_t* keys_sorted;     // sorted keys (tile << shift | depth code)
+    uint32_t* vals_sorted;     // emission slot of each sorted entry
+    uint32_t* pid_sorted;      // pair of each sorted entry
+    uint32_t* tile_cnt;        // entries per global tile
+    uint32_t* tile_cur;        // tile starts, then the scatter cursors
     uint2* ranges;
     uint32_t* tile_order;      // tiles by decreasing list length (raster launch order)
     uint32_t* nlast;
     float* tfinal;
     GradRec* gradrec;
     uint32_t* scan_part;
-    uint32_t* hist;
     float* loss_part;
-    // where the sort leaves its result
-    uint32_t* keys_sorted;
-    uint32_t* vals_sorted;
 };
 
 WsPtrs carve(const Plan& P, void* ws);

@@ -37,7 +37,9 @@ uint32_t* g_scratch_addr[kNaMaxDevices];
 // Device address of the scratch array on the current device.  In host code
 // the array's name is only a host-side stand-in, so the address is looked up
 // once per device with cudaGetSymbolAddress (with that device current) and
-// cached.
+// cached.  It is the address in the device's primary context; a device reset
+// or another current context would make it stale, which the header rules
+// out for callers.
 gs_status scratch_on_current_device(uint32_t** out)
 {
     int dev = -1;

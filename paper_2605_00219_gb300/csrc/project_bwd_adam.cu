@@ -45,15 +45,6 @@ __device__ __forceinline__ void adam1(float& th, float& m, float& v, float g, fl
     th -= __fdividef(alpha * m, sqrt_approx(v) + K.epsp);
 }
 
-// SH coefficient chunk j (flat indices 4j..4j+3) of Gaussian g.
-__device__ __forceinline__ float4 sh_chunk(const SceneDesc& sc, int bf16, int64_t g, int j)
-{
-    if (!bf16) return reinterpret_cast<const float4*>(sc.sh)[(int64_t)j * sc.n + g];
-    const uint4 c = reinterpret_cast<const uint4*>(sc.sh)[(int64_t)(j >> 1) * sc.n + g];
-    const uint32_t u0 = (j & 1) ? c.z : c.x, u1 = (j & 1) ? c.w : c.y;
-    return make_float4(bf16_lo(u0), bf16_hi(u0), bf16_lo(u1), bf16_hi(u1));
-}
-
 // Rotation R of the normalised quaternion q = (w, x, y, z) and
 // M = R diag(s); returns 1 / |q|.
 __device__ __forceinline__ float rot_scale(float4 q, float4 so, float* R, float* M, float& w, float& x, float& y,
@@ -117,11 +108,12 @@ __device__ __forceinline__ void covariance3d_bwd(float4 q, float4 so, const floa
 // accumulates dmu, dSg (dL/dSigma, symmetric) and dop (activated opacity),
 // and returns the SH basis at the view direction (Y) and dL/d(raw colour)
 // (draw) so that the SH gradient sum_v Y_v[k] draw_v[c] can be formed later.
-// The SH coefficients are streamed twice (clamp test, then the direction
-// gradient) instead of being held in registers.
+// The SH coefficients are read twice (clamp test, then the direction
+// gradient) from the thread's shared-memory row instead of being held in
+// registers.
 __device__ __forceinline__ void proj_bwd_view(const float* cam, int W, int H, float4 mu, const float* Sg,
-                                              const SceneDesc& sc, int bf16, int64_t g, const float* g2,
-                                              float* dmu, float* dSg, float& dop, float* Y, float* draw)
+                                              const float4* shrow, const float* g2, float* dmu, float* dSg,
+                                              float& dop, float* Y, float* draw)
 {
     const float fx = cam[12], fy = cam[13];
     const float* C = cam;
@@ -141,7 +133,7 @@ __device__ __forceinline__ void proj_bwd_view(const float* cam, int W, int H, fl
     float raw[3] = {0.5f, 0.5f, 0.5f};
 #pragma unroll
     for (int j = 0; j < 12; j++) {
-        const float4 c4 = sh_chunk(sc, bf16, g, j);
+        const float4 c4 = shrow[j];
         const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
         for (int i = 0; i < 4; i++) raw[(4 * j + i) % 3] = fmaf(cv[i], Y[(4 * j + i) / 3], raw[(4 * j + i) % 3]);
@@ -153,7 +145,7 @@ __device__ __forceinline__ void proj_bwd_view(const float* cam, int W, int H, fl
     for (int k = 0; k < 16; k++) wk[k] = 0.f;
 #pragma unroll
     for (int j = 0; j < 12; j++) {
-        const float4 c4 = sh_chunk(sc, bf16, g, j);
+        const float4 c4 = shrow[j];
         const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
         for (int i = 0; i < 4; i++) wk[(4 * j + i) / 3] = fmaf(cv[i], draw[(4 * j + i) % 3], wk[(4 * j + i) / 3]);
@@ -320,9 +312,13 @@ __global__ void __launch_bounds__(kPbaThreads, 4) k_project_bwd_adam(Views V, Sc
                                                                   float4* __restrict__ grads_out,
                                                                   const WsHeader* __restrict__ hdr, uint32_t cap)
 {
-    // SH gradients, 12 float4 per thread (row stride 13 float4: the 16-byte
-    // accesses of 8 consecutive threads cover all 32 banks once)
-    __shared__ float4 sG[kPbaThreads][13];
+    // per thread, 12 float4 rows (stride 13 float4: the 16-byte accesses of
+    // 8 consecutive threads cover all 32 banks once): the SH gradients, and
+    // the Gaussian's 48 SH coefficients in FP32, read from HBM once and used
+    // by every view and by the SH update
+    extern __shared__ float4 pba_smem[];
+    float4 (*sG)[13] = reinterpret_cast<float4 (*)[13]>(pba_smem);
+    float4 (*sS)[13] = reinterpret_cast<float4 (*)[13]>(pba_smem + kPbaThreads * 13);
     __shared__ AdamConst sK;
     const int tid = threadIdx.x;
     const int64_t gi = (int64_t)blockIdx.x * kPbaThreads + tid;
@@ -353,42 +349,42 @@ __global__ void __launch_bounds__(kPbaThreads, 4) k_project_bwd_adam(Views V, Sc
         float4 q = sc.geom[n + g];
         float4 so = sc.geom[2 * n + g];
         if (!A.grad_only) {
-            // the moments and the SH chunks are read only after the
-            // projection backward of every view: request their lines into L2
-            // now (no registers held)
+            // the moments are read only after the projection backward of
+            // every view: request their lines into L2 now (no registers held)
 #pragma unroll
             for (int ci = 0; ci < 15; ci++) {
                 prefetch_l2(reinterpret_cast<const char*>(sc.m) + ((int64_t)ci * n + g) * (MOM16 ? 8 : 16));
                 prefetch_l2(reinterpret_cast<const char*>(sc.v) + ((int64_t)ci * n + g) * (MOM16 ? 8 : 16));
             }
+        }
+        if (!SH16) {
 #pragma unroll
-            for (int j = 0; j < (SH16 ? 6 : 12); j++)
-                prefetch_l2(reinterpret_cast<const char*>(sc.sh) + ((int64_t)j * n + g) * 16);
+            for (int j = 0; j < 12; j++) sS[tid][j] = reinterpret_cast<const float4*>(sc.sh)[(int64_t)j * n + g];
+        } else {
+#pragma unroll
+            for (int jp = 0; jp < 6; jp++) {
+                const uint4 c = reinterpret_cast<const uint4*>(sc.sh)[(int64_t)jp * n + g];
+                sS[tid][2 * jp] = make_float4(bf16_lo(c.x), bf16_hi(c.x), bf16_lo(c.y), bf16_hi(c.y));
+                sS[tid][2 * jp + 1] = make_float4(bf16_lo(c.z), bf16_hi(c.z), bf16_lo(c.w), bf16_hi(c.w));
+            }
         }
         float dmu[3] = {0.f, 0.f, 0.f}, dSg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, dop = 0.f;
         float Sg[6];
         covariance3d(q, so, Sg);
         float st_sum = 0.f, st_cnt = 0.f;   // densification statistics of this step
-        // the next view's count and offset are loaded while this view is
+        // the Gaussian's intersection records of all views of its scene are
+        // consecutive from its first emission slot (Gaussian-major slot
+        // order); the next view's count is loaded while this view is
         // processed
-        auto seek = [&](int u) {
-            while (u < V.n && V.v[u].scene != s) u++;
-            return u;
-        };
-        int vn = seek(0);
-        uint32_t cnt_n = 0, off_n = 0;
-        if (vn < V.n) {
-            cnt_n = count[V.v[vn].pair_base + g];
-            off_n = offset[V.v[vn].pair_base + g];
-        }
-        while (vn < V.n) {
-            const int v = vn;
-            const uint32_t cnt = cnt_n, off = off_n;
-            vn = seek(v + 1);
-            if (vn < V.n) {
-                cnt_n = count[V.v[vn].pair_base + g];
-                off_n = offset[V.v[vn].pair_base + g];
-            }
+        const int nv = V.nv[s];
+        const int64_t q0 = V.qbase[s] + g * nv;
+        uint32_t e_next = offset[q0];
+        uint32_t cnt_n = count[q0];
+        for (int k = 0; k < nv; k++) {
+            const int v = V.view_of[s][k];
+            const uint32_t cnt = cnt_n, off = e_next;
+            e_next += cnt;
+            if (k + 1 < nv) cnt_n = count[q0 + k + 1];
             if (cnt == 0) continue;
             const ViewDesc& vd = V.v[v];
             const uint32_t end = min(off + cnt, cap);
@@ -413,7 +409,7 @@ __global__ void __launch_bounds__(kPbaThreads, 4) k_project_bwd_adam(Views V, Sc
 #pragma unroll
             for (int i = 0; i < 16; i++) cam[i] = __ldg(cams + 16 * v + i);
             float Y[16], draw[3];
-            proj_bwd_view(cam, vd.W, vd.H, mu, Sg, sc, SH16 ? 1 : 0, g, g2, dmu, dSg, dop, Y, draw);
+            proj_bwd_view(cam, vd.W, vd.H, mu, Sg, sS[tid], g2, dmu, dSg, dop, Y, draw);
 #pragma unroll
             for (int j = 0; j < 12; j++) {
                 float4 a = sG[tid][j];
@@ -490,14 +486,9 @@ __global__ void __launch_bounds__(kPbaThreads, 4) k_project_bwd_adam(Views V, Sc
 #pragma unroll 3
     for (int jp = 0; jp < 6; jp++) {          // pairs of chunks = 8 coefficients
         float th[8];
-        if (!SH16) {
-            const float4 a = reinterpret_cast<const float4*>(sc.sh)[(int64_t)(2 * jp) * n + g];
-            const float4 b = reinterpret_cast<const float4*>(sc.sh)[(int64_t)(2 * jp + 1) * n + g];
+        {
+            const float4 a = sS[tid][2 * jp], b = sS[tid][2 * jp + 1];
             th[0] = a.x; th[1] = a.y; th[2] = a.z; th[3] = a.w; th[4] = b.x; th[5] = b.y; th[6] = b.z; th[7] = b.w;
-        } else {
-            const uint4 c = reinterpret_cast<const uint4*>(sc.sh)[(int64_t)jp * n + g];
-            th[0] = bf16_lo(c.x); th[1] = bf16_hi(c.x); th[2] = bf16_lo(c.y); th[3] = bf16_hi(c.y);
-            th[4] = bf16_lo(c.z); th[5] = bf16_hi(c.z); th[6] = bf16_lo(c.w); th[7] = bf16_hi(c.w);
         }
 #pragma unroll
         for (int h = 0; h < 2; h++) {
@@ -540,8 +531,13 @@ void launch_project_bwd_adam(const Plan& P, const Scenes& S, const float* cams, 
     A.grad_only = grads_out != nullptr;
     A.seed = adam ? adam->seed : 0u;
     const int64_t blocks = (S.total + kPbaThreads - 1) / kPbaThreads;
-#define GS_PBA(SH, MO) k_project_bwd_adam<SH, MO><<<(unsigned)blocks, kPbaThreads, 0, st>>>(P.views, S, cams, w.count, \
-                              w.offset, w.gradrec, A, reinterpret_cast<float4*>(grads_out), w.hdr, (uint32_t)P.cap)
+    const size_t smem = sizeof(float4) * 2 * kPbaThreads * 13;   // 53 KB: above the default 48 KB
+#define GS_PBA(SH, MO)                                                                                              \
+    do {                                                                                                            \
+        cudaFuncSetAttribute(k_project_bwd_adam<SH, MO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);   \
+        k_project_bwd_adam<SH, MO><<<(unsigned)blocks, kPbaThreads, smem, st>>>(P.views, S, cams, w.count, w.offset, \
+                              w.gradrec, A, reinterpret_cast<float4*>(grads_out), w.hdr, (uint32_t)P.cap);         \
+    } while (0)
     if (!P.sh_bf16 && !P.mom_bf16) GS_PBA(false, false);
     else if (P.sh_bf16 && P.mom_bf16) GS_PBA(true, true);
     else if (P.sh_bf16) GS_PBA(true, false);

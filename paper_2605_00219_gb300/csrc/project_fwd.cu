@@ -3,8 +3,12 @@
 // projection-forward pass).  One thread per Gaussian, looping over the views
 // of its scene: the parameters are read from HBM once, the SH coefficients
 // once per surviving (view, Gaussian) pair from the first read's cached
-// lines; SoA float4 loads; the outputs of pair (v, g) go to pair
-// pair_base[v] + g, so consecutive threads write consecutive records.
+// lines; SoA float4 loads; the records of pair (v, g) go to the view-major
+// pair pair_base[v] + g, so consecutive threads write consecutive records,
+// and its tile count to the Gaussian-major pair q (a Gaussian's counts for
+// all views of its scene side by side).  The traversal that counts the tiles
+// also adds one to the counter of every tile it meets: the per-tile list
+// lengths from which the sort places each tile's list.
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -12,8 +16,9 @@ namespace gs {
 // One (view, Gaussian) pair: tile count, and for a pair that meets a tile its
 // projected record and binning geometry.
 __device__ __forceinline__ void project_pair(const ViewDesc& vd, int tw, int th, const SceneDesc& sc, int sh_bf16,
-                                             const float* __restrict__ camp, int64_t g, int64_t p, const float4& mu,
-                                             const float4& q, const float4& so, uint32_t* __restrict__ count,
+                                             const float* __restrict__ camp, int64_t g, int64_t p, int64_t qi,
+                                             const float4& mu, const float4& q, const float4& so,
+                                             uint32_t* __restrict__ count, uint32_t* __restrict__ tile_cnt,
                                              ProjRec* __restrict__ rec, float4* __restrict__ binrec)
 {
     float cam[16];
@@ -22,8 +27,9 @@ __device__ __forceinline__ void project_pair(const ViewDesc& vd, int tw, int th,
     BinGeom bg;
     bin_project(mu, q, so, cam, vd.W, vd.H, bg);
     uint32_t cnt = 0;
-    if (bg.valid) cnt = scanline_tiles(bg, tw, th, vd.TX, vd.TY, [](uint32_t, uint32_t) {});
-    count[p] = cnt;
+    uint32_t* __restrict__ tc = tile_cnt + vd.tile_base;
+    if (bg.valid) cnt = scanline_tiles(bg, tw, th, vd.TX, vd.TY, [&](uint32_t, uint32_t tile) { atomicAdd(tc + tile, 1u); });
+    count[qi] = cnt;
     if (cnt == 0) return;
 
     // conic = inverse of the 2D covariance
@@ -63,8 +69,9 @@ __device__ __forceinline__ void project_pair(const ViewDesc& vd, int tw, int th,
 // 3 CTAs per SM: the register cap (80) costs a few spills but raises occupancy
 // from 2 to 3 CTAs
 __global__ void __launch_bounds__(256, 3) k_project_fwd(Views V, Scenes S, const float* __restrict__ cams,
-                                                     uint32_t* __restrict__ count, ProjRec* __restrict__ rec,
-                                                     float4* __restrict__ binrec, WsHeader* __restrict__ hdr)
+                                                     uint32_t* __restrict__ count, uint32_t* __restrict__ tile_cnt,
+                                                     ProjRec* __restrict__ rec, float4* __restrict__ binrec,
+                                                     WsHeader* __restrict__ hdr)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= S.total) return;
@@ -80,15 +87,18 @@ __global__ void __launch_bounds__(256, 3) k_project_fwd(Views V, Scenes S, const
                         isfinite(q.z) && isfinite(q.w) && isfinite(so.x) && isfinite(so.y) && isfinite(so.z) &&
                         isfinite(so.w);
     if (!finite) atomicOr(&hdr->status, GS_STATUS_NONFINITE);
-    for (int v = 0; v < V.n; v++) {
+    const int nv = V.nv[s];
+    const int64_t q0 = V.qbase[s] + g * nv;
+    for (int k = 0; k < nv; k++) {
+        const int v = V.view_of[s][k];
         const ViewDesc& vd = V.v[v];
-        if (vd.scene != s) continue;
         const int64_t p = vd.pair_base + g;
         if (!finite) {
-            count[p] = 0;
+            count[q0 + k] = 0;
             continue;
         }
-        project_pair(vd, V.tw, V.th, sc, S.sh_bf16, cams + 16 * v, g, p, mu, q, so, count, rec, binrec);
+        project_pair(vd, V.tw, V.th, sc, S.sh_bf16, cams + 16 * v, g, p, q0 + k, mu, q, so, count, tile_cnt, rec,
+                     binrec);
     }
 }
 
@@ -97,7 +107,7 @@ void launch_project_fwd(const Plan& P, const Scenes& S, const float* cams, const
     const int T = 256;
     const int64_t blocks = (S.total + T - 1) / T;
     if (blocks == 0) return;
-    k_project_fwd<<<(unsigned)blocks, T, 0, st>>>(P.views, S, cams, w.count, w.rec, w.binrec, w.hdr);
+    k_project_fwd<<<(unsigned)blocks, T, 0, st>>>(P.views, S, cams, w.count, w.tile_cnt, w.rec, w.binrec, w.hdr);
 }
 
 }  // namespace gs

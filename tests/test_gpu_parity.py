@@ -317,6 +317,39 @@ def test_multi_view_uneven(gs, orc):
         assert np.abs(im.cpu().numpy().astype(np.float64) - r.image)[ok].max() <= 1e-5
 
 
+def test_long_tile_lists(gs, orc, report):
+    """Tile lists far longer than one thread block sorts in shared memory
+    (about 20,000 entries per tile on a 64x64 view): the sorted keys and
+    Gaussians are the oracle's stable sort bit for bit, and the image matches
+    on stable pixels."""
+    gsstep, step_mod = gs
+    rng = np.random.default_rng(21)
+    n = 20000
+    scene = synth.Scene(rng.uniform(-0.3, 0.3, (n, 3)).astype(np.float32),
+                        rng.normal(size=(n, 4)).astype(np.float32),
+                        np.exp(rng.normal(-1.5, 0.2, (n, 3))).astype(np.float32),
+                        (1.0 / (1.0 + np.exp(-rng.normal(-3.0, 0.5, n)))).astype(np.float32),
+                        rng.normal(0.0, 0.3, (n, 16, 3)).astype(np.float32))
+    cam = synth.tiny_camera()
+    cam.width, cam.height, cam.cx, cam.cy = 64, 64, 32.0, 32.0
+    b, p, P, r = _oracle_all(orc, scene, cam, (16, 16))
+    lens = b.ranges[:, 1] - b.ranges[:, 0]
+    assert lens.max() > 3 * 4096
+    tr = _run_forward(step_mod, scene, [cam], capacity=1 << 20)
+    st = tr.stats()
+    assert st.status == 0 and st.k_required == b.K
+    np.testing.assert_array_equal(tr.buffer(2, b.K).cpu().numpy().view(np.uint32), b.keys)
+    np.testing.assert_array_equal(tr.buffer(3, b.K).cpu().numpy().view(np.uint32), b.gidx)
+    rg = tr.buffer(4, 2 * 16).cpu().numpy().view(np.uint32).reshape(16, 2).astype(np.int64)
+    np.testing.assert_array_equal(rg, b.ranges)
+    img = tr.image.view(64, 64, 3).cpu().numpy().astype(np.float64)
+    ok = ~r.unstable_px
+    err = np.abs(img - r.image)[ok].max()
+    assert err <= 1e-5, err
+    report("long_tile_lists", {"longest_list": int(lens.max()), "shortest_list": int(lens.min()),
+                               "image_max_abs_err": float(err), "keys_bit_exact": True})
+
+
 def test_capacity_overflow_sets_status(gs, orc):
     """Too small an intersection capacity is reported, nothing is written
     out of bounds, and a larger capacity then succeeds."""
