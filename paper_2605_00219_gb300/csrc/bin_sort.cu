@@ -20,11 +20,11 @@
 //   sorting      : one thread block per tile sorts the tile's entries by
 //                  (depth code, emission slot) -- unique, so the arrival
 //                  order of the atomics does not matter -- and writes the
-//                  keys, emission slots and pairs: bitonic sort in shared
-//                  memory up to kTileSortMax entries; longer lists are sorted
-//                  in chunks of that size and merged in global memory by
-//                  rank (each entry's position in the other run by binary
-//                  search)
+//                  keys, emission slots and pairs: a block merge sort in
+//                  shared memory up to kTileSortMax entries; longer lists
+//                  are sorted in chunks of that size and merged in global
+//                  memory by rank (each entry's position in the other run by
+//                  binary search)
 // K never leaves the device: every kernel reads it from the workspace header
 // and grids are sized by the plan.  When K exceeds the capacity nothing is
 // emitted and every tile list is empty (GS_STATUS_CAPACITY reports it).
@@ -205,8 +205,8 @@ __global__ void k_tile_setup(int64_t tiles, const uint32_t* __restrict__ tile_cn
 __global__ void __launch_bounds__(256) k_emit(Views V, const uint32_t* __restrict__ count,
                                               const uint32_t* __restrict__ offset, const ProjRec* __restrict__ rec,
                                               const float4* __restrict__ binrec, uint32_t* tile_cur,
-                                              uint32_t* __restrict__ bkey, uint32_t* __restrict__ bval,
-                                              uint32_t* __restrict__ pid, const WsHeader* __restrict__ hdr)
+                                              uint2* __restrict__ bucket, uint32_t* __restrict__ pid,
+                                              const WsHeader* __restrict__ hdr)
 {
     const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (qi >= V.pairs) return;
@@ -235,8 +235,7 @@ __global__ void __launch_bounds__(256) k_emit(Views V, const uint32_t* __restric
     scanline_tiles(gm, V.tw, V.th, vd.TX, vd.TY, [&](uint32_t i, uint32_t tile) {
         const uint32_t e = off + i;
         const uint32_t slot = atomicAdd(cur + tile, 1u);
-        bkey[slot] = low;
-        bval[slot] = e;
+        bucket[slot] = make_uint2(low, e);
         pid[e] = (uint32_t)p;
     });
 }
@@ -250,63 +249,155 @@ __device__ __forceinline__ unsigned long long sort_key(uint32_t low, uint32_t e)
     return ((unsigned long long)low << 32) | e;
 }
 
-// Ascending bitonic sort of N (a power of two) 64-bit keys in shared memory.
-__device__ void bitonic_sort_smem(unsigned long long* a, int N)
+// Ascending sort of N (a power of two, 8 <= N <= 8 * blockDim.x) 64-bit
+// keys in shared memory, block merge sort: thread t owns the 8 keys
+// [8t, 8t + 8); it sorts them with a 19-comparator network in registers,
+// then, at each merge level of run width w, finds where its 8 outputs start
+// in the merge of its two runs (merge-path binary search on the output
+// diagonal) and merges them sequentially.  Two barriers per level.
+__device__ __forceinline__ void cmpx(unsigned long long& a, unsigned long long& b)
 {
-    for (int k = 2; k <= N; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < (N >> 1); i += blockDim.x) {
-                const int lo = ((i & ~(j - 1)) << 1) | (i & (j - 1));
-                const int hi = lo | j;
-                const unsigned long long x = a[lo], y = a[hi];
-                const bool up = (lo & k) == 0;
-                if ((x > y) == up) {
-                    a[lo] = y;
-                    a[hi] = x;
+    const unsigned long long lo = a < b ? a : b, hi = a < b ? b : a;
+    a = lo;
+    b = hi;
+}
+
+__device__ void block_merge_sort_smem(unsigned long long* s, int N)
+{
+    constexpr int IT = 8;
+    const int nt = N / IT, t = threadIdx.x;
+    unsigned long long r[IT];
+    if (t < nt) {
+#pragma unroll
+        for (int k = 0; k < IT; k++) r[k] = s[IT * t + k];
+        cmpx(r[0], r[1]); cmpx(r[2], r[3]); cmpx(r[4], r[5]); cmpx(r[6], r[7]);
+        cmpx(r[0], r[2]); cmpx(r[1], r[3]); cmpx(r[4], r[6]); cmpx(r[5], r[7]);
+        cmpx(r[1], r[2]); cmpx(r[5], r[6]);
+        cmpx(r[0], r[4]); cmpx(r[1], r[5]); cmpx(r[2], r[6]); cmpx(r[3], r[7]);
+        cmpx(r[2], r[4]); cmpx(r[3], r[5]);
+        cmpx(r[1], r[2]); cmpx(r[3], r[4]); cmpx(r[5], r[6]);
+#pragma unroll
+        for (int k = 0; k < IT; k++) s[IT * t + k] = r[k];
+    }
+    __syncthreads();
+    for (int w = IT; w < N; w <<= 1) {
+        if (t < nt) {
+            const int base = (IT * t) & ~(2 * w - 1), diag = IT * t - base;
+            const unsigned long long* A = s + base;
+            const unsigned long long* B = s + base + w;
+            int lo = max(0, diag - w), hi = min(diag, w);
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (A[mid] <= B[diag - 1 - mid]) lo = mid + 1;
+                else hi = mid;
+            }
+            int a = lo, b = diag - lo;
+            unsigned long long ha = a < w ? A[a] : 0ull, hb = b < w ? B[b] : 0ull;
+#pragma unroll
+            for (int k = 0; k < IT; k++) {
+                const bool take_a = b >= w || (a < w && ha <= hb);
+                r[k] = take_a ? ha : hb;
+                if (take_a) {
+                    a++;
+                    ha = a < w ? A[a] : 0ull;
+                } else {
+                    b++;
+                    hb = b < w ? B[b] : 0ull;
                 }
             }
-            __syncthreads();
         }
+        __syncthreads();
+        if (t < nt) {
+#pragma unroll
+            for (int k = 0; k < IT; k++) s[IT * t + k] = r[k];
+        }
+        __syncthreads();
     }
 }
 
-// Entries of a run [b, b + len) below key x (binary search; keys unique).
-__device__ __forceinline__ uint32_t rank_in_run(const uint32_t* k, const uint32_t* v, uint32_t b, uint32_t len,
-                                                unsigned long long x)
+// (depth code, emission slot) lists in two layouts: one uint2 per entry, or
+// two u32 arrays.
+struct PackedList {
+    uint2* kv;
+    __device__ unsigned long long get(uint32_t i) const { const uint2 x = kv[i]; return sort_key(x.x, x.y); }
+    __device__ void put(uint32_t i, unsigned long long x) const { kv[i] = make_uint2((uint32_t)(x >> 32), (uint32_t)x); }
+};
+struct SplitList {
+    uint32_t* k;
+    uint32_t* v;
+    __device__ unsigned long long get(uint32_t i) const { return sort_key(k[i], v[i]); }
+    __device__ void put(uint32_t i, unsigned long long x) const { k[i] = (uint32_t)(x >> 32); v[i] = (uint32_t)x; }
+};
+
+// Entries of a sorted run [b, b + len) below key x (binary search; keys
+// unique).
+template <class L>
+__device__ __forceinline__ uint32_t rank_in_run(const L& l, uint32_t b, uint32_t len, unsigned long long x)
 {
     uint32_t lo = 0, hi = len;
     while (lo < hi) {
         const uint32_t mid = (lo + hi) >> 1;
-        if (sort_key(k[b + mid], v[b + mid]) < x) lo = mid + 1;
+        if (l.get(b + mid) < x) lo = mid + 1;
         else hi = mid;
     }
     return lo;
 }
 
+// One merge level of run width `run` over a list of n entries at s0: each
+// entry goes to its index in its own run plus its rank in the other run.
+template <class Src, class Dst>
+__device__ void merge_level(const Src& src, const Dst& dst, uint32_t s0, uint32_t n, uint32_t run)
+{
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const uint32_t ri = i / run, b = (ri & ~1u) * run;
+        const unsigned long long x = src.get(s0 + i);
+        uint32_t pos;
+        if ((ri & 1u) == 0) {   // left run: rank among the right run
+            const uint32_t pb = b + run, plen = pb < n ? min(run, n - pb) : 0u;
+            pos = i + (plen ? rank_in_run(src, s0 + pb, plen, x) : 0u);
+        } else {                // right run: rank among the left run
+            pos = b + (i - ri * run) + rank_in_run(src, s0 + b, run, x);
+        }
+        dst.put(s0 + pos, x);
+    }
+    __syncthreads();
+}
+
 // One thread block per tile (launched longest lists first).  Input: the
-// tile's bucket [s0, s1) in (bkey, bval), in atomic arrival order.  Output at
-// the same positions: keys_sorted = tile << shift | depth code, vals_sorted
-// = emission slot, pid_sorted = the slot's pair.
-__global__ void __launch_bounds__(kTileSortThreads) k_tile_sort(Views V, const uint32_t* __restrict__ order,
-                                                                 const uint2* __restrict__ ranges, uint32_t* bkey,
-                                                                 uint32_t* bval, const uint32_t* __restrict__ pid,
-                                                                 uint32_t* keys_sorted, uint32_t* vals_sorted,
-                                                                 uint32_t* __restrict__ pid_sorted)
+// tile's bucket [s0, s1) of (depth code, emission slot) in atomic arrival
+// order.  Output at the same positions: keys_sorted = tile << shift | depth
+// code, vals_sorted = emission slot, pid_sorted = the slot's pair.
+//
+// Two instantiations share the tiles: SMALL sorts the lists of 1 to
+// 8 x T entries with T threads (every thread owns keys, many blocks per SM),
+// the other the longer ones with kTileSortThreads threads (8 x that in shared
+// memory, then chunks and merges).
+template <int T, bool SMALL>
+__global__ void __launch_bounds__(T) k_tile_sort(Views V, const uint32_t* __restrict__ order,
+                                                 const uint2* __restrict__ ranges, uint2* bucket,
+                                                 const uint32_t* __restrict__ pid, uint32_t* keys_sorted,
+                                                 uint32_t* vals_sorted, uint32_t* __restrict__ pid_sorted)
 {
     extern __shared__ unsigned long long sk[];
     const int64_t gt = order[blockIdx.x];
     const uint2 r = ranges[gt];
     const uint32_t s0 = r.x, n = r.y - r.x;
-    if (n == 0) return;
+    if (n == 0 || (n <= 8u * kTileSortSmall) != SMALL) return;
     const ViewDesc& vd = V.v[view_of_tile(V, gt)];
     const uint32_t hi_bits = (uint32_t)(gt - vd.tile_base) << vd.shift;
-    if (n <= (uint32_t)kTileSortMax) {
-        int N = 1;
+    if (n <= 8u * (uint32_t)T) {
+        int N = 8;
         while (N < (int)n) N <<= 1;
-        for (int i = threadIdx.x; i < N; i += blockDim.x)
-            sk[i] = i < (int)n ? sort_key(bkey[s0 + i], bval[s0 + i]) : ~0ull;
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            unsigned long long x = ~0ull;
+            if (i < (int)n) {
+                const uint2 b = bucket[s0 + i];
+                x = sort_key(b.x, b.y);
+            }
+            sk[i] = x;
+        }
         __syncthreads();
-        bitonic_sort_smem(sk, N);
+        block_merge_sort_smem(sk, N);
         for (int i = threadIdx.x; i < (int)n; i += blockDim.x) {
             const unsigned long long x = sk[i];
             const uint32_t e = (uint32_t)x;
@@ -316,44 +407,38 @@ __global__ void __launch_bounds__(kTileSortThreads) k_tile_sort(Views V, const u
         }
         return;
     }
-    // long list: sorted chunks of kTileSortMax into (keys_sorted,
-    // vals_sorted), then merges by rank, alternating with (bkey, bval)
+    if (SMALL) return;   // not reached: short lists fit the block
+    // long list: chunks of kTileSortMax sorted in shared memory, then merge
+    // levels alternating between the bucket and the (keys, vals) arrays,
+    // starting where an even number of moves ends in the bucket
+    const PackedList pk{bucket};
+    const SplitList sp{keys_sorted, vals_sorted};
     const uint32_t M = kTileSortMax;
+    int levels = 0;
+    for (uint32_t run = M; run < n; run <<= 1) levels++;
+    const bool chunks_in_bucket = (levels & 1) == 0;
     for (uint32_t c0 = 0; c0 < n; c0 += M) {
         const uint32_t len = min(M, n - c0);
-        for (uint32_t i = threadIdx.x; i < M; i += blockDim.x)
-            sk[i] = i < len ? sort_key(bkey[s0 + c0 + i], bval[s0 + c0 + i]) : ~0ull;
+        for (uint32_t i = threadIdx.x; i < M; i += blockDim.x) sk[i] = i < len ? pk.get(s0 + c0 + i) : ~0ull;
         __syncthreads();
-        bitonic_sort_smem(sk, (int)M);
+        block_merge_sort_smem(sk, (int)M);
         for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
-            keys_sorted[s0 + c0 + i] = (uint32_t)(sk[i] >> 32);
-            vals_sorted[s0 + c0 + i] = (uint32_t)sk[i];
+            if (chunks_in_bucket) pk.put(s0 + c0 + i, sk[i]);
+            else sp.put(s0 + c0 + i, sk[i]);
         }
         __syncthreads();
     }
-    uint32_t *sk_in = keys_sorted, *sv_in = vals_sorted, *sk_out = bkey, *sv_out = bval;
+    bool in_bucket = chunks_in_bucket;
     for (uint32_t run = M; run < n; run <<= 1) {
-        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-            const uint32_t ri = i / run, b = (ri & ~1u) * run;
-            const unsigned long long x = sort_key(sk_in[s0 + i], sv_in[s0 + i]);
-            uint32_t pos;
-            if ((ri & 1u) == 0) {   // left run: rank among the right run
-                const uint32_t pb = b + run, plen = pb < n ? min(run, n - pb) : 0u;
-                pos = i + (plen ? rank_in_run(sk_in, sv_in, s0 + pb, plen, x) : 0u);
-            } else {                // right run: rank among the left run
-                pos = b + (i - ri * run) + rank_in_run(sk_in, sv_in, s0 + b, run, x);
-            }
-            sk_out[s0 + pos] = sk_in[s0 + i];
-            sv_out[s0 + pos] = sv_in[s0 + i];
-        }
-        __syncthreads();
-        uint32_t* t = sk_in; sk_in = sk_out; sk_out = t;
-        t = sv_in; sv_in = sv_out; sv_out = t;
+        if (in_bucket) merge_level(pk, sp, s0, n, run);
+        else merge_level(sp, pk, s0, n, run);
+        in_bucket = !in_bucket;
     }
-    // sk_in / sv_in hold the sorted list; each thread rewrites its own index
+    // the sorted list is in the bucket now
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-        const uint32_t low = sk_in[s0 + i], e = sv_in[s0 + i];
-        keys_sorted[s0 + i] = hi_bits | low;
+        const unsigned long long x = pk.get(s0 + i);
+        const uint32_t e = (uint32_t)x;
+        keys_sorted[s0 + i] = hi_bits | (uint32_t)(x >> 32);
         vals_sorted[s0 + i] = e;
         pid_sorted[s0 + i] = pid[e];
     }
@@ -410,15 +495,17 @@ void launch_bin_sort(const Plan& P, const WsPtrs& w, cudaStream_t st)
     // generate keys into the tile buckets
     {
         const int64_t blocks = (V.pairs + 255) / 256;
-        k_emit<<<(unsigned)blocks, 256, 0, st>>>(V, w.count, w.offset, w.rec, w.binrec, w.tile_cur, w.bkey, w.bval,
-                                                 w.pid, w.hdr);
+        k_emit<<<(unsigned)blocks, 256, 0, st>>>(V, w.count, w.offset, w.rec, w.binrec, w.tile_cur, w.bucket, w.pid,
+                                                 w.hdr);
     }
     // sort each tile's list
     {
-        const size_t smem = sizeof(unsigned long long) * kTileSortMax;   // 32 KB: no opt-in needed
-        k_tile_sort<<<(unsigned)V.tiles, kTileSortThreads, smem, st>>>(V, w.tile_order, w.ranges, w.bkey, w.bval,
-                                                                       w.pid, w.keys_sorted, w.vals_sorted,
-                                                                       w.pid_sorted);
+        const size_t smem_l = sizeof(unsigned long long) * kTileSortMax;            // 32 KB: no opt-in needed
+        const size_t smem_s = sizeof(unsigned long long) * 8 * kTileSortSmall;      // 8 KB
+        k_tile_sort<kTileSortThreads, false><<<(unsigned)V.tiles, kTileSortThreads, smem_l, st>>>(
+            V, w.tile_order, w.ranges, w.bucket, w.pid, w.keys_sorted, w.vals_sorted, w.pid_sorted);
+        k_tile_sort<kTileSortSmall, true><<<(unsigned)V.tiles, kTileSortSmall, smem_s, st>>>(
+            V, w.tile_order, w.ranges, w.bucket, w.pid, w.keys_sorted, w.vals_sorted, w.pid_sorted);
     }
 }
 

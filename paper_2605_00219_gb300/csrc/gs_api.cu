@@ -28,8 +28,7 @@ WsPtrs carve(const Plan& P, void* ws)
     w.offset = reinterpret_cast<uint32_t*>(b + P.off_offset);
     w.rec = reinterpret_cast<ProjRec*>(b + P.off_rec);
     w.binrec = reinterpret_cast<float4*>(b + P.off_binrec);
-    w.bkey = reinterpret_cast<uint32_t*>(b + P.off_bkey);
-    w.bval = reinterpret_cast<uint32_t*>(b + P.off_bval);
+    w.bucket = reinterpret_cast<uint2*>(b + P.off_bucket);
     w.keys_sorted = reinterpret_cast<uint32_t*>(b + P.off_keys);
     w.vals_sorted = reinterpret_cast<uint32_t*>(b + P.off_vals);
     w.pid = reinterpret_cast<uint32_t*>(b + P.off_pid);
@@ -154,8 +153,7 @@ static bool plan_build(Plan& P, const int64_t* scene_n, int32_t n_scenes, const 
     P.off_offset = take(4 * (size_t)(pairs + 1));
     P.off_rec = take(sizeof(ProjRec) * (size_t)pairs);
     P.off_binrec = take(16 * (size_t)pairs);
-    P.off_bkey = take(4 * (size_t)cap);
-    P.off_bval = take(4 * (size_t)cap);
+    P.off_bucket = take(8 * (size_t)cap);
     P.off_keys = take(4 * (size_t)cap);
     P.off_vals = take(4 * (size_t)cap);
     P.off_pid = take(4 * (size_t)cap);

@@ -15,8 +15,9 @@ constexpr int kCapGranule = 2048;
 // Per-tile sort: lists of up to kTileSortMax entries are sorted in shared
 // memory by one thread block; longer lists are sorted in chunks of that size
 // and merged in global memory by the same block.
-constexpr int kTileSortThreads = 256;
+constexpr int kTileSortThreads = 512;     // 8 keys per thread
 constexpr int kTileSortMax = 4096;
+constexpr int kTileSortSmall = 128;       // threads for lists of up to 1024 entries
 
 // Exclusive scan geometry: 512 threads x 8 values per block.
 constexpr int kScanThreads = 512;
@@ -40,7 +41,7 @@ struct Plan {
     int32_t sm_count;            // SMs of the device current at plan creation (152 if none)
     // workspace byte offsets
     size_t off_hdr, off_count, off_offset, off_rec, off_binrec;
-    size_t off_bkey, off_bval, off_keys, off_vals, off_pid, off_pid_sorted;
+    size_t off_bucket, off_keys, off_vals, off_pid, off_pid_sorted;
     size_t off_tile_cnt, off_tile_cur;
     size_t off_ranges, off_nlast, off_tfinal, off_gradrec, off_scan_part, off_loss_part, off_order;
     size_t ws_bytes;
@@ -52,8 +53,7 @@ struct WsPtrs {
     uint32_t* offset;          // its exclusive scan: first emission slot of each pair
     ProjRec* rec;              // projected records, view-major pair order
     float4* binrec;
-    uint32_t* bkey;            // tile buckets: depth code of each entry
-    uint32_t* bval;            // tile buckets: emission slot of each entry
+    uint2* bucket;             // tile lists in arrival order: (depth code, emission slot)
     uint32_t* pid;             // view-major pair of each emission slot
     uint32_t* keys_sorted;     // sorted keys (tile << shift | depth code)
     uint32_t* vals_sorted;     // emission slot of each sorted entry
