@@ -254,7 +254,10 @@ __device__ __forceinline__ unsigned long long sort_key(uint32_t low, uint32_t e)
 // [8t, 8t + 8); it sorts them with a 19-comparator network in registers,
 // then, at each merge level of run width w, finds where its 8 outputs start
 // in the merge of its two runs (merge-path binary search on the output
-// diagonal) and merges them sequentially.  Two barriers per level.
+// diagonal) and merges them sequentially.  While two runs fit in one warp's
+// 256 keys (w <= 128) only that warp reads and writes them, so the level
+// synchronises the warp; a level that reads wider runs synchronises the
+// block, also before its reads.  The caller synchronises the block before.
 __device__ __forceinline__ void cmpx(unsigned long long& a, unsigned long long& b)
 {
     const unsigned long long lo = a < b ? a : b, hi = a < b ? b : a;
@@ -279,8 +282,9 @@ __device__ void block_merge_sort_smem(unsigned long long* s, int N)
 #pragma unroll
         for (int k = 0; k < IT; k++) s[IT * t + k] = r[k];
     }
-    __syncthreads();
+    __syncwarp();
     for (int w = IT; w < N; w <<= 1) {
+        const bool in_warp = 2 * w <= 32 * IT;
         if (t < nt) {
             const int base = (IT * t) & ~(2 * w - 1), diag = IT * t - base;
             const unsigned long long* A = s + base;
@@ -306,13 +310,18 @@ __device__ void block_merge_sort_smem(unsigned long long* s, int N)
                 }
             }
         }
-        __syncthreads();
+        if (in_warp) __syncwarp();
+        else __syncthreads();
         if (t < nt) {
 #pragma unroll
             for (int k = 0; k < IT; k++) s[IT * t + k] = r[k];
         }
-        __syncthreads();
+        // the next level (width 2w) reads other warps' keys unless its runs
+        // still fit in one warp
+        if (4 * w <= 32 * IT) __syncwarp();
+        else __syncthreads();
     }
+    __syncthreads();
 }
 
 // (depth code, emission slot) lists in two layouts: one uint2 per entry, or
@@ -368,21 +377,14 @@ __device__ void merge_level(const Src& src, const Dst& dst, uint32_t s0, uint32_
 // order.  Output at the same positions: keys_sorted = tile << shift | depth
 // code, vals_sorted = emission slot, pid_sorted = the slot's pair.
 //
-// Two instantiations share the tiles: SMALL sorts the lists of 1 to
-// 8 x T entries with T threads (every thread owns keys, many blocks per SM),
-// the other the longer ones with kTileSortThreads threads (8 x that in shared
-// memory, then chunks and merges).
+// One tile's list, sorted by the calling block (T threads): up to 8 x T
+// entries in shared memory, longer lists (SMALL = false) in chunks of
+// kTileSortMax merged in global memory.
 template <int T, bool SMALL>
-__global__ void __launch_bounds__(T) k_tile_sort(Views V, const uint32_t* __restrict__ order,
-                                                 const uint2* __restrict__ ranges, uint2* bucket,
-                                                 const uint32_t* __restrict__ pid, uint32_t* keys_sorted,
-                                                 uint32_t* vals_sorted, uint32_t* __restrict__ pid_sorted)
+__device__ void tile_sort_one(const Views& V, int64_t gt, uint32_t s0, uint32_t n, unsigned long long* sk,
+                              uint2* bucket, const uint32_t* __restrict__ pid, uint32_t* keys_sorted,
+                              uint32_t* vals_sorted, uint32_t* __restrict__ pid_sorted)
 {
-    extern __shared__ unsigned long long sk[];
-    const int64_t gt = order[blockIdx.x];
-    const uint2 r = ranges[gt];
-    const uint32_t s0 = r.x, n = r.y - r.x;
-    if (n == 0 || (n <= 8u * kTileSortSmall) != SMALL) return;
     const ViewDesc& vd = V.v[view_of_tile(V, gt)];
     const uint32_t hi_bits = (uint32_t)(gt - vd.tile_base) << vd.shift;
     if (n <= 8u * (uint32_t)T) {
@@ -405,6 +407,7 @@ __global__ void __launch_bounds__(T) k_tile_sort(Views V, const uint32_t* __rest
             vals_sorted[s0 + i] = e;
             pid_sorted[s0 + i] = pid[e];
         }
+        __syncthreads();   // the block may take another list into sk next
         return;
     }
     if (SMALL) return;   // not reached: short lists fit the block
@@ -442,6 +445,37 @@ __global__ void __launch_bounds__(T) k_tile_sort(Views V, const uint32_t* __rest
         vals_sorted[s0 + i] = e;
         pid_sorted[s0 + i] = pid[e];
     }
+    __syncthreads();
+}
+
+// Short lists (1 to 8 x kTileSortSmall entries): one block per tile.
+__global__ void __launch_bounds__(kTileSortSmall) k_tile_sort_short(Views V, const uint32_t* __restrict__ order,
+                                                                    const uint2* __restrict__ ranges, uint2* bucket,
+                                                                    const uint32_t* __restrict__ pid,
+                                                                    uint32_t* keys_sorted, uint32_t* vals_sorted,
+                                                                    uint32_t* __restrict__ pid_sorted)
+{
+    extern __shared__ unsigned long long sk[];
+    const int64_t gt = order[blockIdx.x];
+    const uint2 r = ranges[gt];
+    const uint32_t n = r.y - r.x;
+    if (n == 0 || n > 8u * kTileSortSmall) return;
+    tile_sort_one<kTileSortSmall, true>(V, gt, r.x, n, sk, bucket, pid, keys_sorted, vals_sorted, pid_sorted);
+}
+
+// Longer lists: one block per tile (the blocks of short lists exit at once).
+__global__ void __launch_bounds__(kTileSortThreads) k_tile_sort_long(Views V, const uint32_t* __restrict__ order,
+                                                                     const uint2* __restrict__ ranges,
+                                                                     uint2* bucket, const uint32_t* __restrict__ pid,
+                                                                     uint32_t* keys_sorted, uint32_t* vals_sorted,
+                                                                     uint32_t* __restrict__ pid_sorted)
+{
+    extern __shared__ unsigned long long sk[];
+    const int64_t gt = order[blockIdx.x];
+    const uint2 r = ranges[gt];
+    const uint32_t n = r.y - r.x;
+    if (n <= 8u * kTileSortSmall) return;
+    tile_sort_one<kTileSortThreads, false>(V, gt, r.x, n, sk, bucket, pid, keys_sorted, vals_sorted, pid_sorted);
 }
 
 // Launch order of the raster kernels: tiles by decreasing list length,
@@ -502,10 +536,12 @@ void launch_bin_sort(const Plan& P, const WsPtrs& w, cudaStream_t st)
     {
         const size_t smem_l = sizeof(unsigned long long) * kTileSortMax;            // 32 KB: no opt-in needed
         const size_t smem_s = sizeof(unsigned long long) * 8 * kTileSortSmall;      // 8 KB
-        k_tile_sort<kTileSortThreads, false><<<(unsigned)V.tiles, kTileSortThreads, smem_l, st>>>(
-            V, w.tile_order, w.ranges, w.bucket, w.pid, w.keys_sorted, w.vals_sorted, w.pid_sorted);
-        k_tile_sort<kTileSortSmall, true><<<(unsigned)V.tiles, kTileSortSmall, smem_s, st>>>(
-            V, w.tile_order, w.ranges, w.bucket, w.pid, w.keys_sorted, w.vals_sorted, w.pid_sorted);
+        k_tile_sort_long<<<(unsigned)V.tiles, kTileSortThreads, smem_l, st>>>(V, w.tile_order, w.ranges, w.bucket,
+                                                                             w.pid, w.keys_sorted, w.vals_sorted,
+                                                                             w.pid_sorted);
+        k_tile_sort_short<<<(unsigned)V.tiles, kTileSortSmall, smem_s, st>>>(V, w.tile_order, w.ranges, w.bucket,
+                                                                             w.pid, w.keys_sorted, w.vals_sorted,
+                                                                             w.pid_sorted);
     }
 }
 

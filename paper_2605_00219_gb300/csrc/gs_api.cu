@@ -2,6 +2,8 @@
 // entry points declared in gs_step.h.
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gs_internal.cuh"
 
 struct gs_plan {
@@ -237,6 +239,13 @@ __global__ void k_set_step(WsHeader* hdr, int32_t step)
 
 static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// NVTX range around one stage call (host-side push / pop; free when no
+// profiler is attached), so a profiler timeline groups the kernels by stage.
+struct StageRange {
+    explicit StageRange(const char* name) { nvtxRangePushA(name); }
+    ~StageRange() { nvtxRangePop(); }
+};
+
 static gs_status launch_status()
 {
     return cudaPeekAtLastError() == cudaSuccess ? GS_OK : (cudaGetLastError(), GS_ERR_CUDA);
@@ -309,6 +318,7 @@ static gs_status check_scenes(const Plan& P, const gs_scene_buf* scenes, bool ne
 gs_status gs_project_fwd(const gs_plan* plan, void* ws, const gs_scene_buf* scenes, const float* cams,
                          void* stream)
 {
+    const StageRange range("gs_project_fwd");
     if (!plan || !ws || !cams) return GS_ERR_INVALID_ARG;
     const Plan& P = plan->p;
     gs_status e = check_scenes(P, scenes, false);
@@ -322,6 +332,7 @@ gs_status gs_project_fwd(const gs_plan* plan, void* ws, const gs_scene_buf* scen
 
 gs_status gs_bin_sort(const gs_plan* plan, void* ws, void* stream)
 {
+    const StageRange range("gs_bin_sort");
     if (!plan || !ws) return GS_ERR_INVALID_ARG;
     WsPtrs w = carve(plan->p, ws);
     launch_bin_sort(plan->p, w, static_cast<cudaStream_t>(stream));
@@ -330,6 +341,7 @@ gs_status gs_bin_sort(const gs_plan* plan, void* ws, void* stream)
 
 gs_status gs_raster_fwd(const gs_plan* plan, void* ws, const float* bg, float* image, void* stream)
 {
+    const StageRange range("gs_raster_fwd");
     if (!plan || !ws || !image || !aligned16(image)) return GS_ERR_INVALID_ARG;
     WsPtrs w = carve(plan->p, ws);
     launch_raster_fwd(plan->p, w, bg, image, static_cast<cudaStream_t>(stream));
@@ -339,6 +351,7 @@ gs_status gs_raster_fwd(const gs_plan* plan, void* ws, const float* bg, float* i
 gs_status gs_loss_l1(const gs_plan* plan, void* ws, const float* image, const float* target, float* dL_dimage,
                      void* stream)
 {
+    const StageRange range("gs_loss_l1");
     if (!plan || !ws || !image || !target || !dL_dimage) return GS_ERR_INVALID_ARG;
     WsPtrs w = carve(plan->p, ws);
     launch_loss_l1(plan->p, w, image, target, dL_dimage, static_cast<cudaStream_t>(stream));
@@ -348,6 +361,7 @@ gs_status gs_loss_l1(const gs_plan* plan, void* ws, const float* image, const fl
 gs_status gs_loss_l1_ssim(const gs_plan* plan, void* ws, const float* image, const void* target_rgba8, float lambda,
                           float* dL_dimage, void* stream)
 {
+    const StageRange range("gs_loss_l1_ssim");
     if (!plan || !ws || !image || !target_rgba8 || !dL_dimage) return GS_ERR_INVALID_ARG;
     if (!(lambda >= 0.f && lambda <= 1.f)) return GS_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(target_rgba8) % 4 != 0) return GS_ERR_INVALID_ARG;
@@ -358,6 +372,7 @@ gs_status gs_loss_l1_ssim(const gs_plan* plan, void* ws, const float* image, con
 
 gs_status gs_raster_bwd(const gs_plan* plan, void* ws, const float* image, const float* dL_dimage, void* stream)
 {
+    const StageRange range("gs_raster_bwd");
     if (!plan || !ws || !image || !dL_dimage) return GS_ERR_INVALID_ARG;
     WsPtrs w = carve(plan->p, ws);
     launch_raster_bwd(plan->p, w, image, dL_dimage, static_cast<cudaStream_t>(stream));
@@ -367,6 +382,7 @@ gs_status gs_raster_bwd(const gs_plan* plan, void* ws, const float* image, const
 gs_status gs_project_bwd_adam(const gs_plan* plan, void* ws, const gs_scene_buf* scenes, const float* cams,
                               const gs_adam* adam, float* grads_out, void* stream)
 {
+    const StageRange range("gs_project_bwd_adam");
     if (!plan || !ws || !cams) return GS_ERR_INVALID_ARG;
     const Plan& P = plan->p;
     if (!grads_out && !adam) return GS_ERR_INVALID_ARG;

@@ -159,8 +159,17 @@ struct BinGeom {
     int valid;
 };
 
-__device__ __forceinline__ void bin_project(float4 mu, float4 q, float4 s, const float* cam, int W, int H,
-                                            BinGeom& o)
+// View-independent part of the bit-specified binning of one Gaussian: the
+// cull radius^2 and the 3D covariance S = (R(q) diag(s))(R(q) diag(s))^T
+// (upper triangle S00, S01, S02, S11, S12, S22).  valid = 0 when the
+// Gaussian is never listed (255 o <= 1, or a zero quaternion).
+struct BinGauss {
+    float S[6];
+    float r2;
+    int valid;
+};
+
+__device__ __forceinline__ void bin_gauss(float4 q, float4 s, BinGauss& o)
 {
     o.valid = 0;
     const float r2 = cull_r2(s.w);
@@ -188,15 +197,25 @@ __device__ __forceinline__ void bin_project(float4 mu, float4 q, float4 s, const
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) M[3 * i + j] = FM(R[3 * i + j], sv[j]);
-    float S[9];
+    int k = 0;
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
-        for (int j = i; j < 3; j++) {
-            float v = FA(FA(FM(M[3 * i], M[3 * j]), FM(M[3 * i + 1], M[3 * j + 1])), FM(M[3 * i + 2], M[3 * j + 2]));
-            S[3 * i + j] = v;
-            S[3 * j + i] = v;
-        }
+        for (int j = i; j < 3; j++)
+            o.S[k++] = FA(FA(FM(M[3 * i], M[3 * j]), FM(M[3 * i + 1], M[3 * j + 1])), FM(M[3 * i + 2], M[3 * j + 2]));
+    o.r2 = r2;
+    o.valid = 1;
+}
+
+// View-dependent part: camera transform, near-plane cull, EWA covariance
+// with the field-of-view clamp, conic determinant, pixel mean and depth
+// code, from the view-independent part.
+__device__ __forceinline__ void bin_view(float4 mu, const BinGauss& bgs, const float* cam, int W, int H, BinGeom& o)
+{
+    o.valid = 0;
+    if (!bgs.valid) return;
+    const float S[9] = {bgs.S[0], bgs.S[1], bgs.S[2], bgs.S[1], bgs.S[3], bgs.S[4], bgs.S[2], bgs.S[4], bgs.S[5]};
+    const float r2 = bgs.r2;
     const float* C = cam;          // R row-major
     const float mv[3] = {mu.x, mu.y, mu.z};
     float t[3];

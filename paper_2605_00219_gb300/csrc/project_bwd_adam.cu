@@ -380,6 +380,14 @@ __global__ void __launch_bounds__(kPbaThreads, 4) k_project_bwd_adam(Views V, Sc
         const int64_t q0 = V.qbase[s] + g * nv;
         uint32_t e_next = offset[q0];
         uint32_t cnt_n = count[q0];
+        {
+            // the records of every view form [offset[q0], offset[q0 + nv]):
+            // request their lines into L2 before the first view needs them
+            const uint32_t e_end = min(offset[q0 + nv], cap);
+            const char* p0 = reinterpret_cast<const char*>(gradrec + e_next);
+            const char* p1 = reinterpret_cast<const char*>(gradrec + max(e_end, e_next));
+            for (int l = 0; l < 16 && p0 + 128 * l < p1; l++) prefetch_l2(p0 + 128 * l);
+        }
         for (int k = 0; k < nv; k++) {
             const int v = V.view_of[s][k];
             const uint32_t cnt = cnt_n, off = e_next;

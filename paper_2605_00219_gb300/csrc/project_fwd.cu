@@ -17,7 +17,7 @@ namespace gs {
 // projected record and binning geometry.
 __device__ __forceinline__ void project_pair(const ViewDesc& vd, int tw, int th, const SceneDesc& sc, int sh_bf16,
                                              const float* __restrict__ camp, int64_t g, int64_t p, int64_t qi,
-                                             const float4& mu, const float4& q, const float4& so,
+                                             const float4& mu, const BinGauss& bgs, const float4& so,
                                              uint32_t* __restrict__ count, uint32_t* __restrict__ tile_cnt,
                                              ProjRec* __restrict__ rec, float4* __restrict__ binrec)
 {
@@ -25,7 +25,7 @@ __device__ __forceinline__ void project_pair(const ViewDesc& vd, int tw, int th,
 #pragma unroll
     for (int i = 0; i < 16; i++) cam[i] = __ldg(camp + i);
     BinGeom bg;
-    bin_project(mu, q, so, cam, vd.W, vd.H, bg);
+    bin_view(mu, bgs, cam, vd.W, vd.H, bg);
     uint32_t cnt = 0;
     uint32_t* __restrict__ tc = tile_cnt + vd.tile_base;
     if (bg.valid) cnt = scanline_tiles(bg, tw, th, vd.TX, vd.TY, [&](uint32_t, uint32_t tile) { atomicAdd(tc + tile, 1u); });
@@ -89,6 +89,9 @@ __global__ void __launch_bounds__(256, 3) k_project_fwd(Views V, Scenes S, const
     if (!finite) atomicOr(&hdr->status, GS_STATUS_NONFINITE);
     const int nv = V.nv[s];
     const int64_t q0 = V.qbase[s] + g * nv;
+    // the view-independent part of the binning (cull radius, 3D covariance)
+    BinGauss bgs;
+    bin_gauss(q, so, bgs);
     for (int k = 0; k < nv; k++) {
         const int v = V.view_of[s][k];
         const ViewDesc& vd = V.v[v];
@@ -97,7 +100,7 @@ __global__ void __launch_bounds__(256, 3) k_project_fwd(Views V, Scenes S, const
             count[q0 + k] = 0;
             continue;
         }
-        project_pair(vd, V.tw, V.th, sc, S.sh_bf16, cams + 16 * v, g, p, q0 + k, mu, q, so, count, tile_cnt, rec,
+        project_pair(vd, V.tw, V.th, sc, S.sh_bf16, cams + 16 * v, g, p, q0 + k, mu, bgs, so, count, tile_cnt, rec,
                      binrec);
     }
 }
