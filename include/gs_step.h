@@ -72,6 +72,10 @@ typedef enum {
 #define GS_STATUS_CAPACITY 0x1u
 #define GS_STATUS_NONFINITE 0x2u
 #define GS_STATUS_TIMEOUT 0x4u
+#define GS_STATUS_BOUNDS 0x8u      /* bounds-checked build (GS_DEBUG) only: an
+                                      index read from the workspace pointed
+                                      outside its buffer; that access was
+                                      skipped */
 
 /* Storage flags for gs_plan_create. */
 #define GS_STORE_SH_BF16 0x1

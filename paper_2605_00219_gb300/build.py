@@ -2,7 +2,10 @@
 
 Each .cu under csrc/ is compiled in parallel (one -gencode, sm_103a), then
 linked into paper_2605_00219_gb300/_lib/libgsstep.so.  Rebuilds only what
-changed.
+changed.  build(debug=True) builds the bounds-checked variant
+(-DGS_DEBUG: indices read from the workspace are checked before use, a bad
+one sets GS_STATUS_BOUNDS and the access is skipped) as
+_lib/libgsstep_debug.so, from objects of its own.
 """
 from __future__ import annotations
 
@@ -20,6 +23,8 @@ INC = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "_lib")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libgsstep.so")
+OBJ_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(OUT, "libgsstep_debug.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
@@ -37,12 +42,12 @@ def _deps() -> list[str]:
     return glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(INC, "gs_step.h")]
 
 
-def _compile(src: str, extra: list[str]) -> str:
-    obj = os.path.join(OBJ, os.path.basename(src) + ".o")
+def _compile(src: str, extra: list[str], objdir: str = OBJ, defines: list[str] = ()) -> str:
+    obj = os.path.join(objdir, os.path.basename(src) + ".o")
     newest = max(os.path.getmtime(p) for p in [src] + _deps())
     if os.path.exists(obj) and os.path.getmtime(obj) >= newest and not extra:
         return obj
-    cmd = [nvcc()] + ARCH + FLAGS + extra + ["-c", src, "-o", obj]
+    cmd = [nvcc()] + ARCH + FLAGS + list(defines) + extra + ["-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -51,21 +56,23 @@ def _compile(src: str, extra: list[str]) -> str:
     return obj
 
 
-def build(verbose_ptxas: bool = False) -> str:
+def build(verbose_ptxas: bool = False, debug: bool = False) -> str:
+    objdir, lib = (OBJ_DEBUG, LIB_DEBUG) if debug else (OBJ, LIB)
+    defines = ["-DGS_DEBUG"] if debug else []
     os.makedirs(OUT, exist_ok=True)
-    os.makedirs(OBJ, exist_ok=True)
+    os.makedirs(objdir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     extra = ["-Xptxas", "-v"] if verbose_ptxas else []
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
-    if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+        objs = list(ex.map(lambda s: _compile(s, extra, objdir, defines), srcs))
+    if not os.path.exists(lib) or os.path.getmtime(lib) < max(os.path.getmtime(o) for o in objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

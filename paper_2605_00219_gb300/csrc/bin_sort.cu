@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(256) k_emit(Views V, const uint32_t* __restric
                                               const uint32_t* __restrict__ offset, const ProjRec* __restrict__ rec,
                                               const float4* __restrict__ binrec, uint32_t* tile_cur,
                                               uint2* __restrict__ bucket, uint32_t* __restrict__ pid,
-                                              const WsHeader* __restrict__ hdr)
+                                              WsHeader* __restrict__ hdr)
 {
     const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (qi >= V.pairs) return;
@@ -235,8 +235,10 @@ __global__ void __launch_bounds__(256) k_emit(Views V, const uint32_t* __restric
     scanline_tiles(gm, V.tw, V.th, vd.TX, vd.TY, [&](uint32_t i, uint32_t tile) {
         const uint32_t e = off + i;
         const uint32_t slot = atomicAdd(cur + tile, 1u);
-        bucket[slot] = make_uint2(low, e);
-        pid[e] = (uint32_t)p;
+        if (GS_DCHECK(slot < hdr->k_eff && e < hdr->k_eff, &hdr->status)) {
+            bucket[slot] = make_uint2(low, e);
+            pid[e] = (uint32_t)p;
+        }
     });
 }
 
@@ -383,8 +385,11 @@ __device__ void merge_level(const Src& src, const Dst& dst, uint32_t s0, uint32_
 template <int T, bool SMALL>
 __device__ void tile_sort_one(const Views& V, int64_t gt, uint32_t s0, uint32_t n, unsigned long long* sk,
                               uint2* bucket, const uint32_t* __restrict__ pid, uint32_t* keys_sorted,
-                              uint32_t* vals_sorted, uint32_t* __restrict__ pid_sorted)
+                              uint32_t* vals_sorted, uint32_t* __restrict__ pid_sorted, uint32_t* status,
+                              uint32_t cap)
 {
+    (void)status;
+    (void)cap;
     const ViewDesc& vd = V.v[view_of_tile(V, gt)];
     const uint32_t hi_bits = (uint32_t)(gt - vd.tile_base) << vd.shift;
     if (n <= 8u * (uint32_t)T) {
@@ -405,7 +410,7 @@ __device__ void tile_sort_one(const Views& V, int64_t gt, uint32_t s0, uint32_t 
             const uint32_t e = (uint32_t)x;
             keys_sorted[s0 + i] = hi_bits | (uint32_t)(x >> 32);
             vals_sorted[s0 + i] = e;
-            pid_sorted[s0 + i] = pid[e];
+            pid_sorted[s0 + i] = GS_DCHECK(e < cap, status) ? pid[e] : 0u;
         }
         __syncthreads();   // the block may take another list into sk next
         return;
@@ -443,7 +448,7 @@ __device__ void tile_sort_one(const Views& V, int64_t gt, uint32_t s0, uint32_t 
         const uint32_t e = (uint32_t)x;
         keys_sorted[s0 + i] = hi_bits | (uint32_t)(x >> 32);
         vals_sorted[s0 + i] = e;
-        pid_sorted[s0 + i] = pid[e];
+        pid_sorted[s0 + i] = GS_DCHECK(e < cap, status) ? pid[e] : 0u;
     }
     __syncthreads();
 }
@@ -453,14 +458,16 @@ __global__ void __launch_bounds__(kTileSortSmall) k_tile_sort_short(Views V, con
                                                                     const uint2* __restrict__ ranges, uint2* bucket,
                                                                     const uint32_t* __restrict__ pid,
                                                                     uint32_t* keys_sorted, uint32_t* vals_sorted,
-                                                                    uint32_t* __restrict__ pid_sorted)
+                                                                    uint32_t* __restrict__ pid_sorted,
+                                                                    uint32_t* status, uint32_t cap)
 {
     extern __shared__ unsigned long long sk[];
     const int64_t gt = order[blockIdx.x];
-    const uint2 r = ranges[gt];
+    const uint2 r = range_at(ranges, gt, cap, status);
     const uint32_t n = r.y - r.x;
     if (n == 0 || n > 8u * kTileSortSmall) return;
-    tile_sort_one<kTileSortSmall, true>(V, gt, r.x, n, sk, bucket, pid, keys_sorted, vals_sorted, pid_sorted);
+    tile_sort_one<kTileSortSmall, true>(V, gt, r.x, n, sk, bucket, pid, keys_sorted, vals_sorted, pid_sorted, status,
+                                        cap);
 }
 
 // Longer lists: one block per tile (the blocks of short lists exit at once).
@@ -468,14 +475,16 @@ __global__ void __launch_bounds__(kTileSortThreads) k_tile_sort_long(Views V, co
                                                                      const uint2* __restrict__ ranges,
                                                                      uint2* bucket, const uint32_t* __restrict__ pid,
                                                                      uint32_t* keys_sorted, uint32_t* vals_sorted,
-                                                                     uint32_t* __restrict__ pid_sorted)
+                                                                     uint32_t* __restrict__ pid_sorted,
+                                                                     uint32_t* status, uint32_t cap)
 {
     extern __shared__ unsigned long long sk[];
     const int64_t gt = order[blockIdx.x];
-    const uint2 r = ranges[gt];
+    const uint2 r = range_at(ranges, gt, cap, status);
     const uint32_t n = r.y - r.x;
     if (n <= 8u * kTileSortSmall) return;
-    tile_sort_one<kTileSortThreads, false>(V, gt, r.x, n, sk, bucket, pid, keys_sorted, vals_sorted, pid_sorted);
+    tile_sort_one<kTileSortThreads, false>(V, gt, r.x, n, sk, bucket, pid, keys_sorted, vals_sorted, pid_sorted,
+                                           status, cap);
 }
 
 // Launch order of the raster kernels: tiles by decreasing list length,
@@ -538,10 +547,10 @@ void launch_bin_sort(const Plan& P, const WsPtrs& w, cudaStream_t st)
         const size_t smem_s = sizeof(unsigned long long) * 8 * kTileSortSmall;      // 8 KB
         k_tile_sort_long<<<(unsigned)V.tiles, kTileSortThreads, smem_l, st>>>(V, w.tile_order, w.ranges, w.bucket,
                                                                              w.pid, w.keys_sorted, w.vals_sorted,
-                                                                             w.pid_sorted);
+                                                                             w.pid_sorted, &w.hdr->status, cap);
         k_tile_sort_short<<<(unsigned)V.tiles, kTileSortSmall, smem_s, st>>>(V, w.tile_order, w.ranges, w.bucket,
                                                                              w.pid, w.keys_sorted, w.vals_sorted,
-                                                                             w.pid_sorted);
+                                                                             w.pid_sorted, &w.hdr->status, cap);
     }
 }
 

@@ -91,6 +91,54 @@ struct __align__(16) GradRec {
     float4 a, b, c;
 };
 
+// Bounds checks of the GS_DEBUG build: GS_DCHECK(cond, status) is true in
+// the normal build; with GS_DEBUG defined it evaluates cond and, when cond is
+// false, sets GS_STATUS_BOUNDS in *status so the caller can skip the access.
+#ifdef GS_DEBUG
+__device__ __forceinline__ bool gs_dcheck(bool ok, uint32_t* status)
+{
+    if (!ok) atomicOr(status, GS_STATUS_BOUNDS);
+    return ok;
+}
+#define GS_DCHECK(cond, status) gs_dcheck((cond), (status))
+#else
+#define GS_DCHECK(cond, status) true
+#endif
+
+// Projected record of a sorted entry's pair; in the GS_DEBUG build an index
+// outside the records gives an all-zero record (opacity 0: no warp block
+// takes it) and sets GS_STATUS_BOUNDS.
+__device__ __forceinline__ ProjRec rec_at(const ProjRec* __restrict__ rec, uint32_t pid, int64_t pairs,
+                                          uint32_t* status)
+{
+#ifdef GS_DEBUG
+    if (!gs_dcheck((int64_t)pid < pairs, status)) {
+        ProjRec z;
+        z.a = z.b = z.c = make_float4(0.f, 0.f, 0.f, 0.f);
+        return z;
+    }
+#else
+    (void)pairs;
+    (void)status;
+#endif
+    return rec[pid];
+}
+
+// A tile's list range, checked against the capacity in the GS_DEBUG build
+// (an out-of-range list is treated as empty).
+__device__ __forceinline__ uint2 range_at(const uint2* __restrict__ ranges, int64_t gt, uint32_t cap,
+                                          uint32_t* status)
+{
+    uint2 r = ranges[gt];
+#ifdef GS_DEBUG
+    if (!gs_dcheck(r.x <= r.y && r.y <= cap, status)) r = make_uint2(0u, 0u);
+#else
+    (void)cap;
+    (void)status;
+#endif
+    return r;
+}
+
 __device__ __forceinline__ int view_of_pair(const Views& V, int64_t p)
 {
     int v = 0;

@@ -404,7 +404,8 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
                                                       const float* __restrict__ tfinal,
                                                       const float* __restrict__ bg, const float* __restrict__ dl,
                                                       const uint32_t* __restrict__ nlast,
-                                                      GradRec* __restrict__ gradrec)
+                                                      GradRec* __restrict__ gradrec, uint32_t* __restrict__ status,
+                                                      uint32_t cap)
 {
     constexpr int NW = BS / 32;
     constexpr int BH = 4 * PPT;            // warp block height, pixels
@@ -431,7 +432,7 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
     const int px = ox + (w % WPR) * 8 + (lane & 7);
     const int py0 = oy + (w / WPR) * BH + (lane >> 3);
     const uint32_t wbit = 1u << w;
-    const uint2 r = ranges[gt];
+    const uint2 r = range_at(ranges, gt, cap, status);
     const float fx = (float)px + 0.5f;
     const int vi = bfly_index(lane);
 
@@ -487,7 +488,7 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
         const int cnt0 = min(BB, L - bb);
         for (int i = tid; i < cnt0; i += BS) {
             const uint32_t k = r.x + bb + i;
-            stage(bb, 0, i, rec[pid_sorted[k]], vals_sorted[k]);
+            stage(bb, 0, i, rec_at(rec, pid_sorted[k], V.pairs, status), vals_sorted[k]);
         }
     }
     __syncthreads();
@@ -508,7 +509,7 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
                 if (i < BB) {
                     const uint32_t k = r.x + bb - BB + i;
                     en[u] = vals_sorted[k];
-                    qn[u] = rec[pid_sorted[k]];
+                    qn[u] = rec_at(rec, pid_sorted[k], V.pairs, status);
                 }
             }
         }
@@ -595,7 +596,7 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
             } else if (comp < 5) {
                 out = comp == 3 ? -s : -0.5f * s;
             }
-            reinterpret_cast<float*>(gradrec + sE[cur][j])[comp] = out;
+            if (GS_DCHECK(sE[cur][j] < cap, status)) reinterpret_cast<float*>(gradrec + sE[cur][j])[comp] = out;
         }
         if (bb > 0) {
 #pragma unroll
@@ -610,7 +611,8 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
     for (uint32_t k = r.x + (uint32_t)L + tid; k < r.y; k += BS) {
         GradRec o;
         o.a = o.b = o.c = make_float4(0.f, 0.f, 0.f, 0.f);
-        gradrec[vals_sorted[k]] = o;
+        const uint32_t e = vals_sorted[k];
+        if (GS_DCHECK(e < cap, status)) gradrec[e] = o;
     }
 }
 
@@ -621,7 +623,8 @@ void launch_raster_bwd_px(const Plan& P, const WsPtrs& w, const float* bg, const
     const int ppt = tile_ppt(P);
 #define GS_RBP(BS, TW, PPT)                                                                                  \
     k_raster_bwd_px<BS, TW, PPT><<<grid, BS, 0, st>>>(V, w.tile_order, w.ranges, w.vals_sorted, w.pid_sorted, \
-                                                      w.rec, w.tfinal, bg, dl, w.nlast, w.gradrec)
+                                                      w.rec, w.tfinal, bg, dl, w.nlast, w.gradrec, &w.hdr->status,   \
+                                                      (uint32_t)P.cap)
     if (V.tw == 8) {
         if (ppt == 1) GS_RBP(64, 8, 1);
         else GS_RBP(32, 8, 2);

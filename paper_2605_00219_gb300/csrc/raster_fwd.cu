@@ -23,7 +23,8 @@ __global__ void __launch_bounds__(BS, (BS == 256 ? 6 : 1)) k_raster_fwd(Views V,
                                                    const uint32_t* __restrict__ pid_sorted,
                                                    const ProjRec* __restrict__ rec, const float* __restrict__ bg,
                                                    float* __restrict__ image, float* __restrict__ tfinal,
-                                                   uint32_t* __restrict__ nlast, WsHeader* __restrict__ hdr)
+                                                   uint32_t* __restrict__ nlast, WsHeader* __restrict__ hdr,
+                                                   uint32_t cap)
 {
     constexpr int CH = BS > 256 ? 256 : BS;   // list entries per staged chunk
     __shared__ float4 sA[2][CH];
@@ -43,7 +44,7 @@ __global__ void __launch_bounds__(BS, (BS == 256 ? 6 : 1)) k_raster_fwd(Views V,
     const int py = oy + (w / WPR) * 4 + (lane >> 3);
     const bool inside = px < vd.W && py < vd.H;
     const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
-    const uint2 r = ranges[gt];
+    const uint2 r = range_at(ranges, gt, cap, &hdr->status);
 
     float Th = 1.0f, Tl = 0.0f;
     float C0 = 0.f, C1 = 0.f, C2 = 0.f;
@@ -52,7 +53,7 @@ __global__ void __launch_bounds__(BS, (BS == 256 ? 6 : 1)) k_raster_fwd(Views V,
     // chunk 0 staged directly; afterwards chunk i+1's records are gathered
     // while chunk i is composited (pair indices one chunk further ahead)
     if (threadIdx.x < CH && r.x + threadIdx.x < r.y) {
-        const ProjRec q = rec[pid_sorted[r.x + threadIdx.x]];
+        const ProjRec q = rec_at(rec, pid_sorted[r.x + threadIdx.x], V.pairs, &hdr->status);
         sA[0][threadIdx.x] = pair_coefs(q.a.x, q.a.y, q.a.z, q.a.w, q.b.x);
         sB[0][threadIdx.x] = make_float4(pair_c2(q.b.x), q.b.y, q.b.z, q.b.w);
         sC[0][threadIdx.x] = make_float4(q.c.x, q.c.z, q.c.w, 0.f);
@@ -64,7 +65,7 @@ __global__ void __launch_bounds__(BS, (BS == 256 ? 6 : 1)) k_raster_fwd(Views V,
         if (__syncthreads_count(done) == BS) break;
         const bool have_next = threadIdx.x < CH && base + CH + threadIdx.x < r.y;
         ProjRec qn;
-        if (have_next) qn = rec[pid_next];
+        if (have_next) qn = rec_at(rec, pid_next, V.pairs, &hdr->status);
         if (threadIdx.x < CH && base + 2 * CH + threadIdx.x < r.y) pid_next = pid_sorted[base + 2 * CH + threadIdx.x];
         const float4* __restrict__ cA = sA[cur];
         const float4* __restrict__ cB = sB[cur];
@@ -147,7 +148,7 @@ void launch_raster_fwd(const Plan& P, const WsPtrs& w, const float* bg, float* i
     const int bs = V.tw * V.th;
     const unsigned grid = (unsigned)V.tiles;
 #define GS_RF(BS, TW) k_raster_fwd<BS, TW><<<grid, BS, 0, st>>>(V, w.tile_order, w.ranges, w.pid_sorted, w.rec, bg, image, \
-                                                                w.tfinal, w.nlast, w.hdr)
+                                                                w.tfinal, w.nlast, w.hdr, (uint32_t)P.cap)
     if (bs == 64) GS_RF(64, 8);
     else if (bs == 256) GS_RF(256, 16);
     else GS_RF(512, 16);

@@ -13,7 +13,10 @@ import os
 import torch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_lib", "libgsstep.so")
+# GS_DEBUG_LIB=1 in the environment loads the bounds-checked build instead
+# (paper_2605_00219_gb300.build.build(debug=True))
+LIB_PATH = os.path.join(HERE, "_lib", "libgsstep_debug.so" if os.environ.get("GS_DEBUG_LIB") == "1"
+                        else "libgsstep.so")
 
 MAX_VIEWS = 64
 MAX_SCENES = 16
@@ -22,6 +25,7 @@ STORE_MOMENTS_BF16 = 0x2
 STATUS_CAPACITY = 0x1
 STATUS_NONFINITE = 0x2
 STATUS_TIMEOUT = 0x4
+STATUS_BOUNDS = 0x8
 
 GS_OK = 0
 STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_CAPACITY", 3: "GS_ERR_NONFINITE",
@@ -80,7 +84,7 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise GSError(f"libgsstep.so not built ({LIB_PATH}); run paper_2605_00219_gb300.build.build()")
+            raise GSError(f"{os.path.basename(LIB_PATH)} not built ({LIB_PATH}); run paper_2605_00219_gb300.build.build()")
         L = ctypes.CDLL(LIB_PATH)
         vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
         L.gs_plan_create.argtypes = [ctypes.POINTER(i64), i32, ctypes.POINTER(gs_view), i32, i64,
