@@ -174,15 +174,17 @@ gs_status gs_workspace_init(const gs_plan* plan, void* ws, void* stream);
  * colour) for every (view, Gaussian) pair, fused with the exact scan-line
  * count of intersected tiles (Sec. 4.1 counts tiles during projection and
  * emits them in a later pass).  Reads geom and sh of every scene and cams;
- * writes the projected records and counts into ws. */
+ * writes the projected records, the counts, the per-tile counts and each
+ * pair's tile span (the bands of its traversal, for the emission) into ws. */
 gs_status gs_project_fwd(const gs_plan* plan, void* ws, const gs_scene_buf* scenes,
                          const float* cams, void* stream);
 
 /* Tiling and sorting (Sec. 4.1, Sec. 4.4, Table 2 "Tiling/Sorting"):
  * exclusive scan of the counts ("index offset"), per-tile [start, end)
- * ranges from the per-tile counts of the projection's traversal, a second
- * scan-line pass emitting every intersected tile into its tile's list
- * ("generate keys"), and a sort of each tile's list, so that the lists hold
+ * ranges from the per-tile counts of the projection's traversal, an
+ * emission of every intersected tile into its tile's list ("generate keys";
+ * the tiles come from the tile spans the traversal kept, and a pair of more
+ * than two bands repeats the scan-line pass), and a sort of each tile's list, so that the lists hold
  * the 32-bit keys (tile id in the top ceil(log2 tiles) bits, depth code
  * (2z+1)/(z+1) mantissa below) in the order of a stable sort of the keys,
  * view by view (ties in emission order, i.e. by Gaussian).  K stays on the
@@ -268,7 +270,18 @@ gs_status gs_read_stats(const gs_plan* plan, const void* ws, gs_stats* out, void
  * + Gaussian), 4 tile ranges u32[tiles][2], 5 n_last u32[pixels], 6 final
  * transmittance f32[pixels], 7 projected records float4[pairs][3]
  * (view-major), 8 gradient records float4[cap][3] (at emission slots),
- * 9 sorted emission slot u32[cap].  Returns NULL for an unknown buffer. */
+ * 9 sorted emission slot u32[cap], 10 tile spans u32[pairs][4] (Gaussian-
+ * major; written for pairs with a nonzero count: word 0 the depth code in
+ * bits 0-22, the number of bands nb in bits 24-25 and the orientation in bit
+ * 26 (1: bands are tile rows); with nb <= 2, word 1 the two bands' row or
+ * column (low, high 16 bits) and words 2, 3 each band's first and last tile
+ * along it (low, high 16 bits); nb = 3 marks more than two bands, words 1-3
+ * then hold the bits of the binning conic a, b, c; bit 27 of word 0 marks a
+ * ranked pair, one of at most four tiles in one or two bands), 11 ranks
+ * u32[pairs][4] (Gaussian-major; for a ranked pair, its place in each of its
+ * tiles' lists, in traversal order), 12 tile counters u32[2][tiles] (entries
+ * of ranked pairs per tile; then, after gs_bin_sort, each tile's cursor for
+ * the other pairs' entries).  Returns NULL for an unknown buffer. */
 void* gs_workspace_buffer(const gs_plan* plan, void* ws, int32_t which);
 
 const char* gs_status_str(gs_status s);

@@ -84,7 +84,8 @@ __device__ __forceinline__ int64_t scan_len(int64_t n, const uint32_t* nb, int m
     return nb ? min(n, (int64_t)(*nb) * mul) : n;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ in, int64_t n_max,
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ in,
+                                                               const uint32_t* __restrict__ in2, int64_t n_max,
                                                                const uint32_t* __restrict__ nb, int mul,
                                                                uint32_t* __restrict__ part)
 {
@@ -95,7 +96,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __
 #pragma unroll
     for (int i = 0; i < kScanItems; i++) {
         int64_t idx = base + i * kScanThreads + threadIdx.x;
-        if (idx < n) s += in[idx];
+        if (idx < n) s += in[idx] + (in2 ? in2[idx] : 0u);
     }
     uint32_t tot;
     block_excl_scan<kScanThreads>(s, ws, &tot);
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(1024) k_scan_part(uint32_t* __restrict__ part,
     if (threadIdx.x == 0) part[nparts] = carry;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* in, int64_t n_max,
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* in, const uint32_t* in2, int64_t n_max,
                                                              const uint32_t* __restrict__ nb, int mul,
                                                              const uint32_t* __restrict__ part, uint32_t* out)
 {
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* in, 
 #pragma unroll
     for (int i = 0; i < kScanItems; i++) {
         int64_t idx = base + i * kScanThreads + threadIdx.x;
-        buf[i * kScanThreads + threadIdx.x] = idx < n ? in[idx] : 0u;
+        buf[i * kScanThreads + threadIdx.x] = idx < n ? in[idx] + (in2 ? in2[idx] : 0u) : 0u;
     }
     __syncthreads();
     uint32_t loc[kScanItems];
@@ -152,18 +153,25 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* in, 
     }
 }
 
-static void scan_u32_dyn(const uint32_t* in, uint32_t* out, int64_t n_max, const uint32_t* nb, int mul,
-                         uint32_t* part, cudaStream_t st)
+static void scan_u32_dyn(const uint32_t* in, const uint32_t* in2, uint32_t* out, int64_t n_max, const uint32_t* nb,
+                         int mul, uint32_t* part, cudaStream_t st)
 {
     const int64_t nparts = (n_max + kScanBlock - 1) / kScanBlock;
-    k_scan_reduce<<<(unsigned)nparts, kScanThreads, 0, st>>>(in, n_max, nb, mul, part);
+    k_scan_reduce<<<(unsigned)nparts, kScanThreads, 0, st>>>(in, in2, n_max, nb, mul, part);
     k_scan_part<<<1, 1024, 0, st>>>(part, nparts);
-    k_scan_down<<<(unsigned)nparts, kScanThreads, 0, st>>>(in, n_max, nb, mul, part, out);
+    k_scan_down<<<(unsigned)nparts, kScanThreads, 0, st>>>(in, in2, n_max, nb, mul, part, out);
 }
 
 void scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* part, cudaStream_t st)
 {
-    scan_u32_dyn(in, out, n, nullptr, 1, part, st);
+    scan_u32_dyn(in, nullptr, out, n, nullptr, 1, part, st);
+}
+
+// Exclusive scan of in[i] + in2[i].
+static void scan_u32_sum2(const uint32_t* in, const uint32_t* in2, uint32_t* out, int64_t n, uint32_t* part,
+                          cudaStream_t st)
+{
+    scan_u32_dyn(in, in2, out, n, nullptr, 1, part, st);
 }
 
 // Total and capacity check after the count scan: k_eff = K when it fits the
@@ -180,17 +188,19 @@ __global__ void k_count_finalize(const uint32_t* __restrict__ part, int64_t npar
     }
 }
 
-// Tile ranges from the scanned tile counts (start in tile_cur, which stays
-// as the tile's scatter cursor); an empty list is [0, 0), and every list is
-// empty when K exceeds the capacity.
-__global__ void k_tile_setup(int64_t tiles, const uint32_t* __restrict__ tile_cnt,
-                             const uint32_t* __restrict__ tile_start, const WsHeader* __restrict__ hdr,
-                             uint2* __restrict__ ranges)
+// Tile ranges from the scanned tile counts: a tile's list holds first the
+// entries of ranked pairs (at their ranks), then the others, placed by a
+// cursor that starts after the ranked ones (it replaces the overflow count).
+// An empty list is [0, 0), and every list is empty when K exceeds the
+// capacity.
+__global__ void k_tile_setup(int64_t tiles, uint32_t* __restrict__ tile_cnt, const uint32_t* __restrict__ tile_start,
+                             const WsHeader* __restrict__ hdr, uint2* __restrict__ ranges)
 {
     const bool fits = hdr->k_eff == hdr->k_required;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tiles; t += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t s0 = tile_start[t], c = tile_cnt[t];
+        const uint32_t s0 = tile_start[t], cr = tile_cnt[t], c = cr + tile_cnt[tiles + t];
         ranges[t] = fits && c ? make_uint2(s0, s0 + c) : make_uint2(0u, 0u);
+        tile_cnt[tiles + t] = s0 + cr;
     }
 }
 
@@ -199,14 +209,19 @@ __global__ void k_tile_setup(int64_t tiles, const uint32_t* __restrict__ tile_cn
 // ---------------------------------------------------------------------------
 
 // One thread per Gaussian-major pair q: its intersections take emission
-// slots offset[q] + i in traversal order; each is placed at the next free
-// slot of its tile's list (depth code and emission slot), and the view-major
-// pair index is recorded at its emission slot.
-__global__ void __launch_bounds__(256) k_emit(Views V, const uint32_t* __restrict__ count,
-                                              const uint32_t* __restrict__ offset, const ProjRec* __restrict__ rec,
-                                              const float4* __restrict__ binrec, uint32_t* tile_cur,
-                                              uint2* __restrict__ bucket, uint32_t* __restrict__ pid,
-                                              WsHeader* __restrict__ hdr)
+// slots offset[q] + i in traversal order; each is placed in its tile's list
+// (depth code and emission slot), and the view-major pair index is recorded
+// at its emission slot.  The tiles come from the pair's tile span.  A ranked
+// pair's entries go to tile start + the rank the projection took; the other
+// pairs' entries take the next free place after the ranked ones (an atomic
+// cursor per tile), and the rare pair of more than two bands repeats the
+// traversal from its binning geometry.
+__global__ void __launch_bounds__(256, 6) k_emit(Views V, const uint32_t* __restrict__ count,
+                                                 const uint32_t* __restrict__ offset, const ProjRec* __restrict__ rec,
+                                                 const uint4* __restrict__ span, const uint4* __restrict__ rank,
+                                                 const uint32_t* __restrict__ tile_start, uint32_t* tile_over,
+                                                 uint2* __restrict__ bucket, uint32_t* __restrict__ pid,
+                                                 WsHeader* __restrict__ hdr)
 {
     const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (qi >= V.pairs) return;
@@ -220,26 +235,70 @@ __global__ void __launch_bounds__(256) k_emit(Views V, const uint32_t* __restric
     const int64_t g = local / nv;
     const int v = V.view_of[s][(int)(local - g * nv)];
     const ViewDesc& vd = V.v[v];
-    const int64_t p = vd.pair_base + g;
+    const uint32_t p = (uint32_t)(vd.pair_base + g);
     const uint32_t off = offset[qi];
-    const float4 ra = rec[p].a;
-    const float4 bb = binrec[p];
-    BinGeom gm;
-    gm.mx = ra.x; gm.my = ra.y; gm.a = bb.x; gm.b = bb.y; gm.c = bb.z;
-    gm.det = FS(FM(gm.a, gm.c), FM(gm.b, gm.b));
-    gm.r2 = cull_r2(rec[p].b.y);   // same bits as in the projection pass
-    gm.mant = __float_as_uint(bb.w);
-    gm.valid = 1;
-    const uint32_t low = gm.mant >> vd.drop;
-    uint32_t* cur = tile_cur + vd.tile_base;
-    scanline_tiles(gm, V.tw, V.th, vd.TX, vd.TY, [&](uint32_t i, uint32_t tile) {
-        const uint32_t e = off + i;
-        const uint32_t slot = atomicAdd(cur + tile, 1u);
-        if (GS_DCHECK(slot < hdr->k_eff && e < hdr->k_eff, &hdr->status)) {
-            bucket[slot] = make_uint2(low, e);
-            pid[e] = (uint32_t)p;
+    const uint4 sp = span[qi];
+    const uint32_t low = (sp.x & 0x7FFFFFu) >> vd.drop;
+    const uint32_t nb = (sp.x >> 24) & 3u;
+    uint32_t* cur = tile_over + vd.tile_base;
+    if (nb == kSpanMany) {
+        const float4 ra = rec[p].a;
+        BinGeom gm;
+        gm.mx = ra.x; gm.my = ra.y;
+        gm.a = __uint_as_float(sp.y); gm.b = __uint_as_float(sp.z); gm.c = __uint_as_float(sp.w);
+        gm.det = FS(FM(gm.a, gm.c), FM(gm.b, gm.b));
+        gm.r2 = cull_r2(rec[p].b.y);   // same bits as in the projection pass
+        gm.mant = sp.x & 0x7FFFFFu;
+        gm.valid = 1;
+        scanline_tiles(gm, V.tw, V.th, vd.TX, vd.TY, [&](uint32_t i, uint32_t tile) {
+            const uint32_t e = off + i;
+            const uint32_t slot = atomicAdd(cur + tile, 1u);
+            if (GS_DCHECK(slot < hdr->k_eff && e < hdr->k_eff, &hdr->status)) {
+                bucket[slot] = make_uint2(low, e);
+                pid[e] = p;
+            }
+        });
+        return;
+    }
+    const bool rows = (sp.x >> 26) & 1u;
+    const uint32_t TX = (uint32_t)vd.TX;
+    const uint32_t c0 = sp.y & 0xFFFFu, c1 = sp.y >> 16;
+    if ((sp.x >> 27) & 1u) {
+        // ranked: at most kRankMax tiles, no atomics
+        const uint4 rk4 = rank[qi];
+        const uint32_t rk[kRankMax] = {rk4.x, rk4.y, rk4.z, rk4.w};
+        const uint32_t* __restrict__ st0 = tile_start + vd.tile_base;
+#pragma unroll
+        for (uint32_t u = 0; u < kRankMax; u++) {
+            const uint32_t e = off + u;
+            if (u < cnt) {
+                const uint32_t slot = st0[span_tile(u, rows, TX, c0, c1, sp.z, sp.w)] + rk[u];
+                if (GS_DCHECK(slot < hdr->k_eff && e < hdr->k_eff, &hdr->status)) {
+                    bucket[slot] = make_uint2(low, e);
+                    pid[e] = p;
+                }
+            }
         }
-    });
+        return;
+    }
+    // one or two bands: the cursors taken four at a time so that the
+    // atomics' round trips overlap
+    for (uint32_t i0 = 0; i0 < cnt; i0 += 4) {
+        uint32_t slot[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const uint32_t i = i0 + u;
+            if (i < cnt) slot[u] = atomicAdd(cur + span_tile(i, rows, TX, c0, c1, sp.z, sp.w), 1u);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const uint32_t i = i0 + u, e = off + i;
+            if (i < cnt && GS_DCHECK(slot[u] < hdr->k_eff && e < hdr->k_eff, &hdr->status)) {
+                bucket[slot[u]] = make_uint2(low, e);
+                pid[e] = p;
+            }
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -251,15 +310,17 @@ __device__ __forceinline__ unsigned long long sort_key(uint32_t low, uint32_t e)
     return ((unsigned long long)low << 32) | e;
 }
 
-// Ascending sort of N (a power of two, 8 <= N <= 8 * blockDim.x) 64-bit
-// keys in shared memory, block merge sort: thread t owns the 8 keys
+// Ascending sort of N (a multiple of 8, 8 <= N <= 8 * blockDim.x) 64-bit
+// keys in shared memory, block merge sort: thread t < N / 8 owns the 8 keys
 // [8t, 8t + 8); it sorts them with a 19-comparator network in registers,
 // then, at each merge level of run width w, finds where its 8 outputs start
 // in the merge of its two runs (merge-path binary search on the output
-// diagonal) and merges them sequentially.  While two runs fit in one warp's
-// 256 keys (w <= 128) only that warp reads and writes them, so the level
-// synchronises the warp; a level that reads wider runs synchronises the
-// block, also before its reads.  The caller synchronises the block before.
+// diagonal) and merges them sequentially.  The last run of a level may be
+// short or alone (then it is already merged), so no padding to a power of
+// two is sorted.  While two runs fit in one warp's 256 keys (w <= 128) only
+// that warp reads and writes them, so the level synchronises the warp; a
+// level that reads wider runs synchronises the block, also before its
+// reads.  The caller synchronises the block before.
 __device__ __forceinline__ void cmpx(unsigned long long& a, unsigned long long& b)
 {
     const unsigned long long lo = a < b ? a : b, hi = a < b ? b : a;
@@ -287,34 +348,36 @@ __device__ void block_merge_sort_smem(unsigned long long* s, int N)
     __syncwarp();
     for (int w = IT; w < N; w <<= 1) {
         const bool in_warp = 2 * w <= 32 * IT;
-        if (t < nt) {
-            const int base = (IT * t) & ~(2 * w - 1), diag = IT * t - base;
+        const int base = (IT * t) & ~(2 * w - 1), diag = IT * t - base;
+        const int la = min(w, N - base), lb = max(0, min(w, N - base - w));
+        const bool merge = t < nt && lb > 0;   // a lone last run stays in place
+        if (merge) {
             const unsigned long long* A = s + base;
             const unsigned long long* B = s + base + w;
-            int lo = max(0, diag - w), hi = min(diag, w);
+            int lo = max(0, diag - lb), hi = min(diag, la);
             while (lo < hi) {
                 const int mid = (lo + hi) >> 1;
                 if (A[mid] <= B[diag - 1 - mid]) lo = mid + 1;
                 else hi = mid;
             }
             int a = lo, b = diag - lo;
-            unsigned long long ha = a < w ? A[a] : 0ull, hb = b < w ? B[b] : 0ull;
+            unsigned long long ha = a < la ? A[a] : 0ull, hb = b < lb ? B[b] : 0ull;
 #pragma unroll
             for (int k = 0; k < IT; k++) {
-                const bool take_a = b >= w || (a < w && ha <= hb);
+                const bool take_a = b >= lb || (a < la && ha <= hb);
                 r[k] = take_a ? ha : hb;
                 if (take_a) {
                     a++;
-                    ha = a < w ? A[a] : 0ull;
+                    ha = a < la ? A[a] : 0ull;
                 } else {
                     b++;
-                    hb = b < w ? B[b] : 0ull;
+                    hb = b < lb ? B[b] : 0ull;
                 }
             }
         }
         if (in_warp) __syncwarp();
         else __syncthreads();
-        if (t < nt) {
+        if (merge) {
 #pragma unroll
             for (int k = 0; k < IT; k++) s[IT * t + k] = r[k];
         }
@@ -393,8 +456,7 @@ __device__ void tile_sort_one(const Views& V, int64_t gt, uint32_t s0, uint32_t 
     const ViewDesc& vd = V.v[view_of_tile(V, gt)];
     const uint32_t hi_bits = (uint32_t)(gt - vd.tile_base) << vd.shift;
     if (n <= 8u * (uint32_t)T) {
-        int N = 8;
-        while (N < (int)n) N <<= 1;
+        const int N = (int)((n + 7u) & ~7u);    // the last thread's keys padded
         for (int i = threadIdx.x; i < N; i += blockDim.x) {
             unsigned long long x = ~0ull;
             if (i < (int)n) {
@@ -529,7 +591,7 @@ void launch_bin_sort(const Plan& P, const WsPtrs& w, cudaStream_t st)
     scan_u32(w.count, w.offset, V.pairs, w.scan_part, st);
     k_count_finalize<<<1, 32, 0, st>>>(w.scan_part, P.count_scan_parts, V.pairs, w.offset, w.hdr, cap);
     // tile ranges and scatter cursors from the per-tile counts
-    scan_u32(w.tile_cnt, w.tile_cur, V.tiles, w.scan_part, st);
+    scan_u32_sum2(w.tile_cnt, w.tile_cnt + V.tiles, w.tile_cur, V.tiles, w.scan_part, st);
     {
         const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((V.tiles + 255) / 256, (int64_t)P.sm_count * 8));
         k_tile_setup<<<(unsigned)blocks, 256, 0, st>>>(V.tiles, w.tile_cnt, w.tile_cur, w.hdr, w.ranges);
@@ -538,8 +600,8 @@ void launch_bin_sort(const Plan& P, const WsPtrs& w, cudaStream_t st)
     // generate keys into the tile buckets
     {
         const int64_t blocks = (V.pairs + 255) / 256;
-        k_emit<<<(unsigned)blocks, 256, 0, st>>>(V, w.count, w.offset, w.rec, w.binrec, w.tile_cur, w.bucket, w.pid,
-                                                 w.hdr);
+        k_emit<<<(unsigned)blocks, 256, 0, st>>>(V, w.count, w.offset, w.rec, w.span, w.rank, w.tile_cur,
+                                                 w.tile_cnt + V.tiles, w.bucket, w.pid, w.hdr);
     }
     // sort each tile's list
     {

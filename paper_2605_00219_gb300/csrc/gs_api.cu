@@ -29,7 +29,8 @@ WsPtrs carve(const Plan& P, void* ws)
     w.count = reinterpret_cast<uint32_t*>(b + P.off_count);
     w.offset = reinterpret_cast<uint32_t*>(b + P.off_offset);
     w.rec = reinterpret_cast<ProjRec*>(b + P.off_rec);
-    w.binrec = reinterpret_cast<float4*>(b + P.off_binrec);
+    w.span = reinterpret_cast<uint4*>(b + P.off_span);
+    w.rank = reinterpret_cast<uint4*>(b + P.off_rank);
     w.bucket = reinterpret_cast<uint2*>(b + P.off_bucket);
     w.keys_sorted = reinterpret_cast<uint32_t*>(b + P.off_keys);
     w.vals_sorted = reinterpret_cast<uint32_t*>(b + P.off_vals);
@@ -154,13 +155,14 @@ static bool plan_build(Plan& P, const int64_t* scene_n, int32_t n_scenes, const 
     P.off_count = take(4 * (size_t)pairs);
     P.off_offset = take(4 * (size_t)(pairs + 1));
     P.off_rec = take(sizeof(ProjRec) * (size_t)pairs);
-    P.off_binrec = take(16 * (size_t)pairs);
+    P.off_span = take(16 * (size_t)pairs);
+    P.off_rank = take(16 * (size_t)pairs);
     P.off_bucket = take(8 * (size_t)cap);
     P.off_keys = take(4 * (size_t)cap);
     P.off_vals = take(4 * (size_t)cap);
     P.off_pid = take(4 * (size_t)cap);
     P.off_pid_sorted = take(4 * (size_t)cap);
-    P.off_tile_cnt = take(4 * (size_t)tiles);
+    P.off_tile_cnt = take(4 * 2 * (size_t)tiles);   // ranked counts, then overflow counts
     P.off_tile_cur = take(4 * (size_t)(tiles + 1));
     P.off_ranges = take(8 * (size_t)tiles);
     P.off_order = take(4 * (size_t)tiles);
@@ -195,7 +197,7 @@ Scenes make_scenes(const Plan& P, const gs_scene_buf* scenes)
 
 // Header reset (and, with `full`, the Adam step counter); the per-tile
 // counters that the projection adds to start from zero.
-__global__ void k_ws_init(WsHeader* hdr, int full, uint32_t* __restrict__ tile_cnt, int64_t tiles)
+__global__ void k_ws_init(WsHeader* hdr, int full, uint32_t* __restrict__ tile_cnt, int64_t n_cnt)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         hdr->status = 0;
@@ -206,7 +208,7 @@ __global__ void k_ws_init(WsHeader* hdr, int full, uint32_t* __restrict__ tile_c
         hdr->loss = 0.f;
         if (full) hdr->step = 0;
     }
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tiles; i += (int64_t)gridDim.x * blockDim.x)
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_cnt; i += (int64_t)gridDim.x * blockDim.x)
         tile_cnt[i] = 0u;
 }
 
@@ -217,12 +219,12 @@ static unsigned init_blocks(const Plan& P)
 
 void launch_ws_init(const Plan& P, const WsPtrs& w, cudaStream_t st)
 {
-    k_ws_init<<<init_blocks(P), 256, 0, st>>>(w.hdr, 1, w.tile_cnt, P.views.tiles);
+    k_ws_init<<<init_blocks(P), 256, 0, st>>>(w.hdr, 1, w.tile_cnt, 2 * P.views.tiles);
 }
 
 static void launch_step_begin(const Plan& P, const WsPtrs& w, cudaStream_t st)
 {
-    k_ws_init<<<init_blocks(P), 256, 0, st>>>(w.hdr, 0, w.tile_cnt, P.views.tiles);
+    k_ws_init<<<init_blocks(P), 256, 0, st>>>(w.hdr, 0, w.tile_cnt, 2 * P.views.tiles);
 }
 
 __global__ void k_adam_advance(WsHeader* hdr)
@@ -443,6 +445,9 @@ void* gs_workspace_buffer(const gs_plan* plan, void* ws, int32_t which)
     case 7: return w.rec;
     case 8: return w.gradrec;
     case 9: return w.vals_sorted;
+    case 10: return w.span;
+    case 11: return w.rank;
+    case 12: return w.tile_cnt;
     default: return nullptr;
     }
 }

@@ -322,11 +322,14 @@ __device__ __forceinline__ int tile_hi(float v, int T, int n)
     return i > n - 1 ? n - 1 : i;
 }
 
-// Scan-line traversal (Sec. 4.1): calls emit(tile_id) for every tile whose
-// pixel-centre rectangle meets the ellipse d^2 <= g.r2, band by band along
-// the shorter dimension of the tile bounding box.  Returns the count.
-template <typename Emit>
-__device__ __forceinline__ uint32_t scanline_tiles(const BinGeom& g, int tw, int th, int TX, int TY, Emit emit)
+// Scan-line traversal (Sec. 4.1) of the tiles whose pixel-centre rectangle
+// meets the ellipse d^2 <= g.r2, band by band along the shorter dimension of
+// the tile bounding box: calls band(rows, coord, lo, hi) for every band that
+// meets a tile, in traversal order -- rows: bands are tile rows (coord = ty,
+// tiles tx = lo..hi), else tile columns (coord = tx, tiles ty = lo..hi).
+// Returns the number of tiles.
+template <typename Band>
+__device__ __forceinline__ uint32_t scanline_bands(const BinGeom& g, int tw, int th, int TX, int TY, Band band)
 {
     const float r2 = g.r2;
     float ex = FQ(FM(r2, g.a));
@@ -350,10 +353,9 @@ __device__ __forceinline__ uint32_t scanline_tiles(const BinGeom& g, int tw, int
             float xR = FA(g.mx, FD(FA(FM(g.b, dR), hR), g.c));
             float xL = FA(g.mx, FD(FS(FM(g.b, dL), hL), g.c));
             int lo = tile_lo(xL, tw, TX), hi = tile_hi(xR, tw, TX);
-            for (int tx = lo; tx <= hi; tx++) {
-                emit(count, (uint32_t)(ty * TX + tx));
-                count++;
-            }
+            if (lo > hi) continue;
+            band(true, ty, lo, hi);
+            count += (uint32_t)(hi - lo + 1);
         }
     } else {
         float xstar = FM(g.b, FQ(FD(r2, g.c)));
@@ -370,13 +372,55 @@ __device__ __forceinline__ uint32_t scanline_tiles(const BinGeom& g, int tw, int
             float yT = FA(g.my, FD(FA(FM(g.b, dT), hT), g.a));
             float yB = FA(g.my, FD(FS(FM(g.b, dB), hB), g.a));
             int lo = tile_lo(yB, th, TY), hi = tile_hi(yT, th, TY);
-            for (int ty = lo; ty <= hi; ty++) {
-                emit(count, (uint32_t)(ty * TX + tx));
-                count++;
-            }
+            if (lo > hi) continue;
+            band(false, tx, lo, hi);
+            count += (uint32_t)(hi - lo + 1);
         }
     }
     return count;
+}
+
+// The same traversal tile by tile: emit(i, tile id) for the i-th tile.
+template <typename Emit>
+__device__ __forceinline__ uint32_t scanline_tiles(const BinGeom& g, int tw, int th, int TX, int TY, Emit emit)
+{
+    uint32_t i = 0;
+    return scanline_bands(g, tw, th, TX, TY, [&](bool rows, int coord, int lo, int hi) {
+        for (int t = lo; t <= hi; t++, i++) emit(i, rows ? (uint32_t)(coord * TX + t) : (uint32_t)(t * TX + coord));
+    });
+}
+
+// Tile span of a pair, written by the projection's traversal and read by
+// the emission, so that the emission repeats no traversal arithmetic
+// (16 bytes, Gaussian-major pair order).  x: depth code (bits 0-22), number
+// of bands nb (bits 24-25), band orientation (bit 26: 1 = tile rows), ranked
+// (bit 27: the projection took the pair's place in each of its tiles' lists,
+// kRankMax tiles at most).  With nb <= 2: y = coord0 | coord1 << 16,
+// z = lo0 | hi0 << 16, w = lo1 | hi1 << 16 (tile coordinates < 2^16).
+// nb = 3 marks a pair with more than two bands: y, z, w then hold the
+// binning conic's a, b, c bits, from which the emission repeats the
+// traversal.
+constexpr uint32_t kSpanMany = 3u;
+constexpr uint32_t kRankMax = 4u;
+
+__device__ __forceinline__ uint4 span_pack(uint32_t mant, uint32_t nb, bool rows, bool ranked, uint32_t c0,
+                                           uint32_t c1, uint32_t r0, uint32_t r1, const BinGeom& g)
+{
+    if (nb > 2) return make_uint4(mant | (kSpanMany << 24), __float_as_uint(g.a), __float_as_uint(g.b),
+                                  __float_as_uint(g.c));
+    return make_uint4(mant | (nb << 24) | (rows ? 1u << 26 : 0u) | (ranked ? 1u << 27 : 0u), c0 | (c1 << 16), r0,
+                      r1);
+}
+
+// The i-th tile (local id) of a span of one or two bands.
+__device__ __forceinline__ uint32_t span_tile(uint32_t i, bool rows, uint32_t TX, uint32_t c0, uint32_t c1,
+                                              uint32_t r0, uint32_t r1)
+{
+    const uint32_t lo0 = r0 & 0xFFFFu, n0 = (r0 >> 16) - lo0 + 1u;
+    const bool second = i >= n0;
+    const uint32_t t = second ? (r1 & 0xFFFFu) + (i - n0) : lo0 + i;
+    const uint32_t cd = second ? c1 : c0;
+    return rows ? cd * TX + t : t * TX + cd;
 }
 
 // --------------------------------------------------------------------------

@@ -40,7 +40,7 @@ struct Plan {
     int64_t raster_blocks;       // total tiles
     int32_t sm_count;            // SMs of the device current at plan creation (152 if none)
     // workspace byte offsets
-    size_t off_hdr, off_count, off_offset, off_rec, off_binrec;
+    size_t off_hdr, off_count, off_offset, off_rec, off_span, off_rank;
     size_t off_bucket, off_keys, off_vals, off_pid, off_pid_sorted;
     size_t off_tile_cnt, off_tile_cur;
     size_t off_ranges, off_nlast, off_tfinal, off_gradrec, off_scan_part, off_loss_part, off_order;
@@ -52,14 +52,16 @@ struct WsPtrs {
     uint32_t* count;           // tiles per pair, Gaussian-major order
     uint32_t* offset;          // its exclusive scan: first emission slot of each pair
     ProjRec* rec;              // projected records, view-major pair order
-    float4* binrec;
+    uint4* span;               // tile span of each pair, Gaussian-major order
+    uint4* rank;               // in-tile ranks of a ranked pair's tiles, Gaussian-major order
     uint2* bucket;             // tile lists in arrival order: (depth code, emission slot)
     uint32_t* pid;             // view-major pair of each emission slot
     uint32_t* keys_sorted;     // sorted keys (tile << shift | depth code)
     uint32_t* vals_sorted;     // emission slot of each sorted entry
     uint32_t* pid_sorted;      // pair of each sorted entry
-    uint32_t* tile_cnt;        // entries per global tile
-    uint32_t* tile_cur;        // tile starts, then the scatter cursors
+    uint32_t* tile_cnt;        // [tiles] entries of ranked pairs per global tile, then [tiles] entries of
+                               // the other pairs (after the tile scan: their scatter cursors)
+    uint32_t* tile_cur;        // tile starts (exclusive scan of both counts)
     uint2* ranges;
     uint32_t* tile_order;      // tiles by decreasing list length (raster launch order)
     uint32_t* nlast;

@@ -104,16 +104,38 @@ __device__ __forceinline__ void covariance3d_bwd(float4 q, float4 so, const floa
     dq[3] += (dqn[3] - z * dqq) * qn_r;
 }
 
+// A Gaussian's SH coefficients in its thread's shared-memory row, chunk j =
+// coefficients 4j .. 4j + 3: FP32 rows of 13 float4, or BF16 rows of 7 uint4
+// (two chunks per uint4) for BF16 storage.  The strides make the 16-byte
+// accesses of 8 consecutive threads cover all 32 banks once.
+template <bool SH16> struct ShRow;
+template <> struct ShRow<false> {
+    static constexpr int kRowBytes = 13 * 16;
+    const float4* r;
+    __device__ __forceinline__ float4 operator()(int j) const { return r[j]; }
+};
+template <> struct ShRow<true> {
+    static constexpr int kRowBytes = 7 * 16;
+    const uint4* r;
+    __device__ __forceinline__ float4 operator()(int j) const
+    {
+        const uint4 u = r[j >> 1];
+        const uint32_t a = (j & 1) ? u.z : u.x, b = (j & 1) ? u.w : u.y;
+        return make_float4(bf16_lo(a), bf16_hi(a), bf16_lo(b), bf16_hi(b));
+    }
+};
+
 // Per-view backward of one Gaussian through projection and colour:
 // accumulates dmu, dSg (dL/dSigma, symmetric) and dop (activated opacity),
-// and returns the SH basis at the view direction (Y) and dL/d(raw colour)
-// (draw) so that the SH gradient sum_v Y_v[k] draw_v[c] can be formed later.
+// and adds this view's SH gradient Y[k] draw[c] (basis at the view
+// direction times dL/d(raw colour)) to the thread's row sgrow.
 // The SH coefficients are read twice (clamp test, then the direction
 // gradient) from the thread's shared-memory row instead of being held in
 // registers.
+template <typename Row>
 __device__ __forceinline__ void proj_bwd_view(const float* cam, int W, int H, float4 mu, const float* Sg,
-                                              const float4* shrow, const float* g2, float* dmu, float* dSg,
-                                              float& dop, float* Y, float* draw)
+                                              const Row& shrow, const float* g2, float* dmu, float* dSg,
+                                              float& dop, float4* sgrow)
 {
     const float fx = cam[12], fy = cam[13];
     const float* C = cam;
@@ -129,23 +151,36 @@ __device__ __forceinline__ void proj_bwd_view(const float* cam, int W, int H, fl
     const float ddx = mu.x - cpx, ddy = mu.y - cpy, ddz = mu.z - cpz;
     const float idist = rsqrtf(ddx * ddx + ddy * ddy + ddz * ddz);
     const float dirx = ddx * idist, diry = ddy * idist, dirz = ddz * idist;
+    float Y[16];
     sh_basis(dirx, diry, dirz, Y);
     float raw[3] = {0.5f, 0.5f, 0.5f};
 #pragma unroll
     for (int j = 0; j < 12; j++) {
-        const float4 c4 = shrow[j];
+        const float4 c4 = shrow(j);
         const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
         for (int i = 0; i < 4; i++) raw[(4 * j + i) % 3] = fmaf(cv[i], Y[(4 * j + i) / 3], raw[(4 * j + i) % 3]);
     }
+    float draw[3];
 #pragma unroll
     for (int c = 0; c < 3; c++) draw[c] = raw[c] < 0.0f ? 0.0f : g2[6 + c];
+    // SH gradient of this view, Y[k] draw[c], added to the thread's row now
+    // so that the basis values are dead during the covariance part
+#pragma unroll
+    for (int j = 0; j < 12; j++) {
+        float4 a = sgrow[j];
+        a.x = fmaf(Y[(4 * j) / 3], draw[(4 * j) % 3], a.x);
+        a.y = fmaf(Y[(4 * j + 1) / 3], draw[(4 * j + 1) % 3], a.y);
+        a.z = fmaf(Y[(4 * j + 2) / 3], draw[(4 * j + 2) % 3], a.z);
+        a.w = fmaf(Y[(4 * j + 3) / 3], draw[(4 * j + 3) % 3], a.w);
+        sgrow[j] = a;
+    }
     float wk[16];
 #pragma unroll
     for (int k = 0; k < 16; k++) wk[k] = 0.f;
 #pragma unroll
     for (int j = 0; j < 12; j++) {
-        const float4 c4 = shrow[j];
+        const float4 c4 = shrow(j);
         const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
         for (int i = 0; i < 4; i++) wk[(4 * j + i) / 3] = fmaf(cv[i], draw[(4 * j + i) % 3], wk[(4 * j + i) / 3]);
@@ -312,13 +347,15 @@ __global__ void __launch_bounds__(kPbaThreads, 4) k_project_bwd_adam(Views V, Sc
                                                                   float4* __restrict__ grads_out,
                                                                   const WsHeader* __restrict__ hdr, uint32_t cap)
 {
-    // per thread, 12 float4 rows (stride 13 float4: the 16-byte accesses of
-    // 8 consecutive threads cover all 32 banks once): the SH gradients, and
-    // the Gaussian's 48 SH coefficients in FP32, read from HBM once and used
-    // by every view and by the SH update
+    // per thread, a row of 12 float4 (stride 13 float4: the 16-byte accesses
+    // of 8 consecutive threads cover all 32 banks once) for the SH gradients,
+    // and a row of the Gaussian's 48 SH coefficients as stored (FP32 or BF16,
+    // ShRow), read from HBM once and used by every view and by the SH update.
+    // (53 KB per block with FP32 rows, 41 KB with BF16 rows)
     extern __shared__ float4 pba_smem[];
     float4 (*sG)[13] = reinterpret_cast<float4 (*)[13]>(pba_smem);
-    float4 (*sS)[13] = reinterpret_cast<float4 (*)[13]>(pba_smem + kPbaThreads * 13);
+    float4 (*sS)[13] = reinterpret_cast<float4 (*)[13]>(pba_smem + kPbaThreads * 13);    // FP32 rows
+    uint4 (*sS16)[7] = reinterpret_cast<uint4 (*)[7]>(pba_smem + kPbaThreads * 13);      // BF16 rows
     __shared__ AdamConst sK;
     const int tid = threadIdx.x;
     const int64_t gi = (int64_t)blockIdx.x * kPbaThreads + tid;
@@ -362,11 +399,7 @@ __global__ void __launch_bounds__(kPbaThreads, 4) k_project_bwd_adam(Views V, Sc
             for (int j = 0; j < 12; j++) sS[tid][j] = reinterpret_cast<const float4*>(sc.sh)[(int64_t)j * n + g];
         } else {
 #pragma unroll
-            for (int jp = 0; jp < 6; jp++) {
-                const uint4 c = reinterpret_cast<const uint4*>(sc.sh)[(int64_t)jp * n + g];
-                sS[tid][2 * jp] = make_float4(bf16_lo(c.x), bf16_hi(c.x), bf16_lo(c.y), bf16_hi(c.y));
-                sS[tid][2 * jp + 1] = make_float4(bf16_lo(c.z), bf16_hi(c.z), bf16_lo(c.w), bf16_hi(c.w));
-            }
+            for (int jp = 0; jp < 6; jp++) sS16[tid][jp] = reinterpret_cast<const uint4*>(sc.sh)[(int64_t)jp * n + g];
         }
         float dmu[3] = {0.f, 0.f, 0.f}, dSg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, dop = 0.f;
         float Sg[6];
@@ -416,17 +449,8 @@ __global__ void __launch_bounds__(kPbaThreads, 4) k_project_bwd_adam(Views V, Sc
             float cam[16];
 #pragma unroll
             for (int i = 0; i < 16; i++) cam[i] = __ldg(cams + 16 * v + i);
-            float Y[16], draw[3];
-            proj_bwd_view(cam, vd.W, vd.H, mu, Sg, sS[tid], g2, dmu, dSg, dop, Y, draw);
-#pragma unroll
-            for (int j = 0; j < 12; j++) {
-                float4 a = sG[tid][j];
-                a.x = fmaf(Y[(4 * j) / 3], draw[(4 * j) % 3], a.x);
-                a.y = fmaf(Y[(4 * j + 1) / 3], draw[(4 * j + 1) % 3], a.y);
-                a.z = fmaf(Y[(4 * j + 2) / 3], draw[(4 * j + 2) % 3], a.z);
-                a.w = fmaf(Y[(4 * j + 3) / 3], draw[(4 * j + 3) % 3], a.w);
-                sG[tid][j] = a;
-            }
+            if (SH16) proj_bwd_view(cam, vd.W, vd.H, mu, Sg, ShRow<true>{sS16[tid]}, g2, dmu, dSg, dop, sG[tid]);
+            else proj_bwd_view(cam, vd.W, vd.H, mu, Sg, ShRow<false>{sS[tid]}, g2, dmu, dSg, dop, sG[tid]);
         }
         float dq[4] = {0.f, 0.f, 0.f, 0.f}, ds[3] = {0.f, 0.f, 0.f};
         covariance3d_bwd(q, so, dSg, dq, ds);
@@ -494,7 +518,11 @@ __global__ void __launch_bounds__(kPbaThreads, 4) k_project_bwd_adam(Views V, Sc
 #pragma unroll 3
     for (int jp = 0; jp < 6; jp++) {          // pairs of chunks = 8 coefficients
         float th[8];
-        {
+        if (SH16) {
+            const uint4 c = sS16[tid][jp];
+            th[0] = bf16_lo(c.x); th[1] = bf16_hi(c.x); th[2] = bf16_lo(c.y); th[3] = bf16_hi(c.y);
+            th[4] = bf16_lo(c.z); th[5] = bf16_hi(c.z); th[6] = bf16_lo(c.w); th[7] = bf16_hi(c.w);
+        } else {
             const float4 a = sS[tid][2 * jp], b = sS[tid][2 * jp + 1];
             th[0] = a.x; th[1] = a.y; th[2] = a.z; th[3] = a.w; th[4] = b.x; th[5] = b.y; th[6] = b.z; th[7] = b.w;
         }
@@ -539,9 +567,10 @@ void launch_project_bwd_adam(const Plan& P, const Scenes& S, const float* cams, 
     A.grad_only = grads_out != nullptr;
     A.seed = adam ? adam->seed : 0u;
     const int64_t blocks = (S.total + kPbaThreads - 1) / kPbaThreads;
-    const size_t smem = sizeof(float4) * 2 * kPbaThreads * 13;   // 53 KB: above the default 48 KB
 #define GS_PBA(SH, MO)                                                                                              \
     do {                                                                                                            \
+        /* 53 KB (FP32 rows) or 41 KB: above the default 48 KB for FP32 */                                          \
+        const size_t smem = (sizeof(float4) * 13 + ShRow<SH>::kRowBytes) * kPbaThreads;                              \
         cudaFuncSetAttribute(k_project_bwd_adam<SH, MO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);   \
         k_project_bwd_adam<SH, MO><<<(unsigned)blocks, kPbaThreads, smem, st>>>(P.views, S, cams, w.count, w.offset, \
                               w.gradrec, A, reinterpret_cast<float4*>(grads_out), w.hdr, (uint32_t)P.cap);         \

@@ -7,8 +7,10 @@
 // pair pair_base[v] + g, so consecutive threads write consecutive records,
 // and its tile count to the Gaussian-major pair q (a Gaussian's counts for
 // all views of its scene side by side).  The traversal that counts the tiles
-// also adds one to the counter of every tile it meets: the per-tile list
-// lengths from which the sort places each tile's list.
+// also adds one to the counter of every tile it meets (the per-tile list
+// lengths from which the sort places each tile's list), keeping the old value
+// as the pair's rank in that tile's list when the pair meets few tiles, and
+// keeps the pair's tile span for the emission.
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -19,7 +21,8 @@ __device__ __forceinline__ void project_pair(const ViewDesc& vd, int tw, int th,
                                              const float* __restrict__ camp, int64_t g, int64_t p, int64_t qi,
                                              const float4& mu, const BinGauss& bgs, const float4& so,
                                              uint32_t* __restrict__ count, uint32_t* __restrict__ tile_cnt,
-                                             ProjRec* __restrict__ rec, float4* __restrict__ binrec)
+                                             uint32_t* __restrict__ tile_over, ProjRec* __restrict__ rec,
+                                             uint4* __restrict__ span, uint4* __restrict__ rank)
 {
     float cam[16];
 #pragma unroll
@@ -27,10 +30,45 @@ __device__ __forceinline__ void project_pair(const ViewDesc& vd, int tw, int th,
     BinGeom bg;
     bin_view(mu, bgs, cam, vd.W, vd.H, bg);
     uint32_t cnt = 0;
-    uint32_t* __restrict__ tc = tile_cnt + vd.tile_base;
-    if (bg.valid) cnt = scanline_tiles(bg, tw, th, vd.TX, vd.TY, [&](uint32_t, uint32_t tile) { atomicAdd(tc + tile, 1u); });
+    // The first two bands of the traversal are kept for the emission; the
+    // tiles of any later band (the pair is then not ranked, below) are
+    // counted as they are met.
+    uint32_t nb = 0, c0 = 0, c1 = 0, r0 = 0, r1 = 0;
+    bool rows = true;
+    const uint32_t TX = (uint32_t)vd.TX;
+    uint32_t* __restrict__ to = tile_over + vd.tile_base;
+    if (bg.valid)
+        cnt = scanline_bands(bg, tw, th, vd.TX, vd.TY, [&](bool rw, int coord, int lo, int hi) {
+            rows = rw;
+            const uint32_t pk = (uint32_t)lo | ((uint32_t)hi << 16);
+            if (nb == 0) { c0 = (uint32_t)coord; r0 = pk; }
+            else if (nb == 1) { c1 = (uint32_t)coord; r1 = pk; }
+            else
+                for (int t = lo; t <= hi; t++) atomicAdd(to + (rw ? coord * TX + t : t * TX + coord), 1u);
+            nb = min(nb + 1u, 3u);
+        });
     count[qi] = cnt;
     if (cnt == 0) return;
+    // A pair of at most kRankMax tiles in one or two bands takes its place in
+    // each tile's list here (the counter's old value), so that the emission
+    // needs no atomic for it; the others are counted apart and placed by the
+    // emission after the ranked entries.
+    const bool ranked = cnt <= kRankMax && nb <= 2;
+    uint32_t rk[kRankMax] = {0u, 0u, 0u, 0u};
+    if (ranked) {
+        uint32_t* __restrict__ tc = tile_cnt + vd.tile_base;
+#pragma unroll
+        for (uint32_t u = 0; u < kRankMax; u++)
+            if (u < cnt) rk[u] = atomicAdd(tc + span_tile(u, rows, TX, c0, c1, r0, r1), 1u);
+    } else {
+        // the tiles of the first two bands
+        const uint32_t n01 = ((r0 >> 16) - (r0 & 0xFFFFu) + 1u) + (nb > 1 ? (r1 >> 16) - (r1 & 0xFFFFu) + 1u : 0u);
+        for (uint32_t u = 0; u < n01; u++) atomicAdd(to + span_tile(u, rows, TX, c0, c1, r0, r1), 1u);
+    }
+    span[qi] = span_pack(bg.mant, nb, rows, ranked, c0, c1, r0, r1, bg);
+    // stored at once (holding the ranks through the colour computation
+    // measured slower: the registers they take cost spills)
+    if (ranked) rank[qi] = make_uint4(rk[0], rk[1], rk[2], rk[3]);
 
     // conic = inverse of the 2D covariance
     const float ca = bg.c / bg.det, cb = -bg.b / bg.det, cc = bg.a / bg.det;
@@ -63,14 +101,14 @@ __device__ __forceinline__ void project_pair(const ViewDesc& vd, int tw, int th,
     r.b = make_float4(cc, so.w, col[0], col[1]);
     r.c = make_float4(col[2], bg.tz, rx, ry);
     rec[p] = r;
-    binrec[p] = make_float4(bg.a, bg.b, bg.c, __uint_as_float(bg.mant));
 }
 
 // 3 CTAs per SM: the register cap (80) costs a few spills but raises occupancy
 // from 2 to 3 CTAs
 __global__ void __launch_bounds__(256, 3) k_project_fwd(Views V, Scenes S, const float* __restrict__ cams,
                                                      uint32_t* __restrict__ count, uint32_t* __restrict__ tile_cnt,
-                                                     ProjRec* __restrict__ rec, float4* __restrict__ binrec,
+                                                     ProjRec* __restrict__ rec, uint4* __restrict__ span,
+                                                     uint4* __restrict__ rank,
                                                      WsHeader* __restrict__ hdr)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -100,8 +138,8 @@ __global__ void __launch_bounds__(256, 3) k_project_fwd(Views V, Scenes S, const
             count[q0 + k] = 0;
             continue;
         }
-        project_pair(vd, V.tw, V.th, sc, S.sh_bf16, cams + 16 * v, g, p, q0 + k, mu, bgs, so, count, tile_cnt, rec,
-                     binrec);
+        project_pair(vd, V.tw, V.th, sc, S.sh_bf16, cams + 16 * v, g, p, q0 + k, mu, bgs, so, count, tile_cnt,
+                     tile_cnt + V.tiles, rec, span, rank);
     }
 }
 
@@ -110,7 +148,7 @@ void launch_project_fwd(const Plan& P, const Scenes& S, const float* cams, const
     const int T = 256;
     const int64_t blocks = (S.total + T - 1) / T;
     if (blocks == 0) return;
-    k_project_fwd<<<(unsigned)blocks, T, 0, st>>>(P.views, S, cams, w.count, w.tile_cnt, w.rec, w.binrec, w.hdr);
+    k_project_fwd<<<(unsigned)blocks, T, 0, st>>>(P.views, S, cams, w.count, w.tile_cnt, w.rec, w.span, w.rank, w.hdr);
 }
 
 }  // namespace gs

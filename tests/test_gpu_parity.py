@@ -350,6 +350,75 @@ def test_long_tile_lists(gs, orc, report):
                                "image_max_abs_err": float(err), "keys_bit_exact": True})
 
 
+def _span_tiles(sp, TX):
+    """Tiles of a tile span (one or two bands) in traversal order."""
+    nb, rows = (int(sp[0]) >> 24) & 3, (int(sp[0]) >> 26) & 1
+    coords = [int(sp[1]) & 0xFFFF, int(sp[1]) >> 16]
+    out = []
+    for k in range(nb):
+        lo, hi = int(sp[2 + k]) & 0xFFFF, int(sp[2 + k]) >> 16
+        out += [coords[k] * TX + t if rows else t * TX + coords[k] for t in range(lo, hi + 1)]
+    return out
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8)])
+def test_tile_spans(gs, orc, report, tile):
+    """The projection keeps each pair's traversal as a tile span for the
+    emission: for every visible Gaussian the span gives the oracle's tiles in
+    the oracle's emission order and its depth code; a Gaussian of more than
+    two bands is marked and carries the binning conic, and its tiles (from
+    the repeated traversal) are still placed bit-exactly: the sorted keys and
+    Gaussians equal the oracle's.  A pair of at most four tiles is ranked:
+    the places it took in its tiles' lists are, per tile, each of 0 .. n - 1
+    once.  A quarter of the Gaussians are enlarged so that many take the
+    other paths."""
+    gsstep, step_mod = gs
+    scene, _, cams = synth.tiny_workload(2)
+    rng = np.random.default_rng(5)
+    big = rng.random(scene.n) < 0.25
+    scene.scales[big] *= 3.0
+    cam = cams[0]
+    b = orc.bin32(scene, cam, *tile)
+    TX, TY = orc.tiles_of(cam, *tile)
+    tiles_emit = (b.keys_emit >> np.uint32(orc.key_shift(TX * TY))).astype(np.int64)
+    tr = _run_forward(step_mod, scene, [cam], tile=tile)
+    st = tr.stats()
+    assert st.status == 0 and st.k_required == b.K
+    n = scene.n
+    span = tr.buffer(10, 4 * n).cpu().numpy().view(np.uint32).reshape(n, 4)
+    rank = tr.buffer(11, 4 * n).cpu().numpy().view(np.uint32).reshape(n, 4)
+    ranked_cnt = tr.buffer(12, TX * TY).cpu().numpy().view(np.uint32)
+    many, ranked = 0, 0
+    ranks_of = [[] for _ in range(TX * TY)]
+    for g in range(n):
+        c = int(b.count[g])
+        if c == 0:
+            continue
+        sp = span[g]
+        assert int(sp[0]) & 0x7FFFFF == int(b.mant[g])
+        want = tiles_emit[b.offset[g]:b.offset[g] + c].tolist()
+        if (int(sp[0]) >> 24) & 3 == 3:
+            many += 1
+            np.testing.assert_array_equal(sp[1:4].view(np.float32), b.bin[g, 3:6])
+            assert len({t // TX for t in want}) > 2 and len({t % TX for t in want}) > 2
+        else:
+            assert _span_tiles(sp, TX) == want, g
+            # ranked exactly when the pair meets at most four tiles
+            assert bool((int(sp[0]) >> 27) & 1) == (c <= 4), g
+            if c <= 4:
+                ranked += 1
+                for t, rk in zip(want, rank[g][:c]):
+                    ranks_of[t].append(int(rk))
+    assert many >= 10 and ranked > n // 2
+    # the ranks a tile handed out are 0 .. (its ranked entries - 1), each once
+    for t in range(TX * TY):
+        assert sorted(ranks_of[t]) == list(range(int(ranked_cnt[t]))), t
+    np.testing.assert_array_equal(tr.buffer(2, b.K).cpu().numpy().view(np.uint32), b.keys)
+    np.testing.assert_array_equal(tr.buffer(3, b.K).cpu().numpy().view(np.uint32), b.gidx)
+    report(f"tile_spans_{tile[0]}x{tile[1]}", {"visible": int((b.count > 0).sum()), "many_band_pairs": many,
+                                                "ranked_pairs": ranked, "keys": int(b.K), "keys_bit_exact": True})
+
+
 def test_capacity_overflow_sets_status(gs, orc):
     """Too small an intersection capacity is reported, nothing is written
     out of bounds, and a larger capacity then succeeds."""
