@@ -681,8 +681,9 @@ def stage_rooflines(work, stage_ms, hbm_peak_gbs, alu_peak_tflops):
 def launches_per_step(plan) -> int:
     """Kernels of this library launched by one step (see the launchers)."""
     project = 2                                        # header reset + projection
-    binsort = 3 + 1 + 3 + 1 + 1 + 1 + 2                # count scan, finalize, tile scan, ranges, order, emit,
-                                                       # sort (long and short lists)
+    binsort = 3 + 3 + 1 + 1 + 2                        # count scan (with K and the capacity check), tile scan
+                                                       # (with the ranges), order, emit, sort (long and short
+                                                       # lists)
     return project + binsort + 1 + 1 + 1 + 1 + 1       # raster fwd, loss, raster bwd, proj bwd+adam, advance
 
 

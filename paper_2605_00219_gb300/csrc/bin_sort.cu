@@ -77,20 +77,11 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* warp_s
     return before + x - v;
 }
 
-// Effective scan length: n, or (*nb) * mul when the length is known only on
-// the device (the radix histograms: 256 digits x blocks holding keys).
-__device__ __forceinline__ int64_t scan_len(int64_t n, const uint32_t* nb, int mul)
-{
-    return nb ? min(n, (int64_t)(*nb) * mul) : n;
-}
-
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ in,
-                                                               const uint32_t* __restrict__ in2, int64_t n_max,
-                                                               const uint32_t* __restrict__ nb, int mul,
+                                                               const uint32_t* __restrict__ in2, int64_t n,
                                                                uint32_t* __restrict__ part)
 {
     __shared__ uint32_t ws[32];
-    const int64_t n = scan_len(n_max, nb, mul);
     const int64_t base = (int64_t)blockIdx.x * kScanBlock;
     uint32_t s = 0;
 #pragma unroll
@@ -103,8 +94,14 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __
     if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
-// Single block: exclusive scan of the block sums in place; grand total at part[nparts].
-__global__ void __launch_bounds__(1024) k_scan_part(uint32_t* __restrict__ part, int64_t nparts)
+// Single block: exclusive scan of the block sums in place; grand total at
+// part[nparts].  With total_at (the scan of the pair counts; hdr then not
+// null): the total is K, also written to total_at (the offsets' last entry),
+// and the capacity check sets k_eff = K when it fits, else 0 (nothing is
+// emitted) with GS_STATUS_CAPACITY.
+__global__ void __launch_bounds__(1024) k_scan_part(uint32_t* __restrict__ part, int64_t nparts,
+                                                    WsHeader* __restrict__ hdr, uint32_t* __restrict__ total_at,
+                                                    uint32_t cap)
 {
     __shared__ uint32_t ws[32];
     uint32_t carry = 0;
@@ -117,16 +114,31 @@ __global__ void __launch_bounds__(1024) k_scan_part(uint32_t* __restrict__ part,
         carry += tot;
         __syncthreads();
     }
-    if (threadIdx.x == 0) part[nparts] = carry;
+    if (threadIdx.x == 0) {
+        part[nparts] = carry;
+        if (total_at) {
+            hdr->k_required = carry;
+            hdr->k_eff = carry <= cap ? carry : 0u;
+            if (carry > cap) atomicOr(&hdr->status, GS_STATUS_CAPACITY);
+            *total_at = carry;
+        }
+    }
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* in, const uint32_t* in2, int64_t n_max,
-                                                             const uint32_t* __restrict__ nb, int mul,
-                                                             const uint32_t* __restrict__ part, uint32_t* out)
+// Down-sweep: out[i] = exclusive prefix of in[i] (+ in2[i]).  With ranges
+// (the scan of the tile counters, in = entries of ranked pairs, in2 = the
+// others' entries; hdr then not null, its K already set): also each tile's
+// range [start, start + both counts) --
+// [0, 0) when empty, and every range empty when K exceeds the capacity --
+// and the cursor for the other pairs' entries, start + the ranked entries,
+// written over in2 (cur2, the same array).
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* in, const uint32_t* in2, int64_t n,
+                                                             const uint32_t* __restrict__ part, uint32_t* out,
+                                                             uint2* __restrict__ ranges, uint32_t* cur2,
+                                                             const WsHeader* __restrict__ hdr)
 {
     __shared__ uint32_t buf[kScanBlock];
     __shared__ uint32_t ws[32];
-    const int64_t n = scan_len(n_max, nb, mul);
     const int64_t base = (int64_t)blockIdx.x * kScanBlock;
     if (base >= n) return;
 #pragma unroll
@@ -143,6 +155,12 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* in, 
         s += buf[threadIdx.x * kScanItems + i];
     }
     uint32_t ex = block_excl_scan<kScanThreads>(s, ws, nullptr) + part[blockIdx.x];
+    // (the list lengths are read back before the prefixes replace them)
+    uint32_t len[kScanItems];
+    if (ranges) {
+#pragma unroll
+        for (int i = 0; i < kScanItems; i++) len[i] = buf[threadIdx.x * kScanItems + i];
+    }
 #pragma unroll
     for (int i = 0; i < kScanItems; i++) buf[threadIdx.x * kScanItems + i] = ex + loc[i];
     __syncthreads();
@@ -151,57 +169,49 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* in, 
         int64_t idx = base + i * kScanThreads + threadIdx.x;
         if (idx < n) out[idx] = buf[i * kScanThreads + threadIdx.x];
     }
+    if (ranges) {
+        const bool fits = hdr->k_eff == hdr->k_required;
+#pragma unroll
+        for (int i = 0; i < kScanItems; i++) {
+            const int64_t idx = base + threadIdx.x * kScanItems + i;
+            if (idx < n) {
+                const uint32_t s0 = ex + loc[i], c = len[i];
+                ranges[idx] = fits && c ? make_uint2(s0, s0 + c) : make_uint2(0u, 0u);
+                cur2[idx] = s0 + in[idx];
+            }
+        }
+    }
 }
 
-static void scan_u32_dyn(const uint32_t* in, const uint32_t* in2, uint32_t* out, int64_t n_max, const uint32_t* nb,
-                         int mul, uint32_t* part, cudaStream_t st)
+static void scan_launch(const uint32_t* in, const uint32_t* in2, uint32_t* out, int64_t n, uint32_t* part,
+                        WsHeader* hdr, uint32_t* total_at, uint32_t cap, uint2* ranges, uint32_t* cur2,
+                        cudaStream_t st)
 {
-    const int64_t nparts = (n_max + kScanBlock - 1) / kScanBlock;
-    k_scan_reduce<<<(unsigned)nparts, kScanThreads, 0, st>>>(in, in2, n_max, nb, mul, part);
-    k_scan_part<<<1, 1024, 0, st>>>(part, nparts);
-    k_scan_down<<<(unsigned)nparts, kScanThreads, 0, st>>>(in, in2, n_max, nb, mul, part, out);
+    const int64_t nparts = (n + kScanBlock - 1) / kScanBlock;
+    k_scan_reduce<<<(unsigned)nparts, kScanThreads, 0, st>>>(in, in2, n, part);
+    k_scan_part<<<1, 1024, 0, st>>>(part, nparts, hdr, total_at, cap);
+    k_scan_down<<<(unsigned)nparts, kScanThreads, 0, st>>>(in, in2, n, part, out, ranges, cur2, hdr);
+}
+
+// Offsets of the pair counts, K and the capacity check.
+static void scan_pair_counts(const Plan& P, const WsPtrs& w, cudaStream_t st)
+{
+    scan_launch(w.count, nullptr, w.offset, P.views.pairs, w.scan_part, w.hdr, w.offset + P.views.pairs,
+                (uint32_t)P.cap, nullptr, nullptr, st);
+}
+
+// Tile starts, ranges and the other pairs' cursors from the two tile
+// counters (after scan_pair_counts: the ranges read K and k_eff).
+static void scan_tile_counts(const Plan& P, const WsPtrs& w, cudaStream_t st)
+{
+    const int64_t tiles = P.views.tiles;
+    scan_launch(w.tile_cnt, w.tile_cnt + tiles, w.tile_cur, tiles, w.scan_part, w.hdr, nullptr, 0u, w.ranges,
+                w.tile_cnt + tiles, st);
 }
 
 void scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* part, cudaStream_t st)
 {
-    scan_u32_dyn(in, nullptr, out, n, nullptr, 1, part, st);
-}
-
-// Exclusive scan of in[i] + in2[i].
-static void scan_u32_sum2(const uint32_t* in, const uint32_t* in2, uint32_t* out, int64_t n, uint32_t* part,
-                          cudaStream_t st)
-{
-    scan_u32_dyn(in, in2, out, n, nullptr, 1, part, st);
-}
-
-// Total and capacity check after the count scan: k_eff = K when it fits the
-// capacity, else 0 (nothing is emitted).
-__global__ void k_count_finalize(const uint32_t* __restrict__ part, int64_t nparts, int64_t pairs,
-                                 uint32_t* __restrict__ offset, WsHeader* __restrict__ hdr, uint32_t cap)
-{
-    if (threadIdx.x == 0) {
-        const uint32_t total = part[nparts];
-        hdr->k_required = total;
-        hdr->k_eff = total <= cap ? total : 0u;
-        if (total > cap) atomicOr(&hdr->status, GS_STATUS_CAPACITY);
-        offset[pairs] = total;
-    }
-}
-
-// Tile ranges from the scanned tile counts: a tile's list holds first the
-// entries of ranked pairs (at their ranks), then the others, placed by a
-// cursor that starts after the ranked ones (it replaces the overflow count).
-// An empty list is [0, 0), and every list is empty when K exceeds the
-// capacity.
-__global__ void k_tile_setup(int64_t tiles, uint32_t* __restrict__ tile_cnt, const uint32_t* __restrict__ tile_start,
-                             const WsHeader* __restrict__ hdr, uint2* __restrict__ ranges)
-{
-    const bool fits = hdr->k_eff == hdr->k_required;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tiles; t += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t s0 = tile_start[t], cr = tile_cnt[t], c = cr + tile_cnt[tiles + t];
-        ranges[t] = fits && c ? make_uint2(s0, s0 + c) : make_uint2(0u, 0u);
-        tile_cnt[tiles + t] = s0 + cr;
-    }
+    scan_launch(in, nullptr, out, n, part, nullptr, nullptr, 0u, nullptr, nullptr, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -587,15 +597,10 @@ void launch_bin_sort(const Plan& P, const WsPtrs& w, cudaStream_t st)
 {
     const Views& V = P.views;
     const uint32_t cap = (uint32_t)P.cap;
-    // index offset (Gaussian-major pair order)
-    scan_u32(w.count, w.offset, V.pairs, w.scan_part, st);
-    k_count_finalize<<<1, 32, 0, st>>>(w.scan_part, P.count_scan_parts, V.pairs, w.offset, w.hdr, cap);
-    // tile ranges and scatter cursors from the per-tile counts
-    scan_u32_sum2(w.tile_cnt, w.tile_cnt + V.tiles, w.tile_cur, V.tiles, w.scan_part, st);
-    {
-        const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((V.tiles + 255) / 256, (int64_t)P.sm_count * 8));
-        k_tile_setup<<<(unsigned)blocks, 256, 0, st>>>(V.tiles, w.tile_cnt, w.tile_cur, w.hdr, w.ranges);
-    }
+    // index offset (Gaussian-major pair order), K and the capacity check
+    scan_pair_counts(P, w, st);
+    // tile starts, ranges and the other pairs' cursors from the tile counters
+    scan_tile_counts(P, w, st);
     k_tile_order<<<1, 1024, 0, st>>>(V.tiles, w.ranges, w.tile_order);
     // generate keys into the tile buckets
     {

@@ -2,7 +2,7 @@
 
 - The launch count that bench.py claims per step equals the count in the ncu
   launch list of the 4 x 1920x1080 workload at 16x16 tiles (one graph-replayed
-  step launches 19 kernels of this library), whatever the views.
+  step launches 17 kernels of this library), whatever the views.
 - The compile-time window taps of the L1 + SSIM kernel are the oracle's
   normalised Gaussian window (11 taps, sigma 1.5) rounded to FP32.
 - The algorithmic work per stage behind the bench's rooflines, and the
@@ -24,12 +24,12 @@ def _plan(views, tile=(16, 16)):
 
 
 def test_launch_count_matches_the_measured_launch_list():
-    assert bench.launches_per_step(_plan([(1920, 1080)] * 4)) == 19
+    assert bench.launches_per_step(_plan([(1920, 1080)] * 4)) == 17
 
 
 def test_launch_count_does_not_depend_on_the_views():
-    assert bench.launches_per_step(_plan([(1920, 1080)])) == 19
-    assert bench.launches_per_step(_plan([(64, 64)] * 16, tile=(8, 8))) == 19
+    assert bench.launches_per_step(_plan([(1920, 1080)])) == 17
+    assert bench.launches_per_step(_plan([(64, 64)] * 16, tile=(8, 8))) == 17
 
 
 def test_ssim_window_constants_are_the_oracle_window_in_fp32(orc):
