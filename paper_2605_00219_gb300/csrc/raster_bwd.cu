@@ -532,40 +532,37 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
                 const float dx = pix_offset(fx, a.x, ml.x);
 #pragma unroll
                 for (int k = 0; k < PPT; k++) {
-                    if (bb + j < (int)nl[k]) {
-                        const float dy = pix_offset(fy[k], a.y, ml.y);
-                        const float p2 = pair_power2(dx, dy, a.z, a.w, b.x);
-                        if (p2 >= kPow2Min) {
-                            const float G = ex2_approx(p2);
-                            const float araw = __fmul_rn(b.y, G);
-                            const float alpha = fminf(kAlphaMax, araw);
-                            if (alpha >= kAlphaMin) {
-                                hit = true;
-                                const float cb = cD[j].w;
-                                // compensated T before this entry
-                                const float rom = div_one_minus(alpha, Th[k], Tl[k]);
-                                const float wgt = alpha * Th[k];
-                                g[6] = fmaf(wgt, d0[k], g[6]);
-                                g[7] = fmaf(wgt, d1[k], g[7]);
-                                g[8] = fmaf(wgt, d2[k], g[8]);
-                                const float dcol = fmaf(d0[k], b.z, fmaf(d1[k], b.w, d2[k] * cb));
-                                const float da = fmaf(Th[k], dcol, -U[k] * rom);
-                                U[k] = fmaf(wgt, dcol, U[k]);
-                                if (araw <= kAlphaMax) {
-                                    // moments of dp = dL/dpower; the conic
-                                    // and the constant factors are applied
-                                    // per entry after the reduction
-                                    g[5] = fmaf(da, G, g[5]);
-                                    const float dp = da * araw;
-                                    const float xdp = dx * dp, ydp = dy * dp;
-                                    g[0] += xdp;
-                                    g[1] += ydp;
-                                    g[2] = fmaf(dx, xdp, g[2]);
-                                    g[3] = fmaf(dx, ydp, g[3]);
-                                    g[4] = fmaf(dy, ydp, g[4]);
-                                }
-                            }
-                        }
+                    const float dy = pix_offset(fy[k], a.y, ml.y);
+                    const float p2 = pair_power2(dx, dy, a.z, a.w, b.x);
+                    const float G = ex2_approx(p2);
+                    const float araw = __fmul_rn(b.y, G);
+                    const float alpha = fminf(kAlphaMax, araw);
+                    // one test for the pixel's three skips (exp2 taken for
+                    // every pixel): no nested divergent branches
+                    if (bb + j < (int)nl[k] && p2 >= kPow2Min && alpha >= kAlphaMin) {
+                        hit = true;
+                        const float cb = cD[j].w;
+                        // compensated T before this entry
+                        const float rom = div_one_minus(alpha, Th[k], Tl[k]);
+                        const float wgt = alpha * Th[k];
+                        g[6] = fmaf(wgt, d0[k], g[6]);
+                        g[7] = fmaf(wgt, d1[k], g[7]);
+                        g[8] = fmaf(wgt, d2[k], g[8]);
+                        const float dcol = fmaf(d0[k], b.z, fmaf(d1[k], b.w, d2[k] * cb));
+                        const float da = fmaf(Th[k], dcol, -U[k] * rom);
+                        U[k] = fmaf(wgt, dcol, U[k]);
+                        // moments of dp = dL/dpower (zero where the 0.99
+                        // clamp holds); the conic and the constant factors
+                        // are applied per entry after the reduction
+                        const float dam = araw <= kAlphaMax ? da : 0.f;
+                        g[5] = fmaf(dam, G, g[5]);
+                        const float dp = dam * araw;
+                        const float xdp = dx * dp, ydp = dy * dp;
+                        g[0] += xdp;
+                        g[1] += ydp;
+                        g[2] = fmaf(dx, xdp, g[2]);
+                        g[3] = fmaf(dx, ydp, g[3]);
+                        g[4] = fmaf(dy, ydp, g[4]);
                     }
                 }
                 // every visiting warp fills its slot (zeros when none of its
@@ -576,27 +573,29 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
             }
         }
         __syncthreads();
-        // add the warps' partial sums in warp order; write each entry's
-        // record.  Slots 0-4 hold sums of dp (dx, dy, dx^2, dx dy, dy^2):
-        // dL/dmean = conic (sum dx dp, sum dy dp) and dL/dconic =
+        // one thread per entry adds the visiting warps' partial sums in warp
+        // order and writes the entry's record (two 16-byte stores and one
+        // 4-byte store).  Slots 0-4 hold sums of dp (dx, dy, dx^2, dx dy,
+        // dy^2): dL/dmean = conic (sum dx dp, sum dy dp) and dL/dconic =
         // -(sum dx^2 dp / 2, sum dx dy dp, sum dy^2 dp / 2).
-        for (int t = tid; t < cnt * 9; t += BS) {
-            const int j = t / 9, comp = t - 9 * j;
-            const int comp2 = comp < 2 ? comp ^ 1 : comp;
-            float s = 0.f, s2 = 0.f;
+        for (int j = tid; j < cnt; j += BS) {
+            float sm[9];
+#pragma unroll
+            for (int c = 0; c < 9; c++) sm[c] = 0.f;
             for (uint32_t m = sM[cur][j]; m; m &= m - 1u) {     // visiting warps, in warp order
                 const int i = __ffs(m) - 1;
-                s += part[i][j][comp];
-                s2 += part[i][j][comp2];
+#pragma unroll
+                for (int c = 0; c < 9; c++) sm[c] += part[i][j][c];
             }
-            float out = s;
-            if (comp < 2) {
-                const float4 cd = sD[cur][j];
-                out = comp == 0 ? fmaf(cd.x, s, cd.y * s2) : fmaf(cd.y, s2, cd.z * s);
-            } else if (comp < 5) {
-                out = comp == 3 ? -s : -0.5f * s;
+            const float4 cd = sD[cur][j];
+            const uint32_t e = sE[cur][j];
+            if (GS_DCHECK(e < cap, status)) {
+                float4* o = reinterpret_cast<float4*>(gradrec + e);
+                o[0] = make_float4(fmaf(cd.x, sm[0], cd.y * sm[1]), fmaf(cd.y, sm[0], cd.z * sm[1]), -0.5f * sm[2],
+                                   -sm[3]);
+                o[1] = make_float4(-0.5f * sm[4], sm[5], sm[6], sm[7]);
+                reinterpret_cast<float*>(o + 2)[0] = sm[8];
             }
-            if (GS_DCHECK(sE[cur][j] < cap, status)) reinterpret_cast<float*>(gradrec + sE[cur][j])[comp] = out;
         }
         if (bb > 0) {
 #pragma unroll

@@ -83,10 +83,10 @@ __global__ void __launch_bounds__(BS, (BS == 256 ? 6 : 1)) k_raster_fwd(Views V,
                 const float dx = pix_offset(fx, a.x, cl.y), dy = pix_offset(fy, a.y, cl.z);
                 const float4 b = cB[j];
                 const float p2 = pair_power2(dx, dy, a.z, a.w, b.x);
-                if (p2 < kPow2Min) continue;
+                // one test for both skips (exp2 taken for every pair)
                 const float G = ex2_approx(p2);
                 const float alpha = fminf(kAlphaMax, __fmul_rn(b.y, G));
-                if (alpha < kAlphaMin) continue;
+                if (!(p2 >= kPow2Min && alpha >= kAlphaMin)) continue;
                 // compensated T * (1 - alpha); the pair is carried without
                 // renormalising (Th the rounded product, Tl its low part),
                 // and the stop test takes their sum
