@@ -255,10 +255,17 @@ __device__ __forceinline__ void bin_gauss(float4 q, float4 s, BinGauss& o)
     o.valid = 1;
 }
 
+// Field-of-view clamp limits of a view, 1.3 x the half extent in normalised
+// image coordinates: (1.3 (W/2) / fx, 1.3 (H/2) / fy).
+__device__ __forceinline__ float2 fov_limits(const float* cam, int W, int H)
+{
+    return make_float2(FM(1.3f, FD(FM(0.5f, (float)W), cam[12])), FM(1.3f, FD(FM(0.5f, (float)H), cam[13])));
+}
+
 // View-dependent part: camera transform, near-plane cull, EWA covariance
-// with the field-of-view clamp, conic determinant, pixel mean and depth
-// code, from the view-independent part.
-__device__ __forceinline__ void bin_view(float4 mu, const BinGauss& bgs, const float* cam, int W, int H, BinGeom& o)
+// with the field-of-view clamp (lim = fov_limits of the view), conic
+// determinant, pixel mean and depth code, from the view-independent part.
+__device__ __forceinline__ void bin_view(float4 mu, const BinGauss& bgs, const float* cam, float2 lim, BinGeom& o)
 {
     o.valid = 0;
     if (!bgs.valid) return;
@@ -272,8 +279,7 @@ __device__ __forceinline__ void bin_view(float4 mu, const BinGauss& bgs, const f
         t[i] = FA(FA(FA(FM(C[3 * i], mv[0]), FM(C[3 * i + 1], mv[1])), FM(C[3 * i + 2], mv[2])), cam[9 + i]);
     if (!(t[2] >= 0.01f)) return;
     const float fx = cam[12], fy = cam[13], cx = cam[14], cy = cam[15];
-    float limx = FM(1.3f, FD(FM(0.5f, (float)W), fx));
-    float limy = FM(1.3f, FD(FM(0.5f, (float)H), fy));
+    const float limx = lim.x, limy = lim.y;
     float ux = fminf(fmaxf(FD(t[0], t[2]), -limx), limx);
     float uy = fminf(fmaxf(FD(t[1], t[2]), -limy), limy);
     float j00 = FD(fx, t[2]), j11 = FD(fy, t[2]);
@@ -306,9 +312,15 @@ __device__ __forceinline__ void bin_view(float4 mu, const BinGauss& bgs, const f
     o.mx = mx; o.my = my; o.a = a; o.b = b; o.c = c; o.det = det; o.tz = t[2]; o.mant = mant; o.r2 = r2;
 }
 
+// 1/T for a power of two T (exponent arithmetic: exact).
+__device__ __forceinline__ float inv_pow2(int T) { return __int_as_float(0x7F000000 - __float_as_int((float)T)); }
+
+// Tile index bounds of a pixel-centre coordinate: the tile sizes are powers
+// of two (8, 16, 32), so the correctly rounded division by T equals the
+// product with the exact reciprocal 1/T, bit for bit.
 __device__ __forceinline__ int tile_lo(float v, int T, int n)
 {
-    float f = ceilf(FD(FS(FA(v, 0.5f), (float)T), (float)T));
+    float f = ceilf(FM(FS(FA(v, 0.5f), (float)T), inv_pow2(T)));
     f = fminf(fmaxf(f, -1.0f), (float)n);
     int i = (int)f;
     return i < 0 ? 0 : i;
@@ -316,7 +328,7 @@ __device__ __forceinline__ int tile_lo(float v, int T, int n)
 
 __device__ __forceinline__ int tile_hi(float v, int T, int n)
 {
-    float f = floorf(FD(FS(v, 0.5f), (float)T));
+    float f = floorf(FM(FS(v, 0.5f), inv_pow2(T)));
     f = fminf(fmaxf(f, -1.0f), (float)n);
     int i = (int)f;
     return i > n - 1 ? n - 1 : i;
@@ -536,12 +548,14 @@ __device__ __forceinline__ void accurate_mean2d(const float* cam, float4 mu, flo
         th[i] = s3;
         tl[i] = ((e[0] + e[1]) + (e[2] + e1)) + (e2 + e3);
     }
+    // the low-order correction needs no correctly rounded division
+    const float itz = __fdividef(1.0f, th[2]);
 #pragma unroll
     for (int k = 0; k < 2; k++) {
         const float f = cam[12 + k], c = cam[14 + k];
         const float q = __fdiv_rn(th[k], th[2]);
         const float rem = __fmaf_rn(-q, th[2], th[k]);                   // exact
-        const float ql = (rem + tl[k] - q * tl[2]) / th[2];
+        const float ql = (rem + tl[k] - q * tl[2]) * itz;
         const float p = __fmul_rn(f, q);
         const float pe = __fmaf_rn(f, q, -p);
         float s, se;

@@ -18,7 +18,8 @@ namespace gs {
 // One (view, Gaussian) pair: tile count, and for a pair that meets a tile its
 // projected record and binning geometry.
 __device__ __forceinline__ void project_pair(const ViewDesc& vd, int tw, int th, const SceneDesc& sc, int sh_bf16,
-                                             const float* __restrict__ camp, int64_t g, int64_t p, int64_t qi,
+                                             const float* __restrict__ camp, float2 lim, int64_t g, int64_t p,
+                                             int64_t qi,
                                              const float4& mu, const BinGauss& bgs, const float4& so,
                                              uint32_t* __restrict__ count, uint32_t* __restrict__ tile_cnt,
                                              uint32_t* __restrict__ tile_over, ProjRec* __restrict__ rec,
@@ -28,7 +29,7 @@ __device__ __forceinline__ void project_pair(const ViewDesc& vd, int tw, int th,
 #pragma unroll
     for (int i = 0; i < 16; i++) cam[i] = __ldg(camp + i);
     BinGeom bg;
-    bin_view(mu, bgs, cam, vd.W, vd.H, bg);
+    bin_view(mu, bgs, cam, lim, bg);
     uint32_t cnt = 0;
     // The first two bands of the traversal are kept for the emission; the
     // tiles of any later band (the pair is then not ranked, below) are
@@ -70,8 +71,10 @@ __device__ __forceinline__ void project_pair(const ViewDesc& vd, int tw, int th,
     // measured slower: the registers they take cost spills)
     if (ranked) rank[qi] = make_uint4(rk[0], rk[1], rk[2], rk[3]);
 
-    // conic = inverse of the 2D covariance
-    const float ca = bg.c / bg.det, cb = -bg.b / bg.det, cc = bg.a / bg.det;
+    // conic = inverse of the 2D covariance (one hardware reciprocal of the
+    // determinant, det >= 0.09 by the low-pass: a few ulp)
+    const float idet = __fdividef(1.0f, bg.det);
+    const float ca = bg.c * idet, cb = -bg.b * idet, cc = bg.a * idet;
 
     // colour from degree-3 SH at the view direction (mu - camera centre)
     const float cpx = -(cam[0] * cam[9] + cam[3] * cam[10] + cam[6] * cam[11]);
@@ -111,6 +114,11 @@ __global__ void __launch_bounds__(256, 3) k_project_fwd(Views V, Scenes S, const
                                                      uint4* __restrict__ rank,
                                                      WsHeader* __restrict__ hdr)
 {
+    // the views' field-of-view limits, once per block (two correctly
+    // rounded divisions a view instead of a pair)
+    __shared__ float2 slim[kMaxViews];
+    for (int v = threadIdx.x; v < V.n; v += blockDim.x) slim[v] = fov_limits(cams + 16 * v, V.v[v].W, V.v[v].H);
+    __syncthreads();
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= S.total) return;
     int s = 0;
@@ -138,8 +146,8 @@ __global__ void __launch_bounds__(256, 3) k_project_fwd(Views V, Scenes S, const
             count[q0 + k] = 0;
             continue;
         }
-        project_pair(vd, V.tw, V.th, sc, S.sh_bf16, cams + 16 * v, g, p, q0 + k, mu, bgs, so, count, tile_cnt,
-                     tile_cnt + V.tiles, rec, span, rank);
+        project_pair(vd, V.tw, V.th, sc, S.sh_bf16, cams + 16 * v, slim[v], g, p, q0 + k, mu, bgs, so, count,
+                     tile_cnt, tile_cnt + V.tiles, rec, span, rank);
     }
 }
 
