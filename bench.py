@@ -60,14 +60,14 @@ LR = (1.6e-4 * 30.0, 1e-3, 5e-3, 5e-2, 2.5e-3, 2.5e-3 / 20)   # mean lr scaled b
 # 4 x 1920x1080, 16x16 tiles, pixel-parallel raster backward).  Valid only
 # while the kernel sources hash to the recorded prefixes.
 MEASURED_TRAFFIC = {
-    "raster_bwd": (3637729536, {"raster_bwd.cu": "4e93ffce6fe0f042"}),
-    "project_bwd_adam": (3304814080, {"project_bwd_adam.cu": "542274191b8e2688"}),
-    "raster_fwd": (1685828096, {"raster_fwd.cu": "eb796557894a3910"}),
-    "project_fwd": (1259325184, {"project_fwd.cu": "1653c497900428cc"}),
-    "bin_sort": (3072882176, {"bin_sort.cu": "49d33c937ce3d28f"}),
-    "loss_l1": (266700800, {"raster_fwd.cu": "eb796557894a3910"}),
+    "raster_bwd": (3727156992, {"raster_bwd.cu": "6964d93683e553e9"}),
+    "project_bwd_adam": (3289885440, {"project_bwd_adam.cu": "9b1e90f515cd9a35"}),
+    "raster_fwd": (1711139072, {"raster_fwd.cu": "176a800dd0210d02"}),
+    "project_fwd": (1629572352, {"project_fwd.cu": "7a785eba31c6a4ab"}),
+    "bin_sort": (1480387840, {"bin_sort.cu": "9971f99c8326e6c5"}),
+    "loss_l1": (266740480, {"raster_fwd.cu": "176a800dd0210d02"}),
 }
-TRAFFIC_COMMON = {"gs_device.cuh": "aaffbe874e2f2481", "gs_internal.cuh": "9999e81ae0e203c9"}
+TRAFFIC_COMMON = {"gs_device.cuh": "0296c783b4672796", "gs_internal.cuh": "940fd77223c88071"}
 
 
 def _measured_traffic(kernel: str, headline: bool):
@@ -533,7 +533,7 @@ def main():
                       int(tr.plan.tiles), sh16, args.loss)
     rooflines = stage_rooflines(work, acc, hbm_peak, alu_peak)
     headline = (args.workload == "batched" and args.n == N_GAUSS and tuple(tile) == (16, 16) and impl == 0
-                and tpt == 256
+                and tpt == 128
                 and args.loss == "l1")
     for k, r in rooflines.items():
         r["traffic"] = _measured_traffic(k, headline)
@@ -637,12 +637,11 @@ def stage_work(scene_sizes, view_scenes, K, evaluated, blended, px, tiles, sh16,
     # each pair's count and offset
     adam_bytes = n * (752 if sh16 else 1416) + K * 36 + pairs * 8
     # sort: the count scan (4 B in, 4 B out per pair), emission (count and
-    # offset read per pair, key and value written per intersection), one key
-    # and value read and written per radix pass (4 digit passes of the 32-bit
-    # key, one more ordering the views when there are several), the ranges
-    # (one key read per intersection, 8 B written per tile)
-    npass = 4 + (1 if len(view_scenes) > 1 else 0)
-    sort_bytes = pairs * 8 + pairs * 8 + K * 8 + npass * K * 16 + K * 4 + tiles * 8
+    # offset read per pair), and the floor for sorting: one 8-byte key and
+    # value written and read once per intersection; 8 B of range per tile.
+    # The buckets, the per-tile merge passes and the pair gathers of this
+    # implementation are not counted.
+    sort_bytes = pairs * 16 + K * 16 + tiles * 8
     work = {
         "project_bwd_adam": ("hbm", adam_bytes),
         "project_fwd": ("hbm", fwd_bytes),

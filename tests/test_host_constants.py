@@ -60,7 +60,7 @@ def test_stage_work_headline_figures():
     pairs = 12_000_000
     assert w["project_fwd"] == ("hbm", 3_000_000 * 140 + pairs * 48)
     assert w["project_bwd_adam"] == ("hbm", 3_000_000 * 752 + K * 36 + pairs * 8)
-    assert w["bin_sort"] == ("hbm", pairs * 16 + K * 8 + 5 * K * 16 + K * 4 + tiles * 8)
+    assert w["bin_sort"] == ("hbm", pairs * 16 + K * 16 + tiles * 8)
     assert w["loss_l1"] == ("hbm", px * 36)
     assert w["raster_bwd"] == ("alu", 2.0 * (ev * 14 + bl * 31))
     assert w["raster_fwd"] == ("alu", 2.0 * (ev * 14 + bl * 13))
@@ -86,7 +86,7 @@ def test_stage_work_ssim_loss_is_alu_work():
     assert "loss_l1" not in w and w["loss_l1_ssim"] == ("alu", 100 * 3 * 209 * 2)
     assert w["project_fwd"][1] == 1000 * 236 + 1000 * 48     # FP32 SH
     assert w["project_bwd_adam"][1] == 1000 * 1416 + 10 * 36 + 1000 * 8
-    assert w["bin_sort"][1] == 1000 * 16 + 10 * 8 + 4 * 10 * 16 + 10 * 4 + 4 * 8   # one view: no view pass
+    assert w["bin_sort"][1] == 1000 * 16 + 10 * 16 + 4 * 8
 
 
 def test_stage_rooflines_units_and_fractions():
