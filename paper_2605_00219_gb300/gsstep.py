@@ -279,6 +279,14 @@ def gs_workspace_buffer(plan: Plan, ws, which: int, numel: int, dtype=torch.int3
     return ws.view(torch.uint8)[off:off + numel * esz].view(dtype)
 
 
+def gs_gradient_records(plan: Plan, ws, k: int):
+    """The first k gradient records (emission slots 0 .. k-1) as a (k, 9)
+    float32 tensor (a copy).  Buffer 8 holds them as float4[cap][3]:
+    (dL/d mean x, y, conic a, b), (conic c, opacity, r, g), (b, unused x 3)."""
+    x = gs_workspace_buffer(plan, ws, 8, 12 * k, torch.float32)
+    return x.view(k, 12)[:, :9].clone()
+
+
 def gs_loss_l1_noalloc(image, target, dl, loss, stream=None):
     """L1 loss and gradient with no plan, no workspace and no device
     allocation (for callers that may not allocate); `loss` is a 1-element

@@ -65,7 +65,7 @@ def test_fullsize_single_view_keys_image_gradients(big, orc, report):
     torch.cuda.synchronize()
     g2_orc = orc.raster_bwd64(cam, P, bs, dl.astype(np.float64))
     K = b.K
-    gr = tr.buffer(8, K * 12, torch.float32).cpu().numpy().reshape(K, 12)[:, :9].astype(np.float64)
+    gr = gsstep.gs_gradient_records(tr.plan, tr.ws, K).cpu().numpy().astype(np.float64)
     slots = tr.buffer(9, K).cpu().numpy().view(np.uint32).astype(np.int64)   # emission slot per sorted entry
     sorted_tile = b.keys >> orc.key_shift(ntiles)
     in_sample = keep[sorted_tile]

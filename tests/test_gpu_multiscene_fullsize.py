@@ -166,7 +166,7 @@ def test_largest_scene_records_sampled_tiles(ms, bins, orc, report):
     the intersection gradient records in sampled tiles."""
     gsstep, R = ms["gsstep"], ms["R"]
     K = sum(b.K for b in bins)
-    gr = gsstep.gs_workspace_buffer(R.plan, R.ws, 8, K * 12, torch.float32).cpu().numpy().reshape(K, 12)[:, :9]
+    gr = gsstep.gs_gradient_records(R.plan, R.ws, K).cpu().numpy()
     slots = gsstep.gs_workspace_buffer(R.plan, R.ws, 9, K).cpu().numpy().view(np.uint32).astype(np.int64)
     sc = ms["scenes"][7]
     p = orc.Params64.from_scene(sc)

@@ -126,7 +126,7 @@ def test_tiny_stages(gs, orc, report, seed, bwd_impl):
     tr.dl.copy_(torch.from_numpy(dl64.astype(np.float32).reshape(-1, 3)))
     gsstep.gs_raster_bwd(tr.plan, tr.ws, tr.image, tr.dl)
     g2_orc = orc.raster_bwd64(cam, P, b, dl64.astype(np.float32).astype(np.float64))
-    gr = tr.buffer(8, b.K * 12, torch.float32).cpu().numpy().reshape(b.K, 12)
+    gr = gsstep.gs_gradient_records(tr.plan, tr.ws, b.K).cpu().numpy()
     off = tr.buffer(1, n + 1).cpu().numpy().view(np.uint32).astype(np.int64)
     g2_gpu = _sum_slots(gr, off, count)
     good = vis & ~_unstable_gaussians(P, r, cam)
@@ -219,7 +219,7 @@ def test_ragged_tiles_and_batches(gs, orc, tile, bwd_batch, bwd_impl):
     g2_orc = orc.raster_bwd64(cam, P, b, dl64, (0, 0, 0), *tile)
     count = tr.buffer(0, n).cpu().numpy().view(np.uint32)
     off = tr.buffer(1, n + 1).cpu().numpy().view(np.uint32).astype(np.int64)
-    gr = tr.buffer(8, b.K * 12, torch.float32).cpu().numpy().reshape(b.K, 12)
+    gr = gsstep.gs_gradient_records(tr.plan, tr.ws, b.K).cpu().numpy()
     g2_gpu = _sum_slots(gr, off, count)
     good = (b.count > 0) & ~_unstable_gaussians(P, r, cam)
     _check_grad(g2_gpu, g2_orc, good, f"grad2d {tile} S={bwd_batch} impl={bwd_impl}")
@@ -256,7 +256,7 @@ def test_pixels_per_thread(gs, orc, report, tile, tpt, bg):
     g2_orc = orc.raster_bwd64(cam, P, b, dl64, bgo, *tile)
     count = tr.buffer(0, n).cpu().numpy().view(np.uint32)
     off = tr.buffer(1, n + 1).cpu().numpy().view(np.uint32).astype(np.int64)
-    gr = tr.buffer(8, b.K * 12, torch.float32).cpu().numpy().reshape(b.K, 12)
+    gr = gsstep.gs_gradient_records(tr.plan, tr.ws, b.K).cpu().numpy()
     good = (b.count > 0) & ~_unstable_gaussians(P, r, cam)
     w = _check_grad(_sum_slots(gr, off, count), g2_orc, good, f"grad2d {tile} tpt={tpt} bg={bg}")
     report(f"pixels_per_thread {tile} tpt={tpt} bg={bg}", {"image_max_abs_err": float(ierr),
@@ -284,7 +284,7 @@ def test_background_colour(gs, orc, bwd_impl):
     n = scene.n
     count = tr.buffer(0, n).cpu().numpy().view(np.uint32)
     off = tr.buffer(1, n + 1).cpu().numpy().view(np.uint32).astype(np.int64)
-    gr = tr.buffer(8, b.K * 12, torch.float32).cpu().numpy().reshape(b.K, 12)
+    gr = gsstep.gs_gradient_records(tr.plan, tr.ws, b.K).cpu().numpy()
     good = (b.count > 0) & ~_unstable_gaussians(P, r, cam)
     _check_grad(_sum_slots(gr, off, count), g2_orc, good, f"grad2d bg impl={bwd_impl}")
 

@@ -62,3 +62,29 @@ def test_noalloc_rejects_sizes_beyond_its_maximum(gs):
     assert rc == 1  # GS_ERR_INVALID_ARG, nothing launched
     rc = lib.gs_loss_l1_noalloc(x.data_ptr(), x.data_ptr(), x.data_ptr(), x.data_ptr(), 0, None)
     assert rc == 1
+
+
+def test_noalloc_inside_a_captured_graph(gs):
+    """After a warm-up call (which looks up the scratch address), the entry
+    point can be captured in a CUDA graph; replays give the eager results."""
+    gsstep = gs
+    w, h = 257, 129
+    rng = np.random.default_rng(1)
+    image = torch.from_numpy(rng.uniform(0, 1, size=(h * w, 3)).astype(np.float32)).cuda()
+    target = torch.from_numpy(rng.uniform(0, 1, size=(h * w, 3)).astype(np.float32)).cuda()
+    dl_ref, loss_ref = _reference(gsstep, image, target, w, h)
+    loss_dev = torch.zeros(1, dtype=torch.float32, device="cuda")
+    dl = torch.zeros_like(image)
+    gsstep.gs_loss_l1_noalloc(image, target, dl, loss_dev)          # warm-up, eager
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        gsstep.gs_loss_l1_noalloc(image, target, dl, loss_dev, stream=s)
+    for _ in range(2):
+        dl.fill_(7.0)
+        loss_dev.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(dl, dl_ref)
+        assert float(loss_dev.item()) == pytest.approx(loss_ref, rel=1e-6, abs=0)
