@@ -235,8 +235,15 @@ __global__ void __launch_bounds__(256, 6) k_emit(Views V, const uint32_t* __rest
 {
     const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (qi >= V.pairs) return;
-    if (hdr->k_eff != hdr->k_required) return;     // over capacity: nothing is emitted
+    // the pair's loads are issued together, before any of them is tested
+    // (one memory round trip instead of three); span and ranks are stale
+    // for a pair without tiles and a pair that is not ranked, and unused
+    const uint32_t kreq = hdr->k_required, keff = hdr->k_eff;
     const uint32_t cnt = count[qi];
+    const uint32_t off = offset[qi];
+    const uint4 sp = span[qi];
+    const uint4 rk4 = rank[qi];
+    if (keff != kreq) return;     // over capacity: nothing is emitted
     if (cnt == 0) return;
     int s = 0;
     while (s + 1 < V.n_scenes && V.qbase[s + 1] <= qi) s++;
@@ -246,8 +253,6 @@ __global__ void __launch_bounds__(256, 6) k_emit(Views V, const uint32_t* __rest
     const int v = V.view_of[s][(int)(local - g * nv)];
     const ViewDesc& vd = V.v[v];
     const uint32_t p = (uint32_t)(vd.pair_base + g);
-    const uint32_t off = offset[qi];
-    const uint4 sp = span[qi];
     const uint32_t low = (sp.x & 0x7FFFFFu) >> vd.drop;
     const uint32_t nb = (sp.x >> 24) & 3u;
     uint32_t* cur = tile_over + vd.tile_base;
@@ -275,7 +280,6 @@ __global__ void __launch_bounds__(256, 6) k_emit(Views V, const uint32_t* __rest
     const uint32_t c0 = sp.y & 0xFFFFu, c1 = sp.y >> 16;
     if ((sp.x >> 27) & 1u) {
         // ranked: at most kRankMax tiles, no atomics
-        const uint4 rk4 = rank[qi];
         const uint32_t rk[kRankMax] = {rk4.x, rk4.y, rk4.z, rk4.w};
         const uint32_t* __restrict__ st0 = tile_start + vd.tile_base;
 #pragma unroll
