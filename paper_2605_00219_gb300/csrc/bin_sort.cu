@@ -333,8 +333,8 @@ __device__ __forceinline__ unsigned long long sort_key(uint32_t low, uint32_t e)
 // short or alone (then it is already merged), so no padding to a power of
 // two is sorted.  While two runs fit in one warp's 256 keys (w <= 128) only
 // that warp reads and writes them, so the level synchronises the warp; a
-// level that reads wider runs synchronises the block, also before its
-// reads.  The caller synchronises the block before.
+// level that reads wider runs synchronises the group, also before its
+// reads.  The caller synchronises the group before.
 __device__ __forceinline__ void cmpx(unsigned long long& a, unsigned long long& b)
 {
     const unsigned long long lo = a < b ? a : b, hi = a < b ? b : a;
@@ -342,10 +342,24 @@ __device__ __forceinline__ void cmpx(unsigned long long& a, unsigned long long& 
     b = hi;
 }
 
-__device__ void block_merge_sort_smem(unsigned long long* s, int N)
+// The threads that sort one list: the whole block, half of it (a named
+// barrier of its own) or one warp.  t is the thread's index in the group.
+struct SortGroup {
+    int t, n, bar;
+    __device__ __forceinline__ void sync() const
+    {
+        if (n == 32) __syncwarp();
+        else if (bar == 0) __syncthreads();
+        else asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(n) : "memory");
+    }
+};
+
+__device__ __forceinline__ SortGroup whole_block() { return SortGroup{(int)threadIdx.x, (int)blockDim.x, 0}; }
+
+__device__ void block_merge_sort_smem(unsigned long long* s, int N, const SortGroup& g)
 {
     constexpr int IT = 8;
-    const int nt = N / IT, t = threadIdx.x;
+    const int nt = N / IT, t = g.t;
     unsigned long long r[IT];
     if (t < nt) {
 #pragma unroll
@@ -390,7 +404,7 @@ __device__ void block_merge_sort_smem(unsigned long long* s, int N)
             }
         }
         if (in_warp) __syncwarp();
-        else __syncthreads();
+        else g.sync();
         if (merge) {
 #pragma unroll
             for (int k = 0; k < IT; k++) s[IT * t + k] = r[k];
@@ -398,9 +412,9 @@ __device__ void block_merge_sort_smem(unsigned long long* s, int N)
         // the next level (width 2w) reads other warps' keys unless its runs
         // still fit in one warp
         if (4 * w <= 32 * IT) __syncwarp();
-        else __syncthreads();
+        else g.sync();
     }
-    __syncthreads();
+    g.sync();
 }
 
 // (depth code, emission slot) lists in two layouts: one uint2 per entry, or
@@ -456,45 +470,51 @@ __device__ void merge_level(const Src& src, const Dst& dst, uint32_t s0, uint32_
 // order.  Output at the same positions: keys_sorted = tile << shift | depth
 // code, vals_sorted = emission slot, pid_sorted = the slot's pair.
 //
-// One tile's list, sorted by the calling block (T threads): up to 8 x T
-// entries in shared memory, longer lists (SMALL = false) in chunks of
-// kTileSortMax merged in global memory.
-template <int T, bool SMALL>
-__device__ void tile_sort_one(const Views& V, int64_t gt, uint32_t s0, uint32_t n, unsigned long long* sk,
-                              uint2* bucket, const uint32_t* __restrict__ pid, uint32_t* keys_sorted,
-                              uint32_t* vals_sorted, uint32_t* __restrict__ pid_sorted, uint32_t* status,
-                              uint32_t cap)
+// One tile's list of n <= 8 g.n entries, sorted in shared memory (sk) by the
+// group g.
+__device__ void tile_sort_group(const Views& V, int64_t gt, uint32_t s0, uint32_t n, unsigned long long* sk,
+                                const SortGroup& g, uint2* bucket, const uint32_t* __restrict__ pid,
+                                uint32_t* keys_sorted, uint32_t* vals_sorted, uint32_t* __restrict__ pid_sorted,
+                                uint32_t* status, uint32_t cap)
 {
     (void)status;
     (void)cap;
     const ViewDesc& vd = V.v[view_of_tile(V, gt)];
     const uint32_t hi_bits = (uint32_t)(gt - vd.tile_base) << vd.shift;
-    if (n <= 8u * (uint32_t)T) {
-        const int N = (int)((n + 7u) & ~7u);    // the last thread's keys padded
-        for (int i = threadIdx.x; i < N; i += blockDim.x) {
-            unsigned long long x = ~0ull;
-            if (i < (int)n) {
-                const uint2 b = bucket[s0 + i];
-                x = sort_key(b.x, b.y);
-            }
-            sk[i] = x;
+    const int N = (int)((n + 7u) & ~7u);    // the last thread's keys padded
+    for (int i = g.t; i < N; i += g.n) {
+        unsigned long long x = ~0ull;
+        if (i < (int)n) {
+            const uint2 b = bucket[s0 + i];
+            x = sort_key(b.x, b.y);
         }
-        __syncthreads();
-        block_merge_sort_smem(sk, N);
-        for (int i = threadIdx.x; i < (int)n; i += blockDim.x) {
-            const unsigned long long x = sk[i];
-            const uint32_t e = (uint32_t)x;
-            keys_sorted[s0 + i] = hi_bits | (uint32_t)(x >> 32);
-            vals_sorted[s0 + i] = e;
-            pid_sorted[s0 + i] = GS_DCHECK(e < cap, status) ? pid[e] : 0u;
-        }
-        __syncthreads();   // the block may take another list into sk next
-        return;
+        sk[i] = x;
     }
-    if (SMALL) return;   // not reached: short lists fit the block
-    // long list: chunks of kTileSortMax sorted in shared memory, then merge
-    // levels alternating between the bucket and the (keys, vals) arrays,
-    // starting where an even number of moves ends in the bucket
+    g.sync();
+    block_merge_sort_smem(sk, N, g);
+    for (int i = g.t; i < (int)n; i += g.n) {
+        const unsigned long long x = sk[i];
+        const uint32_t e = (uint32_t)x;
+        keys_sorted[s0 + i] = hi_bits | (uint32_t)(x >> 32);
+        vals_sorted[s0 + i] = e;
+        pid_sorted[s0 + i] = GS_DCHECK(e < cap, status) ? pid[e] : 0u;
+    }
+}
+
+// A list longer than kTileSortMax, sorted by the whole block: chunks of
+// kTileSortMax sorted in shared memory, then merge levels alternating
+// between the bucket and the (keys, vals) arrays, starting where an even
+// number of moves ends in the bucket.
+__device__ void tile_sort_chunked(const Views& V, int64_t gt, uint32_t s0, uint32_t n, unsigned long long* sk,
+                                  uint2* bucket, const uint32_t* __restrict__ pid, uint32_t* keys_sorted,
+                                  uint32_t* vals_sorted, uint32_t* __restrict__ pid_sorted, uint32_t* status,
+                                  uint32_t cap)
+{
+    (void)status;
+    (void)cap;
+    const ViewDesc& vd = V.v[view_of_tile(V, gt)];
+    const uint32_t hi_bits = (uint32_t)(gt - vd.tile_base) << vd.shift;
+    const SortGroup g = whole_block();
     const PackedList pk{bucket};
     const SplitList sp{keys_sorted, vals_sorted};
     const uint32_t M = kTileSortMax;
@@ -505,7 +525,7 @@ __device__ void tile_sort_one(const Views& V, int64_t gt, uint32_t s0, uint32_t 
         const uint32_t len = min(M, n - c0);
         for (uint32_t i = threadIdx.x; i < M; i += blockDim.x) sk[i] = i < len ? pk.get(s0 + c0 + i) : ~0ull;
         __syncthreads();
-        block_merge_sort_smem(sk, (int)M);
+        block_merge_sort_smem(sk, (int)M, g);
         for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
             if (chunks_in_bucket) pk.put(s0 + c0 + i, sk[i]);
             else sp.put(s0 + c0 + i, sk[i]);
@@ -526,41 +546,79 @@ __device__ void tile_sort_one(const Views& V, int64_t gt, uint32_t s0, uint32_t 
         vals_sorted[s0 + i] = e;
         pid_sorted[s0 + i] = GS_DCHECK(e < cap, status) ? pid[e] : 0u;
     }
-    __syncthreads();
 }
 
-// Short lists (1 to 8 x kTileSortSmall entries): one block per tile.
-__global__ void __launch_bounds__(kTileSortSmall) k_tile_sort_short(Views V, const uint32_t* __restrict__ order,
-                                                                    const uint2* __restrict__ ranges, uint2* bucket,
-                                                                    const uint32_t* __restrict__ pid,
-                                                                    uint32_t* keys_sorted, uint32_t* vals_sorted,
-                                                                    uint32_t* __restrict__ pid_sorted,
-                                                                    uint32_t* status, uint32_t cap)
-{
-    extern __shared__ unsigned long long sk[];
-    const int64_t gt = order[blockIdx.x];
-    const uint2 r = range_at(ranges, gt, cap, status);
-    const uint32_t n = r.y - r.x;
-    if (n == 0 || n > 8u * kTileSortSmall) return;
-    tile_sort_one<kTileSortSmall, true>(V, gt, r.x, n, sk, bucket, pid, keys_sorted, vals_sorted, pid_sorted, status,
-                                        cap);
-}
-
-// Longer lists: one block per tile (the blocks of short lists exit at once).
+// The tile order lists the tiles by size class (k_tile_order): long lists
+// (>= 2047 entries), medium (1023-2046), short (255-1022), tiny (<= 254).
+// Long and medium lists: 512-thread blocks, one long list per block (up to
+// kTileSortMax entries in shared memory, longer ones chunked), or two medium
+// lists per block, one per 256-thread half with a named barrier of its own.
 __global__ void __launch_bounds__(kTileSortThreads) k_tile_sort_long(Views V, const uint32_t* __restrict__ order,
                                                                      const uint2* __restrict__ ranges,
                                                                      uint2* bucket, const uint32_t* __restrict__ pid,
                                                                      uint32_t* keys_sorted, uint32_t* vals_sorted,
                                                                      uint32_t* __restrict__ pid_sorted,
+                                                                     const WsHeader* __restrict__ hdr,
                                                                      uint32_t* status, uint32_t cap)
 {
     extern __shared__ unsigned long long sk[];
-    const int64_t gt = order[blockIdx.x];
+    const uint32_t n_long = hdr->sort_class[0], n_med = hdr->sort_class[1];
+    const uint32_t b = blockIdx.x;
+    if (b < n_long) {
+        const int64_t gt = order[b];
+        const uint2 r = range_at(ranges, gt, cap, status);
+        const uint32_t n = r.y - r.x;
+        if (n <= (uint32_t)kTileSortMax)
+            tile_sort_group(V, gt, r.x, n, sk, whole_block(), bucket, pid, keys_sorted, vals_sorted, pid_sorted,
+                            status, cap);
+        else
+            tile_sort_chunked(V, gt, r.x, n, sk, bucket, pid, keys_sorted, vals_sorted, pid_sorted, status, cap);
+        return;
+    }
+    const uint32_t half = threadIdx.x >= kTileSortThreads / 2 ? 1u : 0u;
+    const uint32_t m = 2u * (b - n_long) + half;     // medium list of this half
+    if (b >= n_long + (n_med + 1u) / 2u || m >= n_med) return;
+    const int64_t gt = order[n_long + m];
     const uint2 r = range_at(ranges, gt, cap, status);
     const uint32_t n = r.y - r.x;
-    if (n <= 8u * kTileSortSmall) return;
-    tile_sort_one<kTileSortThreads, false>(V, gt, r.x, n, sk, bucket, pid, keys_sorted, vals_sorted, pid_sorted,
-                                           status, cap);
+    if (n == 0 || n > 4u * kTileSortThreads) return;
+    const SortGroup g{(int)(threadIdx.x - half * (kTileSortThreads / 2)), kTileSortThreads / 2, 1 + (int)half};
+    tile_sort_group(V, gt, r.x, n, sk + half * (kTileSortMax / 2), g, bucket, pid, keys_sorted, vals_sorted,
+                    pid_sorted, status, cap);
+}
+
+// Short and tiny lists: 128-thread blocks, one short list per block, or four
+// tiny lists per block, one per warp.
+__global__ void __launch_bounds__(kTileSortSmall) k_tile_sort_short(Views V, const uint32_t* __restrict__ order,
+                                                                    const uint2* __restrict__ ranges, uint2* bucket,
+                                                                    const uint32_t* __restrict__ pid,
+                                                                    uint32_t* keys_sorted, uint32_t* vals_sorted,
+                                                                    uint32_t* __restrict__ pid_sorted,
+                                                                    const WsHeader* __restrict__ hdr,
+                                                                    uint32_t* status, uint32_t cap)
+{
+    extern __shared__ unsigned long long sk[];
+    const uint32_t base = hdr->sort_class[0] + hdr->sort_class[1];
+    const uint32_t n_short = hdr->sort_class[2], n_tiny = hdr->sort_class[3];
+    const uint32_t b = blockIdx.x;
+    if (b < n_short) {
+        const int64_t gt = order[base + b];
+        const uint2 r = range_at(ranges, gt, cap, status);
+        const uint32_t n = r.y - r.x;
+        if (n == 0 || n > 8u * kTileSortSmall) return;
+        tile_sort_group(V, gt, r.x, n, sk, whole_block(), bucket, pid, keys_sorted, vals_sorted, pid_sorted, status,
+                        cap);
+        return;
+    }
+    const uint32_t w = threadIdx.x >> 5;
+    const uint32_t m = 4u * (b - n_short) + w;       // tiny list of this warp
+    if (b >= n_short + (n_tiny + 3u) / 4u || m >= n_tiny) return;
+    const int64_t gt = order[base + n_short + m];
+    const uint2 r = range_at(ranges, gt, cap, status);
+    const uint32_t n = r.y - r.x;
+    if (n == 0 || n > 256u) return;
+    const SortGroup g{(int)(threadIdx.x & 31u), 32, 0};
+    tile_sort_group(V, gt, r.x, n, sk + w * 256, g, bucket, pid, keys_sorted, vals_sorted, pid_sorted, status, cap);
 }
 
 // Launch order of the raster kernels: tiles by decreasing list length,
@@ -570,7 +628,7 @@ __global__ void __launch_bounds__(kTileSortThreads) k_tile_sort_long(Views V, co
 // follows shared-memory atomics; it decides only when a tile runs, never its
 // result.
 __global__ void __launch_bounds__(1024) k_tile_order(int64_t tiles, const uint2* __restrict__ ranges,
-                                                     uint32_t* __restrict__ order)
+                                                     uint32_t* __restrict__ order, WsHeader* __restrict__ hdr)
 {
     __shared__ uint32_t cnt[32];
     if (threadIdx.x < 32) cnt[threadIdx.x] = 0;
@@ -581,6 +639,12 @@ __global__ void __launch_bounds__(1024) k_tile_order(int64_t tiles, const uint2*
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+        // the sort's size classes are runs of buckets: long >= 2047 entries
+        // (buckets 11+), medium 1023-2046 (10), short 255-1022 (8, 9), tiny
+        // <= 254 (0-7)
+        uint32_t cls[4] = {0u, 0u, 0u, 0u};
+        for (int b = 0; b < 32; b++) cls[b >= 11 ? 0 : b == 10 ? 1 : b >= 8 ? 2 : 3] += cnt[b];
+        for (int c = 0; c < 4; c++) hdr->sort_class[c] = cls[c];
         uint32_t run = 0;
         for (int b = 31; b >= 0; b--) {
             const uint32_t c = cnt[b];
@@ -605,7 +669,7 @@ void launch_bin_sort(const Plan& P, const WsPtrs& w, cudaStream_t st)
     scan_pair_counts(P, w, st);
     // tile starts, ranges and the other pairs' cursors from the tile counters
     scan_tile_counts(P, w, st);
-    k_tile_order<<<1, 1024, 0, st>>>(V.tiles, w.ranges, w.tile_order);
+    k_tile_order<<<1, 1024, 0, st>>>(V.tiles, w.ranges, w.tile_order, w.hdr);
     // generate keys into the tile buckets
     {
         const int64_t blocks = (V.pairs + 255) / 256;
@@ -618,10 +682,12 @@ void launch_bin_sort(const Plan& P, const WsPtrs& w, cudaStream_t st)
         const size_t smem_s = sizeof(unsigned long long) * 8 * kTileSortSmall;      // 8 KB
         k_tile_sort_long<<<(unsigned)V.tiles, kTileSortThreads, smem_l, st>>>(V, w.tile_order, w.ranges, w.bucket,
                                                                              w.pid, w.keys_sorted, w.vals_sorted,
-                                                                             w.pid_sorted, &w.hdr->status, cap);
+                                                                             w.pid_sorted, w.hdr, &w.hdr->status,
+                                                                             cap);
         k_tile_sort_short<<<(unsigned)V.tiles, kTileSortSmall, smem_s, st>>>(V, w.tile_order, w.ranges, w.bucket,
                                                                              w.pid, w.keys_sorted, w.vals_sorted,
-                                                                             w.pid_sorted, &w.hdr->status, cap);
+                                                                             w.pid_sorted, w.hdr, &w.hdr->status,
+                                                                             cap);
     }
 }
 

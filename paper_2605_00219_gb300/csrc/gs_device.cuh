@@ -71,6 +71,7 @@ struct WsHeader {
     float loss;
     uint32_t pad;
     float bg[4];                  // background colour of the last raster_fwd
+    uint32_t sort_class[4];       // tiles per list-size class (long, medium, short, tiny), by k_tile_order
 };
 
 // Projected record of one (view, Gaussian) pair, read by the raster kernels.
