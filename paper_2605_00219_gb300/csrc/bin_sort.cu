@@ -624,73 +624,38 @@ __global__ void __launch_bounds__(kTileSortSmall) k_tile_sort_short(Views V, con
 // Launch order of the raster kernels: tiles by decreasing list length,
 // bucketed by floor(log2(length + 1)).  Blocks are dispatched roughly in
 // index order, so the longest tiles start first and the short ones fill the
-// tail (longest-processing-time scheduling).  Within a bucket the tiles
-// follow in a fixed order (by warp, pass and lane of this block); the order
-// decides only when a tile runs, never its result.
+// tail (longest-processing-time scheduling).  Within a bucket the order
+// follows shared-memory atomics; it decides only when a tile runs, never its
+// result.
 __global__ void __launch_bounds__(1024) k_tile_order(int64_t tiles, const uint2* __restrict__ ranges,
                                                      uint32_t* __restrict__ order, WsHeader* __restrict__ hdr)
 {
-    // per-warp bucket counters (lanes of a warp that share a bucket add once,
-    // through their leader), then each (bucket, warp) counter becomes that
-    // warp's first place in the order: buckets from the longest, warps in
-    // index order within a bucket
-    __shared__ uint32_t wc[32][33];     // [bucket][warp]
-    __shared__ uint32_t btot[32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    wc[w][lane] = 0u;
+    __shared__ uint32_t cnt[32];
+    if (threadIdx.x < 32) cnt[threadIdx.x] = 0;
     __syncthreads();
-    auto bucket_of = [&](int64_t t) { const uint2 r = ranges[t]; return 31 - __clz(r.y - r.x + 1u); };
-    for (int64_t t0 = 0; t0 < tiles; t0 += blockDim.x) {
-        const int64_t t = t0 + threadIdx.x;
-        const int bk = t < tiles ? bucket_of(t) : -1;
-        const uint32_t same = __match_any_sync(0xffffffffu, bk);
-        if (bk >= 0 && lane == __ffs(same) - 1) wc[bk][w] += __popc(same);
+    for (int64_t t = threadIdx.x; t < tiles; t += blockDim.x) {
+        const uint2 r = ranges[t];
+        atomicAdd(&cnt[31 - __clz(r.y - r.x + 1u)], 1u);
     }
     __syncthreads();
-    {
-        // warp b scans bucket b over the warps
-        uint32_t c = wc[w][lane], x = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
+    if (threadIdx.x == 0) {
+        // the sort's size classes are runs of buckets: long >= 2047 entries
+        // (buckets 11+), medium 1023-2046 (10), short 255-1022 (8, 9), tiny
+        // <= 254 (0-7)
+        uint32_t cls[4] = {0u, 0u, 0u, 0u};
+        for (int b = 0; b < 32; b++) cls[b >= 11 ? 0 : b == 10 ? 1 : b >= 8 ? 2 : 3] += cnt[b];
+        for (int c = 0; c < 4; c++) hdr->sort_class[c] = cls[c];
+        uint32_t run = 0;
+        for (int b = 31; b >= 0; b--) {
+            const uint32_t c = cnt[b];
+            cnt[b] = run;
+            run += c;
         }
-        wc[w][lane] = x - c;
-        if (lane == 31) btot[w] = x;
     }
     __syncthreads();
-    if (w == 0) {
-        // bucket starts, from the longest bucket down.  The sort's size
-        // classes are runs of buckets: long >= 2047 entries (buckets 11+),
-        // medium 1023-2046 (10), short 255-1022 (8, 9), tiny <= 254 (0-7)
-        const uint32_t c = btot[31 - lane];
-        uint32_t x = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        btot[31 - lane] = x - c;
-    }
-    __syncthreads();
-    if (threadIdx.x < 4) {
-        // class sizes from the bucket starts: long = buckets 11+, medium =
-        // 10, short = 9 and 8, tiny = 7 and below
-        const uint32_t start[5] = {0u, btot[10], btot[9], btot[7], (uint32_t)tiles};
-        hdr->sort_class[threadIdx.x] = start[threadIdx.x + 1] - start[threadIdx.x];
-    }
-    for (int64_t t0 = 0; t0 < tiles; t0 += blockDim.x) {
-        const int64_t t = t0 + threadIdx.x;
-        const int bk = t < tiles ? bucket_of(t) : -1;
-        const uint32_t same = __match_any_sync(0xffffffffu, bk);
-        const int leader = __ffs(same) - 1;
-        uint32_t base = 0;
-        if (bk >= 0 && lane == leader) {
-            base = wc[bk][w];
-            wc[bk][w] = base + __popc(same);
-        }
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (bk >= 0) order[btot[bk] + base + __popc(same & ((1u << lane) - 1u))] = (uint32_t)t;
+    for (int64_t t = threadIdx.x; t < tiles; t += blockDim.x) {
+        const uint2 r = ranges[t];
+        order[atomicAdd(&cnt[31 - __clz(r.y - r.x + 1u)], 1u)] = (uint32_t)t;
     }
 }
 
