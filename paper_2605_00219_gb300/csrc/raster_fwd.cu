@@ -162,6 +162,12 @@ void launch_raster_fwd(const Plan& P, const WsPtrs& w, const float* bg, float* i
 constexpr int kLossThreads = 256;
 constexpr int kLossItems = 8;
 
+__device__ __forceinline__ float l1_sign(float d, float inv_n) { return d > 0.f ? inv_n : (d < 0.f ? -inv_n : 0.f); }
+
+// VEC: the three arrays are 16-byte aligned; each thread takes kLossItems / 2
+// float4 (a block 2 x kLossThreads x kLossItems values), the ragged end
+// value by value.
+template <bool VEC>
 __global__ void __launch_bounds__(kLossThreads) k_loss_l1(const float* __restrict__ image,
                                                           const float* __restrict__ target, float* __restrict__ dl,
                                                           int64_t n, float inv_n, float* __restrict__ part,
@@ -169,15 +175,37 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_l1(const float* __restric
 {
     __shared__ float ws[kLossThreads / 32];
     __shared__ bool is_last;
-    const int64_t base = (int64_t)blockIdx.x * kLossThreads * kLossItems;
     float s = 0.f;
+    if (VEC) {
+        const int64_t base4 = (int64_t)blockIdx.x * kLossThreads * (kLossItems / 2);
 #pragma unroll
-    for (int i = 0; i < kLossItems; i++) {
-        const int64_t idx = base + i * kLossThreads + threadIdx.x;
-        if (idx < n) {
-            const float d = image[idx] - target[idx];
-            dl[idx] = d > 0.f ? inv_n : (d < 0.f ? -inv_n : 0.f);
-            s += fabsf(d);
+        for (int i = 0; i < kLossItems / 2; i++) {
+            const int64_t i4 = base4 + i * kLossThreads + threadIdx.x, e = 4 * i4;
+            if (e + 3 < n) {
+                const float4 a = reinterpret_cast<const float4*>(image)[i4];
+                const float4 b = reinterpret_cast<const float4*>(target)[i4];
+                const float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z, d3 = a.w - b.w;
+                reinterpret_cast<float4*>(dl)[i4] =
+                    make_float4(l1_sign(d0, inv_n), l1_sign(d1, inv_n), l1_sign(d2, inv_n), l1_sign(d3, inv_n));
+                s += (fabsf(d0) + fabsf(d1)) + (fabsf(d2) + fabsf(d3));
+            } else {
+                for (int64_t k = e; k < n && k < e + 4; k++) {
+                    const float d = image[k] - target[k];
+                    dl[k] = l1_sign(d, inv_n);
+                    s += fabsf(d);
+                }
+            }
+        }
+    } else {
+        const int64_t base = (int64_t)blockIdx.x * kLossThreads * kLossItems;
+#pragma unroll
+        for (int i = 0; i < kLossItems; i++) {
+            const int64_t idx = base + i * kLossThreads + threadIdx.x;
+            if (idx < n) {
+                const float d = image[idx] - target[idx];
+                dl[idx] = l1_sign(d, inv_n);
+                s += fabsf(d);
+            }
         }
     }
 #pragma unroll
@@ -221,9 +249,16 @@ void launch_loss_l1(const Plan& P, const WsPtrs& w, const float* image, const fl
                     cudaStream_t st)
 {
     const int64_t n = 3 * P.views.pixels;
-    const int64_t blocks = (n + kLossThreads * kLossItems - 1) / (kLossThreads * kLossItems);
-    k_loss_l1<<<(unsigned)blocks, kLossThreads, 0, st>>>(image, target, dl, n, 1.0f / (float)n, w.loss_part,
-                                                          w.hdr);
+    const bool vec = ((reinterpret_cast<uintptr_t>(image) | reinterpret_cast<uintptr_t>(target) |
+                       reinterpret_cast<uintptr_t>(dl)) & 15u) == 0;
+    const int64_t per_block = (int64_t)kLossThreads * kLossItems * (vec ? 2 : 1);
+    const int64_t blocks = (n + per_block - 1) / per_block;
+    if (vec)
+        k_loss_l1<true><<<(unsigned)blocks, kLossThreads, 0, st>>>(image, target, dl, n, 1.0f / (float)n,
+                                                                   w.loss_part, w.hdr);
+    else
+        k_loss_l1<false><<<(unsigned)blocks, kLossThreads, 0, st>>>(image, target, dl, n, 1.0f / (float)n,
+                                                                    w.loss_part, w.hdr);
 }
 
 }  // namespace gs

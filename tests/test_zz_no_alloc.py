@@ -88,3 +88,32 @@ def test_noalloc_inside_a_captured_graph(gs):
         torch.cuda.synchronize()
         assert torch.equal(dl, dl_ref)
         assert float(loss_dev.item()) == pytest.approx(loss_ref, rel=1e-6, abs=0)
+
+
+def test_workspace_l1_on_unaligned_and_ragged_buffers(gs):
+    """gs_loss_l1 reads four values at a time when the three buffers are
+    16-byte aligned and one at a time otherwise; both give the closed form
+    on a value count that is not a multiple of 4."""
+    gsstep = gs
+    w, h = 101, 37
+    n = 3 * w * h
+    rng = np.random.default_rng(2)
+    img = rng.uniform(0, 1, size=n).astype(np.float32)
+    tgt = rng.uniform(0, 1, size=n).astype(np.float32)
+    tgt[:50] = img[:50]
+    ref_dl = np.sign(img - tgt).astype(np.float32) / np.float32(n)
+    ref_loss = float(np.abs(img.astype(np.float64) - tgt.astype(np.float64)).mean())
+    plan = gsstep.Plan([1], [(w, h, 0)])
+    ws = torch.empty(plan.workspace_bytes(), dtype=torch.uint8, device="cuda")
+    for shift in (0, 1):                       # 0: aligned, 1: 4-byte offset
+        bi = torch.zeros(n + 4, dtype=torch.float32, device="cuda")
+        bt = torch.zeros(n + 4, dtype=torch.float32, device="cuda")
+        bd = torch.zeros(n + 4, dtype=torch.float32, device="cuda")
+        image, target, dl = bi[shift:shift + n], bt[shift:shift + n], bd[shift:shift + n]
+        image.copy_(torch.from_numpy(img))
+        target.copy_(torch.from_numpy(tgt))
+        gsstep.gs_workspace_init(plan, ws)
+        gsstep.gs_loss_l1(plan, ws, image, target, dl)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(dl.cpu().numpy(), ref_dl)
+        assert gsstep.gs_read_stats(plan, ws).loss == pytest.approx(ref_loss, rel=1e-5)
