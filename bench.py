@@ -60,14 +60,14 @@ LR = (1.6e-4 * 30.0, 1e-3, 5e-3, 5e-2, 2.5e-3, 2.5e-3 / 20)   # mean lr scaled b
 # 4 x 1920x1080, 16x16 tiles, pixel-parallel raster backward).  Valid only
 # while the kernel sources hash to the recorded prefixes.
 MEASURED_TRAFFIC = {
-    "raster_bwd": (3727156992, {"raster_bwd.cu": "6964d93683e553e9"}),
-    "project_bwd_adam": (3289885440, {"project_bwd_adam.cu": "9b1e90f515cd9a35"}),
-    "raster_fwd": (1711139072, {"raster_fwd.cu": "176a800dd0210d02"}),
-    "project_fwd": (1629572352, {"project_fwd.cu": "7a785eba31c6a4ab"}),
-    "bin_sort": (1480387840, {"bin_sort.cu": "9971f99c8326e6c5"}),
-    "loss_l1": (266740480, {"raster_fwd.cu": "176a800dd0210d02"}),
+    "raster_bwd": (3741149184, {"raster_bwd.cu": "6964d93683e553e9"}),
+    "project_bwd_adam": (3289832704, {"project_bwd_adam.cu": "9b1e90f515cd9a35"}),
+    "raster_fwd": (1701600000, {"raster_fwd.cu": "861f3437702e278d"}),
+    "project_fwd": (1629031936, {"project_fwd.cu": "7a785eba31c6a4ab"}),
+    "bin_sort": (1481550592, {"bin_sort.cu": "d92d0a747dcb654f"}),
+    "loss_l1": (259529472, {"raster_fwd.cu": "861f3437702e278d"}),
 }
-TRAFFIC_COMMON = {"gs_device.cuh": "0296c783b4672796", "gs_internal.cuh": "940fd77223c88071"}
+TRAFFIC_COMMON = {"gs_device.cuh": "59b0556cdcc1ad9f", "gs_internal.cuh": "940fd77223c88071"}
 
 
 def _measured_traffic(kernel: str, headline: bool):
