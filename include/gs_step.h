@@ -4,8 +4,9 @@
  * Sec. 2 pipeline and Sec. 4), each a call on a CUDA stream.
  *
  *   gs_project_fwd      projection forward + exact tile count  (Sec. 4.1)
- *   gs_bin_sort         index offset, key generation, 32-bit radix sort,
- *                       tile ranges                             (Sec. 4.1, 4.4)
+ *   gs_bin_sort         index offset, key generation, the stable order of
+ *                       the 32-bit keys (per-tile lists), tile
+ *                       ranges                                  (Sec. 4.1, 4.4)
  *   gs_raster_fwd       front-to-back alpha compositing         (Sec. 2)
  *   gs_loss_l1          L1 loss and its gradient                (Sec. 4.5, L1 term)
  *   gs_loss_l1_ssim     L1 + SSIM loss, RGBA8 reference         (Sec. 4.5)
