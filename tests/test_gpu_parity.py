@@ -419,6 +419,40 @@ def test_tile_spans(gs, orc, report, tile):
                                                 "ranked_pairs": ranked, "keys": int(b.K), "keys_bit_exact": True})
 
 
+@pytest.mark.parametrize("n", [300, 2500, 6000])
+def test_tile_lists_of_every_size_class(gs, orc, report, n):
+    """Tile lists in every size class of the per-tile sort -- tiny (<= 254
+    entries, four lists per block, one per warp), short (255-1022), medium
+    (1023-2046, two lists per block, one per half), long (>= 2047, in shared
+    memory up to 4096, chunked beyond) -- on a 64x64 view: the sorted keys
+    and Gaussians equal the oracle's stable sort bit for bit."""
+    gsstep, step_mod = gs
+    rng = np.random.default_rng(30 + n)
+    scene = synth.Scene(rng.uniform(-0.3, 0.3, (n, 3)).astype(np.float32),
+                        rng.normal(size=(n, 4)).astype(np.float32),
+                        np.exp(rng.normal(-2.2, 0.5, (n, 3))).astype(np.float32),
+                        (1.0 / (1.0 + np.exp(-rng.normal(-2.0, 1.0, n)))).astype(np.float32),
+                        rng.normal(0.0, 0.3, (n, 16, 3)).astype(np.float32))
+    cam = synth.tiny_camera()
+    cam.width, cam.height, cam.cx, cam.cy = 64, 64, 32.0, 32.0
+    b = orc.bin32(scene, cam)
+    lens = b.ranges[:, 1] - b.ranges[:, 0]
+    tr = _run_forward(step_mod, scene, [cam], capacity=1 << 20)
+    st = tr.stats()
+    assert st.status == 0 and st.k_required == b.K
+    np.testing.assert_array_equal(tr.buffer(2, b.K).cpu().numpy().view(np.uint32), b.keys)
+    np.testing.assert_array_equal(tr.buffer(3, b.K).cpu().numpy().view(np.uint32), b.gidx)
+    classes = {"tiny": int((lens <= 254).sum()), "short": int(((lens >= 255) & (lens <= 1022)).sum()),
+               "medium": int(((lens >= 1023) & (lens <= 2046)).sum()), "long": int((lens >= 2047).sum())}
+    report(f"tile_lists_size_classes_n{n}", {**classes, "keys": int(b.K), "keys_bit_exact": True})
+    # the inputs reach the classes they are meant for (all four over the three
+    # cases, and lists beyond 4096 entries for the chunked path)
+    want = {300: ("tiny", "short"), 2500: ("tiny", "short", "long"), 6000: ("short", "medium", "long")}[n]
+    assert all(classes[c] > 0 for c in want), classes
+    if n == 6000:
+        assert lens.max() > 4096
+
+
 def test_capacity_overflow_sets_status(gs, orc):
     """Too small an intersection capacity is reported, nothing is written
     out of bounds, and a larger capacity then succeeds."""
