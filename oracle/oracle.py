@@ -428,7 +428,12 @@ def rgba8_to_float(target_rgba8):
     return np.asarray(target_rgba8, np.float64)[..., :3] / 255.0
 
 
-def l1_ssim_loss_grad(images, targets, lam: float = 0.2):
+def rgba8_alpha(target_rgba8):
+    """8-bit RGBA reference -> its alpha in [0, 1] (the mask)."""
+    return np.asarray(target_rgba8, np.float64)[..., 3] / 255.0
+
+
+def l1_ssim_loss_grad(images, targets, lam: float = 0.2, masks=None):
     """L = (1 - lam) L1 + lam (1 - SSIM) over all pixels and channels of all
     views (means over 3 x pixels); SSIM per channel with an 11x11 Gaussian
     window (sigma 1.5), zero padding, C1 = 0.01^2, C2 = 0.03^2.  Returns
@@ -437,15 +442,25 @@ def l1_ssim_loss_grad(images, targets, lam: float = 0.2):
     The SSIM map at q depends on the rendered image x through the window
     moments mu_x, E[x^2], E[xy] at q; with A = dSSIM/dmu_x, B = dSSIM/dE[x^2]
     and Cc = dSSIM/dE[xy] at every q, dSSIM_sum/dx_p = (w * A)(p) +
-    2 x_p (w * B)(p) + y_p (w * Cc)(p) (the window is symmetric)."""
+    2 x_p (w * B)(p) + y_p (w * Cc)(p) (the window is symmetric).
+
+    masks (alpha masking, Sec. 4.5; one (H, W) array in [0, 1] per view, the
+    reference's alpha): the loss is taken on the masked images m x and m y,
+    so masked-out pixels add nothing, and the chain rule multiplies the
+    gradient by m."""
     g = ssim_window()
     total = sum(int(np.prod(im.shape)) for im in images)
     l1 = 0.0
     ssim_sum = 0.0
     grads = []
-    for x3, y3 in zip(images, targets):
+    if masks is None:
+        masks = [None] * len(images)
+    for x3, y3, m in zip(images, targets, masks):
         x3 = np.asarray(x3, np.float64)
         y3 = np.asarray(y3, np.float64)
+        if m is not None:
+            m3 = np.asarray(m, np.float64)[..., None]
+            x3, y3 = x3 * m3, y3 * m3
         d = np.zeros_like(x3)
         for c in range(3):
             x, y = x3[..., c], y3[..., c]
@@ -465,6 +480,8 @@ def l1_ssim_loss_grad(images, targets, lam: float = 0.2):
             dS = _wfilter(A, g) + 2 * x * _wfilter(B, g) + y * _wfilter(Cc, g)
             d[..., c] = (1 - lam) * np.sign(x - y) / total - lam * dS / total
         l1 += float(np.abs(x3 - y3).sum())
+        if m is not None:
+            d = d * m3
         grads.append(d)
     loss = (1 - lam) * l1 / total + lam * (1 - ssim_sum / total)
     return loss, grads

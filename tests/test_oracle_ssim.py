@@ -113,3 +113,54 @@ def test_loss_equals_direct_window_sums():
     for lam in (0.0, 0.2, 1.0):
         loss, _ = orc.l1_ssim_loss_grad(xs, ys, lam)
         assert loss == pytest.approx((1 - lam) * l1_sum / cnt + lam * (1 - ssim_sum / cnt), rel=1e-12)
+
+
+def test_alpha_mask_of_ones_is_the_unmasked_loss(orc):
+    rng = np.random.default_rng(5)
+    x, y = rng.uniform(size=(2, 14, 17, 3))
+    l0, (g0,) = orc.l1_ssim_loss_grad([x], [y], 0.2)
+    l1, (g1,) = orc.l1_ssim_loss_grad([x], [y], 0.2, masks=[np.ones((14, 17))])
+    assert l1 == l0 and np.array_equal(g1, g0)
+
+
+def test_alpha_mask_of_zeros_gives_no_loss(orc):
+    """Everything masked out: both masked images are 0, SSIM of two zero
+    images is 1 and the L1 term 0, so the loss and its gradient vanish."""
+    rng = np.random.default_rng(6)
+    x, y = rng.uniform(size=(2, 12, 12, 3))
+    loss, (g,) = orc.l1_ssim_loss_grad([x], [y], 0.2, masks=[np.zeros((12, 12))])
+    assert loss == pytest.approx(0.0, abs=1e-15) and not g.any()
+
+
+def test_alpha_mask_excludes_masked_pixels(orc):
+    """A 0/1 mask: the render's values under m = 0 change neither the loss
+    nor any gradient, and their own gradient is 0."""
+    rng = np.random.default_rng(7)
+    x, y = rng.uniform(size=(2, 16, 15, 3))
+    m = (rng.uniform(size=(16, 15)) > 0.4).astype(float)
+    l0, (g0,) = orc.l1_ssim_loss_grad([x], [y], 0.2, masks=[m])
+    x2 = x.copy()
+    x2[m == 0] = rng.uniform(size=((m == 0).sum(), 3))
+    l2, (g2,) = orc.l1_ssim_loss_grad([x2], [y], 0.2, masks=[m])
+    assert l2 == pytest.approx(l0, rel=1e-13)
+    assert np.allclose(g2, g0, rtol=0, atol=1e-15)
+    assert not g0[m == 0].any()
+
+
+def test_alpha_masked_gradient_fd(orc):
+    """Fractional mask: the analytic gradient (with the factor m) against
+    central differences of the masked loss."""
+    rng = np.random.default_rng(8)
+    x = rng.uniform(0.1, 0.9, size=(11, 13, 3))
+    y = rng.uniform(0.1, 0.9, size=x.shape)
+    m = rng.uniform(size=(11, 13))
+    m[0, 0] = 0.0
+    _, (g,) = orc.l1_ssim_loss_grad([x], [y], 0.2, masks=[m])
+    h = 1e-6
+    for idx in [(0, 0, 0), (5, 6, 1), (10, 12, 2), (3, 0, 2), (7, 9, 0)]:
+        xp, xm = x.copy(), x.copy()
+        xp[idx] += h
+        xm[idx] -= h
+        fd = (orc.l1_ssim_loss_grad([xp], [y], 0.2, masks=[m])[0] -
+              orc.l1_ssim_loss_grad([xm], [y], 0.2, masks=[m])[0]) / (2 * h)
+        assert g[idx] == pytest.approx(fd, rel=1e-5, abs=1e-9), idx
