@@ -10,6 +10,7 @@
  *   gs_raster_fwd       front-to-back alpha compositing         (Sec. 2)
  *   gs_loss_l1          L1 loss and its gradient                (Sec. 4.5, L1 term)
  *   gs_loss_l1_ssim     L1 + SSIM loss, RGBA8 reference         (Sec. 4.5)
+ *   gs_loss_l1_ssim_masked  the same with the reference's alpha as mask
  *   gs_raster_bwd       per-Gaussian rasterization backward     (Sec. 4.2)
  *   gs_project_bwd_adam projection backward fused with Adam     (Sec. 4.3)
  *
@@ -214,13 +215,22 @@ gs_status gs_loss_l1(const gs_plan* plan, void* ws, const float* image, const fl
  * SSIM per colour channel with an 11x11 Gaussian window (sigma 1.5), zero
  * padding at the image border, C1 = 0.01^2, C2 = 0.03^2; means over
  * 3 x pixels of all views.  target_rgba8: device uint8[pixels][4] (R, G, B, A;
- * A ignored; colour = byte / 255), 4-byte aligned; image and dL_dimage:
+ * A ignored here, the mask of gs_loss_l1_ssim_masked; colour = byte / 255),
+ * 4-byte aligned; image and dL_dimage:
  * device float[pixels][3].  lambda in [0, 1] (the paper uses 0.2), else
  * GS_ERR_INVALID_ARG.  The loss value lands in the workspace statistics.
  * Deterministic: per-tile partial sums added in a fixed order. */
 gs_status gs_loss_l1_ssim(const gs_plan* plan, void* ws, const float* image,
                           const void* target_rgba8, float lambda, float* dL_dimage,
                           void* stream);
+
+/* The same loss with alpha masking (Sec. 4.5 fuses it into the loss): the
+ * reference's alpha m = A / 255 multiplies both the render and the reference
+ * before the loss, so pixels with m = 0 add nothing to it, and dL_dimage
+ * carries the factor m.  Arguments and errors as gs_loss_l1_ssim. */
+gs_status gs_loss_l1_ssim_masked(const gs_plan* plan, void* ws, const float* image,
+                                 const void* target_rgba8, float lambda, float* dL_dimage,
+                                 void* stream);
 
 /* Rasterization backward (Sec. 4.2), one thread block per tile, no atomics:
  * one 9-float gradient record (mean2D, conic, opacity, colour) per

@@ -360,16 +360,30 @@ gs_status gs_loss_l1(const gs_plan* plan, void* ws, const float* image, const fl
     return launch_status();
 }
 
-gs_status gs_loss_l1_ssim(const gs_plan* plan, void* ws, const float* image, const void* target_rgba8, float lambda,
-                          float* dL_dimage, void* stream)
+static gs_status loss_l1_ssim(const gs_plan* plan, void* ws, const float* image, const void* target_rgba8,
+                              float lambda, bool alpha_mask, float* dL_dimage, void* stream)
 {
-    const StageRange range("gs_loss_l1_ssim");
     if (!plan || !ws || !image || !target_rgba8 || !dL_dimage) return GS_ERR_INVALID_ARG;
     if (!(lambda >= 0.f && lambda <= 1.f)) return GS_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(target_rgba8) % 4 != 0) return GS_ERR_INVALID_ARG;
     WsPtrs w = carve(plan->p, ws);
-    launch_loss_l1_ssim(plan->p, w, image, target_rgba8, lambda, dL_dimage, static_cast<cudaStream_t>(stream));
+    launch_loss_l1_ssim(plan->p, w, image, target_rgba8, lambda, alpha_mask, dL_dimage,
+                        static_cast<cudaStream_t>(stream));
     return launch_status();
+}
+
+gs_status gs_loss_l1_ssim(const gs_plan* plan, void* ws, const float* image, const void* target_rgba8, float lambda,
+                          float* dL_dimage, void* stream)
+{
+    const StageRange range("gs_loss_l1_ssim");
+    return loss_l1_ssim(plan, ws, image, target_rgba8, lambda, false, dL_dimage, stream);
+}
+
+gs_status gs_loss_l1_ssim_masked(const gs_plan* plan, void* ws, const float* image, const void* target_rgba8,
+                                 float lambda, float* dL_dimage, void* stream)
+{
+    const StageRange range("gs_loss_l1_ssim_masked");
+    return loss_l1_ssim(plan, ws, image, target_rgba8, lambda, true, dL_dimage, stream);
 }
 
 gs_status gs_raster_bwd(const gs_plan* plan, void* ws, const float* image, const float* dL_dimage, void* stream)

@@ -115,7 +115,7 @@ void launch_loss_l1(const Plan& P, const WsPtrs& w, const float* image, const fl
 void scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* part, cudaStream_t st);
 int64_t ssim_tiles(const Views& V);  // 16x16 tiles of the fused L1 + SSIM loss
 void launch_loss_l1_ssim(const Plan& P, const WsPtrs& w, const float* image, const void* target_rgba8, float lam,
-                         float* dl, cudaStream_t st);
+                         bool alpha_mask, float* dl, cudaStream_t st);
 void launch_raster_bwd(const Plan& P, const WsPtrs& w, const float* image, const float* dl, cudaStream_t st);
 void launch_raster_bwd2(const Plan& P, const WsPtrs& w, const float* bg, const float* dl, cudaStream_t st);
 void launch_project_bwd_adam(const Plan& P, const Scenes& S, const float* cams, const WsPtrs& w,

@@ -62,6 +62,16 @@ __device__ __forceinline__ float target_channel(uchar4 t, int c)
     return (float)(c == 0 ? t.x : (c == 1 ? t.y : t.z)) * (1.0f / 255.0f);
 }
 
+// Alpha masking (MASK): the loss is taken on the render and the reference
+// both multiplied by the reference's alpha m = A / 255, so masked-out pixels
+// add nothing; the gradient with respect to the render carries the factor m.
+template <bool MASK>
+__device__ __forceinline__ float pix_mask(uchar4 t)
+{
+    return MASK ? (float)t.w * (1.0f / 255.0f) : 1.0f;
+}
+
+template <bool MASK>
 __global__ void __launch_bounds__(256) k_loss_l1_ssim(Views V, const float* __restrict__ image,
                                                       const uchar4* __restrict__ target, float lam,
                                                       float inv_n, float* __restrict__ dl,
@@ -94,7 +104,9 @@ __global__ void __launch_bounds__(256) k_loss_l1_ssim(Views V, const float* __re
 
     const int64_t cpix = vd.pix_base + (int64_t)min(oy + kSsT / 2, vd.H - 1) * vd.W + min(ox + kSsT / 2, vd.W - 1);
     for (int c = 0; c < 3; c++) {
-        const float shx = image[3 * cpix + c], shy = target_channel(target[cpix], c);
+        const uchar4 tc = target[cpix];
+        const float mc = pix_mask<MASK>(tc);
+        const float shx = image[3 * cpix + c] * mc, shy = target_channel(tc, c) * mc;
         __syncthreads();
         for (int i = tid; i < kSsX * kSsX; i += 256) {
             const int r = i / kSsX, col = i % kSsX;
@@ -102,8 +114,10 @@ __global__ void __launch_bounds__(256) k_loss_l1_ssim(Views V, const float* __re
             float a = 0.f, b = 0.f;
             if (x >= 0 && y >= 0 && x < vd.W && y < vd.H) {
                 const int64_t pix = vd.pix_base + (int64_t)y * vd.W + x;
-                a = image[3 * pix + c];
-                b = target_channel(target[pix], c);
+                const uchar4 t4 = target[pix];
+                const float m = pix_mask<MASK>(t4);
+                a = image[3 * pix + c] * m;
+                b = target_channel(t4, c) * m;
             }
             sxy[r][col] = make_float2(a - shx, b - shy);
         }
@@ -186,11 +200,13 @@ __global__ void __launch_bounds__(256) k_loss_l1_ssim(Views V, const float* __re
             wc = fmaf(w, habc2[pr + k][pc], wc);
         }
         if (pin) {
-            const float x = image[3 * ppix + c], y = target_channel(target[ppix], c);
+            const uchar4 t4 = target[ppix];
+            const float m = pix_mask<MASK>(t4);
+            const float x = image[3 * ppix + c] * m, y = target_channel(t4, c) * m;
             const float d = x - y;
             const float dS = wa + 2.f * x * wb + y * wc;
             const float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
-            dl[3 * ppix + c] = ((1.f - lam) * sg - lam * dS) * inv_n;
+            dl[3 * ppix + c] = MASK ? m * (((1.f - lam) * sg - lam * dS) * inv_n) : ((1.f - lam) * sg - lam * dS) * inv_n;
             l1 += fabsf(d);
         }
     }
@@ -243,12 +259,15 @@ int64_t ssim_tiles(const Views& V)
 }
 
 void launch_loss_l1_ssim(const Plan& P, const WsPtrs& w, const float* image, const void* target_rgba8, float lam,
-                         float* dl, cudaStream_t st)
+                         bool alpha_mask, float* dl, cudaStream_t st)
 {
     const int64_t tiles = ssim_tiles(P.views);
     const float inv_n = 1.0f / (float)(3 * P.views.pixels);
-    k_loss_l1_ssim<<<(unsigned)tiles, 256, 0, st>>>(P.views, image, static_cast<const uchar4*>(target_rgba8), lam,
-                                                   inv_n, dl, w.loss_part, w.hdr);
+    const uchar4* t = static_cast<const uchar4*>(target_rgba8);
+    if (alpha_mask)
+        k_loss_l1_ssim<true><<<(unsigned)tiles, 256, 0, st>>>(P.views, image, t, lam, inv_n, dl, w.loss_part, w.hdr);
+    else
+        k_loss_l1_ssim<false><<<(unsigned)tiles, 256, 0, st>>>(P.views, image, t, lam, inv_n, dl, w.loss_part, w.hdr);
 }
 
 }  // namespace gs

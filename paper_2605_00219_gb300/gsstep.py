@@ -35,7 +35,7 @@ STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_CAPACITY", 3: "G
 SYMBOLS = ["gs_plan_create", "gs_plan_destroy", "gs_workspace_bytes", "gs_plan_query", "gs_workspace_init",
            "gs_project_fwd", "gs_bin_sort", "gs_raster_fwd", "gs_loss_l1", "gs_raster_bwd",
            "gs_project_bwd_adam", "gs_adam_advance", "gs_read_stats", "gs_workspace_buffer", "gs_status_str",
-           "gs_loss_l1_noalloc", "gs_loss_l1_ssim", "gs_densify_scratch_bytes", "gs_densify_count",
+           "gs_loss_l1_noalloc", "gs_loss_l1_ssim", "gs_loss_l1_ssim_masked", "gs_densify_scratch_bytes", "gs_densify_count",
            "gs_densify_counts", "gs_densify_apply", "gs_reset_opacity", "gs_workspace_set_step"]
 L1_NOALLOC_MAX_VALUES = 67108864
 
@@ -102,6 +102,7 @@ def lib():
         L.gs_raster_fwd.argtypes = [vp, vp, vp, vp, vp]
         L.gs_loss_l1.argtypes = [vp, vp, vp, vp, vp, vp]
         L.gs_loss_l1_ssim.argtypes = [vp, vp, vp, vp, ctypes.c_float, vp, vp]
+        L.gs_loss_l1_ssim_masked.argtypes = [vp, vp, vp, vp, ctypes.c_float, vp, vp]
         L.gs_raster_bwd.argtypes = [vp, vp, vp, vp, vp]
         L.gs_project_bwd_adam.argtypes = [vp, vp, ctypes.POINTER(gs_scene_buf), vp, ctypes.POINTER(gs_adam), vp, vp]
         L.gs_adam_advance.argtypes = [vp, vp, vp]
@@ -121,7 +122,8 @@ def lib():
         L.gs_status_str.argtypes = [ctypes.c_int]
         L.gs_status_str.restype = ctypes.c_char_p
         for name in ["gs_workspace_init", "gs_project_fwd", "gs_bin_sort", "gs_raster_fwd", "gs_loss_l1",
-                     "gs_loss_l1_ssim", "gs_raster_bwd", "gs_project_bwd_adam", "gs_adam_advance", "gs_read_stats",
+                     "gs_loss_l1_ssim", "gs_loss_l1_ssim_masked", "gs_raster_bwd", "gs_project_bwd_adam",
+                     "gs_adam_advance", "gs_read_stats",
                      "gs_densify_count", "gs_densify_counts", "gs_densify_apply", "gs_reset_opacity",
                      "gs_workspace_set_step"]:
             getattr(L, name).restype = ctypes.c_int
@@ -233,6 +235,12 @@ def gs_loss_l1_ssim(plan: Plan, ws, image, target_rgba8, lam, dl, stream=None):
     """target_rgba8: uint8 device tensor [pixels][4]; lam in [0, 1]."""
     _check(lib().gs_loss_l1_ssim(plan.handle, _ptr(ws), _ptr(image), _ptr(target_rgba8), float(lam), _ptr(dl),
                                  _stream(stream)), "gs_loss_l1_ssim")
+
+
+def gs_loss_l1_ssim_masked(plan: Plan, ws, image, target_rgba8, lam, dl, stream=None):
+    """gs_loss_l1_ssim with the reference's alpha (A / 255) as mask."""
+    _check(lib().gs_loss_l1_ssim_masked(plan.handle, _ptr(ws), _ptr(image), _ptr(target_rgba8), float(lam),
+                                        _ptr(dl), _stream(stream)), "gs_loss_l1_ssim_masked")
 
 
 def gs_raster_bwd(plan: Plan, ws, image, dl, stream=None):

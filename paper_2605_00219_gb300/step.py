@@ -5,7 +5,8 @@
 plan and workspace and runs
 
     gs_project_fwd -> gs_bin_sort -> gs_raster_fwd -> gs_loss_l1 (or
-    gs_loss_l1_ssim against an 8-bit RGBA target) -> gs_raster_bwd
+    gs_loss_l1_ssim against an 8-bit RGBA target, or gs_loss_l1_ssim_masked
+    with its alpha as mask) -> gs_raster_bwd
     -> gs_project_bwd_adam
 
 on one stream, eagerly or as one captured CUDA graph whose replay reads the
@@ -93,8 +94,8 @@ class Trainer:
                  sh_bf16: bool = False, mom_bf16: bool = False, bg=None, lr=DEFAULT_LR, device="cuda",
                  bwd_impl: int = 0, loss: str = "l1", ssim_lambda: float = 0.2, seed: int = 0,
                  threads_per_tile: int = 0):
-        if loss not in ("l1", "l1_ssim"):
-            raise ValueError(f"loss must be 'l1' or 'l1_ssim', not {loss!r}")
+        if loss not in ("l1", "l1_ssim", "l1_ssim_masked"):
+            raise ValueError(f"loss must be 'l1', 'l1_ssim' or 'l1_ssim_masked', not {loss!r}")
         self.loss = loss
         self.ssim_lambda = float(ssim_lambda)
         self.seed = int(seed)         # stochastic rounding of BF16 storage
@@ -160,8 +161,11 @@ class Trainer:
     def backward_adam(self, step: int = 0, stream=None):
         if self.loss == "l1":
             gsstep.gs_loss_l1(self.plan, self.ws, self.image, self.target, self.dl, stream)
-        else:
+        elif self.loss == "l1_ssim":
             gsstep.gs_loss_l1_ssim(self.plan, self.ws, self.image, self.target, self.ssim_lambda, self.dl, stream)
+        else:   # the reference's alpha as mask
+            gsstep.gs_loss_l1_ssim_masked(self.plan, self.ws, self.image, self.target, self.ssim_lambda, self.dl,
+                                          stream)
         gsstep.gs_raster_bwd(self.plan, self.ws, self.image, self.dl, stream)
         adam = gsstep.make_adam(self.lr, step=step, seed=self.seed)
         gsstep.gs_project_bwd_adam(self.plan, self.ws, self.scenes, self.cams, adam, None, stream)

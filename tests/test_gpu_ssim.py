@@ -81,6 +81,37 @@ def test_l1_ssim_matches_oracle(gs, orc, report, smooth, lam):
            {"loss_rel_err": abs(loss - ref_loss) / abs(ref_loss), "grad_max_err": worst})
 
 
+@pytest.mark.parametrize("lam", [0.2, 1.0])
+def test_l1_ssim_alpha_masked_matches_oracle(gs, orc, report, lam):
+    """gs_loss_l1_ssim_masked: the reference's alpha (0, 255 and values in
+    between) masks render and reference; loss and every pixel's gradient
+    against the oracle's masked loss."""
+    gsstep, _ = gs
+    imgs, tgts = synth.loss_images(SHAPES, seed=21, smooth=True)
+    rng = np.random.default_rng(22)
+    for t in tgts:
+        u = rng.uniform(size=t.shape[:2])
+        t[..., 3] = np.where(u < 0.3, 0, np.where(u < 0.6, 255, rng.integers(1, 255, size=u.shape))).astype(np.uint8)
+    plan, ws = _plan(gsstep, SHAPES)
+    dl = torch.full_like(_flat(imgs, 3), np.nan)
+    gsstep.gs_loss_l1_ssim_masked(plan, ws, _flat(imgs, 3), _flat(tgts, 4), lam, dl)
+    torch.cuda.synchronize()
+    loss, dl = gsstep.gs_read_stats(plan, ws).loss, dl.cpu().numpy()
+    masks = [orc.rgba8_alpha(t) for t in tgts]
+    ref_loss, ref_g = orc.l1_ssim_loss_grad(imgs, [orc.rgba8_to_float(t) for t in tgts], lam, masks=masks)
+    assert abs(loss - ref_loss) <= 1e-5 * abs(ref_loss), (loss, ref_loss)
+    worst = 0.0
+    for got, ref, img, t, m in zip(_split(dl, SHAPES), ref_g, imgs, tgts, masks):
+        tie = np.abs(m[..., None] * (img.astype(np.float64) - orc.rgba8_to_float(t))) < 1e-6
+        err = _grad_err(got, ref, tie)
+        assert np.isfinite(got).all()
+        assert not got[m == 0].any()
+        assert err.max() <= 1e-3, err.max()
+        worst = max(worst, err.max())
+    report(f"l1_ssim_alpha_masked_lambda{lam}", {"loss_rel_err": abs(loss - ref_loss) / abs(ref_loss),
+                                                  "grad_max_err": worst})
+
+
 def test_lambda_zero_is_l1(gs):
     gsstep, _ = gs
     imgs, tgts = synth.loss_images(SHAPES, seed=5)
