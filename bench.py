@@ -60,14 +60,14 @@ LR = (1.6e-4 * 30.0, 1e-3, 5e-3, 5e-2, 2.5e-3, 2.5e-3 / 20)   # mean lr scaled b
 # 4 x 1920x1080, 16x16 tiles, pixel-parallel raster backward).  Valid only
 # while the kernel sources hash to the recorded prefixes.
 MEASURED_TRAFFIC = {
-    "raster_bwd": (3741149184, {"raster_bwd.cu": "6964d93683e553e9"}),
-    "project_bwd_adam": (3289832704, {"project_bwd_adam.cu": "9b1e90f515cd9a35"}),
-    "raster_fwd": (1701600000, {"raster_fwd.cu": "861f3437702e278d"}),
-    "project_fwd": (1629031936, {"project_fwd.cu": "7a785eba31c6a4ab"}),
-    "bin_sort": (1481550592, {"bin_sort.cu": "d92d0a747dcb654f"}),
-    "loss_l1": (259529472, {"raster_fwd.cu": "861f3437702e278d"}),
+    "raster_bwd": (3743537920, {"raster_bwd.cu": "6964d93683e553e9"}),
+    "project_bwd_adam": (3290240512, {"project_bwd_adam.cu": "9b1e90f515cd9a35"}),
+    "raster_fwd": (1710455040, {"raster_fwd.cu": "861f3437702e278d"}),
+    "project_fwd": (1628788480, {"project_fwd.cu": "7a785eba31c6a4ab"}),
+    "bin_sort": (1481361152, {"bin_sort.cu": "d92d0a747dcb654f"}),
+    "loss_l1": (259828224, {"raster_fwd.cu": "861f3437702e278d"}),
 }
-TRAFFIC_COMMON = {"gs_device.cuh": "59b0556cdcc1ad9f", "gs_internal.cuh": "940fd77223c88071"}
+TRAFFIC_COMMON = {"gs_device.cuh": "59b0556cdcc1ad9f", "gs_internal.cuh": "5fbc73f81b77bed3"}
 
 
 def _measured_traffic(kernel: str, headline: bool):
