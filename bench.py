@@ -61,7 +61,7 @@ LR = (1.6e-4 * 30.0, 1e-3, 5e-3, 5e-2, 2.5e-3, 2.5e-3 / 20)   # mean lr scaled b
 # while the kernel sources hash to the recorded prefixes.
 MEASURED_TRAFFIC = {
     "raster_bwd": (3743537920, {"raster_bwd.cu": "6964d93683e553e9"}),
-    "project_bwd_adam": (3290240512, {"project_bwd_adam.cu": "9b1e90f515cd9a35"}),
+    "project_bwd_adam": (3288097792, {"project_bwd_adam.cu": "8148569f70771762"}),
     "raster_fwd": (1710455040, {"raster_fwd.cu": "861f3437702e278d"}),
     "project_fwd": (1628788480, {"project_fwd.cu": "7a785eba31c6a4ab"}),
     "bin_sort": (1481361152, {"bin_sort.cu": "d92d0a747dcb654f"}),

@@ -515,7 +515,7 @@ __global__ void __launch_bounds__(kPbaThreads, 4) k_project_bwd_adam(Views V, Sc
         return;
     }
     const AdamConst K = sK;
-#pragma unroll 3
+#pragma unroll 1
     for (int jp = 0; jp < 6; jp++) {          // pairs of chunks = 8 coefficients
         float th[8];
         if (SH16) {
