@@ -319,6 +319,26 @@ __device__ __forceinline__ float4 load_mom(const void* base, int64_t idx)
     return make_float4(bf16_lo(u.x), bf16_hi(u.x), bf16_lo(u.y), bf16_hi(u.y));
 }
 
+// The stored words of one moment chunk, loaded ahead of their use.
+template <bool MOM16> struct MomWords { float4 w; };
+template <> struct MomWords<true> { uint2 w; };
+
+template <bool MOM16>
+__device__ __forceinline__ MomWords<MOM16> load_mom_words(const void* base, int64_t idx)
+{
+    MomWords<MOM16> r;
+    if constexpr (MOM16) r.w = reinterpret_cast<const uint2*>(base)[idx];
+    else r.w = reinterpret_cast<const float4*>(base)[idx];
+    return r;
+}
+
+template <bool MOM16>
+__device__ __forceinline__ float4 mom_value(const MomWords<MOM16>& r)
+{
+    if constexpr (MOM16) return make_float4(bf16_lo(r.w.x), bf16_hi(r.w.x), bf16_lo(r.w.y), bf16_hi(r.w.y));
+    else return r.w;
+}
+
 template <bool MOM16>
 __device__ __forceinline__ void store_mom(void* base, int64_t idx, float4 m, uint32_t key, uint32_t ctr)
 {
@@ -515,8 +535,28 @@ __global__ void __launch_bounds__(kPbaThreads, 4) k_project_bwd_adam(Views V, Sc
         return;
     }
     const AdamConst K = sK;
+    // the moments of the next pair of chunks are loaded while this pair is
+    // updated
+    MomWords<MOM16> nw[4];
+    {
+        const int64_t c0 = 3 * n + g;
+        nw[0] = load_mom_words<MOM16>(sc.m, c0);
+        nw[1] = load_mom_words<MOM16>(sc.v, c0);
+        nw[2] = load_mom_words<MOM16>(sc.m, c0 + n);
+        nw[3] = load_mom_words<MOM16>(sc.v, c0 + n);
+    }
 #pragma unroll 1
     for (int jp = 0; jp < 6; jp++) {          // pairs of chunks = 8 coefficients
+        MomWords<MOM16> cw[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) cw[i] = nw[i];
+        if (jp < 5) {
+            const int64_t c0 = (int64_t)(3 + 2 * jp + 2) * n + g;
+            nw[0] = load_mom_words<MOM16>(sc.m, c0);
+            nw[1] = load_mom_words<MOM16>(sc.v, c0);
+            nw[2] = load_mom_words<MOM16>(sc.m, c0 + n);
+            nw[3] = load_mom_words<MOM16>(sc.v, c0 + n);
+        }
         float th[8];
         if (SH16) {
             const uint4 c = sS16[tid][jp];
@@ -530,7 +570,7 @@ __global__ void __launch_bounds__(kPbaThreads, 4) k_project_bwd_adam(Views V, Sc
         for (int h = 0; h < 2; h++) {
             const int j = 2 * jp + h;
             const int64_t ci = (int64_t)(3 + j) * n + g;
-            float4 m = load_mom<MOM16>(sc.m, ci), vv = load_mom<MOM16>(sc.v, ci);
+            float4 m = mom_value<MOM16>(cw[2 * h]), vv = mom_value<MOM16>(cw[2 * h + 1]);
             const float4 g4 = sG[tid][j];
             float* mp = &m.x;
             float* vp = &vv.x;
