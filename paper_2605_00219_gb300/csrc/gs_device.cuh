@@ -511,11 +511,21 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
-// Pixel-centre offset from a Gaussian's mean: (p - mean) - residual.  Both
-// raster kernels use this one expression, so they agree bit for bit.
-__device__ __forceinline__ float pix_offset(float pc, float m_hi, float m_lo)
+// A Gaussian's mean (hi + residual lo) relative to a tile's first pixel o,
+// rounded once to FP32 when a list entry is staged: (hi - o) + lo.  Its
+// error is at most about one ulp of the tile-relative mean (1e-6 px within
+// 16 px of the tile), like the two roundings of (p - hi) - lo.
+__device__ __forceinline__ float tile_mean(float m_hi, float m_lo, int o)
 {
-    return __fsub_rn(__fsub_rn(pc, m_hi), m_lo);
+    return __fadd_rn(__fsub_rn(m_hi, (float)o), m_lo);
+}
+
+// Pixel-centre offset from a Gaussian's mean, both relative to the tile's
+// first pixel: one subtraction per pair.  The raster forward and every
+// backward use these two helpers, so they agree bit for bit.
+__device__ __forceinline__ float pix_offset(float pc_tile, float m_tile)
+{
+    return __fsub_rn(pc_tile, m_tile);
 }
 
 // Error-free transforms (Knuth TwoSum, FMA-based TwoProduct) for the

@@ -32,10 +32,9 @@ struct BwdSmem {
     float4* pimg;   // [P] (C r, g, b, -)
     float4* pdl;    // [P] (dL/dC r, g, b, n_last bits)
     float4* st;     // [4][P] state (T, S r, S g, S b) after each sub-batch
-    float4* gA;     // [128] (mx, my, ca, cb)
+    float4* gA;     // [128] (mx, my relative to the tile's first pixel, ca, cb)
     float4* gB;     // [128] (cc, o, r, g)
     float* gC;      // [128] blue
-    float2* gL;     // [128] mean residuals
     uint32_t* ge;   // [128] emission slot
     float* red;     // [128][9] partial gradients
     int* misc;
@@ -43,7 +42,7 @@ struct BwdSmem {
 
 __host__ __device__ constexpr size_t bwd_smem_bytes(int P)
 {
-    return (size_t)16 * P * 4 + (size_t)16 * 4 * P + 128 * (16 + 16 + 8 + 4 + 4) + 128 * 9 * 4 + 16;
+    return (size_t)16 * P * 4 + (size_t)16 * 4 * P + 128 * (16 + 16 + 4 + 4) + 128 * 9 * 4 + 16;
 }
 
 __device__ __forceinline__ void neumaier_add(float& s, float& c, float x)
@@ -73,8 +72,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(Views V, const uint3
     sm.st = sm.pdl + P;
     sm.gA = sm.st + 4 * P;
     sm.gB = sm.gA + 128;
-    sm.gL = reinterpret_cast<float2*>(sm.gB + 128);
-    sm.gC = reinterpret_cast<float*>(sm.gL + 128);
+    sm.gC = reinterpret_cast<float*>(sm.gB + 128);
     sm.ge = reinterpret_cast<uint32_t*>(sm.gC + 128);
     sm.red = reinterpret_cast<float*>(sm.ge + 128);
     sm.misc = reinterpret_cast<int*>(sm.red + 128 * 9);
@@ -131,10 +129,9 @@ __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(Views V, const uint3
         if (tid < cnt) {
             const uint32_t k = start + bb + tid;
             const ProjRec q = rec[pid_sorted[k]];
-            sm.gA[tid] = q.a;
+            sm.gA[tid] = make_float4(tile_mean(q.a.x, q.c.z, ox), tile_mean(q.a.y, q.c.w, oy), q.a.z, q.a.w);
             sm.gB[tid] = q.b;
             sm.gC[tid] = q.c.x;
-            sm.gL[tid] = make_float2(q.c.z, q.c.w);
             sm.ge[tid] = vals_sorted[k];
         }
         __syncthreads();
@@ -148,15 +145,15 @@ __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(Views V, const uint3
             const float4 d = sm.pdl[pi];
             const float4 im = sm.pimg[pi];
             const uint32_t nl = __float_as_uint(d.w);
-            const float fx = (float)(ox + pi % tw) + 0.5f, fy = (float)(oy + pi / tw) + 0.5f;
+            // pixel centre relative to the tile's first pixel (the staged means are too)
+            const float fx = (float)(pi % tw) + 0.5f, fy = (float)(pi / tw) + 0.5f;
             for (int k = 0; k < nsub_used; k++) {
                 const int j1 = min(cnt, 32 * k + 32);
                 for (int j = 32 * k; j < j1; j++) {
                     if (bb + j >= nl) break;
                     const float4 a = sm.gA[j];
                     const float4 b = sm.gB[j];
-                    const float2 ml = sm.gL[j];
-                    const float dx = pix_offset(fx, a.x, ml.x), dy = pix_offset(fy, a.y, ml.y);
+                    const float dx = pix_offset(fx, a.x), dy = pix_offset(fy, a.y);
                     const float4 pc = pair_coefs(a.x, a.y, a.z, a.w, b.x);
                     const float p2 = pair_power2(dx, dy, pc.z, pc.w, pair_c2(b.x));
                     if (p2 < kPow2Min) continue;
@@ -195,8 +192,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(Views V, const uint3
         if (warp_on) {
             float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
             float cbl = 0.f;
-            float2 ml = make_float2(0.f, 0.f);
-            if (act) { a = sm.gA[j]; b = sm.gB[j]; cbl = sm.gC[j]; ml = sm.gL[j]; }
+            if (act) { a = sm.gA[j]; b = sm.gB[j]; cbl = sm.gC[j]; }
             const uint32_t myidx = bb + j;
             const int p0 = pg * glen;
             float T = 1.f, S0 = 0.f, S1 = 0.f, S2 = 0.f;
@@ -215,8 +211,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(Views V, const uint3
                     const int pi = p0 + pl;
                     const float4 d = sm.pdl[pi];
                     if (myidx < __float_as_uint(d.w)) {
-                        const float dx = pix_offset((float)(ox + pi % tw) + 0.5f, a.x, ml.x);
-                        const float dy = pix_offset((float)(oy + pi / tw) + 0.5f, a.y, ml.y);
+                        const float dx = pix_offset((float)(pi % tw) + 0.5f, a.x);
+                        const float dy = pix_offset((float)(pi / tw) + 0.5f, a.y);
                         const float4 pc = pair_coefs(a.x, a.y, a.z, a.w, b.x);
                         const float p2 = pair_power2(dx, dy, pc.z, pc.w, pair_c2(b.x));
                         if (p2 >= kPow2Min) {
@@ -417,7 +413,6 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
     __shared__ float4 sA[2][BB];
     __shared__ float4 sB[2][BB];
     __shared__ float4 sD[2][BB];          // (conic a, b, c, blue)
-    __shared__ float2 sL[2][BB];          // mean residuals
     __shared__ uint32_t sE[2][BB];
     __shared__ uint32_t sM[2][BB];
     __shared__ float part[NW][BB][9];
@@ -433,7 +428,8 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
     const int py0 = oy + (w / WPR) * BH + (lane >> 3);
     const uint32_t wbit = 1u << w;
     const uint2 r = range_at(ranges, gt, cap, status);
-    const float fx = (float)px + 0.5f;
+    // pixel centres relative to the tile's first pixel (the staged means are too)
+    const float fx = (float)(px - ox) + 0.5f;
     const int vi = bfly_index(lane);
 
     // per pixel k (row py0 + 4k): last blended entry, compensated T after
@@ -446,7 +442,7 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
         const int py = py0 + 4 * k;
-        fy[k] = (float)py + 0.5f;
+        fy[k] = (float)(py - oy) + 0.5f;
         nl[k] = 0;
         Th[k] = 1.f; Tl[k] = 0.f; d0[k] = 0.f; d1[k] = 0.f; d2[k] = 0.f; U[k] = 0.f;
         if (px < vd.W && py < vd.H) {
@@ -476,10 +472,9 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
         uint32_t live = 0;
 #pragma unroll
         for (int k = 0; k < NW; k++) live |= (bbx + i < smax[k] ? 1u : 0u) << k;
-        sA[buf][i] = pair_coefs(q.a.x, q.a.y, q.a.z, q.a.w, q.b.x);
+        sA[buf][i] = pair_coefs(tile_mean(q.a.x, q.c.z, ox), tile_mean(q.a.y, q.c.w, oy), q.a.z, q.a.w, q.b.x);
         sB[buf][i] = make_float4(pair_c2(q.b.x), q.b.y, q.b.z, q.b.w);
         sD[buf][i] = make_float4(q.a.z, q.a.w, q.b.x, q.c.x);
-        sL[buf][i] = make_float2(q.c.z, q.c.w);
         sE[buf][i] = e;
         sM[buf][i] = warp_block_mask(q.a.x, q.a.y, q.a.z, q.a.w, q.b.x, q.b.y, ox, oy, WPR, RPB, BH) & live;
     };
@@ -497,7 +492,6 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
         const float4* __restrict__ cA = sA[cur];
         const float4* __restrict__ cB = sB[cur];
         const float4* __restrict__ cD = sD[cur];
-        const float2* __restrict__ cL = sL[cur];
         const uint32_t* __restrict__ cM = sM[cur];
         // gathers for the next (lower) batch, all entries full since bb > 0
         ProjRec qn[IPT];
@@ -528,11 +522,10 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
                 bool hit = false;
                 const float4 a = cA[j];
                 const float4 b = cB[j];
-                const float2 ml = cL[j];
-                const float dx = pix_offset(fx, a.x, ml.x);
+                const float dx = pix_offset(fx, a.x);
 #pragma unroll
                 for (int k = 0; k < PPT; k++) {
-                    const float dy = pix_offset(fy[k], a.y, ml.y);
+                    const float dy = pix_offset(fy[k], a.y);
                     const float p2 = pair_power2(dx, dy, a.z, a.w, b.x);
                     const float G = ex2_approx(p2);
                     const float araw = __fmul_rn(b.y, G);

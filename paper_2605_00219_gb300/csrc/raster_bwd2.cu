@@ -44,10 +44,9 @@ struct Bwd2Smem {
     float pa[32 * C::NPS];        // dL/dalpha * G per [pixel in block][pair]
     float pr[9][BS + 1];          // phase-2 sums per thread
     float4 sd[32][C::NW];         // dL/dC per [pixel in block][block]
-    float4 sA[2][C::BB];          // mean, prescaled conic a, b
+    float4 sA[2][C::BB];          // mean (relative to the tile's first pixel), prescaled conic a, b
     float4 sB[2][C::BB];          // prescaled conic c, opacity, red, green
     float4 sD[2][C::BB];          // conic a, b, c, blue
-    float2 sL[2][C::BB];          // mean residuals
     uint32_t sE[2][C::BB];        // emission slot
     uint32_t sM[2][C::BB];        // warp-block mask
     int pbase[C::BB + 1];         // first pair of each entry of the current chunk
@@ -123,7 +122,8 @@ __global__ void __launch_bounds__(BS) k_raster_bwd2(Views V, const uint32_t* __r
     const uint32_t wbit = 1u << w;
     const bool inside = px < vd.W && py < vd.H;
     const uint2 r = ranges[gt];
-    const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+    // pixel centre relative to the tile's first pixel (the staged means are too)
+    const float fx = (float)(px - ox) + 0.5f, fy = (float)(py - oy) + 0.5f;
 
     uint32_t nl = 0;
     float Th = 1.f, Tl = 0.f, d0 = 0.f, d1 = 0.f, d2 = 0.f;
@@ -157,10 +157,9 @@ __global__ void __launch_bounds__(BS) k_raster_bwd2(Views V, const uint32_t* __r
         return m;
     };
     auto stage = [&](int buf, int i, int pos, const ProjRec& q, uint32_t e) {
-        S.sA[buf][i] = pair_coefs(q.a.x, q.a.y, q.a.z, q.a.w, q.b.x);
+        S.sA[buf][i] = pair_coefs(tile_mean(q.a.x, q.c.z, ox), tile_mean(q.a.y, q.c.w, oy), q.a.z, q.a.w, q.b.x);
         S.sB[buf][i] = make_float4(pair_c2(q.b.x), q.b.y, q.b.z, q.b.w);
         S.sD[buf][i] = make_float4(q.a.z, q.a.w, q.b.x, q.c.x);
-        S.sL[buf][i] = make_float2(q.c.z, q.c.w);
         S.sE[buf][i] = e;
         S.sM[buf][i] = warp_block_mask(q.a.x, q.a.y, q.a.z, q.a.w, q.b.x, q.b.y, ox, oy, WPR, RPB) & live(pos);
     };
@@ -194,7 +193,6 @@ __global__ void __launch_bounds__(BS) k_raster_bwd2(Views V, const uint32_t* __r
         const float4* __restrict__ cA = S.sA[cur];
         const float4* __restrict__ cB = S.sB[cur];
         const float4* __restrict__ cD = S.sD[cur];
-        const float2* __restrict__ cL = S.sL[cur];
         const uint32_t* __restrict__ cM = S.sM[cur];
         // sub-batches of at most NP pairs, cut from the back (a short last
         // one leaves most warps free for other CTAs in its phase 2)
@@ -215,8 +213,7 @@ __global__ void __launch_bounds__(BS) k_raster_bwd2(Views V, const uint32_t* __r
                     if (bb + j < (int)nl) {
                         const float4 a = cA[j];
                         const float4 b = cB[j];
-                        const float2 ml = cL[j];
-                        const float dx = pix_offset(fx, a.x, ml.x), dy = pix_offset(fy, a.y, ml.y);
+                        const float dx = pix_offset(fx, a.x), dy = pix_offset(fy, a.y);
                         const float p2 = pair_power2(dx, dy, a.z, a.w, b.x);
                         if (p2 >= kPow2Min) {
                             const float G = ex2_approx(p2);
@@ -253,16 +250,15 @@ __global__ void __launch_bounds__(BS) k_raster_bwd2(Views V, const uint32_t* __r
                 if (pq < npair) {
                     const int j = S.pj[pq], b = S.pb[pq];
                     const float4 a = cA[j];
-                    const float2 ml = cL[j];
                     const float op = cB[j].y;
-                    const float bx = (float)(ox + (b % WPR) * 8) + 0.5f, by = (float)(oy + (b / WPR) * 4) + 0.5f;
+                    const float bx = (float)((b % WPR) * 8) + 0.5f, by = (float)((b / WPR) * 4) + 0.5f;
 #pragma unroll
                     for (int i = 0; i < PPT; i++) {
                         const int k = part * PPT + i;
                         const float wv = S.pw[k * NPS + pq], av = S.pa[k * NPS + pq];
                         const float4 dv = S.sd[k][b];
-                        const float dx = pix_offset(bx + (float)(k & 7), a.x, ml.x);
-                        const float dy = pix_offset(by + (float)(k >> 3), a.y, ml.y);
+                        const float dx = pix_offset(bx + (float)(k & 7), a.x);
+                        const float dy = pix_offset(by + (float)(k >> 3), a.y);
                         acc[6] = fmaf(wv, dv.x, acc[6]);
                         acc[7] = fmaf(wv, dv.y, acc[7]);
                         acc[8] = fmaf(wv, dv.z, acc[8]);

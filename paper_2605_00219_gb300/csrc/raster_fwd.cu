@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(BS, (BS == 256 ? 6 : 1)) k_raster_fwd(Views V,
     constexpr int CH = BS > 256 ? 256 : BS;   // list entries per staged chunk
     __shared__ float4 sA[2][CH];
     __shared__ float4 sB[2][CH];
-    __shared__ float4 sC[2][CH];   // (blue, mean residual x, y, -)
+    __shared__ float sCb[2][CH];   // blue
     __shared__ uint32_t sM[2][CH];
     __shared__ unsigned long long sblend[BS / 32];
     constexpr int WPR = TW / 8, RPB = BS / TW / 4;
@@ -43,7 +43,8 @@ __global__ void __launch_bounds__(BS, (BS == 256 ? 6 : 1)) k_raster_fwd(Views V,
     const int px = ox + (w % WPR) * 8 + (lane & 7);
     const int py = oy + (w / WPR) * 4 + (lane >> 3);
     const bool inside = px < vd.W && py < vd.H;
-    const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+    // pixel centre relative to the tile's first pixel (the staged means are too)
+    const float fx = (float)(px - ox) + 0.5f, fy = (float)(py - oy) + 0.5f;
     const uint2 r = range_at(ranges, gt, cap, &hdr->status);
 
     float Th = 1.0f, Tl = 0.0f;
@@ -54,9 +55,9 @@ __global__ void __launch_bounds__(BS, (BS == 256 ? 6 : 1)) k_raster_fwd(Views V,
     // while chunk i is composited (pair indices one chunk further ahead)
     if (threadIdx.x < CH && r.x + threadIdx.x < r.y) {
         const ProjRec q = rec_at(rec, pid_sorted[r.x + threadIdx.x], V.pairs, &hdr->status);
-        sA[0][threadIdx.x] = pair_coefs(q.a.x, q.a.y, q.a.z, q.a.w, q.b.x);
+        sA[0][threadIdx.x] = pair_coefs(tile_mean(q.a.x, q.c.z, ox), tile_mean(q.a.y, q.c.w, oy), q.a.z, q.a.w, q.b.x);
         sB[0][threadIdx.x] = make_float4(pair_c2(q.b.x), q.b.y, q.b.z, q.b.w);
-        sC[0][threadIdx.x] = make_float4(q.c.x, q.c.z, q.c.w, 0.f);
+        sCb[0][threadIdx.x] = q.c.x;
         sM[0][threadIdx.x] = warp_block_mask(q.a.x, q.a.y, q.a.z, q.a.w, q.b.x, q.b.y, ox, oy, WPR, RPB);
     }
     uint32_t pid_next = threadIdx.x < CH && r.x + CH + threadIdx.x < r.y ? pid_sorted[r.x + CH + threadIdx.x] : 0u;
@@ -69,7 +70,7 @@ __global__ void __launch_bounds__(BS, (BS == 256 ? 6 : 1)) k_raster_fwd(Views V,
         if (threadIdx.x < CH && base + 2 * CH + threadIdx.x < r.y) pid_next = pid_sorted[base + 2 * CH + threadIdx.x];
         const float4* __restrict__ cA = sA[cur];
         const float4* __restrict__ cB = sB[cur];
-        const float4* __restrict__ cC = sC[cur];
+        const float* __restrict__ cCb = sCb[cur];
         const uint32_t* __restrict__ cM = sM[cur];
         const int cnt = (int)min((uint32_t)CH, r.y - base);
         for (int c0 = 0; c0 < cnt; c0 += 32) {
@@ -79,8 +80,8 @@ __global__ void __launch_bounds__(BS, (BS == 256 ? 6 : 1)) k_raster_fwd(Views V,
                 const int j = c0 + __ffs(bits) - 1;
                 bits &= bits - 1;
                 const float4 a = cA[j];
-                const float4 cl = cC[j];
-                const float dx = pix_offset(fx, a.x, cl.y), dy = pix_offset(fy, a.y, cl.z);
+                const float blue = cCb[j];   // read on every visit: faster than on the blend path
+                const float dx = pix_offset(fx, a.x), dy = pix_offset(fy, a.y);
                 const float4 b = cB[j];
                 const float p2 = pair_power2(dx, dy, a.z, a.w, b.x);
                 // one test for both skips (exp2 taken for every pair)
@@ -102,7 +103,7 @@ __global__ void __launch_bounds__(BS, (BS == 256 ? 6 : 1)) k_raster_fwd(Views V,
                 const float wgt = alpha * Th;
                 C0 = fmaf(b.z, wgt, C0);
                 C1 = fmaf(b.w, wgt, C1);
-                C2 = fmaf(cl.x, wgt, C2);
+                C2 = fmaf(blue, wgt, C2);
                 Tl = lo;
                 Th = pr;
                 last = base - r.x + j + 1;
@@ -111,9 +112,10 @@ __global__ void __launch_bounds__(BS, (BS == 256 ? 6 : 1)) k_raster_fwd(Views V,
         }
         if (have_next) {
             const int nb = cur ^ 1;
-            sA[nb][threadIdx.x] = pair_coefs(qn.a.x, qn.a.y, qn.a.z, qn.a.w, qn.b.x);
+            sA[nb][threadIdx.x] = pair_coefs(tile_mean(qn.a.x, qn.c.z, ox), tile_mean(qn.a.y, qn.c.w, oy), qn.a.z, qn.a.w,
+                                             qn.b.x);
             sB[nb][threadIdx.x] = make_float4(pair_c2(qn.b.x), qn.b.y, qn.b.z, qn.b.w);
-            sC[nb][threadIdx.x] = make_float4(qn.c.x, qn.c.z, qn.c.w, 0.f);
+            sCb[nb][threadIdx.x] = qn.c.x;
             sM[nb][threadIdx.x] = warp_block_mask(qn.a.x, qn.a.y, qn.a.z, qn.a.w, qn.b.x, qn.b.y, ox, oy, WPR, RPB);
         }
     }
