@@ -516,24 +516,34 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
                 const int jj = 31 - __clz(bits);
                 bits &= ~(1u << jj);
                 const int j = 32 * c + jj;
-                float g[9];
-#pragma unroll
-                for (int i = 0; i < 9; i++) g[i] = 0.f;
-                bool hit = false;
                 const float4 a = cA[j];
                 const float4 b = cB[j];
                 const float dx = pix_offset(fx, a.x);
+                // the skip tests of the lane's pixels first; the nine sums
+                // are zeroed and formed only when a pixel of the warp blends
+                float dyk[PPT], Gk[PPT], ak[PPT];
+                bool hk[PPT], any = false;
 #pragma unroll
                 for (int k = 0; k < PPT; k++) {
-                    const float dy = pix_offset(fy[k], a.y);
-                    const float p2 = pair_power2(dx, dy, a.z, a.w, b.x);
-                    const float G = ex2_approx(p2);
-                    const float araw = __fmul_rn(b.y, G);
-                    const float alpha = fminf(kAlphaMax, araw);
+                    dyk[k] = pix_offset(fy[k], a.y);
+                    const float p2 = pair_power2(dx, dyk[k], a.z, a.w, b.x);
+                    Gk[k] = ex2_approx(p2);
+                    ak[k] = __fmul_rn(b.y, Gk[k]);
                     // one test for the pixel's three skips (exp2 taken for
                     // every pixel): no nested divergent branches
-                    if (bb + j < (int)nl[k] && p2 >= kPow2Min && alpha >= kAlphaMin) {
-                        hit = true;
+                    hk[k] = bb + j < (int)nl[k] && p2 >= kPow2Min && fminf(kAlphaMax, ak[k]) >= kAlphaMin;
+                    any |= hk[k];
+                }
+                float x = 0.f;
+                if (__any_sync(0xffffffffu, any)) {
+                    float g[9];
+#pragma unroll
+                    for (int i = 0; i < 9; i++) g[i] = 0.f;
+#pragma unroll
+                    for (int k = 0; k < PPT; k++) {
+                        if (!hk[k]) continue;
+                        const float araw = ak[k], G = Gk[k], dy = dyk[k];
+                        const float alpha = fminf(kAlphaMax, araw);
                         const float cb = cD[j].w;
                         // compensated T before this entry
                         const float rom = div_one_minus(alpha, Th[k], Tl[k]);
@@ -557,11 +567,10 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
                         g[3] = fmaf(dx, ydp, g[3]);
                         g[4] = fmaf(dy, ydp, g[4]);
                     }
+                    x = bfly9(g, lane);
                 }
                 // every visiting warp fills its slot (zeros when none of its
                 // pixels blended the entry)
-                float x = 0.f;
-                if (__any_sync(0xffffffffu, hit)) x = bfly9(g, lane);
                 if (vi >= 0) part[w][j][vi] = x;
             }
         }
