@@ -485,10 +485,12 @@ __device__ __forceinline__ uint32_t warp_block_mask(float mx, float my, float ca
     return ((2u << bx1) - (1u << bx0)) * rows;
 }
 
-// Exponent in base 2: power2 = log2(e) * power = dx (A dx + B dy) + C dy^2
+// Exponent in base 2: power2 = log2(e) * power = A dx^2 + B dx dy + C dy^2
 // with (A, B, C) = -log2(e) (ca / 2, cb, cc / 2), prescaled once per staged
 // list entry; G = 2^power2 by the hardware exp2.  Raster forward and backward
-// use these same helpers, so they take the same decisions.
+// use these same helpers, so they take the same decisions.  The opacity test
+// o G >= 1/255 is taken before the 0.99 clamp (the same decision, since
+// 0.99 > 1/255).
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kPow2Min = -4.5f * 1.4426950408889634f;   // d^2 = 9
 
@@ -499,9 +501,25 @@ __device__ __forceinline__ float4 pair_coefs(float mx, float my, float ca, float
 
 __device__ __forceinline__ float pair_c2(float cc) { return __fmul_rn(-0.5f * kLog2e, cc); }
 
+// The exponent as dy (C dy + B dx) + (A dx) dx: the two dx terms are shared
+// by the pixels of one column.
+struct PowX {
+    float adx2, bdx;
+};
+
+__device__ __forceinline__ PowX pair_power2_x(float dx, float A, float B)
+{
+    return PowX{__fmul_rn(__fmul_rn(A, dx), dx), __fmul_rn(B, dx)};
+}
+
+__device__ __forceinline__ float pair_power2_y(const PowX& x, float dy, float C)
+{
+    return __fmaf_rn(dy, __fmaf_rn(C, dy, x.bdx), x.adx2);
+}
+
 __device__ __forceinline__ float pair_power2(float dx, float dy, float A, float B, float C)
 {
-    return __fmaf_rn(dx, __fmaf_rn(A, dx, __fmul_rn(B, dy)), __fmul_rn(__fmul_rn(C, dy), dy));
+    return pair_power2_y(pair_power2_x(dx, A, B), dy, C);
 }
 
 __device__ __forceinline__ float ex2_approx(float x)

@@ -158,8 +158,9 @@ __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(Views V, const uint3
                     const float p2 = pair_power2(dx, dy, pc.z, pc.w, pair_c2(b.x));
                     if (p2 < kPow2Min) continue;
                     const float G = ex2_approx(p2);
-                    const float alpha = fminf(kAlphaMax, __fmul_rn(b.y, G));
-                    if (alpha < kAlphaMin) continue;
+                    const float araw = __fmul_rn(b.y, G);
+                    if (araw < kAlphaMin) continue;
+                    const float alpha = fminf(kAlphaMax, araw);
                     const float wgt = alpha * Th;
                     neumaier_add(ps0, pc0, b.z * wgt);
                     neumaier_add(ps1, pc1, b.w * wgt);
@@ -219,7 +220,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_raster_bwd(Views V, const uint3
                             const float G = ex2_approx(p2);
                             const float araw = __fmul_rn(b.y, G);
                             const float alpha = fminf(kAlphaMax, araw);
-                            if (alpha >= kAlphaMin) {
+                            if (araw >= kAlphaMin) {
                                 const float om = 1.0f - alpha;
                                 const float rom = 1.0f / om;
                                 const float Tb = Ti * rom;
@@ -519,6 +520,7 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
                 const float4 a = cA[j];
                 const float4 b = cB[j];
                 const float dx = pix_offset(fx, a.x);
+                const PowX px2 = pair_power2_x(dx, a.z, a.w);   // shared by the lane's pixels
                 // the skip tests of the lane's pixels first; the nine sums
                 // are zeroed and formed only when a pixel of the warp blends
                 float dyk[PPT], Gk[PPT], ak[PPT];
@@ -526,12 +528,12 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
 #pragma unroll
                 for (int k = 0; k < PPT; k++) {
                     dyk[k] = pix_offset(fy[k], a.y);
-                    const float p2 = pair_power2(dx, dyk[k], a.z, a.w, b.x);
+                    const float p2 = pair_power2_y(px2, dyk[k], b.x);
                     Gk[k] = ex2_approx(p2);
                     ak[k] = __fmul_rn(b.y, Gk[k]);
                     // one test for the pixel's three skips (exp2 taken for
                     // every pixel): no nested divergent branches
-                    hk[k] = bb + j < (int)nl[k] && p2 >= kPow2Min && fminf(kAlphaMax, ak[k]) >= kAlphaMin;
+                    hk[k] = bb + j < (int)nl[k] && p2 >= kPow2Min && ak[k] >= kAlphaMin;
                     any |= hk[k];
                 }
                 float x = 0.f;

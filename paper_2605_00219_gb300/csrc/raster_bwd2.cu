@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(BS) k_raster_bwd2(Views V, const uint32_t* __r
                             const float G = ex2_approx(p2);
                             const float araw = __fmul_rn(b.y, G);
                             const float alpha = fminf(kAlphaMax, araw);
-                            if (alpha >= kAlphaMin) {
+                            if (araw >= kAlphaMin) {
                                 const float cb = cD[j].w;
                                 // compensated T before this entry
                                 const float rom = div_one_minus(alpha, Th, Tl);

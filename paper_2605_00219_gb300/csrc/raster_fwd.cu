@@ -86,8 +86,9 @@ __global__ void __launch_bounds__(BS, (BS == 256 ? 6 : 1)) k_raster_fwd(Views V,
                 const float p2 = pair_power2(dx, dy, a.z, a.w, b.x);
                 // one test for both skips (exp2 taken for every pair)
                 const float G = ex2_approx(p2);
-                const float alpha = fminf(kAlphaMax, __fmul_rn(b.y, G));
-                if (!(p2 >= kPow2Min && alpha >= kAlphaMin)) continue;
+                const float araw = __fmul_rn(b.y, G);
+                if (!(p2 >= kPow2Min && araw >= kAlphaMin)) continue;
+                const float alpha = fminf(kAlphaMax, araw);
                 // compensated T * (1 - alpha); the pair is carried without
                 // renormalising (Th the rounded product, Tl its low part),
                 // and the stop test takes their sum
