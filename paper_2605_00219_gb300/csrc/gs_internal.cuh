@@ -80,29 +80,6 @@ inline int tile_ppt(const Plan& P)
     return P.tuning.threads_per_tile > 0 ? np / P.tuning.threads_per_tile : 1;
 }
 
-// Degree-3 SH of Gaussian g (48 floats, flat index 3*k + channel).
-__device__ __forceinline__ void load_sh(const SceneDesc& sc, int bf16, int64_t g, float* shv)
-{
-    if (!bf16) {
-        const float4* s4 = reinterpret_cast<const float4*>(sc.sh);
-#pragma unroll
-        for (int j = 0; j < 12; j++) {
-            float4 c = s4[j * sc.n + g];
-            shv[4 * j] = c.x; shv[4 * j + 1] = c.y; shv[4 * j + 2] = c.z; shv[4 * j + 3] = c.w;
-        }
-    } else {
-        const uint4* s8 = reinterpret_cast<const uint4*>(sc.sh);
-#pragma unroll
-        for (int j = 0; j < 6; j++) {
-            uint4 c = s8[j * sc.n + g];
-            shv[8 * j + 0] = bf16_lo(c.x); shv[8 * j + 1] = bf16_hi(c.x);
-            shv[8 * j + 2] = bf16_lo(c.y); shv[8 * j + 3] = bf16_hi(c.y);
-            shv[8 * j + 4] = bf16_lo(c.z); shv[8 * j + 5] = bf16_hi(c.z);
-            shv[8 * j + 6] = bf16_lo(c.w); shv[8 * j + 7] = bf16_hi(c.w);
-        }
-    }
-}
-
 Scenes make_scenes(const Plan& P, const gs_scene_buf* scenes);
 
 void launch_project_fwd(const Plan& P, const Scenes& S, const float* cams, const WsPtrs& w, cudaStream_t st);

@@ -562,13 +562,16 @@ __global__ void __launch_bounds__(BS) k_raster_bwd_px(Views V, const uint32_t* _
                         const float dam = araw <= kAlphaMax ? da : 0.f;
                         g[5] = fmaf(dam, G, g[5]);
                         const float dp = dam * araw;
-                        const float xdp = dx * dp, ydp = dy * dp;
-                        g[0] += xdp;
+                        const float ydp = dy * dp;
+                        g[0] += dp;
                         g[1] += ydp;
-                        g[2] = fmaf(dx, xdp, g[2]);
-                        g[3] = fmaf(dx, ydp, g[3]);
                         g[4] = fmaf(dy, ydp, g[4]);
                     }
+                    // the lane's pixels share dx: sum dx dp = dx S, sum dx^2 dp
+                    // = dx (dx S), sum dx dy dp = dx sum dy dp
+                    g[0] *= dx;
+                    g[2] = dx * g[0];
+                    g[3] = dx * g[1];
                     x = bfly9(g, lane);
                 }
                 // every visiting warp fills its slot (zeros when none of its
