@@ -142,7 +142,7 @@ __device__ __forceinline__ void proj_bwd_view(const float* cam, int W, int H, fl
     const float tx = fmaf(C[0], mu.x, fmaf(C[1], mu.y, fmaf(C[2], mu.z, cam[9])));
     const float ty = fmaf(C[3], mu.x, fmaf(C[4], mu.y, fmaf(C[5], mu.z, cam[10])));
     const float tz = fmaf(C[6], mu.x, fmaf(C[7], mu.y, fmaf(C[8], mu.z, cam[11])));
-    const float itz = 1.0f / tz;
+    const float itz = __fdividef(1.0f, tz);   // hardware reciprocal: a few ulp, far inside the gradient bound
 
     // ---- colour: SH and view direction
     const float cpx = -(C[0] * cam[9] + C[3] * cam[10] + C[6] * cam[11]);
@@ -216,7 +216,7 @@ __device__ __forceinline__ void proj_bwd_view(const float* cam, int W, int H, fl
     const float va = TS[0] * T[0] + TS[1] * T[1] + TS[2] * T[2] + 0.3f;
     const float vb = TS[0] * T[3] + TS[1] * T[4] + TS[2] * T[5];
     const float vc = TS[3] * T[3] + TS[4] * T[4] + TS[5] * T[5] + 0.3f;
-    const float idet = 1.0f / (va * vc - vb * vb);
+    const float idet = __fdividef(1.0f, va * vc - vb * vb);
     const float qa = vc * idet, qb = -vb * idet, qc = va * idet;
     // dL/dV = -Q G Q, G = [[dca, dcb/2], [dcb/2, dcc]] (symmetric)
     const float ga = g2[2], gb = 0.5f * g2[3], gc = g2[4];
