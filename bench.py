@@ -60,12 +60,12 @@ LR = (1.6e-4 * 30.0, 1e-3, 5e-3, 5e-2, 2.5e-3, 2.5e-3 / 20)   # mean lr scaled b
 # 4 x 1920x1080, 16x16 tiles, pixel-parallel raster backward).  Valid only
 # while the kernel sources hash to the recorded prefixes.
 MEASURED_TRAFFIC = {
-    "raster_bwd": (3749960448, {"raster_bwd.cu": "1bd9c982611a3a21"}),
-    "project_bwd_adam": (3304520448, {"project_bwd_adam.cu": "39d52bcf9ef7e80b"}),
-    "raster_fwd": (1652099072, {"raster_fwd.cu": "9bbe3a93408bf2b9"}),
-    "project_fwd": (1738441472, {"project_fwd.cu": "b375359fd7001cef"}),
-    "bin_sort": (1482143744, {"bin_sort.cu": "d92d0a747dcb654f"}),
-    "loss_l1": (260053504, {"raster_fwd.cu": "9bbe3a93408bf2b9"}),
+    "raster_bwd": (3760561664, {"raster_bwd.cu": "1bd9c982611a3a21"}),
+    "project_bwd_adam": (3303079168, {"project_bwd_adam.cu": "25d756dbe4558831"}),
+    "raster_fwd": (1647618560, {"raster_fwd.cu": "9bbe3a93408bf2b9"}),
+    "project_fwd": (1741351168, {"project_fwd.cu": "b375359fd7001cef"}),
+    "bin_sort": (1483329536, {"bin_sort.cu": "d92d0a747dcb654f"}),
+    "loss_l1": (259586048, {"raster_fwd.cu": "9bbe3a93408bf2b9"}),
 }
 TRAFFIC_COMMON = {"gs_device.cuh": "89b3b04643ff706e", "gs_internal.cuh": "9a90b6b319a8d190"}
 
