@@ -65,7 +65,8 @@ typedef enum {
     GS_ERR_INVALID_ARG = 1,
     GS_ERR_CAPACITY = 2,      /* status bit 1: more intersections than capacity */
     GS_ERR_NONFINITE = 3,     /* status bit 2: a non-finite parameter was found */
-    GS_ERR_TIMEOUT = 4,       /* status bit 3: a bounded wait gave up */
+    GS_ERR_TIMEOUT = 4,       /* status bit 3: a bounded wait gave up (reserved: no kernel of
+                                 this library waits on another block, so it is never set) */
     GS_ERR_CUDA = 5,
     GS_ERR_UNIMPLEMENTED = 6
 } gs_status;
@@ -73,7 +74,7 @@ typedef enum {
 /* Device status word bits (gs_stats.status). */
 #define GS_STATUS_CAPACITY 0x1u
 #define GS_STATUS_NONFINITE 0x2u
-#define GS_STATUS_TIMEOUT 0x4u
+#define GS_STATUS_TIMEOUT 0x4u     /* reserved, never set (no kernel waits) */
 #define GS_STATUS_BOUNDS 0x8u      /* bounds-checked build (GS_DEBUG) only: an
                                       index read from the workspace pointed
                                       outside its buffer; that access was
